@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Time-to-spectrum benchmark of the TACAW hot path on one GB300.
+
+One step = the whole path on the paper-scale workload (fcc 20x20x50 cells,
+80 000 atoms, 512^2 grid, 101 slices of 2 A, 200 keV, 4096 snapshots at
+5 fs): slice potentials and multislice for every snapshot, FP64 time mean,
+temporal transform on the natural energy grid and |Phi|^2 / T^2.  The
+metric is grid-point x slice x snapshot per second of that step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload (the path is not sharded across GPUs); value = all ranks' units /
+the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multislice gridpt*slice*snapshot/s (time-to-spectrum)"
+UNIT = "gridpt*slice*snapshot/s"
+DESIGN_BYTES_PER_PT_SLICE = 36        # row pass 8+8+4, column pass 8+8
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="paper_scale")
+    p.add_argument("--batch", type=int, default=32)
+    p.add_argument("--snapshots", type=int, default=0, help="override T (testing only)")
+    p.add_argument("--cpu-snapshots", type=int, default=6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(args):
+    import workloads as W
+    w = W.WORKLOADS[args.workload]
+    if args.snapshots:
+        w = w.with_(n_t=args.snapshots)
+    return w
+
+
+def workload_config(w, extra=None):
+    g = w.grid
+    cfg = {
+        "workload": f"{w.name}: {w.lattice} {w.ncell[0]}x{w.ncell[1]}x{w.ncell[2]} cells a={w.a} A, "
+                    f"{g.nx}x{g.ny} grid over {g.lx}x{g.ly} A, {g.n_slices} slices of {g.dz} A, "
+                    f"{g.kev:g} keV plane wave, {w.n_t} snapshots at {w.dt_fs} fs, {w.n_modes} harmonic modes",
+        "grid": [g.nx, g.ny], "slices": g.n_slices, "snapshots": w.n_t,
+        "spectrum": "natural energy grid (n_omega = T), FP32 temporal transform",
+        "l2": "inputs larger than L2 (positions 3.9 GB, exit waves 8.6 GB per step)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ oracle leg
+def oracle_sample(w, n_snap, processes):
+    """Run the FP64 oracle (as it stands) on the first n_snap snapshots."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    inp = W.build_inputs(w)
+    pos = inp.positions(range(n_snap)).astype(np.float64)
+    g = O.grid_from_spec(w.grid)
+    t0 = time.perf_counter()
+    psi = O.exit_waves(g, pos, inp.species, inp.amp_sigma.astype(np.float64), processes=processes)
+    O.spectrum(psi.reshape(n_snap, -1), w.dt_fs)
+    dt = time.perf_counter() - t0
+    units = n_snap * w.grid.nx * w.grid.ny * w.grid.n_slices
+    return units / dt, dt
+
+
+def cpu_baseline(w, n_snap):
+    cores = min(n_snap, os.cpu_count() or 1)
+    value, dt = oracle_sample(w, n_snap, cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_snap} snapshots of {w.name} (FP64 potential + multislice per snapshot "
+                      f"in a {cores}-process pool, then the spectrum of those snapshots); {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args)
+    n_snap = args.cpu_snapshots
+    cores = min(n_snap, os.cpu_count() or 1)
+    for _ in range(args.warmup):
+        oracle_sample(w, n_snap, cores)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = oracle_sample(w, n_snap, cores)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: first {n_snap} snapshots of {w.name}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("multislice.cu", "fft.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_15599_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(units_per_launch):
+    """DRAM bytes of one slice step (row + column pass) from the committed ncu
+    summary, scaled to the launch size, or None if absent or stale."""
+    path = os.path.join(ROOT, "profiles", "multislice_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_point_slice"] * units_per_launch
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2401_15599_gb300 import _lib
+    from paper_2401_15599_gb300.pipeline import TimeToSpectrum
+    import workloads as W
+
+    _lib.load()
+    w = workload(args)
+    g = w.grid
+
+    cpu = None
+    if rank == 0 and world >= 1 and args.gpus == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_snapshots)
+
+    inp = W.build_inputs(w)
+    pos_host = torch.from_numpy(inp.positions()).pin_memory()
+    species = torch.from_numpy(inp.species).to(dev)
+    pos = pos_host.to(dev, non_blocking=True)
+    n_t, n_atoms = pos.shape[0], pos.shape[1]
+    tts = TimeToSpectrum(g, n_t, n_atoms, inp.amp_sigma, w.dt_fs, batch=args.batch, device=dev)
+    tts.prepare(None, None)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    ms_events = []
+
+    def step(record):
+        tts.psi_sum.zero_()
+        for t0 in range(0, n_t, tts.batch):
+            t1 = min(n_t, t0 + tts.batch)
+            v = tts.V[: t1 - t0]
+            from paper_2401_15599_gb300 import api
+            api.potential(g, pos[t0:t1], species, inp.amp_sigma, out=v, workspace=tts._ws.get("pot"))
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            api.multislice(g, v, out=tts.psi[t0:t1], psi_sum=tts.psi_sum, workspace=tts._ws.get("ms"))
+            if record:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                ms_events.append((e0, e1))
+        return tts.spectrum()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = start.elapsed_time(end)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    units_step = g.nx * g.ny * g.n_slices * n_t
+    value = units_step * world / (ms_step * 1e-3)
+
+    # dominant kernel: the multislice slice step (row + column pass), timed per call
+    ms_call = [a.elapsed_time(b) for a, b in ms_events]
+    units_call = g.nx * g.ny * g.n_slices * tts.batch
+    full_calls = [m for m in ms_call]
+    avg_call_ms = statistics.mean(full_calls)
+    achieved = DESIGN_BYTES_PER_PT_SLICE * units_call / (avg_call_ms * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    traffic = profiled_traffic(units_call)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "multislice slice step (row pass + column pass kernels, all slices of one "
+                          f"{tts.batch}-snapshot batch per call)",
+                "bytes_per_unit": DESIGN_BYTES_PER_PT_SLICE, "peak_kind": f"{peak_kind} (hbm_gbs)"}
+
+    # end to end: host positions in, host spectrum out, through the same C-ABI calls
+    e2e = None
+    if not args.no_e2e:
+        i_host = torch.empty(tts.I.shape, dtype=torch.float32).pin_memory()
+        el_host = torch.empty(tts.I_el.shape, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        s2 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(args.steps):
+            pos.copy_(pos_host, non_blocking=True)
+            step(False)
+            i_host.copy_(tts.I, non_blocking=True)
+            el_host.copy_(tts.I_el, non_blocking=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s2.elapsed_time(e2) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": units_step * world / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(pos_host.numel() * 4),
+               "d2h_bytes_per_step": int(i_host.numel() * 4 + el_host.numel() * 8)}
+
+    n_batches = (n_t + tts.batch - 1) // tts.batch
+    launches = n_batches * (2 + 1 + 2 * g.n_slices + 1) + 3
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, {"batch": tts.batch,
+                                          "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "time_to_spectrum_ms": ms_step,
+            "stage_ms": {"multislice": sum(ms_call) / args.steps},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * tacaw.h -- C-ABI of libtacaw, the GB300 (sm_103a) hot path of the
+ * time-auto-correlation method for angle-resolved phonon / magnon EELS and
+ * EEGS (Castellanos-Reyes, Zeiger, Rusz, arXiv 2401.15599).
+ *
+ * The path follows the paper's two-step procedure (the paragraphs after
+ * Eq. (9)): for every snapshot of a trajectory, build the slice potentials of
+ * that configuration and propagate a plane wave through them by multislice;
+ * stack the exit waves phi_MD(q, t), Fourier transform over time, take
+ * |.|^2 (Eq. (9), via the convolution theorem), optionally apply the Kubo
+ * detailed-balance factor (Eq. (8)) and the fractional-intensity
+ * normalisation (the unnumbered equation after Eq. (9)).  The elastic
+ * (time-averaged) wave is removed before the temporal transform and returned
+ * separately (the paper keeps the elastic channel at E = 0 in its spectra).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Array arguments are DEVICE pointers owned by the caller unless a comment
+ *   says "host".  The library never frees them and keeps no reference to
+ *   them after the call returns.
+ * - `stream` is a cudaStream_t cast to void*; NULL means the legacy default
+ *   stream.  Work is enqueued asynchronously on that stream; outputs are
+ *   valid once the stream reaches that point.
+ * - Scratch memory comes only from the caller: `ws` (device) and
+ *   `*ws_bytes`.  Call once with ws == NULL to receive the required size in
+ *   *ws_bytes (nothing is computed then); then call again with a buffer of at
+ *   least that size.  No call allocates device memory.
+ * - Return value: TACAW_OK (0) on success or a negative TACAW_E* code;
+ *   tacaw_last_error() gives a message for the calling thread.  Argument
+ *   errors are detected on the host before anything is enqueued.
+ * - Complex numbers are (re, im) pairs of float (float2) or double (double2).
+ * - Layouts are row-major, last index fastest.  Wave arrays are [ny][nx];
+ *   q-space arrays are in FFT order (index k <-> frequency k for k < n/2,
+ *   k - n otherwise; q = frequency / L).
+ */
+#ifndef TACAW_H
+#define TACAW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TACAW_OK 0
+#define TACAW_EINVAL (-1)       /* bad argument (detected on the host) */
+#define TACAW_ECUDA (-2)        /* a CUDA runtime call or launch failed */
+#define TACAW_ENOMEM (-3)       /* workspace smaller than required */
+#define TACAW_ETIMEOUT (-4)     /* a bounded device wait gave up */
+#define TACAW_EUNSUPPORTED (-5) /* size or option not supported by this build */
+
+/* precision of the temporal transform (tacaw_spectrum) */
+#define TACAW_FP32 0            /* FP32 SIMT complex GEMM */
+#define TACAW_BF16X3 1          /* split BF16 (hi+lo), 3 products, FP32 accumulation */
+
+/* flags of tacaw_spectrum */
+#define TACAW_KUBO 1            /* multiply by beta E / (1 - exp(-beta E)), Eq. (8) */
+#define TACAW_NORMALIZE 2       /* scale I and I_el so sum I + sum I_el = 1 */
+
+/*
+ * Simulation box and beam.  Lengths in Angstrom, beam energy in keV.
+ * Pixel (i, j) sits at (i * lx / nx, j * ly / ny).  Slice s covers
+ * [z0 + s dz, z0 + (s + 1) dz); for splitting atoms the first slice reaches
+ * -inf and the last +inf.  `bandlimit` is the fraction of the Nyquist radius
+ * min(nx / 2lx, ny / 2ly) kept by the propagator (2/3 is the usual choice).
+ */
+typedef struct tacaw_grid {
+    int32_t nx, ny;
+    double lx, ly;
+    int32_t n_slices;
+    double dz, z0;
+    double kev;
+    double bandlimit;
+} tacaw_grid;
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* tacaw_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t tacaw_version(void);
+
+/*
+ * Relativistic wavelength lambda (Angstrom) and interaction constant sigma_e
+ * (rad / (V Angstrom)) at beam energy `kev` (host outputs).  The paper
+ * defers to standard multislice (Cowley-Moodie); these are the textbook
+ * values lambda = h / sqrt(2 m0 e U (1 + eU / 2 m0 c^2)) and
+ * sigma_e = 2 pi gamma m0 e lambda / h^2.
+ */
+int tacaw_beam_constants(double kev, double* lambda_A, double* sigma_e);
+
+/*
+ * Slice potentials of T configurations (the scattering potential of a
+ * configuration tau that the multislice step of the procedure after Eq. (9)
+ * propagates through).
+ *
+ *   v_s(r) = sum_a amp_a exp(-|r - R_a|^2 / (2 s_a^2)) w_s(z_a)
+ *
+ * over atoms whose minimum-image lateral distance is <= 6 s_a (each atom an
+ * isotropic 3-D Gaussian whose z-projection peaks at amp_a, in V*A), with
+ * w_s(z) = (erf((z_{s+1} - z)/(sqrt2 s)) - erf((z_s - z)/(sqrt2 s))) / 2 the
+ * fraction of the atom inside slice s (0 if the slice misses
+ * [z - 6 s, z + 6 s]).  Requires 6 s_a < min(lx, ly) / 2.
+ *
+ * pos       [T][n_atoms][3] float, Angstrom (any values; wrapped laterally)
+ * species   [n_atoms] int32 in [0, n_species); out-of-range entries give EINVAL
+ *           only if detected -- the kernel skips atoms with a bad species
+ * amp_sigma HOST [n_species][2] float: amplitude (V*A), width s (A);
+ *           n_species <= TACAW_MAX_SPECIES
+ * V         out [T][n_slices][ny][nx] float, V*A
+ * Deterministic: identical configurations give bit-identical V (per-pixel
+ * sums are accumulated in 64-bit fixed point, 2^-32 V*A, so the order in
+ * which atoms are added does not matter).
+ * Errors: EINVAL for bad sizes or pointers, EUNSUPPORTED if the binning
+ * tables exceed shared memory, ENOMEM for a short workspace.
+ */
+#define TACAW_MAX_SPECIES 8
+int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
+                    const float* pos, const int32_t* species, int32_t n_species,
+                    const float* amp_sigma, float* V, void* ws, size_t* ws_bytes,
+                    void* stream);
+
+/*
+ * Multislice propagation of one incident wave through each of T snapshots
+ * (second step of the procedure after Eq. (9)).  For every snapshot:
+ *   psi_0 = psi_in (real space) or the unit plane wave;
+ *   for s = 0 .. n_slices-1:
+ *     chi = exp(i sigma_e v_s) psi_s,  Chi = F2[chi] (unitary: 1/(nx ny)),
+ *     Chi' = BL(q) exp(-i pi lambda dz |q|^2) Chi,  psi_{s+1} = F2^-1[Chi'];
+ *   the exit wave is Chi' of the last slice, returned in q-space.
+ *
+ * V        [T][n_slices][ny][nx] float, V*A (as written by tacaw_potential)
+ * psi_in   [ny][nx] float2 real-space incident wave, or NULL for psi = 1
+ * psi_q    out [T][ny][nx] float2, exit waves in q-space, FFT order; also
+ *          used as the working buffer (no other scratch for the waves)
+ * psi_sum  in/out [ny][nx] double2 running sum over snapshots, or NULL; when
+ *          given, sum_t psi_q(t) is ADDED to it in FP64 (snapshot order)
+ * flags    0 (reserved)
+ * Supported sizes: nx, ny in {64, 128, 256, 512, 1024}.
+ */
+int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,
+                     const void* psi_in, void* psi_q, void* psi_sum, int32_t flags,
+                     void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Energy-resolved intensity from exit waves (Eq. (9) with Eq. (8) and the
+ * normalisation after it).  With A(q, t_n) = psi(q, t_n) - m_q and
+ * m_q = (1/T) sum_n psi(q, t_n) (FP64):
+ *
+ *   Phi(q, E_k) = sum_n A(q, t_n) exp(-i E_k t_n / hbar),  t_n = n dt
+ *   I(q, E_k)   = |Phi(q, E_k)|^2 / T^2,   I_el(q) = |m_q|^2
+ *
+ * E > 0 is energy loss.  Natural grid (omega_meV == NULL, n_omega == T):
+ * E_k = h (k - T/2) / (T dt), k = 0 .. T-1 (ascending).
+ *
+ * nq         number of q-points (columns of psi)
+ * psi        [T][nq] float2 exit waves (time-major, e.g. tacaw_multislice's
+ *            psi_q viewed as [T][ny*nx])
+ * psi_sum    [nq] double2 sum_t psi, or NULL to compute it here (FP64)
+ * omega_meV  DEVICE [n_omega] double energies in meV, or NULL for the natural grid
+ * I          out [nq][n_omega] float
+ * I_el       out [nq] double, or NULL
+ * precision  TACAW_FP32 or TACAW_BF16X3
+ * flags      TACAW_KUBO | TACAW_NORMALIZE (temperature_K used by KUBO)
+ */
+int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
+                   const double* omega_meV, const void* psi, const void* psi_sum,
+                   float* I, double* I_el, int32_t precision, int32_t flags,
+                   double temperature_K, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Adjoint of tacaw_spectrum (flags 0) for gradient-based fitting: given
+ * dL/dI (real, [nq][n_omega]) returns the gradient with respect to psi in
+ * the PyTorch convention for complex inputs (dL/dRe + i dL/dIm):
+ *   g_Phi = (2 / T^2) dL/dI * Phi,   g_A(q, n) = sum_k g_Phi(q, k) exp(+i E_k t_n / hbar),
+ *   g_psi(q, n) = g_A(q, n) - (1/T) sum_n' g_A(q, n')   (centring is self-adjoint).
+ * dL_dpsi out [T][nq] float2.  Other arguments as in tacaw_spectrum.
+ */
+int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
+                            const double* omega_meV, const void* psi, const void* psi_sum,
+                            const float* dL_dI, void* dL_dpsi,
+                            void* ws, size_t* ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TACAW_H */

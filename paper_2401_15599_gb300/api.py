@@ -1,0 +1,146 @@
+"""PyTorch-facing wrappers of the libtacaw C-ABI (argument marshalling only).
+
+Tensors provide device memory and the current CUDA stream; every step of the
+computation runs in the library's CUDA kernels.  Functions take a grid
+object with attributes nx, ny, lx, ly, n_slices, dz, z0, kev, bandlimit.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need_cuda(name, t, dtype, ndim=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions")
+
+
+def _workspace(query, device):
+    nbytes = ctypes.c_size_t(0)
+    query(ctypes.c_void_p(0), ctypes.byref(nbytes))
+    ws = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=device)
+    return ws, nbytes
+
+
+def beam_constants(kev: float):
+    lam, sig = ctypes.c_double(), ctypes.c_double()
+    L.check("tacaw_beam_constants", L.load().tacaw_beam_constants(kev, ctypes.byref(lam), ctypes.byref(sig)))
+    return lam.value, sig.value
+
+
+def potential(grid, pos, species, amp_sigma, out=None, workspace=None):
+    """Slice potentials V [T, n_slices, ny, nx] (float32, V*A) of positions pos [T, Na, 3]."""
+    lib = L.load()
+    _need_cuda("pos", pos, torch.float32, 3)
+    _need_cuda("species", species, torch.int32, 1)
+    n_t, n_atoms = pos.shape[0], pos.shape[1]
+    if pos.shape[2] != 3 or species.shape[0] != n_atoms:
+        raise ValueError("pos must be [T, Na, 3] and species [Na]")
+    amp = torch.as_tensor(amp_sigma, dtype=torch.float32).reshape(-1, 2).contiguous().cpu()
+    n_species = amp.shape[0]
+    amp_c = (ctypes.c_float * (2 * n_species))(*amp.flatten().tolist())
+    g = L.make_grid(grid)
+    if out is None:
+        out = torch.empty((n_t, grid.n_slices, grid.ny, grid.nx), dtype=torch.float32, device=pos.device)
+    _need_cuda("out", out, torch.float32, 4)
+
+    def call(ws, nbytes):
+        return lib.tacaw_potential(ctypes.byref(g), n_t, n_atoms, _ptr(pos), _ptr(species), n_species,
+                                   amp_c, _ptr(out), ws, nbytes, _stream(pos.device))
+
+    nbytes = ctypes.c_size_t(0)
+    L.check("tacaw_potential", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=pos.device)
+    nbytes = ctypes.c_size_t(workspace.numel())
+    L.check("tacaw_potential", call(_ptr(workspace), ctypes.byref(nbytes)))
+    return out
+
+
+def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None):
+    """Exit waves psi_q [T, ny, nx] (complex64, q-space, FFT order) for potentials V."""
+    lib = L.load()
+    _need_cuda("V", V, torch.float32, 4)
+    n_t = V.shape[0]
+    if tuple(V.shape[1:]) != (grid.n_slices, grid.ny, grid.nx):
+        raise ValueError("V must be [T, n_slices, ny, nx]")
+    if out is None:
+        out = torch.empty((n_t, grid.ny, grid.nx), dtype=torch.complex64, device=V.device)
+    _need_cuda("out", out, torch.complex64, 3)
+    if psi_in is not None:
+        _need_cuda("psi_in", psi_in, torch.complex64, 2)
+    if psi_sum is not None:
+        _need_cuda("psi_sum", psi_sum, torch.complex128)
+    g = L.make_grid(grid)
+
+    def call(ws, nbytes):
+        return lib.tacaw_multislice(ctypes.byref(g), n_t, _ptr(V), _ptr(psi_in), _ptr(out), _ptr(psi_sum),
+                                    0, ws, nbytes, _stream(V.device))
+
+    nbytes = ctypes.c_size_t(0)
+    L.check("tacaw_multislice", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=V.device)
+    nbytes = ctypes.c_size_t(workspace.numel())
+    L.check("tacaw_multislice", call(_ptr(workspace), ctypes.byref(nbytes)))
+    return out
+
+
+_PRECISION = {"fp32": L.TACAW_FP32, "bf16x3": L.TACAW_BF16X3}
+
+
+def spectrum(psi, dt_fs, omega_meV=None, psi_sum=None, precision="fp32", kubo=False,
+             temperature_K=300.0, normalize=False, out=None, i_el=None, workspace=None):
+    """I(q, E) [nq, n_omega] (float32) and I_el [nq] (float64) from psi [T, nq] (complex64)."""
+    lib = L.load()
+    if psi.dim() > 2:
+        psi = psi.reshape(psi.shape[0], -1)
+    _need_cuda("psi", psi, torch.complex64, 2)
+    n_t, nq = psi.shape
+    dev = psi.device
+    if omega_meV is not None:
+        omega_meV = torch.as_tensor(omega_meV, dtype=torch.float64).to(dev).contiguous()
+        n_w = omega_meV.numel()
+    else:
+        n_w = n_t
+    if psi_sum is not None:
+        _need_cuda("psi_sum", psi_sum, torch.complex128)
+    if out is None:
+        out = torch.empty((nq, n_w), dtype=torch.float32, device=dev)
+    if i_el is None:
+        i_el = torch.empty(nq, dtype=torch.float64, device=dev)
+    _need_cuda("out", out, torch.float32, 2)
+    _need_cuda("i_el", i_el, torch.float64, 1)
+    flags = (L.TACAW_KUBO if kubo else 0) | (L.TACAW_NORMALIZE if normalize else 0)
+    prec = _PRECISION[precision]
+
+    def call(ws, nbytes):
+        return lib.tacaw_spectrum(nq, n_t, float(dt_fs), n_w, _ptr(omega_meV), _ptr(psi), _ptr(psi_sum),
+                                  _ptr(out), _ptr(i_el), prec, flags, float(temperature_K), ws, nbytes,
+                                  _stream(dev))
+
+    nbytes = ctypes.c_size_t(0)
+    L.check("tacaw_spectrum", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    nbytes = ctypes.c_size_t(workspace.numel())
+    L.check("tacaw_spectrum", call(_ptr(workspace), ctypes.byref(nbytes)))
+    return out, i_el

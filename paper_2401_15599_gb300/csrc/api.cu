@@ -1,0 +1,178 @@
+// C-ABI entry points of libtacaw (declared in include/tacaw.h): argument
+// validation, workspace queries and dispatch to the kernels.  Everything is
+// enqueued on the caller's stream; nothing here allocates device memory.
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "common.cuh"
+
+namespace tacaw {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = '\0'; }
+
+// -------------------------------------------------------- beam constants
+// CODATA 2018: Planck constant, speed of light, electron rest mass and
+// elementary charge (SI).
+void beam_constants(double kev, double* lambda_A, double* sigma_e) {
+    const double h = 6.62607015e-34, c = 299792458.0, m0 = 9.1093837015e-31, e = 1.602176634e-19;
+    const double eu = kev * 1e3 * e;                         // kinetic energy, J
+    const double p = sqrt(2.0 * m0 * eu * (1.0 + eu / (2.0 * m0 * c * c)));
+    const double lam_m = h / p;
+    const double gamma = 1.0 + eu / (m0 * c * c);
+    *lambda_A = lam_m * 1e10;
+    *sigma_e = 2.0 * M_PI * gamma * m0 * e * lam_m / (h * h) * 1e-10;
+}
+
+// declared in the kernel files
+bool multislice_size_supported(int n);
+size_t multislice_ws_bytes(const tacaw_grid& g);
+int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st);
+int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes);
+int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
+                  int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st);
+size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel);
+int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
+                 size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
+                 int flags, double temperature_K, void* ws, cudaStream_t st);
+
+static int check_grid(const tacaw_grid* g, const char* fn) {
+    TACAW_REQUIRE(g != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
+    TACAW_REQUIRE(g->nx > 0 && g->ny > 0 && g->n_slices > 0 && g->n_slices <= 65535, TACAW_EINVAL,
+                  "%s: nx, ny must be positive and n_slices in [1, 65535]", fn);
+    TACAW_REQUIRE(g->lx > 0 && g->ly > 0 && g->dz > 0 && isfinite(g->lx) && isfinite(g->ly) &&
+                      isfinite(g->dz) && isfinite(g->z0),
+                  TACAW_EINVAL, "%s: lx, ly, dz must be positive and finite", fn);
+    TACAW_REQUIRE(g->kev > 0 && isfinite(g->kev), TACAW_EINVAL, "%s: kev must be positive", fn);
+    TACAW_REQUIRE(g->bandlimit > 0 && isfinite(g->bandlimit), TACAW_EINVAL,
+                  "%s: bandlimit must be positive", fn);
+    return TACAW_OK;
+}
+
+static int check_ws(void* ws, size_t* ws_bytes, size_t need, const char* fn, bool* query) {
+    TACAW_REQUIRE(ws_bytes != nullptr, TACAW_EINVAL, "%s: ws_bytes is NULL", fn);
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        *query = true;
+        return TACAW_OK;
+    }
+    *query = false;
+    TACAW_REQUIRE(*ws_bytes >= need, TACAW_ENOMEM, "%s: workspace of %zu bytes, %zu needed", fn,
+                  *ws_bytes, need);
+    TACAW_REQUIRE(((uintptr_t)ws & 255) == 0, TACAW_EINVAL, "%s: workspace must be 256-byte aligned",
+                  fn);
+    return TACAW_OK;
+}
+
+}  // namespace tacaw
+
+using namespace tacaw;
+
+extern "C" {
+
+const char* tacaw_last_error(void) { return g_err; }
+
+int32_t tacaw_version(void) { return 100; }
+
+int tacaw_beam_constants(double kev, double* lambda_A, double* sigma_e) {
+    clear_error();
+    TACAW_REQUIRE(kev > 0 && isfinite(kev) && lambda_A && sigma_e, TACAW_EINVAL,
+                  "tacaw_beam_constants: bad argument");
+    beam_constants(kev, lambda_A, sigma_e);
+    return TACAW_OK;
+}
+
+int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms, const float* pos,
+                    const int32_t* species, int32_t n_species, const float* amp_sigma, float* V,
+                    void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_potential";
+    int rc = check_grid(grid, fn);
+    if (rc) return rc;
+    TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
+    TACAW_REQUIRE(n_atoms >= 0, TACAW_EINVAL, "%s: n_atoms must be >= 0", fn);
+    TACAW_REQUIRE(n_species >= 1 && n_species <= TACAW_MAX_SPECIES && amp_sigma, TACAW_EINVAL,
+                  "%s: need 1..%d species with amp_sigma", fn, TACAW_MAX_SPECIES);
+    size_t need = 0;
+    potential_ws_bytes(*grid, n_t, n_atoms, &need);
+    bool query = false;
+    rc = check_ws(ws, ws_bytes, need, fn, &query);
+    if (rc || query) return rc;
+    if (n_t == 0) return TACAW_OK;
+    TACAW_REQUIRE(V != nullptr && (n_atoms == 0 || (pos && species)), TACAW_EINVAL,
+                  "%s: NULL array", fn);
+    return potential_run(*grid, n_t, n_atoms, pos, species, n_species, amp_sigma, V, ws,
+                         (cudaStream_t)stream);
+}
+
+int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const void* psi_in,
+                     void* psi_q, void* psi_sum, int32_t flags, void* ws, size_t* ws_bytes,
+                     void* stream) {
+    clear_error();
+    const char* fn = "tacaw_multislice";
+    int rc = check_grid(grid, fn);
+    if (rc) return rc;
+    TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny),
+                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 512, 1024}", fn,
+                  grid->nx, grid->ny);
+    TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
+    TACAW_REQUIRE(flags == 0, TACAW_EINVAL, "%s: flags must be 0", fn);
+    bool query = false;
+    rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
+    if (rc || query) return rc;
+    if (n_t == 0) return TACAW_OK;
+    TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
+    return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
+                          ws, (cudaStream_t)stream);
+}
+
+int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const double* omega_meV,
+                   const void* psi, const void* psi_sum, float* I, double* I_el, int32_t precision,
+                   int32_t flags, double temperature_K, void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_spectrum";
+    TACAW_REQUIRE(nq > 0 && n_t > 0 && n_t <= 65535 && n_omega > 0, TACAW_EINVAL,
+                  "%s: nq, n_omega must be positive and n_t in [1, 65535]", fn);
+    TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
+    TACAW_REQUIRE(omega_meV != nullptr || n_omega == n_t, TACAW_EINVAL,
+                  "%s: the natural grid (omega NULL) has n_omega == T", fn);
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3, TACAW_EINVAL,
+                  "%s: unknown precision %d", fn, precision);
+    TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags",
+                  fn);
+    TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)),
+                  TACAW_EINVAL, "%s: the Kubo factor needs a positive temperature", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes,
+                      spectrum_ws_bytes(nq, n_t, n_omega, psi_sum != nullptr, I_el != nullptr), fn,
+                      &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(psi && I, TACAW_EINVAL, "%s: NULL array", fn);
+    return spectrum_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
+                        (const double2*)psi_sum, I, I_el, precision, flags, temperature_K, ws,
+                        (cudaStream_t)stream);
+}
+
+int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
+                            const double* omega_meV, const void* psi, const void* psi_sum,
+                            const float* dL_dI, void* dL_dpsi, void* ws, size_t* ws_bytes,
+                            void* stream) {
+    clear_error();
+    set_error("tacaw_spectrum_backward: not available in this build");
+    (void)nq; (void)n_t; (void)dt_fs; (void)n_omega; (void)omega_meV; (void)psi; (void)psi_sum;
+    (void)dL_dI; (void)dL_dpsi; (void)ws; (void)ws_bytes; (void)stream;
+    return TACAW_EUNSUPPORTED;
+}
+
+}  // extern "C"

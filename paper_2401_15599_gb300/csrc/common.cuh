@@ -1,0 +1,76 @@
+// Shared helpers of libtacaw: status handling, complex arithmetic, launch
+// checks.  Host-side state is limited to a thread-local error message.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/tacaw.h"
+
+namespace tacaw {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define TACAW_REQUIRE(cond, code, ...)       \
+    do {                                     \
+        if (!(cond)) {                       \
+            ::tacaw::set_error(__VA_ARGS__); \
+            return (code);                   \
+        }                                    \
+    } while (0)
+
+#define TACAW_CUDA_CHECK(expr)                                                         \
+    do {                                                                               \
+        cudaError_t err__ = (expr);                                                    \
+        if (err__ != cudaSuccess) {                                                    \
+            ::tacaw::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(err__), \
+                               __FILE__, __LINE__);                                    \
+            return TACAW_ECUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+#define TACAW_LAUNCH_CHECK() TACAW_CUDA_CHECK(cudaGetLastError())
+
+// Workspace carving: aligned sub-buffers of a caller-provided block.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count, size_t align = 256) {
+        off = (off + align - 1) / align * align;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+    size_t bytes() const { return (off + 255) / 256 * 256; }
+};
+
+// Beam constants (textbook relativistic values, CODATA 2018).
+void beam_constants(double kev, double* lambda_A, double* sigma_e);
+
+inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ---------------------------------------------------------------- complex
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    return make_float2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+    return make_float2(a.x * s, a.y * s);
+}
+
+}  // namespace tacaw

@@ -1,0 +1,247 @@
+// Device FFT building blocks for the multislice passes.
+//
+// A length-N transform is done by TPT = N / E cooperating threads, each
+// holding E complex values in registers.  The algorithm is the Stockham
+// autosort formulation: for stage l with radix R and NS = R_1 ... R_{l-1},
+// butterfly j (0 <= j < N/R) reads positions j + r N/R, multiplies input r by
+// W_{NS R}^{(j mod NS) r}, applies an R-point DFT and writes output r to
+// position (j / NS) NS R + (j mod NS) + r NS.  Thread t owns butterflies
+// j = t + b TPT, b = 0 .. E/R - 1.  Values move between stages through
+// shared memory (two buffers, one barrier per exchange).
+//
+// At the boundaries (first-stage input, last-stage output) thread t holds
+// positions t + TPT m, m = 0 .. E-1, in register m ("canonical order"), so
+// global loads and stores are coalesced across threads and point-wise
+// multiplications (transmission, propagator) can be applied in registers
+// between an inverse and a forward transform without any exchange.
+//
+// Twiddles W_N^k = exp(-2 pi i k / N) come from a table computed in FP64
+// and rounded once to float; the inverse transform uses their conjugates and
+// is unnormalised.
+#pragma once
+
+#include "common.cuh"
+
+namespace tacaw {
+namespace fft {
+
+// ---------------------------------------------------------------- small DFTs
+__device__ __forceinline__ float2 mul_neg_i(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ float2 mul_pos_i(float2 a) { return make_float2(-a.y, a.x); }
+
+template <bool INV>
+__device__ __forceinline__ float2 rot4(float2 a) {  // multiply by W_4 = -i (forward) / +i (inverse)
+    return INV ? mul_pos_i(a) : mul_neg_i(a);
+}
+
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+    __device__ __forceinline__ static void run(float2* x) {
+        float2 a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    }
+};
+
+template <bool INV>
+struct Dft<3, INV> {
+    __device__ __forceinline__ static void run(float2* x) {
+        const float h = 0.8660254037844386f;  // sqrt(3)/2
+        float2 t1 = cadd(x[1], x[2]);
+        float2 t2 = csub(x[1], x[2]);
+        float2 m = make_float2(x[0].x - 0.5f * t1.x, x[0].y - 0.5f * t1.y);
+        // forward: W_3 = -1/2 - i sqrt(3)/2 ; the i sqrt(3)/2 t2 term takes the sign
+        float2 r = INV ? mul_pos_i(t2) : mul_neg_i(t2);
+        r = cscale(r, h);
+        x[0] = cadd(x[0], t1);
+        x[1] = cadd(m, r);
+        x[2] = csub(m, r);
+    }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+    __device__ __forceinline__ static void run(float2* x) {
+        float2 t0 = cadd(x[0], x[2]), t1 = csub(x[0], x[2]);
+        float2 t2 = cadd(x[1], x[3]), t3 = rot4<INV>(csub(x[1], x[3]));
+        x[0] = cadd(t0, t2);
+        x[2] = csub(t0, t2);
+        x[1] = cadd(t1, t3);
+        x[3] = csub(t1, t3);
+    }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+    // y[k] = E[k] + W8^k O[k], y[k+4] = E[k] - W8^k O[k] with E, O the
+    // 4-point DFTs of the even and odd inputs.
+    __device__ __forceinline__ static void run(float2* x) {
+        const float c = 0.70710678118654752f;
+        float2 e[4] = {x[0], x[2], x[4], x[6]};
+        float2 o[4] = {x[1], x[3], x[5], x[7]};
+        Dft<4, INV>::run(e);
+        Dft<4, INV>::run(o);
+        float2 o1, o2, o3;
+        if (!INV) {
+            o1 = make_float2((o[1].x + o[1].y) * c, (o[1].y - o[1].x) * c);   // * (1 - i)/sqrt2
+            o2 = mul_neg_i(o[2]);                                            // * -i
+            o3 = make_float2((o[3].y - o[3].x) * c, -(o[3].x + o[3].y) * c);  // * (-1 - i)/sqrt2
+        } else {
+            o1 = make_float2((o[1].x - o[1].y) * c, (o[1].x + o[1].y) * c);   // * (1 + i)/sqrt2
+            o2 = mul_pos_i(o[2]);                                            // * +i
+            o3 = make_float2(-(o[3].x + o[3].y) * c, (o[3].x - o[3].y) * c);  // * (-1 + i)/sqrt2
+        }
+        x[0] = cadd(e[0], o[0]);
+        x[4] = csub(e[0], o[0]);
+        x[1] = cadd(e[1], o1);
+        x[5] = csub(e[1], o1);
+        x[2] = cadd(e[2], o2);
+        x[6] = csub(e[2], o2);
+        x[3] = cadd(e[3], o3);
+        x[7] = csub(e[3], o3);
+    }
+};
+
+// ---------------------------------------------------------------- plans
+template <int... Rs>
+struct Radices {};
+
+template <int N>
+struct Plan;
+template <>
+struct Plan<64> { static constexpr int E = 8; using R = Radices<8, 8>; };
+template <>
+struct Plan<128> { static constexpr int E = 8; using R = Radices<8, 4, 4>; };
+template <>
+struct Plan<256> { static constexpr int E = 8; using R = Radices<8, 8, 4>; };
+template <>
+struct Plan<512> { static constexpr int E = 8; using R = Radices<8, 8, 8>; };
+template <>
+struct Plan<1024> { static constexpr int E = 8; using R = Radices<8, 8, 4, 4>; };
+
+template <int A, int... Rest>
+struct First { static constexpr int value = A; };
+
+// Shared-memory layouts.  RowLayout: one transform per row, positions swizzled
+// inside the row to spread 8-byte accesses over the banks.  ColLayout: W
+// transforms interleaved (position-major), lanes of a warp on adjacent
+// transforms, conflict free without a swizzle.
+struct RowLayout {
+    int base;  // row * N
+    __device__ __forceinline__ int operator()(int p) const { return base + (p ^ ((p >> 4) & 15)); }
+};
+template <int W>
+struct ColLayout {
+    int c;
+    __device__ __forceinline__ int operator()(int p) const { return p * W + c; }
+};
+
+// Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
+template <int N, int E, int R, int NS, bool INV>
+__device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* __restrict__ tw) {
+    constexpr int TPT = N / E;
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+        float2* x = v + b * R;
+        if (NS > 1) {
+            const int j = t + b * TPT;
+            const int jm = j % NS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(tw + jm * r * (N / (NS * R)));
+                if (INV) w.y = -w.y;
+                x[r] = cmul(x[r], w);
+            }
+        }
+        Dft<R, INV>::run(x);
+    }
+}
+
+template <int N, int E, int R, int NS, class L>
+__device__ __forceinline__ void write_out(const float2 (&v)[E], float2* buf, int t, L lay) {
+    constexpr int TPT = N / E;
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+        const int j = t + b * TPT;
+        const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[lay(base + r * NS)] = v[b * R + r];
+    }
+}
+
+template <int N, int E, int R, class L>
+__device__ __forceinline__ void read_in(float2 (&v)[E], const float2* buf, int t, L lay) {
+    constexpr int TPT = N / E;
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+        const int j = t + b * TPT;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay(j + r * (N / R))];
+    }
+}
+
+// canonical (position t + TPT m in v[m]) <-> stage order (b, r) for the first
+// / last stage of radix R: position t + TPT (b + r E/R).
+template <int E, int R>
+__device__ __forceinline__ void canon_to_stage(float2 (&v)[E]) {
+    float2 tmp[E];
+#pragma unroll
+    for (int b = 0; b < E / R; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) tmp[b * R + r] = v[b + r * (E / R)];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = tmp[m];
+}
+template <int E, int R>
+__device__ __forceinline__ void stage_to_canon(float2 (&v)[E]) {
+    float2 tmp[E];
+#pragma unroll
+    for (int b = 0; b < E / R; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) tmp[b + r * (E / R)] = v[b * R + r];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = tmp[m];
+}
+
+template <int N, int E, bool INV, int NS, class L, int R, int... Rest>
+__device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
+                                           const float2* __restrict__ tw, L lay) {
+    stage<N, E, R, NS, INV>(v, t, tw);
+    if constexpr (sizeof...(Rest) > 0) {
+        constexpr int RN = First<Rest...>::value;
+        write_out<N, E, R, NS>(v, b0, t, lay);
+        __syncthreads();
+        read_in<N, E, RN>(v, b0, t, lay);
+        run_stages<N, E, INV, NS * R, L, Rest...>(v, b1, b0, t, tw, lay);
+    } else {
+        stage_to_canon<E, R>(v);
+    }
+}
+
+template <int N, bool INV, class L, int R0, int... Rs>
+__device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[Plan<N>::E],
+                                               float2* b0, float2* b1, int t,
+                                               const float2* __restrict__ tw, L lay) {
+    constexpr int E = Plan<N>::E;
+    canon_to_stage<E, R0>(v);
+    run_stages<N, E, INV, 1, L, R0, Rs...>(v, b0, b1, t, tw, lay);
+}
+
+// Full length-N transform of the values held in canonical order by the TPT
+// threads of one transform.  Every thread of the block must call it the same
+// number of times (it contains __syncthreads).  tw: table W_N^k, k < N.
+// The leading barrier separates the last shared-memory reads of a previous
+// transform from the first writes of this one (plans with one exchange would
+// otherwise reuse a buffer without a barrier in between).
+template <int N, bool INV, class L>
+__device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, float2* b1, int t,
+                                          const float2* __restrict__ tw, L lay) {
+    __syncthreads();
+    transform_impl<N, INV, L>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay);
+}
+
+}  // namespace fft
+}  // namespace tacaw

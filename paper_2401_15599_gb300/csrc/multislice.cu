@@ -1,0 +1,282 @@
+// Multislice slice step as two fused passes per slice over the wave held in
+// the exit-wave buffer itself (second step of the procedure after Eq. (9);
+// textbook multislice: transmit, Fourier transform, propagate, inverse).
+//
+// With F2 = Fy Fx, one slice  psi_{s+1} = F2^-1[ P BL F2[ t_s psi_s ] ] is
+// split into
+//   row pass    (along x):  Fx^-1 -> multiply by t_s = exp(i sigma_e v_s) -> Fx
+//   column pass (along y):  Fy -> multiply by P BL / (nx ny) -> Fy^-1
+// so between passes the wave is stored "hybrid" as (k_x, y).  The first row
+// pass starts from the real-space incident wave (no inverse transform); the
+// last column pass skips Fy^-1 and leaves the exit wave in q-space.
+// Each pass reads and writes every point once (8 + 8 bytes per point), the
+// row pass also reads v_s (4 bytes per point): 36 bytes per point and slice.
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace tacaw {
+
+namespace {
+
+constexpr int kRowThreads = 256;
+
+// Tables computed in FP64 on the device once per call (into the workspace):
+//   twx[k] = W_nx^k, twy[k] = W_ny^k (rounded to float),
+//   px[kx] = exp(-i pi lambda dz qx^2), py[ky] = exp(-i pi lambda dz qy^2) / (nx ny),
+//   kymax[kx] = largest |ky| index with qx^2 + qy^2 <= qmax^2 (-1 if none).
+// q = k * (1 / (n * (L / n))) with k the signed FFT frequency index: the same
+// FP64 expression sequence as numpy.fft.fftfreq(n, d=L/n), evaluated without
+// FMA contraction so the band-limit decision is bit-identical to it.
+__device__ double fft_freq(int k, int n, double len) {
+    const int half = (n - 1) / 2 + 1;
+    const int kk = k < half ? k : k - n;
+    const double d = __ddiv_rn(len, (double)n);
+    const double val = __ddiv_rn(1.0, __dmul_rn((double)n, d));
+    return __dmul_rn((double)kk, val);
+}
+
+__global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py, int* kymax,
+                                int nx, int ny, double lx, double ly, double lam_dz,
+                                double qmax2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nx) {
+        double s, c;
+        sincospi(-2.0 * (double)i / (double)nx, &s, &c);
+        twx[i] = make_float2((float)c, (float)s);
+        const double qx = fft_freq(i, nx, lx);
+        const double qx2 = __dmul_rn(qx, qx);
+        sincospi(-lam_dz * qx2, &s, &c);
+        px[i] = make_float2((float)c, (float)s);
+        int kmax = -1;
+        for (int k = 0; k <= ny / 2; ++k) {  // |q_y| grows with k: stop at the first miss
+            const double qy = fft_freq(k, ny, ly);
+            if (__dadd_rn(qx2, __dmul_rn(qy, qy)) <= qmax2) kmax = k; else break;
+        }
+        kymax[i] = kmax;
+    }
+    if (i < ny) {
+        double s, c;
+        sincospi(-2.0 * (double)i / (double)ny, &s, &c);
+        twy[i] = make_float2((float)c, (float)s);
+        const double qy = fft_freq(i, ny, ly);
+        sincospi(-lam_dz * __dmul_rn(qy, qy), &s, &c);
+        const double inv_n = 1.0 / ((double)nx * (double)ny);
+        py[i] = make_float2((float)(c * inv_n), (float)(s * inv_n));
+    }
+}
+
+// Row pass: ROWS rows of one snapshot per block.
+// mode 0: stored rows are (k_x, y) -> Fx^-1 first; 1: unit plane wave; 2: psi_in.
+template <int NX>
+__global__ void __launch_bounds__(kRowThreads)
+row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
+                const float2* __restrict__ psi_in, const float2* __restrict__ twx,
+                int ny, int n_slices, int s, float sigma, int mode) {
+    using namespace fft;
+    constexpr int E = Plan<NX>::E;
+    constexpr int TPT = NX / E;
+    constexpr int ROWS = kRowThreads / TPT;
+    extern __shared__ float2 smem[];
+    float2* b0 = smem;
+    float2* b1 = smem + ROWS * NX;
+
+    const int t = threadIdx.x % TPT;
+    const int row = threadIdx.x / TPT;
+    const int y = blockIdx.x * ROWS + row;
+    const size_t snap = blockIdx.y;
+    float2* rowp = psi + (snap * ny + y) * NX;
+    const float* vrow = V + ((snap * n_slices + s) * ny + y) * NX;
+    const RowLayout lay{row * NX};
+
+    float2 v[E];
+    if (mode == 0) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = rowp[t + TPT * m];
+        transform<NX, true>(v, b0, b1, t, twx, lay);
+    } else if (mode == 1) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = make_float2(1.f, 0.f);
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = psi_in[(size_t)y * NX + t + TPT * m];
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float sn, cs;
+        sincosf(sigma * __ldg(vrow + t + TPT * m), &sn, &cs);
+        v[m] = cmul(v[m], make_float2(cs, sn));
+    }
+    transform<NX, false>(v, b0, b1, t, twx, lay);
+#pragma unroll
+    for (int m = 0; m < E; ++m) rowp[t + TPT * m] = v[m];
+}
+
+template <int NY>
+struct ColCfg { static constexpr int W = (NY >= 512) ? 8 : 16; };
+
+// Column pass: W adjacent columns of one snapshot per block.
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E))
+col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
+                const float2* __restrict__ px, const float2* __restrict__ py,
+                const int* __restrict__ kymax, int nx, int last) {
+    using namespace fft;
+    constexpr int E = Plan<NY>::E;
+    constexpr int TPT = NY / E;
+    constexpr int W = ColCfg<NY>::W;
+    extern __shared__ float2 smem[];
+    float2* b0 = smem;
+    float2* b1 = smem + W * NY;
+
+    const int c = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int kx = blockIdx.x * W + c;
+    const size_t snap = blockIdx.y;
+    float2* col = psi + snap * NY * (size_t)nx + kx;
+    const ColLayout<W> lay{c};
+
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = col[(size_t)(t + TPT * m) * nx];
+    transform<NY, false>(v, b0, b1, t, twy, lay);
+
+    const float2 pxv = __ldg(px + kx);
+    const int kmax = __ldg(kymax + kx);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int ky = t + TPT * m;
+        const int aky = ky < NY / 2 ? ky : NY - ky;
+        v[m] = (aky <= kmax) ? cmul(cmul(v[m], pxv), __ldg(py + ky)) : make_float2(0.f, 0.f);
+    }
+    if (!last) transform<NY, true>(v, b0, b1, t, twy, lay);
+#pragma unroll
+    for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
+}
+
+// psi_sum[q] += sum_t psi[t][q], FP64, snapshots added in order.
+__global__ void snapshot_sum_kernel(const float2* __restrict__ psi, double2* __restrict__ sum,
+                                    int n_t, size_t nq) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double re = 0.0, im = 0.0;
+    for (int t = 0; t < n_t; ++t) {
+        const float2 v = __ldg(psi + (size_t)t * nq + q);
+        re += (double)v.x;
+        im += (double)v.y;
+    }
+    double2 acc = sum[q];
+    acc.x += re;
+    acc.y += im;
+    sum[q] = acc;
+}
+
+template <int NX>
+cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const float2* twx,
+                       int ny, int n_t, int n_slices, int s, float sigma, int mode,
+                       cudaStream_t st) {
+    constexpr int TPT = NX / fft::Plan<NX>::E;
+    constexpr int ROWS = kRowThreads / TPT;
+    const size_t smem = 2 * ROWS * NX * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<NX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ny / ROWS, n_t);
+    row_pass_kernel<NX><<<grid, kRowThreads, smem, st>>>(psi, V, psi_in, twx, ny, n_slices, s, sigma, mode);
+    return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t launch_col(float2* psi, const float2* twy, const float2* px, const float2* py,
+                       const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
+    constexpr int TPT = NY / fft::Plan<NY>::E;
+    constexpr int W = ColCfg<NY>::W;
+    const size_t smem = 2 * W * NY * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(nx / W, n_t);
+    col_pass_kernel<NY><<<grid, W * TPT, smem, st>>>(psi, twy, px, py, kymax, nx, last);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_in, const float2* twx,
+                         int ny, int n_t, int n_slices, int s, float sigma, int mode, cudaStream_t st) {
+    switch (nx) {
+        case 64: return launch_row<64>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+        case 128: return launch_row<128>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+        case 256: return launch_row<256>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+        case 512: return launch_row<512>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+        case 1024: return launch_row<1024>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_col(int ny, float2* psi, const float2* twy, const float2* px, const float2* py,
+                         const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
+    switch (ny) {
+        case 64: return launch_col<64>(psi, twy, px, py, kymax, nx, n_t, last, st);
+        case 128: return launch_col<128>(psi, twy, px, py, kymax, nx, n_t, last, st);
+        case 256: return launch_col<256>(psi, twy, px, py, kymax, nx, n_t, last, st);
+        case 512: return launch_col<512>(psi, twy, px, py, kymax, nx, n_t, last, st);
+        case 1024: return launch_col<1024>(psi, twy, px, py, kymax, nx, n_t, last, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool multislice_size_supported(int n) {
+    return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+}
+
+struct MsTables {
+    float2 *twx, *twy, *px, *py;
+    int* kymax;
+};
+
+static MsTables carve_ms(Carver& cv, const tacaw_grid& g) {
+    MsTables t;
+    t.twx = cv.take<float2>(g.nx);
+    t.twy = cv.take<float2>(g.ny);
+    t.px = cv.take<float2>(g.nx);
+    t.py = cv.take<float2>(g.ny);
+    t.kymax = cv.take<int>(g.nx);
+    return t;
+}
+
+size_t multislice_ws_bytes(const tacaw_grid& g) {
+    Carver cv(nullptr);
+    carve_ms(cv, g);
+    return cv.bytes();
+}
+
+int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    MsTables tb = carve_ms(cv, g);
+    double lam = 0.0, sig = 0.0;
+    beam_constants(g.kev, &lam, &sig);
+    const double qmax = g.bandlimit * fmin((double)g.nx / (2.0 * g.lx), (double)g.ny / (2.0 * g.ly));
+    const double qmax2 = qmax * qmax;
+    const int nmax = g.nx > g.ny ? g.nx : g.ny;
+    ms_setup_kernel<<<(nmax + 127) / 128, 128, 0, st>>>(tb.twx, tb.twy, tb.px, tb.py, tb.kymax,
+                                                       g.nx, g.ny, g.lx, g.ly, lam * g.dz, qmax2);
+    TACAW_LAUNCH_CHECK();
+    const float sigma = (float)sig;
+    for (int s = 0; s < g.n_slices; ++s) {
+        const int mode = s > 0 ? 0 : (psi_in ? 2 : 1);
+        TACAW_CUDA_CHECK(dispatch_row(g.nx, psi_q, V, psi_in, tb.twx, g.ny, n_t, g.n_slices, s,
+                                      sigma, mode, st));
+        TACAW_CUDA_CHECK(dispatch_col(g.ny, psi_q, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t,
+                                      s + 1 == g.n_slices, st));
+    }
+    if (psi_sum) {
+        const size_t nq = (size_t)g.nx * g.ny;
+        snapshot_sum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(psi_q, psi_sum, n_t, nq);
+        TACAW_LAUNCH_CHECK();
+    }
+    return TACAW_OK;
+}
+
+}  // namespace tacaw

@@ -1,0 +1,265 @@
+// Temporal transform of the exit waves into I(q, E) (Eq. (9): the spectrum
+// is |phi_MD(q, E)|^2 by the convolution theorem, with the Kubo factor of
+// Eq. (8) and the fractional-intensity normalisation after Eq. (9)).
+//
+//   m_q = (1/T) sum_n psi(q, t_n)                    FP64, snapshot order
+//   A(q, t_n) = psi(q, t_n) - m_q                    FP64 subtract, rounded to float
+//   Phi(q, E_k) = sum_n A(q, t_n) E(t_n, E_k),  E = exp(-i E_k t_n / hbar)
+//   I(q, E_k) = |Phi|^2 / T^2 (* Kubo factor),  I_el(q) = |m_q|^2
+//
+// The transform is a complex GEMM [nq x T] x [T x n_omega].  This file holds
+// the FP32 SIMT form; the DFT matrix is built in FP64 on the device (exact
+// integer phase reduction on the natural grid) and rounded once to float.
+
+#include "common.cuh"
+
+namespace tacaw {
+
+namespace {
+
+// CODATA 2018: h in meV*fs and the Boltzmann constant in meV/K.
+constexpr double kPlanckMeVfs = 6.62607015e-34 / 1.602176634e-19 * 1e3 * 1e15;
+constexpr double kBoltzmannMeVK = 1.380649e-23 / 1.602176634e-19 * 1e3;
+
+__global__ void time_sum_kernel(const float2* __restrict__ psi, size_t ld, double2* __restrict__ sum,
+                                int n_t, int nq) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double re = 0.0, im = 0.0;
+    for (int t = 0; t < n_t; ++t) {
+        const float2 v = __ldg(psi + (size_t)t * ld + q);
+        re += (double)v.x;
+        im += (double)v.y;
+    }
+    sum[q] = make_double2(re, im);
+}
+
+// A = psi - sum / T in FP64, rounded to float; also I_el = |sum / T|^2.
+__global__ void centre_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restrict__ sum,
+                              float2* __restrict__ a, double* __restrict__ i_el, int n_t, int nq) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (q >= nq) return;
+    const double2 s = sum[q];
+    const double inv_t = 1.0 / (double)n_t;
+    const double mr = s.x * inv_t, mi = s.y * inv_t;
+    const float2 v = __ldg(psi + (size_t)t * ld + q);
+    a[(size_t)t * nq + q] = make_float2((float)((double)v.x - mr), (float)((double)v.y - mi));
+    if (t == 0 && i_el) i_el[q] = mr * mr + mi * mi;
+}
+
+// E[n][k] = exp(-i E_k t_n / hbar) = exp(-2 pi i E_k t_n / h).
+// Natural grid: E_k = h (k - T/2) / (T dt) -> phase = -2 pi ((k - T/2) n mod T) / T.
+// Explicit grid: cycles = E_k t_n / h in FP64, reduced to its fractional part.
+// kubo[k] = beta E_k / (1 - exp(-beta E_k)) (1 at E = 0) when requested.
+__global__ void dft_table_kernel(float2* __restrict__ e, float* __restrict__ kubo,
+                                 const double* __restrict__ omega, int n_t, int n_w, double dt,
+                                 double beta) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (k >= n_w) return;
+    double s, c, ek;
+    if (omega == nullptr) {
+        const long long kk = (long long)k - n_t / 2;
+        long long r = (kk * n) % n_t;
+        if (r < 0) r += n_t;
+        sincospi(-2.0 * (double)r / (double)n_t, &s, &c);
+        ek = (double)kk * kPlanckMeVfs / ((double)n_t * dt);
+    } else {
+        ek = omega[k];
+        const double cyc = ek * ((double)n * dt) / kPlanckMeVfs;
+        const double frac = cyc - rint(cyc);
+        sincospi(-2.0 * frac, &s, &c);
+    }
+    e[(size_t)n * n_w + k] = make_float2((float)c, (float)s);
+    if (n == 0 && kubo) {
+        const double be = beta * ek;
+        kubo[k] = (be == 0.0) ? 1.0f : (float)(be / (-expm1(-be)));
+    }
+}
+
+// I[q][k] = |sum_n A[n][q] E[n][k]|^2 * scale (* kubo[k]), FP32 SIMT.
+constexpr int BM = 64, BN = 64, BK = 16;
+__global__ void __launch_bounds__(256)
+cgemm_power_kernel(const float2* __restrict__ a, const float2* __restrict__ e,
+                   const float* __restrict__ kubo, float* __restrict__ out, int nq, int n_t,
+                   int n_w, float scale) {
+    __shared__ float2 as[BK][BM];
+    __shared__ float2 es[BK][BN];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int w0 = blockIdx.x * BN, q0 = blockIdx.y * BM;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+    for (int k0 = 0; k0 < n_t; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = threadIdx.x + 256 * i;
+            const int kk = idx / BM, mm = idx % BM;
+            const int n = k0 + kk;
+            as[kk][mm] = (n < n_t && q0 + mm < nq) ? __ldg(a + (size_t)n * nq + q0 + mm)
+                                                   : make_float2(0.f, 0.f);
+            es[kk][mm] = (n < n_t && w0 + mm < n_w) ? __ldg(e + (size_t)n * n_w + w0 + mm)
+                                                    : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 av[4], ev[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = as[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ev[j] = es[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(av[i].x, ev[j].x, fmaf(-av[i].y, ev[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(av[i].x, ev[j].y, fmaf(av[i].y, ev[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int q = q0 + ty + 16 * i;
+        if (q >= nq) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = w0 + tx + 16 * j;
+            if (k >= n_w) continue;
+            float v = (acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y) * scale;
+            if (kubo) v *= __ldg(kubo + k);
+            out[(size_t)q * n_w + k] = v;
+        }
+    }
+}
+
+// Deterministic FP64 sum: fixed partition into blocks, fixed order inside.
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+__global__ void __launch_bounds__(kRedThreads)
+partial_sum_kernel(const float* __restrict__ x, size_t n, double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    const size_t per = (n + gridDim.x - 1) / gridDim.x;
+    const size_t b0 = (size_t)blockIdx.x * per, b1 = min(n, b0 + per);
+    for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)x[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+total_kernel(const double* __restrict__ partial, int n_partial, const double* __restrict__ i_el,
+             int nq, double* __restrict__ total) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n_partial; i += blockDim.x) acc += partial[i];
+    if (i_el)
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) acc += i_el[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) total[0] = sh[0];
+}
+
+__global__ void scale_kernel(float* __restrict__ x, size_t n, double* __restrict__ i_el, int nq,
+                             const double* __restrict__ total) {
+    const double inv = 1.0 / total[0];
+    const float finv = (float)inv;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] *= finv;
+    if (i_el)
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)nq;
+             i += (size_t)gridDim.x * blockDim.x)
+            i_el[i] *= inv;
+}
+
+struct SpecWs {
+    double2* sum;
+    float2* a;
+    float2* e;
+    float* kubo;
+    double* partial;
+    double* total;
+    double* i_el;
+};
+
+SpecWs carve_spec(Carver& cv, int nq, int n_t, int n_w, bool need_sum, bool need_iel) {
+    SpecWs w;
+    w.sum = need_sum ? cv.take<double2>(nq) : nullptr;
+    w.a = cv.take<float2>((size_t)n_t * nq);
+    w.e = cv.take<float2>((size_t)n_t * n_w);
+    w.kubo = cv.take<float>(n_w);
+    w.partial = cv.take<double>(kRedBlocks);
+    w.total = cv.take<double>(1);
+    w.i_el = need_iel ? cv.take<double>(nq) : nullptr;
+    return w;
+}
+
+}  // namespace
+
+size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel) {
+    Carver cv(nullptr);
+    carve_spec(cv, nq, n_t, n_w, !have_sum, !have_iel);
+    return cv.bytes();
+}
+
+int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
+                 size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
+                 int flags, double temperature_K, void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    SpecWs w = carve_spec(cv, nq, n_t, n_w, psi_sum == nullptr, i_el == nullptr);
+    const double2* sum = psi_sum;
+    if (!sum) {
+        time_sum_kernel<<<(nq + 255) / 256, 256, 0, st>>>(psi, ld, w.sum, n_t, nq);
+        TACAW_LAUNCH_CHECK();
+        sum = w.sum;
+    }
+    double* iel = i_el ? i_el : w.i_el;
+    {
+        dim3 grid((nq + 255) / 256, n_t);
+        centre_kernel<<<grid, 256, 0, st>>>(psi, ld, sum, w.a, iel, n_t, nq);
+        TACAW_LAUNCH_CHECK();
+    }
+    const bool kubo = (flags & TACAW_KUBO) != 0;
+    const double beta = kubo ? 1.0 / (kBoltzmannMeVK * temperature_K) : 0.0;
+    {
+        dim3 grid((n_w + 127) / 128, n_t);
+        dft_table_kernel<<<grid, 128, 0, st>>>(w.e, kubo ? w.kubo : nullptr, omega, n_t, n_w, dt_fs, beta);
+        TACAW_LAUNCH_CHECK();
+    }
+    if (precision != TACAW_FP32) {
+        set_error("tacaw_spectrum: precision %d is not available in this build", precision);
+        return TACAW_EUNSUPPORTED;
+    }
+    {
+        dim3 grid((n_w + BN - 1) / BN, (nq + BM - 1) / BM);
+        const float scale = (float)(1.0 / ((double)n_t * (double)n_t));
+        cgemm_power_kernel<<<grid, 256, 0, st>>>(w.a, w.e, kubo ? w.kubo : nullptr, out, nq, n_t, n_w, scale);
+        TACAW_LAUNCH_CHECK();
+    }
+    if (flags & TACAW_NORMALIZE) {
+        const size_t n = (size_t)nq * n_w;
+        partial_sum_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(out, n, w.partial);
+        TACAW_LAUNCH_CHECK();
+        total_kernel<<<1, kRedThreads, 0, st>>>(w.partial, kRedBlocks, iel, nq, w.total);
+        TACAW_LAUNCH_CHECK();
+        scale_kernel<<<1024, 256, 0, st>>>(out, n, i_el, nq, w.total);
+        TACAW_LAUNCH_CHECK();
+    }
+    return TACAW_OK;
+}
+
+}  // namespace tacaw
