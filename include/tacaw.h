@@ -143,6 +143,28 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,
                      void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * tacaw_multislice without a workspace, for callers that cannot allocate
+ * device memory at all (for example a plug-in whose host application owns
+ * every device allocation, or a real-time service that forbids allocation
+ * after start-up).  The paper has no counterpart: this is a deployment
+ * convenience.  Same arguments, results and supported sizes as
+ * tacaw_multislice, minus ws / ws_bytes; it calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * Scratch lives in one fixed 64 KiB device array inside the library (enough
+ * for every supported grid, up to 1024 x 1024); each GPU that loads the
+ * library holds it until the process exits.  A grid needing more is rejected
+ * with TACAW_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array and
+ * rewrite it at the start of each call: calls whose kernels overlap on the GPU
+ * (concurrent streams or graph replays) race and must be serialised.
+ */
+int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, const float* V,
+                            const void* psi_in, void* psi_q, void* psi_sum, int32_t flags,
+                            void* stream);
+
+/*
  * Energy-resolved intensity from exit waves (Eq. (9) with Eq. (8) and the
  * normalisation after it).  With A(q, t_n) = psi(q, t_n) - m_q and
  * m_q = (1/T) sum_n psi(q, t_n) (FP64):

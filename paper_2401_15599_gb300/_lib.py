@@ -58,6 +58,8 @@ SIGNATURES = {
                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _P, _P, _SZ, _P]),
     "tacaw_multislice": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,
                                         ctypes.c_int32, _P, _SZ, _P]),
+    "tacaw_multislice_static": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,
+                                               ctypes.c_int32, _P]),
     "tacaw_spectrum": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P,
                                       _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                       _P, _SZ, _P]),

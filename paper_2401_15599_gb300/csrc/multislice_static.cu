@@ -1,0 +1,95 @@
+// tacaw_multislice_static: the multislice of tacaw_multislice with its
+// scratch in a fixed device array of this library instead of a caller
+// workspace, for callers that cannot allocate device memory at all -- for
+// example a plug-in whose host application owns every device allocation,
+// or a real-time service that forbids allocation after start-up -- and so
+// can neither call cudaMalloc nor hand over a workspace buffer.
+//
+// The scratch holds only the per-call tables of the slice step (twiddles,
+// separable propagator factors, band-limit extents): at most 36 KiB for the
+// largest supported grid, so kStaticScratchBytes = 64 KiB covers every
+// supported size.  Every GPU that loads the library keeps this array until
+// the process exits.
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace tacaw {
+
+size_t multislice_ws_bytes(const tacaw_grid& g);
+int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st);
+bool multislice_size_supported(int n);
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 64 * 1024;
+constexpr int kMaxDevices = 64;
+
+// One shared scratch block per device.  All calls on a device reuse it, so
+// two calls whose kernels overlap on the GPU (different streams, or graphs
+// replayed concurrently) overwrite each other's tables and race.
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// In host code g_static_scratch names a host-side shadow, not device memory;
+// the device address is looked up once per device with that device current.
+int static_scratch(void** out) {
+    int dev = -1;
+    TACAW_CUDA_CHECK(cudaGetDevice(&dev));
+    TACAW_REQUIRE(dev >= 0 && dev < kMaxDevices, TACAW_EUNSUPPORTED,
+                  "tacaw_multislice_static: device ordinal %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_addr[dev] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("tacaw_multislice_static: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+            return TACAW_ECUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return TACAW_OK;
+}
+
+}  // namespace
+}  // namespace tacaw
+
+using namespace tacaw;
+
+extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, const float* V,
+                                       const void* psi_in, void* psi_q, void* psi_sum,
+                                       int32_t flags, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_multislice_static";
+    TACAW_REQUIRE(grid != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
+    TACAW_REQUIRE(grid->nx > 0 && grid->ny > 0 && grid->n_slices > 0 && grid->n_slices <= 65535 &&
+                      grid->lx > 0 && grid->ly > 0 && grid->dz > 0 && grid->kev > 0 &&
+                      grid->bandlimit > 0 && isfinite(grid->lx) && isfinite(grid->ly) &&
+                      isfinite(grid->dz) && isfinite(grid->z0) && isfinite(grid->kev) &&
+                      isfinite(grid->bandlimit),
+                  TACAW_EINVAL, "%s: bad grid", fn);
+    TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny),
+                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 512, 1024}", fn,
+                  grid->nx, grid->ny);
+    const size_t need = multislice_ws_bytes(*grid);
+    TACAW_REQUIRE(need <= kStaticScratchBytes, TACAW_EINVAL,
+                  "%s: this grid needs %zu bytes of scratch, more than the fixed %zu", fn, need,
+                  kStaticScratchBytes);
+    TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
+    TACAW_REQUIRE(flags == 0, TACAW_EINVAL, "%s: flags must be 0", fn);
+    if (n_t == 0) return TACAW_OK;
+    TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
+    void* scratch = nullptr;
+    int rc = static_scratch(&scratch);
+    if (rc != TACAW_OK) return rc;
+    // The tables are rewritten in full at the start of every call, so no part
+    // of the shared array has to start at zero.
+    return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
+                          scratch, (cudaStream_t)stream);
+}
