@@ -15,9 +15,11 @@
 // multiplications (transmission, propagator) can be applied in registers
 // between an inverse and a forward transform without any exchange.
 //
-// Twiddles W_N^k = exp(-2 pi i k / N) come from a table computed in FP64
-// and rounded once to float; the inverse transform uses their conjugates and
-// is unnormalised.
+// Twiddles come from per-stage tables computed in FP64 and rounded once to
+// float: for every stage with NS > 1 the block tw[OFF + (r-1) NS + jm] holds
+// W_{NS R}^{jm r} (r = 1 .. R-1, jm = 0 .. NS-1), so lanes with consecutive
+// jm read consecutive entries (or the same entry) of shared memory.  The
+// inverse transform uses their conjugates and is unnormalised.
 #pragma once
 
 #include "common.cuh"
@@ -140,8 +142,8 @@ struct ColLayout {
 };
 
 // Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
-template <int N, int E, int R, int NS, bool INV>
-__device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* __restrict__ tw) {
+template <int N, int E, int R, int NS, int OFF, bool INV>
+__device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw) {
     constexpr int TPT = N / E;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
@@ -151,7 +153,7 @@ __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* __res
             const int jm = j % NS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(tw + jm * r * (N / (NS * R)));
+                float2 w = tw[OFF + (r - 1) * NS + jm];
                 if (INV) w.y = -w.y;
                 x[r] = cmul(x[r], w);
             }
@@ -206,16 +208,17 @@ __device__ __forceinline__ void stage_to_canon(float2 (&v)[E]) {
     for (int m = 0; m < E; ++m) v[m] = tmp[m];
 }
 
-template <int N, int E, bool INV, int NS, class L, int R, int... Rest>
+template <int N, int E, bool INV, int NS, int OFF, class L, int R, int... Rest>
 __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
-                                           const float2* __restrict__ tw, L lay) {
-    stage<N, E, R, NS, INV>(v, t, tw);
+                                           const float2* tw, L lay) {
+    stage<N, E, R, NS, OFF, INV>(v, t, tw);
     if constexpr (sizeof...(Rest) > 0) {
         constexpr int RN = First<Rest...>::value;
+        constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
         write_out<N, E, R, NS>(v, b0, t, lay);
         __syncthreads();
         read_in<N, E, RN>(v, b0, t, lay);
-        run_stages<N, E, INV, NS * R, L, Rest...>(v, b1, b0, t, tw, lay);
+        run_stages<N, E, INV, NS * R, NEXT_OFF, L, Rest...>(v, b1, b0, t, tw, lay);
     } else {
         stage_to_canon<E, R>(v);
     }
@@ -223,22 +226,58 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b
 
 template <int N, bool INV, class L, int R0, int... Rs>
 __device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[Plan<N>::E],
-                                               float2* b0, float2* b1, int t,
-                                               const float2* __restrict__ tw, L lay) {
+                                               float2* b0, float2* b1, int t, const float2* tw,
+                                               L lay) {
     constexpr int E = Plan<N>::E;
     canon_to_stage<E, R0>(v);
-    run_stages<N, E, INV, 1, L, R0, Rs...>(v, b0, b1, t, tw, lay);
+    run_stages<N, E, INV, 1, 0, L, R0, Rs...>(v, b0, b1, t, tw, lay);
+}
+
+// Size of the per-stage twiddle table of a plan.
+template <int NS, int R, int... Rest>
+constexpr int tw_entries() {
+    constexpr int here = NS > 1 ? (R - 1) * NS : 0;
+    if constexpr (sizeof...(Rest) > 0) return here + tw_entries<NS * R, Rest...>();
+    else return here;
+}
+template <int... Rs>
+constexpr int tw_entries_of(Radices<Rs...>) { return tw_entries<1, Rs...>(); }
+template <int N>
+struct TwSize { static constexpr int value = tw_entries_of(typename Plan<N>::R{}); };
+
+// Fill the per-stage twiddle table of Plan<N> in FP64 (threads tid of nthr).
+template <int NS, int OFF, int R, int... Rest>
+__device__ void fill_twiddles_impl(float2* tw, int tid, int nthr) {
+    if constexpr (NS > 1) {
+        for (int e = tid; e < (R - 1) * NS; e += nthr) {
+            const int r = 1 + e / NS, jm = e % NS;
+            double sn, cs;
+            sincospi(-2.0 * (double)(jm * r) / (double)(NS * R), &sn, &cs);
+            tw[OFF + e] = make_float2((float)cs, (float)sn);
+        }
+    }
+    if constexpr (sizeof...(Rest) > 0)
+        fill_twiddles_impl<NS * R, OFF + (NS > 1 ? (R - 1) * NS : 0), Rest...>(tw, tid, nthr);
+}
+template <int... Rs>
+__device__ void fill_twiddles_of(Radices<Rs...>, float2* tw, int tid, int nthr) {
+    fill_twiddles_impl<1, 0, Rs...>(tw, tid, nthr);
+}
+template <int N>
+__device__ void fill_twiddles(float2* tw, int tid, int nthr) {
+    fill_twiddles_of(typename Plan<N>::R{}, tw, tid, nthr);
 }
 
 // Full length-N transform of the values held in canonical order by the TPT
 // threads of one transform.  Every thread of the block must call it the same
-// number of times (it contains __syncthreads).  tw: table W_N^k, k < N.
+// number of times (it contains __syncthreads).  tw: the plan's per-stage
+// twiddle table (TwSize<N> entries), normally staged in shared memory.
 // The leading barrier separates the last shared-memory reads of a previous
 // transform from the first writes of this one (plans with one exchange would
 // otherwise reuse a buffer without a barrier in between).
 template <int N, bool INV, class L>
 __device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, float2* b1, int t,
-                                          const float2* __restrict__ tw, L lay) {
+                                          const float2* tw, L lay) {
     __syncthreads();
     transform_impl<N, INV, L>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay);
 }

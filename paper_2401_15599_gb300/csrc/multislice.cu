@@ -22,7 +22,7 @@ namespace {
 constexpr int kRowThreads = 256;
 
 // Tables computed in FP64 on the device once per call (into the workspace):
-//   twx[k] = W_nx^k, twy[k] = W_ny^k (rounded to float),
+//   twx, twy: per-stage twiddle tables of the nx / ny FFT plans (rounded to float),
 //   px[kx] = exp(-i pi lambda dz qx^2), py[ky] = exp(-i pi lambda dz qy^2) / (nx ny),
 //   kymax[kx] = largest |ky| index with qx^2 + qy^2 <= qmax^2 (-1 if none).
 // q = k * (1 / (n * (L / n))) with k the signed FFT frequency index: the same
@@ -36,14 +36,33 @@ __device__ double fft_freq(int k, int n, double len) {
     return __dmul_rn((double)kk, val);
 }
 
+__device__ void fill_plan_twiddles(int n, float2* tw, int tid, int nthr) {
+    switch (n) {
+        case 64: fft::fill_twiddles<64>(tw, tid, nthr); break;
+        case 128: fft::fill_twiddles<128>(tw, tid, nthr); break;
+        case 256: fft::fill_twiddles<256>(tw, tid, nthr); break;
+        case 512: fft::fill_twiddles<512>(tw, tid, nthr); break;
+        case 1024: fft::fill_twiddles<1024>(tw, tid, nthr); break;
+    }
+}
+
+// Copy a plan's twiddle table into shared memory (made visible by the
+// barrier at the start of the first transform).
+template <int N>
+__device__ __forceinline__ void stage_twiddles(float2* dst, const float2* __restrict__ src) {
+    for (int i = threadIdx.x; i < fft::TwSize<N>::value; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
 __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py, int* kymax,
                                 int nx, int ny, double lx, double ly, double lam_dz,
                                 double qmax2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0) {
+        fill_plan_twiddles(nx, twx, threadIdx.x, blockDim.x);
+        fill_plan_twiddles(ny, twy, threadIdx.x, blockDim.x);
+    }
     if (i < nx) {
         double s, c;
-        sincospi(-2.0 * (double)i / (double)nx, &s, &c);
-        twx[i] = make_float2((float)c, (float)s);
         const double qx = fft_freq(i, nx, lx);
         const double qx2 = __dmul_rn(qx, qx);
         sincospi(-lam_dz * qx2, &s, &c);
@@ -57,8 +76,6 @@ __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py
     }
     if (i < ny) {
         double s, c;
-        sincospi(-2.0 * (double)i / (double)ny, &s, &c);
-        twy[i] = make_float2((float)c, (float)s);
         const double qy = fft_freq(i, ny, ly);
         sincospi(-lam_dz * __dmul_rn(qy, qy), &s, &c);
         const double inv_n = 1.0 / ((double)nx * (double)ny);
@@ -80,6 +97,8 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
     extern __shared__ float2 smem[];
     float2* b0 = smem;
     float2* b1 = smem + ROWS * NX;
+    float2* tw = smem + 2 * ROWS * NX;
+    stage_twiddles<NX>(tw, twx);
 
     const int t = threadIdx.x % TPT;
     const int row = threadIdx.x / TPT;
@@ -93,7 +112,7 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
     if (mode == 0) {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = rowp[t + TPT * m];
-        transform<NX, true>(v, b0, b1, t, twx, lay);
+        transform<NX, true>(v, b0, b1, t, tw, lay);
     } else if (mode == 1) {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = make_float2(1.f, 0.f);
@@ -104,10 +123,10 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float sn, cs;
-        sincosf(sigma * __ldg(vrow + t + TPT * m), &sn, &cs);
+        sincosf(sigma * __ldcs(vrow + t + TPT * m), &sn, &cs);
         v[m] = cmul(v[m], make_float2(cs, sn));
     }
-    transform<NX, false>(v, b0, b1, t, twx, lay);
+    transform<NX, false>(v, b0, b1, t, tw, lay);
 #pragma unroll
     for (int m = 0; m < E; ++m) rowp[t + TPT * m] = v[m];
 }
@@ -117,7 +136,7 @@ struct ColCfg { static constexpr int W = (NY >= 512) ? 8 : 16; };
 
 // Column pass: W adjacent columns of one snapshot per block.
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E))
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
 col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
                 const float2* __restrict__ px, const float2* __restrict__ py,
                 const int* __restrict__ kymax, int nx, int last) {
@@ -128,6 +147,8 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     extern __shared__ float2 smem[];
     float2* b0 = smem;
     float2* b1 = smem + W * NY;
+    float2* tw = smem + 2 * W * NY;
+    stage_twiddles<NY>(tw, twy);
 
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
@@ -139,7 +160,7 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = col[(size_t)(t + TPT * m) * nx];
-    transform<NY, false>(v, b0, b1, t, twy, lay);
+    transform<NY, false>(v, b0, b1, t, tw, lay);
 
     const float2 pxv = __ldg(px + kx);
     const int kmax = __ldg(kymax + kx);
@@ -149,7 +170,7 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
         const int aky = ky < NY / 2 ? ky : NY - ky;
         v[m] = (aky <= kmax) ? cmul(cmul(v[m], pxv), __ldg(py + ky)) : make_float2(0.f, 0.f);
     }
-    if (!last) transform<NY, true>(v, b0, b1, t, twy, lay);
+    if (!last) transform<NY, true>(v, b0, b1, t, tw, lay);
 #pragma unroll
     for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
 }
@@ -177,7 +198,7 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
                        cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
-    const size_t smem = 2 * ROWS * NX * sizeof(float2);
+    const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<NX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -191,7 +212,7 @@ cudaError_t launch_col(float2* psi, const float2* twy, const float2* px, const f
                        const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
     constexpr int TPT = NY / fft::Plan<NY>::E;
     constexpr int W = ColCfg<NY>::W;
-    const size_t smem = 2 * W * NY * sizeof(float2);
+    const size_t smem = (2 * W * NY + fft::TwSize<NY>::value) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -29,23 +29,51 @@ namespace {
 constexpr int kBandRows = 8;
 constexpr int kBinThreads = 1024;
 constexpr int kPotThreads = 256;
-constexpr float kFixScale = 4294967296.0f;            // 2^32
-constexpr float kFixInv = 2.3283064365386963e-10f;    // 2^-32
+// Fixed point: each contribution is rounded to a multiple of 2^-20 V*A as a
+// 32-bit integer (so one contribution must stay below 2048 V*A; the host
+// checks the amplitudes) and summed exactly into a 64-bit accumulator.
+// 64-bit float<->int conversions are avoided on purpose: on this GPU they
+// run on the FP64 pipe.
+constexpr float kFixScale = 1048576.0f;              // 2^20
+constexpr float kFixInv = 9.5367431640625e-07f;      // 2^-20
+constexpr float kMaxAmp = 2000.0f;
 
 struct PotParams {
     int nx, ny, n_slices, n_atoms, n_species;
     int n_bands, n_bins, slab_reach, band_reach;
-    float lx, ly, dx, dy, inv_dx, inv_ly, z0, dz, inv_dz, inv_band_h;
+    float lx, ly, dx, dy, inv_dx, inv_lx, inv_ly, z0, dz, inv_dz, inv_band_h;
+    double dx_d, dy_d, inv_dx_d, inv_dy_d;
     float amp[TACAW_MAX_SPECIES], sigma[TACAW_MAX_SPECIES];
 };
 
-// The bin is computed twice per atom (count, then scatter); explicit
-// round-to-nearest operations keep the compiler from contracting the two
-// copies differently, so both passes always agree.
-__device__ __forceinline__ int atom_bin(float y, float z, const PotParams& p) {
-    const float yw = __fsub_rn(y, __fmul_rn(floorf(__fmul_rn(y, p.inv_ly)), p.ly));
-    int band = (int)floorf(__fmul_rn(yw, p.inv_band_h));
-    band = min(max(band, 0), p.n_bands - 1);
+// An atom's position is split once, in FP64, into the pixel (ic, jc) that
+// holds it and a small offset (fx, fy) from that pixel, so that later
+// pixel-atom distances k*d - f carry no rounding from large coordinates.
+// Its band is the exact integer row band of jc; its slab comes from z with
+// explicit round-to-nearest operations (the bin is computed twice per atom,
+// count then scatter, and both passes must agree).
+struct Split {
+    int ic, jc;
+    float fx, fy;
+    bool ok;
+};
+
+__device__ __forceinline__ Split split_position(float x, float y, const PotParams& p) {
+    Split r;
+    const double fxd = (double)x * p.inv_dx_d, fyd = (double)y * p.inv_dy_d;
+    r.ok = fabs(fxd) < 1e9 && fabs(fyd) < 1e9;
+    const double icd = r.ok ? floor(fxd) : 0.0, jcd = r.ok ? floor(fyd) : 0.0;
+    r.ic = (int)icd;
+    r.jc = (int)jcd;
+    r.fx = (float)((fxd - icd) * p.dx_d);
+    r.fy = (float)((fyd - jcd) * p.dy_d);
+    return r;
+}
+
+__device__ __forceinline__ int atom_bin(int jc, float z, const PotParams& p) {
+    int jw = jc % p.ny;
+    if (jw < 0) jw += p.ny;
+    const int band = jw / kBandRows;
     int slab = (int)floorf(__fmul_rn(__fsub_rn(z, p.z0), p.inv_dz));
     slab = min(max(slab, 0), p.n_slices - 1);
     return slab * p.n_bands + band;
@@ -53,15 +81,17 @@ __device__ __forceinline__ int atom_bin(float y, float z, const PotParams& p) {
 
 __global__ void __launch_bounds__(kBinThreads)
 bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotParams p,
-           int* __restrict__ bin_off, float4* __restrict__ binned) {
+           int* __restrict__ bin_off, float4* __restrict__ binned, int2* __restrict__ binned_px) {
     extern __shared__ int cnt[];
     __shared__ int warp_off[kBinThreads / 32];
     const size_t t = blockIdx.x;
     const float* P = pos + t * (size_t)p.n_atoms * 3;
     for (int b = threadIdx.x; b < p.n_bins; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
-    for (int a = threadIdx.x; a < p.n_atoms; a += blockDim.x)
-        atomicAdd(&cnt[atom_bin(P[3 * a + 1], P[3 * a + 2], p)], 1);
+    for (int a = threadIdx.x; a < p.n_atoms; a += blockDim.x) {
+        const Split sp = split_position(P[3 * a], P[3 * a + 1], p);
+        atomicAdd(&cnt[atom_bin(sp.jc, P[3 * a + 2], p)], 1);
+    }
     __syncthreads();
 
     // exclusive scan of the counts; thread i owns a contiguous chunk of bins
@@ -102,92 +132,237 @@ bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotPa
     __syncthreads();
 
     float4* out = binned + t * (size_t)p.n_atoms;
+    int2* out_px = binned_px + t * (size_t)p.n_atoms;
     for (int a = threadIdx.x; a < p.n_atoms; a += blockDim.x) {
-        const float x = P[3 * a], y = P[3 * a + 1], z = P[3 * a + 2];
-        const int slot = atomicAdd(&cnt[atom_bin(y, z, p)], 1);
-        out[slot] = make_float4(x, y, z, __int_as_float(__ldg(species + a)));
+        const float z = P[3 * a + 2];
+        const Split sp = split_position(P[3 * a], P[3 * a + 1], p);
+        const int slot = atomicAdd(&cnt[atom_bin(sp.jc, z, p)], 1);
+        // a species of -1 marks an atom that is skipped (non-finite or absurd position)
+        const int spc = (sp.ok && fabsf(z) < 1e9f) ? __ldg(species + a) : -1;
+        out[slot] = make_float4(sp.fx, sp.fy, z, __int_as_float(spc));
+        out_px[slot] = make_int2(sp.ic, sp.jc);
     }
 }
 
+// Candidate atoms of one block, gathered per chunk of source atoms.
+constexpr int kChunk = kPotThreads;      // source atoms examined per chunk
+constexpr int kSegs = kPotThreads / 32;  // one column segment per warp
+constexpr int kMaxNbBins = 64;           // neighbouring bins scanned per block
+
+struct CandSmem {
+    int ic[kChunk], jc[kChunk];                 // pixel index of the atom (floor of x/dx, y/dy)
+    float fx[kChunk], fy[kChunk];               // offset of the atom from that pixel, A
+    float aw[kChunk], inv2s2[kChunk], rc2[kChunk];
+    float gy[kChunk][kBandRows];
+    float dy2[kChunk][kBandRows];
+    unsigned short seg_list[kSegs][kChunk];
+    int seg_cnt[kSegs];
+    int n_cand;
+    int bin_start[kMaxNbBins], bin_cum[kMaxNbBins + 1];
+    int n_nb;
+};
+
+// One block per (band of kBandRows rows, slice, snapshot).  Warp w owns the
+// column segment [w * seg_w, (w + 1) * seg_w) (CPL columns per lane) and keeps
+// the band's sums for those columns in 64-bit fixed-point registers: no
+// atomics on pixels, the Gaussian is evaluated separably (one row factor per
+// candidate and row, one column factor per candidate and column), and the
+// result does not depend on the order in which candidates arrive.
+template <int CPL>
 __global__ void __launch_bounds__(kPotThreads)
-potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned, PotParams p,
-                 float* __restrict__ V) {
-    extern __shared__ unsigned long long acc[];
+potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                 const int2* __restrict__ binned_px, PotParams p, float* __restrict__ V) {
+    __shared__ CandSmem sm;
     const int band = blockIdx.x, s = blockIdx.y;
     const size_t t = blockIdx.z;
     const int r0 = band * kBandRows;
     const int nrows = min(kBandRows, p.ny - r0);
-    for (int i = threadIdx.x; i < kBandRows * p.nx; i += blockDim.x) acc[i] = 0ull;
-    __syncthreads();
-
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seg_w = (p.nx + kSegs - 1) / kSegs;
     const int* off = bin_off + t * (size_t)(p.n_bins + 1);
     const float4* atoms = binned + t * (size_t)p.n_atoms;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
     const bool first = (s == 0), lastsl = (s == p.n_slices - 1);
     const float lo = first ? -INFINITY : p.z0 + (float)s * p.dz;
     const float hi = lastsl ? INFINITY : p.z0 + (float)(s + 1) * p.dz;
+    const float band_span = (float)(nrows - 1) * p.dy;
+
+    // neighbouring bins (slabs s +- slab_reach, bands +- band_reach) as one
+    // flat list: one thread per bin loads its range, warp 0 scans the counts
     const int slab0 = max(0, s - p.slab_reach), slab1 = min(p.n_slices - 1, s + p.slab_reach);
     const bool all_bands = 2 * p.band_reach + 1 >= p.n_bands;
     const int nb = all_bands ? p.n_bands : 2 * p.band_reach + 1;
-
-    for (int slab = slab0; slab <= slab1; ++slab) {
-        for (int k = 0; k < nb; ++k) {
-            int b = all_bands ? k : band - p.band_reach + k;
-            b = ((b % p.n_bands) + p.n_bands) % p.n_bands;
-            const int bin = slab * p.n_bands + b;
-            const int a1 = off[bin + 1];
-            for (int a = off[bin] + warp; a < a1; a += nwarps) {
-                const float4 at = atoms[a];
-                const int sp = __float_as_int(at.w);
-                if (sp < 0 || sp >= p.n_species) continue;
-                const float sg = p.sigma[sp];
-                const float rc = 6.0f * sg;
-                if (!(hi > at.z - rc && lo < at.z + rc)) continue;
-                const float kz = 0.70710678118654752f / sg;
-                const float fh = lastsl ? 0.5f : 0.5f * erff((hi - at.z) * kz);
-                const float fl = first ? -0.5f : 0.5f * erff((lo - at.z) * kz);
-                const float aw = p.amp[sp] * (fh - fl);
-                const float inv2s2 = 0.5f / (sg * sg);
-                const float rc2 = rc * rc;
-                // one spare column on each side: the disc test below decides
-                const int i0 = (int)ceilf((at.x - rc) * p.inv_dx) - 1;
-                const int wx = (int)floorf(2.0f * rc * p.inv_dx) + 3;
-                for (int row = 0; row < nrows; ++row) {
-                    float ddy = (float)(r0 + row) * p.dy - at.y;
-                    ddy -= p.ly * rintf(ddy * p.inv_ly);
-                    const float ddy2 = ddy * ddy;
-                    if (ddy2 > rc2) continue;
-                    for (int ii = lane; ii < wx; ii += 32) {
-                        const int i = i0 + ii;
-                        const float ddx = (float)i * p.dx - at.x;
-                        const float r2 = ddx * ddx + ddy2;
-                        if (r2 <= rc2) {
-                            const float c = aw * expf(-r2 * inv2s2);
-                            const long long f = __float2ll_rn(c * kFixScale);
-                            int iw = i % p.nx;
-                            if (iw < 0) iw += p.nx;
-                            atomicAdd(&acc[row * p.nx + iw], (unsigned long long)f);
-                        }
-                    }
-                }
+    const int n_nb = nb * (slab1 - slab0 + 1);
+    if (threadIdx.x < 32) {
+        int carry = 0;
+        for (int base = 0; base < n_nb; base += 32) {
+            const int i = base + lane;
+            int cnt = 0, start = 0;
+            if (i < n_nb) {
+                const int slab = slab0 + i / nb, k = i % nb;
+                int b = all_bands ? k : band - p.band_reach + k;
+                b = ((b % p.n_bands) + p.n_bands) % p.n_bands;
+                const int bin = slab * p.n_bands + b;
+                start = __ldg(off + bin);
+                cnt = __ldg(off + bin + 1) - start;
             }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (i < n_nb) {
+                sm.bin_start[i] = start;
+                sm.bin_cum[i] = carry + incl - cnt;
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) {
+            sm.bin_cum[n_nb] = carry;
+            sm.n_nb = n_nb;
         }
     }
     __syncthreads();
+    const int n_src = sm.bin_cum[sm.n_nb];
+
+    long long acc[CPL][kBandRows];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k)
+#pragma unroll
+        for (int r = 0; r < kBandRows; ++r) acc[k][r] = 0;
+    const int col0 = warp * seg_w;
+    const int col1 = min(col0 + seg_w, p.nx);
+
+    for (int c0 = 0; c0 < n_src; c0 += kChunk) {
+        if (threadIdx.x < kSegs) sm.seg_cnt[threadIdx.x] = 0;
+        if (threadIdx.x == 0) sm.n_cand = 0;
+        __syncthreads();
+        // 1. one source atom per thread; accepted atoms become candidates and are
+        //    listed in every column segment their window touches
+        const int src = c0 + threadIdx.x;
+        if (src < n_src) {
+            int bi = 0;
+            while (sm.bin_cum[bi + 1] <= src) ++bi;
+            const int ai = sm.bin_start[bi] + (src - sm.bin_cum[bi]);
+            const float4 at = atoms[ai];               // (fx, fy, z, species)
+            const int2 px = atoms_px[ai];              // (ic, jc)
+            const int sp = __float_as_int(at.w);
+            bool ok = sp >= 0 && sp < p.n_species;
+            const float sg = ok ? p.sigma[sp] : 1.f;
+            const float rc = 6.0f * sg;
+            ok = ok && (hi > at.z - rc) && (lo < at.z + rc);
+            const int ic = px.x, jc = px.y;
+            const float fx = at.x, fy = at.y;
+            int k0 = (r0 - jc) % p.ny;                  // wrapped pixel distance of the band's first row
+            if (k0 < 0) k0 += p.ny;
+            if (k0 >= (p.ny + 1) / 2) k0 -= p.ny;
+            const float d0 = (float)k0 * p.dy - fy;
+            ok = ok && (d0 <= rc) && (d0 + band_span >= -rc);
+            if (ok) {
+                const float kz = 0.70710678118654752f / sg;
+                const float fh = lastsl ? 0.5f : 0.5f * erff((hi - at.z) * kz);
+                const float fl = first ? -0.5f : 0.5f * erff((lo - at.z) * kz);
+                const int c = atomicAdd(&sm.n_cand, 1);
+                int icw = ic % p.nx, jcw = jc % p.ny;   // pixel indices wrapped into the box
+                if (icw < 0) icw += p.nx;
+                if (jcw < 0) jcw += p.ny;
+                sm.ic[c] = icw;
+                sm.jc[c] = jcw;
+                sm.fx[c] = fx;
+                sm.fy[c] = fy;
+                sm.aw[c] = p.amp[sp] * (fh - fl);
+                sm.inv2s2[c] = 0.5f / (sg * sg);
+                sm.rc2[c] = rc * rc;
+                // columns within the cut-off lie in [i0, i0 + wx) (one spare column each side)
+                const int reach = (int)ceilf(rc * p.inv_dx);
+                const int i0 = ic - reach - 1;
+                const int wx = 2 * reach + 3;
+                unsigned mask = 0;
+                if (wx >= p.nx) {
+                    mask = (1u << kSegs) - 1u;
+                } else {
+                    int a = i0 % p.nx;
+                    if (a < 0) a += p.nx;
+                    const int b = a + wx - 1;
+                    for (int col = a; col <= b; col += seg_w) mask |= 1u << ((col % p.nx) / seg_w);
+                    mask |= 1u << ((b % p.nx) / seg_w);
+                }
+                while (mask) {
+                    const int si = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int slot = atomicAdd(&sm.seg_cnt[si], 1);
+                    sm.seg_list[si][slot] = (unsigned short)c;
+                }
+            }
+        }
+        __syncthreads();
+        // 2. per candidate and band row: squared row distance and Gaussian row factor
+        const int nc = sm.n_cand;
+        for (int e = threadIdx.x; e < nc * kBandRows; e += blockDim.x) {
+            const int c = e / kBandRows, r = e % kBandRows;
+            int k = r0 + r - sm.jc[c];                  // in (-ny, ny): wrap to the nearest image
+            if (k >= (p.ny + 1) / 2) k -= p.ny;
+            if (k < -(p.ny / 2)) k += p.ny;
+            const float ddy = (float)k * p.dy - sm.fy[c];
+            const float d2 = ddy * ddy;
+            const bool in = r < nrows && d2 <= sm.rc2[c];
+            sm.dy2[c][r] = in ? d2 : INFINITY;
+            sm.gy[c][r] = in ? expf(-d2 * sm.inv2s2[c]) : 0.f;
+        }
+        __syncthreads();
+        // 3. the warp adds the candidates listed in its segment to its columns
+        const int cnt = sm.seg_cnt[warp];
+        for (int j = 0; j < cnt; ++j) {
+            const int c = sm.seg_list[warp][j];
+            const int ic = sm.ic[c];
+            const float fx = sm.fx[c], aw = sm.aw[c], inv2s2 = sm.inv2s2[c], rc2 = sm.rc2[c];
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int col = col0 + lane + 32 * k;
+                if (col >= col1) continue;
+                int kx = col - ic;                      // in (-nx, nx): wrap to the nearest image
+                if (kx >= (p.nx + 1) / 2) kx -= p.nx;
+                if (kx < -(p.nx / 2)) kx += p.nx;
+                const float ddx = (float)kx * p.dx - fx;
+                const float dx2 = ddx * ddx;
+                if (dx2 > rc2) continue;
+                const float gx = aw * expf(-dx2 * inv2s2);
+#pragma unroll
+                for (int r = 0; r < kBandRows; ++r)
+                    if (dx2 + sm.dy2[c][r] <= rc2) acc[k][r] += __float2int_rn(gx * sm.gy[c][r] * kFixScale);
+            }
+        }
+        __syncthreads();
+    }
+    // 4. write the band (lanes on consecutive columns)
     float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + r0) * p.nx;
-    for (int i = threadIdx.x; i < nrows * p.nx; i += blockDim.x)
-        out[i] = __ll2float_rn((long long)acc[i]) * kFixInv;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int col = col0 + lane + 32 * k;
+        if (col >= col1) continue;
+#pragma unroll
+        for (int r = 0; r < kBandRows; ++r)
+            if (r < nrows) {
+                // sums below 2048 V*A fit in 32 bits: convert those without the FP64 pipe
+                const long long a = acc[k][r];
+                const float f = (a == (long long)(int)a) ? (float)(int)a : (float)a;
+                out[(size_t)r * p.nx + col] = f * kFixInv;
+            }
+    }
 }
 
 struct PotWs {
     int* bin_off;
     float4* binned;
+    int2* binned_px;
 };
 
 PotWs carve_pot(Carver& cv, int n_t, int n_atoms, int n_bins) {
     PotWs w;
     w.bin_off = cv.take<int>((size_t)n_t * (n_bins + 1));
     w.binned = cv.take<float4>((size_t)n_t * n_atoms);
+    w.binned_px = cv.take<int2>((size_t)n_t * n_atoms);
     return w;
 }
 
@@ -196,8 +371,10 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
     float smax = 0.f;
     for (int i = 0; i < n_species; ++i) {
         TACAW_REQUIRE(amp_sigma[2 * i + 1] > 0.f && isfinite(amp_sigma[2 * i + 1]) &&
-                          isfinite(amp_sigma[2 * i]),
-                      TACAW_EINVAL, "tacaw_potential: species %d has a bad amplitude/width", i);
+                          fabsf(amp_sigma[2 * i]) <= kMaxAmp,
+                      TACAW_EINVAL,
+                      "tacaw_potential: species %d needs a width > 0 and |amplitude| <= %g V*A", i,
+                      (double)kMaxAmp);
         p->amp[i] = amp_sigma[2 * i];
         p->sigma[i] = amp_sigma[2 * i + 1];
         smax = fmaxf(smax, amp_sigma[2 * i + 1]);
@@ -214,13 +391,20 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
     p->n_bands = (g.ny + kBandRows - 1) / kBandRows;
     p->n_bins = g.n_slices * p->n_bands;
     const double dy = g.ly / g.ny;
-    p->band_reach = (int)ceil(rc / (kBandRows * dy));
-    p->slab_reach = (int)ceil(rc / g.dz);
+    // an atom in pixel row jc reaches rows jc - ceil(rc/dy) .. jc + 1 + ceil(rc/dy); the
+    // slab is assigned in float, so its reach gets a little slack
+    p->band_reach = (int)ceil((ceil(rc / dy) + 1.0) / kBandRows);
+    p->slab_reach = (int)ceil((rc + 1e-4 * g.dz) / g.dz);
     p->lx = (float)g.lx;
     p->ly = (float)g.ly;
     p->dx = (float)(g.lx / g.nx);
     p->dy = (float)dy;
     p->inv_dx = (float)(g.nx / g.lx);
+    p->inv_lx = (float)(1.0 / g.lx);
+    p->dx_d = g.lx / g.nx;
+    p->dy_d = g.ly / g.ny;
+    p->inv_dx_d = g.nx / g.lx;
+    p->inv_dy_d = g.ny / g.ly;
     p->inv_ly = (float)(1.0 / g.ly);
     p->z0 = (float)g.z0;
     p->dz = (float)g.dz;
@@ -247,19 +431,27 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
     const size_t bin_smem = (size_t)p.n_bins * sizeof(int);
     TACAW_REQUIRE(bin_smem <= 200 * 1024, TACAW_EUNSUPPORTED,
                   "tacaw_potential: %d bins exceed the shared-memory histogram", p.n_bins);
-    const size_t pot_smem = (size_t)kBandRows * g.nx * sizeof(unsigned long long);
-    TACAW_REQUIRE(pot_smem <= 200 * 1024, TACAW_EUNSUPPORTED,
-                  "tacaw_potential: nx = %d too large for the band accumulator", g.nx);
+    TACAW_REQUIRE(g.nx <= 4 * 32 * kSegs, TACAW_EUNSUPPORTED,
+                  "tacaw_potential: nx = %d above the supported %d", g.nx, 4 * 32 * kSegs);
+    const int nb = (2 * p.band_reach + 1 >= p.n_bands) ? p.n_bands : 2 * p.band_reach + 1;
+    const int n_nb = nb * (min(g.n_slices - 1, 2 * p.slab_reach) + 1);
+    TACAW_REQUIRE(n_nb <= kMaxNbBins, TACAW_EUNSUPPORTED,
+                  "tacaw_potential: %d neighbouring bins per tile exceed %d (widths too large for "
+                  "the slice thickness or pixel size)", n_nb, kMaxNbBins);
     Carver cv(ws);
     PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
     TACAW_CUDA_CHECK(cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)bin_smem));
-    TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pot_smem));
-    bin_kernel<<<n_t, kBinThreads, bin_smem, st>>>(pos, species, p, w.bin_off, w.binned);
+    bin_kernel<<<n_t, kBinThreads, bin_smem, st>>>(pos, species, p, w.bin_off, w.binned, w.binned_px);
     TACAW_LAUNCH_CHECK();
     dim3 grid(p.n_bands, g.n_slices, n_t);
-    potential_kernel<<<grid, kPotThreads, pot_smem, st>>>(w.bin_off, w.binned, p, V);
+    const int cpl = ((g.nx + kSegs - 1) / kSegs + 31) / 32;
+    if (cpl <= 1)
+        potential_kernel<1><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
+    else if (cpl == 2)
+        potential_kernel<2><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
+    else
+        potential_kernel<4><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
     TACAW_LAUNCH_CHECK();
     return TACAW_OK;
 }
