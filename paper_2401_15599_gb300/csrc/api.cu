@@ -42,7 +42,7 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
 int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes);
 int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
                   int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st);
-size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel);
+size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int precision);
 int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
                  size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
                  int flags, double temperature_K, void* ws, cudaStream_t st);
@@ -153,10 +153,13 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
                   fn);
     TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)),
                   TACAW_EINVAL, "%s: the Kubo factor needs a positive temperature", fn);
+    TACAW_REQUIRE(precision != TACAW_BF16X3 || n_omega <= 32640, TACAW_EUNSUPPORTED,
+                  "%s: the tensor-core path takes at most 32640 energies", fn);
     bool query = false;
     int rc = check_ws(ws, ws_bytes,
-                      spectrum_ws_bytes(nq, n_t, n_omega, psi_sum != nullptr, I_el != nullptr), fn,
-                      &query);
+                      spectrum_ws_bytes(nq, n_t, n_omega, psi_sum != nullptr, I_el != nullptr,
+                                        precision),
+                      fn, &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(psi && I, TACAW_EINVAL, "%s: NULL array", fn);
     return spectrum_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,

@@ -186,6 +186,16 @@ __global__ void scale_kernel(float* __restrict__ x, size_t n, double* __restrict
             i_el[i] *= inv;
 }
 
+// kubo[k] = beta E_k / (1 - exp(-beta E_k)), 1 at E = 0 (natural grid when omega is NULL).
+__global__ void kubo_kernel(float* __restrict__ kubo, const double* __restrict__ omega, int n_t, int n_w,
+                            double dt, double beta) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_w) return;
+    const double ek = omega ? omega[k] : (double)((long long)k - n_t / 2) * kPlanckMeVfs / ((double)n_t * dt);
+    const double be = beta * ek;
+    kubo[k] = (be == 0.0) ? 1.0f : (float)(be / (-expm1(-be)));
+}
+
 struct SpecWs {
     double2* sum;
     float2* a;
@@ -210,7 +220,41 @@ SpecWs carve_spec(Carver& cv, int nq, int n_t, int n_w, bool need_sum, bool need
 
 }  // namespace
 
-size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel) {
+int launch_time_sum(const float2* psi, size_t ld, double2* sum, int n_t, int nq, cudaStream_t st) {
+    time_sum_kernel<<<(nq + 255) / 256, 256, 0, st>>>(psi, ld, sum, n_t, nq);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+int launch_kubo(float* kubo, const double* omega, int n_t, int n_w, double dt, double beta,
+                cudaStream_t st) {
+    kubo_kernel<<<(n_w + 255) / 256, 256, 0, st>>>(kubo, omega, n_t, n_w, dt, beta);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+size_t normalize_ws_doubles() { return kRedBlocks + 1; }
+
+// Scale I and I_el so that sum I + sum I_el = 1 (deterministic FP64 sums).
+// i_el_user: caller's I_el (scaled too) or NULL; i_el: the values to add.
+int launch_normalize(float* out, size_t n, double* i_el_user, const double* i_el, int nq,
+                     double* partial, double* total, cudaStream_t st) {
+    partial_sum_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(out, n, partial);
+    TACAW_LAUNCH_CHECK();
+    total_kernel<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, i_el, nq, total);
+    TACAW_LAUNCH_CHECK();
+    scale_kernel<<<1024, 256, 0, st>>>(out, n, i_el_user, nq, total);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+size_t spectrum_tc_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel);
+int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
+                    size_t ld, const double2* psi_sum, float* out, double* i_el, int flags,
+                    double beta, void* ws, cudaStream_t st);
+
+size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int precision) {
+    if (precision == TACAW_BF16X3) return spectrum_tc_ws_bytes(nq, n_t, n_w, have_sum, have_iel);
     Carver cv(nullptr);
     carve_spec(cv, nq, n_t, n_w, !have_sum, !have_iel);
     return cv.bytes();
@@ -219,6 +263,10 @@ size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel)
 int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
                  size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
                  int flags, double temperature_K, void* ws, cudaStream_t st) {
+    if (precision == TACAW_BF16X3) {
+        const double beta = (flags & TACAW_KUBO) ? 1.0 / (kBoltzmannMeVK * temperature_K) : 0.0;
+        return spectrum_tc_run(nq, n_t, dt_fs, n_w, omega, psi, ld, psi_sum, out, i_el, flags, beta, ws, st);
+    }
     Carver cv(ws);
     SpecWs w = carve_spec(cv, nq, n_t, n_w, psi_sum == nullptr, i_el == nullptr);
     const double2* sum = psi_sum;
@@ -239,10 +287,6 @@ int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, co
         dim3 grid((n_w + 127) / 128, n_t);
         dft_table_kernel<<<grid, 128, 0, st>>>(w.e, kubo ? w.kubo : nullptr, omega, n_t, n_w, dt_fs, beta);
         TACAW_LAUNCH_CHECK();
-    }
-    if (precision != TACAW_FP32) {
-        set_error("tacaw_spectrum: precision %d is not available in this build", precision);
-        return TACAW_EUNSUPPORTED;
     }
     {
         dim3 grid((n_w + BN - 1) / BN, (nq + BM - 1) / BM);

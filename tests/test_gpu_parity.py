@@ -162,11 +162,12 @@ def _waves(rng, n_t, nq, inel=0.02):
             ).astype(np.complex64)
 
 
-@pytest.mark.parametrize("n_t,nq", [(256, 4096), (100, 1000), (37, 65), (1, 70)])
-def test_spectrum_natural_grid_matches_oracle(api, n_t, nq):
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("n_t,nq", [(256, 4096), (100, 1000), (37, 65), (1, 70), (512, 300)])
+def test_spectrum_natural_grid_matches_oracle(api, n_t, nq, precision):
     rng = np.random.default_rng(n_t + nq)
     psi = _waves(rng, n_t, nq)
-    inten, iel = api.spectrum(_dev(psi), 5.0)
+    inten, iel = api.spectrum(_dev(psi), 5.0, precision=precision)
     ref, ref_el, _ = O.spectrum(psi.astype(np.complex128), 5.0)
     assert inten.shape == (nq, n_t)
     if n_t == 1:
@@ -176,13 +177,14 @@ def test_spectrum_natural_grid_matches_oracle(api, n_t, nq):
     assert rel_l2(iel.cpu().numpy(), ref_el) < 1e-13
 
 
-def test_spectrum_explicit_grid_kubo_normalise(api):
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_spectrum_explicit_grid_kubo_normalise(api, precision):
     rng = np.random.default_rng(9)
     n_t, nq = 200, 777
     psi = _waves(rng, n_t, nq)
     omega = np.linspace(-200.0, 200.0, 1024, endpoint=False)
     inten, iel = api.spectrum(_dev(psi), 5.0, omega_meV=omega, kubo=True, temperature_K=300.0,
-                              normalize=True)
+                              normalize=True, precision=precision)
     ref, ref_el, _ = O.spectrum(psi.astype(np.complex128), 5.0, omega, kubo=True, temperature_K=300.0,
                                 normalize=True)
     assert rel_l2(inten.cpu().numpy(), ref) < SPEC_TOL
@@ -200,21 +202,23 @@ def test_spectrum_given_sum_equals_computed_sum(api):
 
 
 # ---------------------------------------------------------------- end to end
-def _e2e(api, w, snapshots=None, batch=64):
+def _e2e(api, w, snapshots=None, batch=64, precision="fp32"):
     from paper_2401_15599_gb300.pipeline import TimeToSpectrum
     inp = W.build_inputs(w)
     pos = inp.positions(snapshots)
     n_t = pos.shape[0]
-    tts = TimeToSpectrum(w.grid, n_t, pos.shape[1], inp.amp_sigma, w.dt_fs, batch=batch)
+    tts = TimeToSpectrum(w.grid, n_t, pos.shape[1], inp.amp_sigma, w.dt_fs, batch=batch,
+                         precision=precision)
     tts.prepare(None, None)
     inten, iel = tts.run(_dev(pos), _dev(inp.species))
     torch.cuda.synchronize()
     return inp, pos, tts, inten.cpu().numpy(), iel.cpu().numpy()
 
 
-def test_end_to_end_plain_small(api):
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_end_to_end_plain_small(api, precision):
     w = W.WORKLOADS["plain_small"]
-    inp, pos, tts, inten, iel = _e2e(api, w)
+    inp, pos, tts, inten, iel = _e2e(api, w, precision=precision)
     g = O.grid_from_spec(w.grid)
     psi = O.exit_waves(g, pos.astype(np.float64), inp.species, inp.amp_sigma.astype(np.float64))
     ref, ref_el, _ = O.spectrum(psi, w.dt_fs)
