@@ -33,6 +33,7 @@ METRIC = "multislice gridpt*slice*snapshot/s (time-to-spectrum)"
 UNIT = "gridpt*slice*snapshot/s"
 DESIGN_BYTES_PER_PT_SLICE = 36        # row pass 8+8+4, column pass 8+8
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS_SUSTAINED = 1700.0
 
 
 def parse_args():
@@ -43,6 +44,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="paper_scale")
     p.add_argument("--batch", type=int, default=32)
+    p.add_argument("--precision", choices=["bf16x3", "fp32"], default="bf16x3")
     p.add_argument("--snapshots", type=int, default=0, help="override T (testing only)")
     p.add_argument("--cpu-snapshots", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,7 +72,7 @@ def workload_config(w, extra=None):
                     f"{g.nx}x{g.ny} grid over {g.lx}x{g.ly} A, {g.n_slices} slices of {g.dz} A, "
                     f"{g.kev:g} keV plane wave, {w.n_t} snapshots at {w.dt_fs} fs, {w.n_modes} harmonic modes",
         "grid": [g.nx, g.ny], "slices": g.n_slices, "snapshots": w.n_t,
-        "spectrum": "natural energy grid (n_omega = T), FP32 temporal transform",
+        "spectrum": "natural energy grid (n_omega = T)",
         "l2": "inputs larger than L2 (positions 3.9 GB, exit waves 8.6 GB per step)",
     }
     if extra:
@@ -179,13 +181,14 @@ class ClockSampler:
 
 
 def load_peaks():
+    """(HBM GB/s, sustained BF16 dense TFLOP/s, 'measured' | 'fallback')."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d["bf16_tflops_sustained"]), "measured"
     except (OSError, KeyError, ValueError):
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS_SUSTAINED, "fallback"
 
 
 def kernel_source_hash():
@@ -238,29 +241,37 @@ def run_ours(args):
     species = torch.from_numpy(inp.species).to(dev)
     pos = pos_host.to(dev, non_blocking=True)
     n_t, n_atoms = pos.shape[0], pos.shape[1]
-    tts = TimeToSpectrum(g, n_t, n_atoms, inp.amp_sigma, w.dt_fs, batch=args.batch, device=dev)
+    tts = TimeToSpectrum(g, n_t, n_atoms, inp.amp_sigma, w.dt_fs, batch=args.batch, device=dev,
+                         precision=args.precision)
     tts.prepare(None, None)
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream(dev)
-    ms_events = []
+    events = {"potential": [], "multislice": [], "spectrum": []}
+    from paper_2401_15599_gb300 import api
 
-    def step(record):
+    def timed(name, record, fn):
+        if not record:
+            return fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        events[name].append((e0, e1))
+        return out
+
+    def step(record, precision=args.precision):
         tts.psi_sum.zero_()
         for t0 in range(0, n_t, tts.batch):
             t1 = min(n_t, t0 + tts.batch)
             v = tts.V[: t1 - t0]
-            from paper_2401_15599_gb300 import api
-            api.potential(g, pos[t0:t1], species, inp.amp_sigma, out=v, workspace=tts._ws.get("pot"))
-            if record:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            api.multislice(g, v, out=tts.psi[t0:t1], psi_sum=tts.psi_sum, workspace=tts._ws.get("ms"))
-            if record:
-                e1 = torch.cuda.Event(enable_timing=True)
-                e1.record(stream)
-                ms_events.append((e0, e1))
-        return tts.spectrum()
+            timed("potential", record, lambda: api.potential(
+                g, pos[t0:t1], species, inp.amp_sigma, out=v, workspace=tts._ws.get("pot")))
+            timed("multislice", record, lambda: api.multislice(
+                g, v, out=tts.psi[t0:t1], psi_sum=tts.psi_sum, workspace=tts._ws.get("ms")))
+        tts.precision = precision
+        return timed("spectrum", record, tts.spectrum)
 
     for _ in range(args.warmup):
         step(False)
@@ -290,19 +301,47 @@ def run_ours(args):
     units_step = g.nx * g.ny * g.n_slices * n_t
     value = units_step * world / (ms_step * 1e-3)
 
+    def stage_ms(name):
+        return [a.elapsed_time(b) for a, b in events[name]]
+
     # dominant kernel: the multislice slice step (row + column pass), timed per call
-    ms_call = [a.elapsed_time(b) for a, b in ms_events]
+    ms_call = stage_ms("multislice")
     units_call = g.nx * g.ny * g.n_slices * tts.batch
-    full_calls = [m for m in ms_call]
-    avg_call_ms = statistics.mean(full_calls)
+    avg_call_ms = statistics.mean(ms_call)
     achieved = DESIGN_BYTES_PER_PT_SLICE * units_call / (avg_call_ms * 1e-3) / 1e9
-    peak, peak_kind = load_peaks()
+    peak, peak_tf, peak_kind = load_peaks()
     traffic = profiled_traffic(units_call)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "multislice slice step (row pass + column pass kernels, all slices of one "
                           f"{tts.batch}-snapshot batch per call)",
-                "bytes_per_unit": DESIGN_BYTES_PER_PT_SLICE, "peak_kind": f"{peak_kind} (hbm_gbs)"}
+                "bytes_per_unit": DESIGN_BYTES_PER_PT_SLICE, "peak_kind": f"{peak_kind} hbm_gbs"}
+    spec_ms = statistics.mean(stage_ms("spectrum"))
+    nq = g.nx * g.ny
+    complex_flop = 8.0 * nq * n_t * n_t                 # 8 real flop per q, snapshot, energy
+    roofline_spectrum = None
+    if args.precision == "bf16x3":
+        tf = 3 * complex_flop / (spec_ms * 1e-3) / 1e12   # three BF16 products per complex flop
+        roofline_spectrum = {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                             "frac": tf / peak_tf, "traffic": None,
+                             "kernel": "tacaw_spectrum BF16X3 (split, centre, tcgen05 GEMM + |Phi|^2 epilogue)",
+                             "flop_per_unit": "3 x 8 real flop per q x snapshot x energy",
+                             "peak_kind": f"{peak_kind} bf16_tflops_sustained"}
+    stages = {k: sum(stage_ms(k)) / args.steps for k in events}
+
+    # the plain FP32 form of the spectrum on the same exit waves, for comparison
+    fp32_ms = None
+    if args.precision != "fp32":
+        events["spectrum"].clear()
+        for _ in range(2):
+            tts.precision = "fp32"
+            timed("spectrum", False, tts.spectrum)
+        for _ in range(args.steps):
+            tts.precision = "fp32"
+            timed("spectrum", True, tts.spectrum)
+        torch.cuda.synchronize()
+        fp32_ms = statistics.mean(stage_ms("spectrum"))
+        tts.precision = args.precision
 
     # end to end: host positions in, host spectrum out, through the same C-ABI calls
     e2e = None
@@ -332,17 +371,22 @@ def run_ours(args):
                "d2h_bytes_per_step": int(i_host.numel() * 4 + el_host.numel() * 8)}
 
     n_batches = (n_t + tts.batch - 1) // tts.batch
-    launches = n_batches * (2 + 1 + 2 * g.n_slices + 1) + 3
+    spec_launches = 3 if args.precision == "bf16x3" else 3   # split A, split B, GEMM | centre, table, GEMM
+    launches = n_batches * (2 + 1 + 2 * g.n_slices + 1) + spec_launches
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(w, {"batch": tts.batch,
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+bf16x3",
+            "data": "synthetic",
+            "config": workload_config(w, {"batch": tts.batch, "spectrum_precision": args.precision,
                                           "parallelism": "replicas" if world > 1 else "single GPU"}),
             "time_to_spectrum_ms": ms_step,
-            "stage_ms": {"multislice": sum(ms_call) / args.steps},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "stage_ms": stages,
+            "plain_fp32_spectrum_ms": fp32_ms,
+            "time_to_spectrum_plain_fp32_ms": (ms_step - stages["spectrum"] + fp32_ms) if fp32_ms else None,
+            "roofline": roofline, "roofline_spectrum": roofline_spectrum,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line))

@@ -84,11 +84,13 @@ class TimeToSpectrum:
                                                          null, ctypes.byref(n), null))
         self._workspace("ms", n.value)
         n_w = self.n_t if self.omega is None else self.omega.numel()
-        prec = {"fp32": L.TACAW_FP32, "bf16x3": L.TACAW_BF16X3}[self.precision]
-        L.check("tacaw_spectrum", lib.tacaw_spectrum(self.grid.nx * self.grid.ny, self.n_t, self.dt_fs, n_w,
-                                                     null, null, ctypes.c_void_p(1), null, ctypes.c_void_p(1),
-                                                     prec, 0, 300.0, null, ctypes.byref(n), null))
-        self._workspace("spec", n.value)
+        need = 0
+        for prec in (L.TACAW_FP32, L.TACAW_BF16X3):     # one workspace serves both precisions
+            L.check("tacaw_spectrum", lib.tacaw_spectrum(self.grid.nx * self.grid.ny, self.n_t, self.dt_fs, n_w,
+                                                         null, null, ctypes.c_void_p(1), null, ctypes.c_void_p(1),
+                                                         prec, 0, 300.0, null, ctypes.byref(n), null))
+            need = max(need, n.value)
+        self._workspace("spec", need)
 
     def run(self, pos, species):
         self.exit_waves(pos, species)
