@@ -196,12 +196,49 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
  * the PyTorch convention for complex inputs (dL/dRe + i dL/dIm):
  *   g_Phi = (2 / T^2) dL/dI * Phi,   g_A(q, n) = sum_k g_Phi(q, k) exp(+i E_k t_n / hbar),
  *   g_psi(q, n) = g_A(q, n) - (1/T) sum_n' g_A(q, n')   (centring is self-adjoint).
- * dL_dpsi out [T][nq] float2.  Other arguments as in tacaw_spectrum.
+ * dL_dpsi out [T][nq] float2 (FP32 SIMT).  Other arguments as in tacaw_spectrum.
  */
 int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
                             const double* omega_meV, const void* psi, const void* psi_sum,
                             const float* dL_dI, void* dL_dpsi,
                             void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Adjoint of tacaw_multislice for gradient-based fitting (PyTorch convention
+ * for complex quantities: g = dL/dRe + i dL/dIm).  Given the gradient with
+ * respect to the exit waves, reverses every slice step of the forward:
+ *   g_X = conj(P BL) g_Y,  g_chi = F2^H g_X / (nx ny),
+ *   dL/dv_s = sigma_e Im(g_chi conj(chi)),  g_psi = exp(-i sigma_e v_s) g_chi,
+ *   g_Y(previous slice) = F2 g_psi.
+ * The forward waves are recomputed from checkpoints stored every
+ * `ckpt_every` slices (<= 0: ceil(sqrt(n_slices))), so the workspace holds
+ * about (n_slices / ckpt_every + ckpt_every + 2) wave sets of [T][ny][nx].
+ *
+ * V          [T][n_slices][ny][nx] float, the forward's slice potentials
+ * psi_in     [ny][nx] float2 incident wave of the forward, or NULL (plane wave)
+ * dL_dpsi_q  [T][ny][nx] float2 gradient with respect to the exit waves
+ * dL_dV      out [T][n_slices][ny][nx] float
+ */
+int tacaw_multislice_backward(const tacaw_grid* grid, int32_t n_t, const float* V,
+                              const void* psi_in, const void* dL_dpsi_q, float* dL_dV,
+                              int32_t ckpt_every, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Adjoint of tacaw_potential for the per-species Gaussian parameters: with
+ * P = exp(-rho^2 / 2 s^2) inside the 6 s cut-off and g = dL/dv_s,
+ *   dL/d amp = sum g P w_s,   dL/d s = sum g amp P (rho^2 / s^3 w_s + dw_s/ds)
+ * summed over pixels, slices, atoms of the species and the T snapshots (the
+ * cut-offs are held fixed).  Block totals are kept in FP64; the result is
+ * reproducible up to the FP64 rounding of the order in which candidate
+ * atoms are added.
+ *
+ * pos, species, amp_sigma as in tacaw_potential; dL_dV [T][n_slices][ny][nx];
+ * dL_damp_sigma out DEVICE [n_species][2] double (d amp, d s), overwritten.
+ */
+int tacaw_potential_backward(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
+                             const float* pos, const int32_t* species, int32_t n_species,
+                             const float* amp_sigma, const float* dL_dV, double* dL_damp_sigma,
+                             void* ws, size_t* ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -65,6 +65,11 @@ SIGNATURES = {
                                       _P, _SZ, _P]),
     "tacaw_spectrum_backward": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                ctypes.c_int32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "tacaw_multislice_backward": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,
+                                                 ctypes.c_int32, _P, _SZ, _P]),
+    "tacaw_potential_backward": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                                ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _P, _P, _P, _SZ,
+                                                _P]),
 }
 
 _lib = None

@@ -144,3 +144,76 @@ def spectrum(psi, dt_fs, omega_meV=None, psi_sum=None, precision="fp32", kubo=Fa
     nbytes = ctypes.c_size_t(workspace.numel())
     L.check("tacaw_spectrum", call(_ptr(workspace), ctypes.byref(nbytes)))
     return out, i_el
+
+
+def _call_with_workspace(fn_name, call, device, workspace=None):
+    nbytes = ctypes.c_size_t(0)
+    L.check(fn_name, call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=device)
+    nbytes = ctypes.c_size_t(workspace.numel())
+    L.check(fn_name, call(_ptr(workspace), ctypes.byref(nbytes)))
+
+
+def spectrum_backward(psi, dt_fs, dl_di, omega_meV=None, psi_sum=None, out=None, workspace=None):
+    """dL/dpsi [T, nq] (complex64) given dL/dI [nq, n_omega] (float32), FP32."""
+    lib = L.load()
+    if psi.dim() > 2:
+        psi = psi.reshape(psi.shape[0], -1)
+    _need_cuda("psi", psi, torch.complex64, 2)
+    _need_cuda("dl_di", dl_di, torch.float32, 2)
+    n_t, nq = psi.shape
+    dev = psi.device
+    if omega_meV is not None:
+        omega_meV = torch.as_tensor(omega_meV, dtype=torch.float64).to(dev).contiguous()
+    n_w = n_t if omega_meV is None else omega_meV.numel()
+    if tuple(dl_di.shape) != (nq, n_w):
+        raise ValueError("dl_di must be [nq, n_omega]")
+    if out is None:
+        out = torch.empty((n_t, nq), dtype=torch.complex64, device=dev)
+    _need_cuda("out", out, torch.complex64)
+
+    def call(ws, nbytes):
+        return lib.tacaw_spectrum_backward(nq, n_t, float(dt_fs), n_w, _ptr(omega_meV), _ptr(psi), _ptr(psi_sum),
+                                           _ptr(dl_di), _ptr(out), ws, nbytes, _stream(dev))
+    _call_with_workspace("tacaw_spectrum_backward", call, dev, workspace)
+    return out
+
+
+def multislice_backward(grid, V, dl_dpsi_q, psi_in=None, ckpt_every=0, out=None, workspace=None):
+    """dL/dV [T, n_slices, ny, nx] (float32) given dL/d(exit waves) [T, ny, nx] (complex64)."""
+    lib = L.load()
+    _need_cuda("V", V, torch.float32, 4)
+    _need_cuda("dl_dpsi_q", dl_dpsi_q, torch.complex64, 3)
+    n_t = V.shape[0]
+    if out is None:
+        out = torch.empty_like(V)
+    _need_cuda("out", out, torch.float32, 4)
+    g = L.make_grid(grid)
+
+    def call(ws, nbytes):
+        return lib.tacaw_multislice_backward(ctypes.byref(g), n_t, _ptr(V), _ptr(psi_in), _ptr(dl_dpsi_q),
+                                             _ptr(out), int(ckpt_every), ws, nbytes, _stream(V.device))
+    _call_with_workspace("tacaw_multislice_backward", call, V.device, workspace)
+    return out
+
+
+def potential_backward(grid, pos, species, amp_sigma, dl_dv, out=None, workspace=None):
+    """dL/d(amp, sigma) [n_species, 2] (float64, device) given dL/dV [T, n_slices, ny, nx]."""
+    lib = L.load()
+    _need_cuda("pos", pos, torch.float32, 3)
+    _need_cuda("species", species, torch.int32, 1)
+    _need_cuda("dl_dv", dl_dv, torch.float32, 4)
+    n_t, n_atoms = pos.shape[0], pos.shape[1]
+    amp = torch.as_tensor(amp_sigma, dtype=torch.float32).detach().reshape(-1, 2).contiguous().cpu()
+    n_species = amp.shape[0]
+    amp_c = (ctypes.c_float * (2 * n_species))(*amp.flatten().tolist())
+    if out is None:
+        out = torch.empty((n_species, 2), dtype=torch.float64, device=pos.device)
+    g = L.make_grid(grid)
+
+    def call(ws, nbytes):
+        return lib.tacaw_potential_backward(ctypes.byref(g), n_t, n_atoms, _ptr(pos), _ptr(species), n_species,
+                                            amp_c, _ptr(dl_dv), _ptr(out), ws, nbytes, _stream(pos.device))
+    _call_with_workspace("tacaw_potential_backward", call, pos.device, workspace)
+    return out

@@ -43,6 +43,17 @@ int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes)
 int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
                   int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st);
 size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int precision);
+size_t spectrum_backward_ws_bytes(int nq, int n_t, int n_w, bool have_sum);
+int spectrum_backward_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
+                          size_t ld, const double2* psi_sum, const float* dldi, float2* gpsi, void* ws,
+                          cudaStream_t st);
+size_t multislice_backward_ws_bytes(const tacaw_grid& g, int n_t, int every);
+int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
+                            const float2* g_exit, float* dV, int every, void* ws, cudaStream_t st);
+int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n_species, size_t* bytes);
+int potential_backward_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos,
+                           const int* species, int n_species, const float* amp_sigma, const float* dV,
+                           double* grad, void* ws, cudaStream_t st);
 int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
                  size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
                  int flags, double temperature_K, void* ws, cudaStream_t st);
@@ -172,10 +183,65 @@ int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_ome
                             const float* dL_dI, void* dL_dpsi, void* ws, size_t* ws_bytes,
                             void* stream) {
     clear_error();
-    set_error("tacaw_spectrum_backward: not available in this build");
-    (void)nq; (void)n_t; (void)dt_fs; (void)n_omega; (void)omega_meV; (void)psi; (void)psi_sum;
-    (void)dL_dI; (void)dL_dpsi; (void)ws; (void)ws_bytes; (void)stream;
-    return TACAW_EUNSUPPORTED;
+    const char* fn = "tacaw_spectrum_backward";
+    TACAW_REQUIRE(nq > 0 && n_t > 0 && n_t <= 65535 && n_omega > 0, TACAW_EINVAL,
+                  "%s: nq, n_omega must be positive and n_t in [1, 65535]", fn);
+    TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
+    TACAW_REQUIRE(omega_meV != nullptr || n_omega == n_t, TACAW_EINVAL,
+                  "%s: the natural grid (omega NULL) has n_omega == T", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, spectrum_backward_ws_bytes(nq, n_t, n_omega, psi_sum != nullptr), fn,
+                      &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(psi && dL_dI && dL_dpsi, TACAW_EINVAL, "%s: NULL array", fn);
+    return spectrum_backward_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
+                                 (const double2*)psi_sum, dL_dI, (float2*)dL_dpsi, ws, (cudaStream_t)stream);
+}
+
+int tacaw_multislice_backward(const tacaw_grid* grid, int32_t n_t, const float* V, const void* psi_in,
+                              const void* dL_dpsi_q, float* dL_dV, int32_t ckpt_every, void* ws,
+                              size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_multislice_backward";
+    int rc = check_grid(grid, fn);
+    if (rc) return rc;
+    TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny),
+                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 512, 1024}", fn,
+                  grid->nx, grid->ny);
+    TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
+    int every = ckpt_every;
+    if (every <= 0) every = (int)ceil(sqrt((double)grid->n_slices));
+    if (every > grid->n_slices) every = grid->n_slices;
+    bool query = false;
+    rc = check_ws(ws, ws_bytes, multislice_backward_ws_bytes(*grid, n_t, every), fn, &query);
+    if (rc || query) return rc;
+    if (n_t == 0) return TACAW_OK;
+    TACAW_REQUIRE(V && dL_dpsi_q && dL_dV, TACAW_EINVAL, "%s: NULL array", fn);
+    return multislice_backward_run(*grid, n_t, V, (const float2*)psi_in, (const float2*)dL_dpsi_q, dL_dV,
+                                   every, ws, (cudaStream_t)stream);
+}
+
+int tacaw_potential_backward(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms, const float* pos,
+                             const int32_t* species, int32_t n_species, const float* amp_sigma,
+                             const float* dL_dV, double* dL_damp_sigma, void* ws, size_t* ws_bytes,
+                             void* stream) {
+    clear_error();
+    const char* fn = "tacaw_potential_backward";
+    int rc = check_grid(grid, fn);
+    if (rc) return rc;
+    TACAW_REQUIRE(n_t >= 1 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [1, 65535]", fn);
+    TACAW_REQUIRE(n_atoms >= 0, TACAW_EINVAL, "%s: n_atoms must be >= 0", fn);
+    TACAW_REQUIRE(n_species >= 1 && n_species <= TACAW_MAX_SPECIES && amp_sigma, TACAW_EINVAL,
+                  "%s: need 1..%d species with amp_sigma", fn, TACAW_MAX_SPECIES);
+    size_t need = 0;
+    potential_backward_ws_bytes(*grid, n_t, n_atoms, n_species, &need);
+    bool query = false;
+    rc = check_ws(ws, ws_bytes, need, fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(dL_dV && dL_damp_sigma && (n_atoms == 0 || (pos && species)), TACAW_EINVAL,
+                  "%s: NULL array", fn);
+    return potential_backward_run(*grid, n_t, n_atoms, pos, species, n_species, amp_sigma, dL_dV,
+                                  dL_damp_sigma, ws, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -135,7 +135,10 @@ template <int NY>
 struct ColCfg { static constexpr int W = (NY >= 512) ? 8 : 16; };
 
 // Column pass: W adjacent columns of one snapshot per block.
-template <int NY>
+//   forward  (CONJ = false, FFT_IN = true):  Fy -> x P BL / (nx ny) -> Fy^-1 (unless `last`)
+//   adjoint  (CONJ = true):  [Fy] -> x conj(P BL) / (nx ny) -> Fy^-1, where the leading
+//   Fy is skipped (FFT_IN = false) when the input is already in q-space.
+template <int NY, bool CONJ, bool FFT_IN>
 __global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
 col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
                 const float2* __restrict__ px, const float2* __restrict__ py,
@@ -160,7 +163,7 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = col[(size_t)(t + TPT * m) * nx];
-    transform<NY, false>(v, b0, b1, t, tw, lay);
+    if (FFT_IN) transform<NY, false>(v, b0, b1, t, tw, lay);
 
     const float2 pxv = __ldg(px + kx);
     const int kmax = __ldg(kymax + kx);
@@ -168,11 +171,73 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     for (int m = 0; m < E; ++m) {
         const int ky = t + TPT * m;
         const int aky = ky < NY / 2 ? ky : NY - ky;
-        v[m] = (aky <= kmax) ? cmul(cmul(v[m], pxv), __ldg(py + ky)) : make_float2(0.f, 0.f);
+        const float2 p = cmul(pxv, __ldg(py + ky));
+        v[m] = (aky <= kmax) ? (CONJ ? cmulc(v[m], p) : cmul(v[m], p)) : make_float2(0.f, 0.f);
     }
     if (!last) transform<NY, true>(v, b0, b1, t, tw, lay);
 #pragma unroll
     for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
+}
+
+// Adjoint row pass of slice s.  g holds the gradient (k_x, y) rows after the
+// adjoint column pass; `state` the forward wave entering slice s in the same
+// hybrid form (mode 0), or the incident wave is the unit plane wave (mode 1)
+// / psi_in (mode 2).  With chi = t psi, t = exp(i sigma v):
+//   g_chi = Fx^-1 g,  dL/dv = sigma Im(g_chi conj(chi)),  g_psi = conj(t) g_chi,
+// and g_psi is transformed back with Fx (unless fft_out == 0: slice 0, real space).
+template <int NX>
+__global__ void __launch_bounds__(kRowThreads)
+row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const float* __restrict__ V,
+                float* __restrict__ dV, const float2* __restrict__ psi_in,
+                const float2* __restrict__ twx, int ny, int n_slices, int s, float sigma, int mode,
+                int fft_out) {
+    using namespace fft;
+    constexpr int E = Plan<NX>::E;
+    constexpr int TPT = NX / E;
+    constexpr int ROWS = kRowThreads / TPT;
+    extern __shared__ float2 smem[];
+    float2* b0 = smem;
+    float2* b1 = smem + ROWS * NX;
+    float2* tw = smem + 2 * ROWS * NX;
+    stage_twiddles<NX>(tw, twx);
+
+    const int t = threadIdx.x % TPT;
+    const int row = threadIdx.x / TPT;
+    const int y = blockIdx.x * ROWS + row;
+    const size_t snap = blockIdx.y;
+    float2* grow = g + (snap * ny + y) * NX;
+    const size_t vrow_off = ((snap * n_slices + s) * ny + y) * NX;
+    const RowLayout lay{row * NX};
+
+    float2 gv[E], sv[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) gv[m] = grow[t + TPT * m];
+    transform<NX, true>(gv, b0, b1, t, tw, lay);
+    if (mode == 0) {
+        const float2* srow = state + (snap * ny + y) * NX;
+#pragma unroll
+        for (int m = 0; m < E; ++m) sv[m] = srow[t + TPT * m];
+        transform<NX, true>(sv, b0, b1, t, tw, lay);
+    } else if (mode == 1) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) sv[m] = make_float2(1.f, 0.f);
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) sv[m] = psi_in[(size_t)y * NX + t + TPT * m];
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float sn, cs;
+        sincosf(sigma * __ldg(V + vrow_off + t + TPT * m), &sn, &cs);
+        const float2 tt = make_float2(cs, sn);
+        const float2 chi = cmul(tt, sv[m]);
+        const float2 gc = cmulc(gv[m], chi);            // g_chi conj(chi)
+        dV[vrow_off + t + TPT * m] = sigma * gc.y;
+        gv[m] = cmulc(gv[m], tt);                       // conj(t) g_chi
+    }
+    if (fft_out) transform<NX, false>(gv, b0, b1, t, tw, lay);
+#pragma unroll
+    for (int m = 0; m < E; ++m) grow[t + TPT * m] = gv[m];
 }
 
 // psi_sum[q] += sum_t psi[t][q], FP64, snapshots added in order.
@@ -207,17 +272,42 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
     return cudaGetLastError();
 }
 
-template <int NY>
-cudaError_t launch_col(float2* psi, const float2* twy, const float2* px, const float2* py,
-                       const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
+template <int NY, bool CONJ, bool FFT_IN>
+cudaError_t launch_col_t(float2* psi, const float2* twy, const float2* px, const float2* py,
+                         const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
     constexpr int TPT = NY / fft::Plan<NY>::E;
     constexpr int W = ColCfg<NY>::W;
     const size_t smem = (2 * W * NY + fft::TwSize<NY>::value) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY>,
+    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY, CONJ, FFT_IN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(nx / W, n_t);
-    col_pass_kernel<NY><<<grid, W * TPT, smem, st>>>(psi, twy, px, py, kymax, nx, last);
+    col_pass_kernel<NY, CONJ, FFT_IN><<<grid, W * TPT, smem, st>>>(psi, twy, px, py, kymax, nx, last);
+    return cudaGetLastError();
+}
+
+// dir 0: forward; 1: adjoint with a leading Fy; 2: adjoint of q-space input (no leading Fy)
+template <int NY>
+cudaError_t launch_col(float2* psi, const float2* twy, const float2* px, const float2* py,
+                       const int* kymax, int nx, int n_t, int last, cudaStream_t st, int dir = 0) {
+    if (dir == 0) return launch_col_t<NY, false, true>(psi, twy, px, py, kymax, nx, n_t, last, st);
+    if (dir == 1) return launch_col_t<NY, true, true>(psi, twy, px, py, kymax, nx, n_t, last, st);
+    return launch_col_t<NY, true, false>(psi, twy, px, py, kymax, nx, n_t, last, st);
+}
+
+template <int NX>
+cudaError_t launch_row_back(float2* g, const float2* state, const float* V, float* dV,
+                            const float2* psi_in, const float2* twx, int ny, int n_t, int n_slices,
+                            int s, float sigma, int mode, int fft_out, cudaStream_t st) {
+    constexpr int TPT = NX / fft::Plan<NX>::E;
+    constexpr int ROWS = kRowThreads / TPT;
+    const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(row_back_kernel<NX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ny / ROWS, n_t);
+    row_back_kernel<NX><<<grid, kRowThreads, smem, st>>>(g, state, V, dV, psi_in, twx, ny, n_slices, s,
+                                                          sigma, mode, fft_out);
     return cudaGetLastError();
 }
 
@@ -234,13 +324,26 @@ cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_
 }
 
 cudaError_t dispatch_col(int ny, float2* psi, const float2* twy, const float2* px, const float2* py,
-                         const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
+                         const int* kymax, int nx, int n_t, int last, cudaStream_t st, int dir = 0) {
     switch (ny) {
-        case 64: return launch_col<64>(psi, twy, px, py, kymax, nx, n_t, last, st);
-        case 128: return launch_col<128>(psi, twy, px, py, kymax, nx, n_t, last, st);
-        case 256: return launch_col<256>(psi, twy, px, py, kymax, nx, n_t, last, st);
-        case 512: return launch_col<512>(psi, twy, px, py, kymax, nx, n_t, last, st);
-        case 1024: return launch_col<1024>(psi, twy, px, py, kymax, nx, n_t, last, st);
+        case 64: return launch_col<64>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 128: return launch_col<128>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 256: return launch_col<256>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 512: return launch_col<512>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 1024: return launch_col<1024>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_row_back(int nx, float2* g, const float2* state, const float* V, float* dV,
+                              const float2* psi_in, const float2* twx, int ny, int n_t, int n_slices,
+                              int s, float sigma, int mode, int fft_out, cudaStream_t st) {
+    switch (nx) {
+        case 64: return launch_row_back<64>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
+        case 128: return launch_row_back<128>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
+        case 256: return launch_row_back<256>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
+        case 512: return launch_row_back<512>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
+        case 1024: return launch_row_back<1024>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -296,6 +399,99 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
         const size_t nq = (size_t)g.nx * g.ny;
         snapshot_sum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(psi_q, psi_sum, n_t, nq);
         TACAW_LAUNCH_CHECK();
+    }
+    return TACAW_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+// Workspace of the adjoint: the set-up tables, a working wave set W (forward
+// recompute), the gradient wave set G, n_ck checkpoints and `every` segment
+// states, each [T][ny][nx] complex64.
+struct MsBackWs {
+    MsTables tb;
+    float2 *w, *g, *ck, *seg;
+};
+
+static MsBackWs carve_ms_back(Carver& cv, const tacaw_grid& g, int n_t, int every) {
+    MsBackWs b;
+    b.tb = carve_ms(cv, g);
+    const size_t wave = (size_t)n_t * g.nx * g.ny;
+    const int n_ck = (g.n_slices + every - 1) / every;
+    b.w = cv.take<float2>(wave);
+    b.g = cv.take<float2>(wave);
+    b.ck = cv.take<float2>(wave * n_ck);
+    b.seg = cv.take<float2>(wave * every);
+    return b;
+}
+
+size_t multislice_backward_ws_bytes(const tacaw_grid& g, int n_t, int every) {
+    Carver cv(nullptr);
+    carve_ms_back(cv, g, n_t, every);
+    return cv.bytes();
+}
+
+// dL/dV [T][n_slices][ny][nx] from dL/d(exit wave) [T][ny][nx] with checkpoints
+// every `every` slices: forward to the checkpoints, then for each segment (last
+// first) recompute its states and run the adjoint slice steps in reverse.
+int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
+                            const float2* g_exit, float* dV, int every, void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    MsBackWs b = carve_ms_back(cv, g, n_t, every);
+    const MsTables& tb = b.tb;
+    double lam = 0.0, sig = 0.0;
+    beam_constants(g.kev, &lam, &sig);
+    const double qmax = g.bandlimit * fmin((double)g.nx / (2.0 * g.lx), (double)g.ny / (2.0 * g.ly));
+    const int nmax = g.nx > g.ny ? g.nx : g.ny;
+    ms_setup_kernel<<<(nmax + 127) / 128, 128, 0, st>>>(tb.twx, tb.twy, tb.px, tb.py, tb.kymax,
+                                                       g.nx, g.ny, g.lx, g.ly, lam * g.dz, qmax * qmax);
+    TACAW_LAUNCH_CHECK();
+    const float sigma = (float)sig;
+    const size_t wave = (size_t)n_t * g.nx * g.ny;
+    const size_t wave_bytes = wave * sizeof(float2);
+    const int first_mode = psi_in ? 2 : 1;
+    const int n_ck = (g.n_slices + every - 1) / every;
+
+    // forward to the checkpoints: ck[c] = state entering slice c * every (c >= 1)
+    for (int s = 0; s + 1 < (n_ck - 1) * every + 1 && s < g.n_slices; ++s) {
+        if (s > 0 && s % every == 0)
+            TACAW_CUDA_CHECK(cudaMemcpyAsync(b.ck + (size_t)(s / every) * wave, b.w, wave_bytes,
+                                             cudaMemcpyDeviceToDevice, st));
+        TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, g.ny, n_t, g.n_slices, s, sigma,
+                                      s > 0 ? 0 : first_mode, st));
+        TACAW_CUDA_CHECK(dispatch_col(g.ny, b.w, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st));
+    }
+    if (n_ck > 1 && (n_ck - 1) * every < g.n_slices)
+        TACAW_CUDA_CHECK(cudaMemcpyAsync(b.ck + (size_t)(n_ck - 1) * wave, b.w, wave_bytes,
+                                         cudaMemcpyDeviceToDevice, st));
+
+    TACAW_CUDA_CHECK(cudaMemcpyAsync(b.g, g_exit, wave_bytes, cudaMemcpyDeviceToDevice, st));
+    bool first = true;
+    for (int c = n_ck - 1; c >= 0; --c) {
+        const int s0 = c * every, s1 = min(s0 + every, g.n_slices);
+        // recompute the states entering slices s0 .. s1-1 (seg[j] for slice s0 + j, j >= 1;
+        // slice s0 reads its checkpoint, slice 0 the incident wave)
+        if (s1 - s0 > 1) {
+            if (c > 0)
+                TACAW_CUDA_CHECK(cudaMemcpyAsync(b.w, b.ck + (size_t)c * wave, wave_bytes,
+                                                 cudaMemcpyDeviceToDevice, st));
+            for (int s = s0; s + 1 < s1; ++s) {
+                TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, g.ny, n_t, g.n_slices, s,
+                                              sigma, s > 0 ? 0 : first_mode, st));
+                TACAW_CUDA_CHECK(dispatch_col(g.ny, b.w, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st));
+                TACAW_CUDA_CHECK(cudaMemcpyAsync(b.seg + (size_t)(s + 1 - s0) * wave, b.w, wave_bytes,
+                                                 cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        for (int s = s1 - 1; s >= s0; --s) {
+            TACAW_CUDA_CHECK(dispatch_col(g.ny, b.g, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st,
+                                          first ? 2 : 1));
+            first = false;
+            const float2* state = (s == s0) ? (c > 0 ? b.ck + (size_t)c * wave : nullptr)
+                                            : b.seg + (size_t)(s - s0) * wave;
+            TACAW_CUDA_CHECK(dispatch_row_back(g.nx, b.g, state, V, dV, psi_in, tb.twx, g.ny, n_t,
+                                               g.n_slices, s, sigma, s > 0 ? 0 : first_mode, s > 0 ? 1 : 0,
+                                               st));
+        }
     }
     return TACAW_OK;
 }

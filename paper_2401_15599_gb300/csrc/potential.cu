@@ -150,9 +150,11 @@ constexpr int kSegs = kPotThreads / 32;  // one column segment per warp
 constexpr int kMaxNbBins = 64;           // neighbouring bins scanned per block
 
 struct CandSmem {
-    int ic[kChunk], jc[kChunk];                 // pixel index of the atom (floor of x/dx, y/dy)
+    int ic[kChunk], jc[kChunk];                 // pixel index of the atom (wrapped into the box)
     float fx[kChunk], fy[kChunk];               // offset of the atom from that pixel, A
     float aw[kChunk], inv2s2[kChunk], rc2[kChunk];
+    int sp[kChunk];
+    float w[kChunk], dw[kChunk];                // slice weight and d(weight)/d(sigma)
     float gy[kChunk][kBandRows];
     float dy2[kChunk][kBandRows];
     unsigned short seg_list[kSegs][kChunk];
@@ -162,34 +164,36 @@ struct CandSmem {
     int n_nb;
 };
 
-// One block per (band of kBandRows rows, slice, snapshot).  Warp w owns the
-// column segment [w * seg_w, (w + 1) * seg_w) (CPL columns per lane) and keeps
-// the band's sums for those columns in 64-bit fixed-point registers: no
-// atomics on pixels, the Gaussian is evaluated separably (one row factor per
-// candidate and row, one column factor per candidate and column), and the
-// result does not depend on the order in which candidates arrive.
-template <int CPL>
-__global__ void __launch_bounds__(kPotThreads)
-potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
-                 const int2* __restrict__ binned_px, PotParams p, float* __restrict__ V) {
-    __shared__ CandSmem sm;
-    const int band = blockIdx.x, s = blockIdx.y;
-    const size_t t = blockIdx.z;
-    const int r0 = band * kBandRows;
-    const int nrows = min(kBandRows, p.ny - r0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int seg_w = (p.nx + kSegs - 1) / kSegs;
-    const int* off = bin_off + t * (size_t)(p.n_bins + 1);
-    const float4* atoms = binned + t * (size_t)p.n_atoms;
-    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
-    const bool first = (s == 0), lastsl = (s == p.n_slices - 1);
-    const float lo = first ? -INFINITY : p.z0 + (float)s * p.dz;
-    const float hi = lastsl ? INFINITY : p.z0 + (float)(s + 1) * p.dz;
-    const float band_span = (float)(nrows - 1) * p.dy;
+struct Tile {
+    int band, s, r0, nrows, seg_w;
+    size_t t;
+    bool first, lastsl;
+    float lo, hi, band_span;
+};
 
-    // neighbouring bins (slabs s +- slab_reach, bands +- band_reach) as one
-    // flat list: one thread per bin loads its range, warp 0 scans the counts
-    const int slab0 = max(0, s - p.slab_reach), slab1 = min(p.n_slices - 1, s + p.slab_reach);
+__device__ __forceinline__ Tile make_tile(const PotParams& p) {
+    Tile tl;
+    tl.band = blockIdx.x;
+    tl.s = blockIdx.y;
+    tl.t = blockIdx.z;
+    tl.r0 = tl.band * kBandRows;
+    tl.nrows = min(kBandRows, p.ny - tl.r0);
+    tl.seg_w = (p.nx + kSegs - 1) / kSegs;
+    tl.first = (tl.s == 0);
+    tl.lastsl = (tl.s == p.n_slices - 1);
+    tl.lo = tl.first ? -INFINITY : p.z0 + (float)tl.s * p.dz;
+    tl.hi = tl.lastsl ? INFINITY : p.z0 + (float)(tl.s + 1) * p.dz;
+    tl.band_span = (float)(tl.nrows - 1) * p.dy;
+    return tl;
+}
+
+// Neighbouring bins (slabs s +- slab_reach, bands +- band_reach) as one flat
+// list: warp 0 loads the ranges and scans the counts.  Returns the number of
+// source atoms (after a block barrier).
+__device__ int load_neighbour_bins(CandSmem& sm, const PotParams& p, const int* __restrict__ off,
+                                   const Tile& tl) {
+    const int lane = threadIdx.x & 31;
+    const int slab0 = max(0, tl.s - p.slab_reach), slab1 = min(p.n_slices - 1, tl.s + p.slab_reach);
     const bool all_bands = 2 * p.band_reach + 1 >= p.n_bands;
     const int nb = all_bands ? p.n_bands : 2 * p.band_reach + 1;
     const int n_nb = nb * (slab1 - slab0 + 1);
@@ -200,7 +204,7 @@ potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ bin
             int cnt = 0, start = 0;
             if (i < n_nb) {
                 const int slab = slab0 + i / nb, k = i % nb;
-                int b = all_bands ? k : band - p.band_reach + k;
+                int b = all_bands ? k : tl.band - p.band_reach + k;
                 b = ((b % p.n_bands) + p.n_bands) % p.n_bands;
                 const int bin = slab * p.n_bands + b;
                 start = __ldg(off + bin);
@@ -224,108 +228,141 @@ potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ bin
         }
     }
     __syncthreads();
-    const int n_src = sm.bin_cum[sm.n_nb];
+    return sm.bin_cum[sm.n_nb];
+}
+
+// Candidates of one chunk of source atoms: the atoms that reach this slice
+// and band, listed in every column segment their window touches, with their
+// per-row Gaussian factors.  Ends with a block barrier.
+__device__ void gather_chunk(CandSmem& sm, const PotParams& p, const float4* __restrict__ atoms,
+                             const int2* __restrict__ atoms_px, const Tile& tl, int c0, int n_src) {
+    if (threadIdx.x < kSegs) sm.seg_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) sm.n_cand = 0;
+    __syncthreads();
+    const int src = c0 + threadIdx.x;
+    if (src < n_src) {
+        int bi = 0;
+        while (sm.bin_cum[bi + 1] <= src) ++bi;
+        const int ai = sm.bin_start[bi] + (src - sm.bin_cum[bi]);
+        const float4 at = atoms[ai];               // (fx, fy, z, species)
+        const int2 px = atoms_px[ai];              // (ic, jc)
+        const int sp = __float_as_int(at.w);
+        bool ok = sp >= 0 && sp < p.n_species;
+        const float sg = ok ? p.sigma[sp] : 1.f;
+        const float rc = 6.0f * sg;
+        ok = ok && (tl.hi > at.z - rc) && (tl.lo < at.z + rc);
+        const int ic = px.x, jc = px.y;
+        int k0 = (tl.r0 - jc) % p.ny;              // wrapped pixel distance of the band's first row
+        if (k0 < 0) k0 += p.ny;
+        if (k0 >= (p.ny + 1) / 2) k0 -= p.ny;
+        const float d0 = (float)k0 * p.dy - at.y;
+        ok = ok && (d0 <= rc) && (d0 + tl.band_span >= -rc);
+        if (ok) {
+            const float kz = 0.70710678118654752f / sg;
+            const float uh = (tl.hi - at.z) * kz, ul = (tl.lo - at.z) * kz;
+            const float fh = tl.lastsl ? 0.5f : 0.5f * erff(uh);
+            const float fl = tl.first ? -0.5f : 0.5f * erff(ul);
+            // d/dsigma of erf(u)/2 with u = (edge - z)/(sqrt2 sigma): -(u/sigma) exp(-u^2)/sqrt(pi)
+            const float dh = tl.lastsl ? 0.f : -(uh / sg) * expf(-uh * uh) * 0.56418958354775628f;
+            const float dl = tl.first ? 0.f : -(ul / sg) * expf(-ul * ul) * 0.56418958354775628f;
+            const int c = atomicAdd(&sm.n_cand, 1);
+            int icw = ic % p.nx, jcw = jc % p.ny;   // pixel indices wrapped into the box
+            if (icw < 0) icw += p.nx;
+            if (jcw < 0) jcw += p.ny;
+            sm.ic[c] = icw;
+            sm.jc[c] = jcw;
+            sm.fx[c] = at.x;
+            sm.fy[c] = at.y;
+            sm.sp[c] = sp;
+            sm.w[c] = fh - fl;
+            sm.dw[c] = dh - dl;
+            sm.aw[c] = p.amp[sp] * (fh - fl);
+            sm.inv2s2[c] = 0.5f / (sg * sg);
+            sm.rc2[c] = rc * rc;
+            // columns within the cut-off lie in [i0, i0 + wx) (one spare column each side)
+            const int reach = (int)ceilf(rc * p.inv_dx);
+            const int i0 = ic - reach - 1;
+            const int wx = 2 * reach + 3;
+            unsigned mask = 0;
+            if (wx >= p.nx) {
+                mask = (1u << kSegs) - 1u;
+            } else {
+                int a = i0 % p.nx;
+                if (a < 0) a += p.nx;
+                const int b = a + wx - 1;
+                for (int col = a; col <= b; col += tl.seg_w) mask |= 1u << ((col % p.nx) / tl.seg_w);
+                mask |= 1u << ((b % p.nx) / tl.seg_w);
+            }
+            while (mask) {
+                const int si = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int slot = atomicAdd(&sm.seg_cnt[si], 1);
+                sm.seg_list[si][slot] = (unsigned short)c;
+            }
+        }
+    }
+    __syncthreads();
+    const int nc = sm.n_cand;
+    for (int e = threadIdx.x; e < nc * kBandRows; e += blockDim.x) {
+        const int c = e / kBandRows, r = e % kBandRows;
+        int k = tl.r0 + r - sm.jc[c];              // in (-ny, ny): wrap to the nearest image
+        if (k >= (p.ny + 1) / 2) k -= p.ny;
+        if (k < -(p.ny / 2)) k += p.ny;
+        const float ddy = (float)k * p.dy - sm.fy[c];
+        const float d2 = ddy * ddy;
+        const bool in = r < tl.nrows && d2 <= sm.rc2[c];
+        sm.dy2[c][r] = in ? d2 : INFINITY;
+        sm.gy[c][r] = in ? expf(-d2 * sm.inv2s2[c]) : 0.f;
+    }
+    __syncthreads();
+}
+
+// Squared distance from column `col` to candidate c (nearest image), wrapped
+// integer pixel distance times dx minus the atom's offset in its pixel.
+__device__ __forceinline__ float col_dist2(const CandSmem& sm, const PotParams& p, int c, int col) {
+    int kx = col - sm.ic[c];                        // in (-nx, nx): wrap to the nearest image
+    if (kx >= (p.nx + 1) / 2) kx -= p.nx;
+    if (kx < -(p.nx / 2)) kx += p.nx;
+    const float ddx = (float)kx * p.dx - sm.fx[c];
+    return ddx * ddx;
+}
+
+// One block per (band of kBandRows rows, slice, snapshot).  Warp w owns the
+// column segment [w * seg_w, (w + 1) * seg_w) (CPL columns per lane) and keeps
+// the band's sums for those columns in 64-bit fixed-point registers: no
+// atomics on pixels, the Gaussian is evaluated separably (one row factor per
+// candidate and row, one column factor per candidate and column), and the
+// result does not depend on the order in which candidates arrive.
+template <int CPL>
+__global__ void __launch_bounds__(kPotThreads)
+potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                 const int2* __restrict__ binned_px, PotParams p, float* __restrict__ V) {
+    __shared__ CandSmem sm;
+    const Tile tl = make_tile(p);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* atoms = binned + tl.t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + tl.t * (size_t)p.n_atoms;
+    const int n_src = load_neighbour_bins(sm, p, bin_off + tl.t * (size_t)(p.n_bins + 1), tl);
 
     long long acc[CPL][kBandRows];
 #pragma unroll
     for (int k = 0; k < CPL; ++k)
 #pragma unroll
         for (int r = 0; r < kBandRows; ++r) acc[k][r] = 0;
-    const int col0 = warp * seg_w;
-    const int col1 = min(col0 + seg_w, p.nx);
+    const int col0 = warp * tl.seg_w;
+    const int col1 = min(col0 + tl.seg_w, p.nx);
 
     for (int c0 = 0; c0 < n_src; c0 += kChunk) {
-        if (threadIdx.x < kSegs) sm.seg_cnt[threadIdx.x] = 0;
-        if (threadIdx.x == 0) sm.n_cand = 0;
-        __syncthreads();
-        // 1. one source atom per thread; accepted atoms become candidates and are
-        //    listed in every column segment their window touches
-        const int src = c0 + threadIdx.x;
-        if (src < n_src) {
-            int bi = 0;
-            while (sm.bin_cum[bi + 1] <= src) ++bi;
-            const int ai = sm.bin_start[bi] + (src - sm.bin_cum[bi]);
-            const float4 at = atoms[ai];               // (fx, fy, z, species)
-            const int2 px = atoms_px[ai];              // (ic, jc)
-            const int sp = __float_as_int(at.w);
-            bool ok = sp >= 0 && sp < p.n_species;
-            const float sg = ok ? p.sigma[sp] : 1.f;
-            const float rc = 6.0f * sg;
-            ok = ok && (hi > at.z - rc) && (lo < at.z + rc);
-            const int ic = px.x, jc = px.y;
-            const float fx = at.x, fy = at.y;
-            int k0 = (r0 - jc) % p.ny;                  // wrapped pixel distance of the band's first row
-            if (k0 < 0) k0 += p.ny;
-            if (k0 >= (p.ny + 1) / 2) k0 -= p.ny;
-            const float d0 = (float)k0 * p.dy - fy;
-            ok = ok && (d0 <= rc) && (d0 + band_span >= -rc);
-            if (ok) {
-                const float kz = 0.70710678118654752f / sg;
-                const float fh = lastsl ? 0.5f : 0.5f * erff((hi - at.z) * kz);
-                const float fl = first ? -0.5f : 0.5f * erff((lo - at.z) * kz);
-                const int c = atomicAdd(&sm.n_cand, 1);
-                int icw = ic % p.nx, jcw = jc % p.ny;   // pixel indices wrapped into the box
-                if (icw < 0) icw += p.nx;
-                if (jcw < 0) jcw += p.ny;
-                sm.ic[c] = icw;
-                sm.jc[c] = jcw;
-                sm.fx[c] = fx;
-                sm.fy[c] = fy;
-                sm.aw[c] = p.amp[sp] * (fh - fl);
-                sm.inv2s2[c] = 0.5f / (sg * sg);
-                sm.rc2[c] = rc * rc;
-                // columns within the cut-off lie in [i0, i0 + wx) (one spare column each side)
-                const int reach = (int)ceilf(rc * p.inv_dx);
-                const int i0 = ic - reach - 1;
-                const int wx = 2 * reach + 3;
-                unsigned mask = 0;
-                if (wx >= p.nx) {
-                    mask = (1u << kSegs) - 1u;
-                } else {
-                    int a = i0 % p.nx;
-                    if (a < 0) a += p.nx;
-                    const int b = a + wx - 1;
-                    for (int col = a; col <= b; col += seg_w) mask |= 1u << ((col % p.nx) / seg_w);
-                    mask |= 1u << ((b % p.nx) / seg_w);
-                }
-                while (mask) {
-                    const int si = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const int slot = atomicAdd(&sm.seg_cnt[si], 1);
-                    sm.seg_list[si][slot] = (unsigned short)c;
-                }
-            }
-        }
-        __syncthreads();
-        // 2. per candidate and band row: squared row distance and Gaussian row factor
-        const int nc = sm.n_cand;
-        for (int e = threadIdx.x; e < nc * kBandRows; e += blockDim.x) {
-            const int c = e / kBandRows, r = e % kBandRows;
-            int k = r0 + r - sm.jc[c];                  // in (-ny, ny): wrap to the nearest image
-            if (k >= (p.ny + 1) / 2) k -= p.ny;
-            if (k < -(p.ny / 2)) k += p.ny;
-            const float ddy = (float)k * p.dy - sm.fy[c];
-            const float d2 = ddy * ddy;
-            const bool in = r < nrows && d2 <= sm.rc2[c];
-            sm.dy2[c][r] = in ? d2 : INFINITY;
-            sm.gy[c][r] = in ? expf(-d2 * sm.inv2s2[c]) : 0.f;
-        }
-        __syncthreads();
-        // 3. the warp adds the candidates listed in its segment to its columns
+        gather_chunk(sm, p, atoms, atoms_px, tl, c0, n_src);
         const int cnt = sm.seg_cnt[warp];
         for (int j = 0; j < cnt; ++j) {
             const int c = sm.seg_list[warp][j];
-            const int ic = sm.ic[c];
-            const float fx = sm.fx[c], aw = sm.aw[c], inv2s2 = sm.inv2s2[c], rc2 = sm.rc2[c];
+            const float aw = sm.aw[c], inv2s2 = sm.inv2s2[c], rc2 = sm.rc2[c];
 #pragma unroll
             for (int k = 0; k < CPL; ++k) {
                 const int col = col0 + lane + 32 * k;
                 if (col >= col1) continue;
-                int kx = col - ic;                      // in (-nx, nx): wrap to the nearest image
-                if (kx >= (p.nx + 1) / 2) kx -= p.nx;
-                if (kx < -(p.nx / 2)) kx += p.nx;
-                const float ddx = (float)kx * p.dx - fx;
-                const float dx2 = ddx * ddx;
+                const float dx2 = col_dist2(sm, p, c, col);
                 if (dx2 > rc2) continue;
                 const float gx = aw * expf(-dx2 * inv2s2);
 #pragma unroll
@@ -335,21 +372,112 @@ potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ bin
         }
         __syncthreads();
     }
-    // 4. write the band (lanes on consecutive columns)
-    float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + r0) * p.nx;
+    // write the band (lanes on consecutive columns)
+    float* out = V + ((tl.t * p.n_slices + tl.s) * (size_t)p.ny + tl.r0) * p.nx;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         const int col = col0 + lane + 32 * k;
         if (col >= col1) continue;
 #pragma unroll
         for (int r = 0; r < kBandRows; ++r)
-            if (r < nrows) {
+            if (r < tl.nrows) {
                 // sums below 2048 V*A fit in 32 bits: convert those without the FP64 pipe
                 const long long a = acc[k][r];
                 const float f = (a == (long long)(int)a) ? (float)(int)a : (float)a;
                 out[(size_t)r * p.nx + col] = f * kFixInv;
             }
     }
+}
+
+// Adjoint of the potential for the per-species Gaussian parameters: with
+// P = exp(-rho^2 / 2 s^2) inside the cut-off and g = dL/dv,
+//   dL/d amp += g P w,   dL/d s += g amp P (rho^2 / s^3 w + dw/ds).
+// Each lane sums its contributions per candidate, the warp reduces them and
+// adds to per-species FP64 block totals; every block writes its totals to
+// `partial` [block][n_species][2] for a fixed-order final reduction.
+template <int CPL>
+__global__ void __launch_bounds__(kPotThreads)
+potential_backward_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                          const int2* __restrict__ binned_px, PotParams p, const float* __restrict__ dV,
+                          double* __restrict__ partial) {
+    __shared__ CandSmem sm;
+    __shared__ double tot[TACAW_MAX_SPECIES][2];
+    extern __shared__ float gtile[];                // [kBandRows][nx]: dL/dv of the band
+    const Tile tl = make_tile(p);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* atoms = binned + tl.t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + tl.t * (size_t)p.n_atoms;
+    if (threadIdx.x < 2 * TACAW_MAX_SPECIES) tot[threadIdx.x / 2][threadIdx.x % 2] = 0.0;
+    const float* grow = dV + ((tl.t * p.n_slices + tl.s) * (size_t)p.ny + tl.r0) * p.nx;
+    for (int i = threadIdx.x; i < tl.nrows * p.nx; i += blockDim.x)
+        gtile[i] = __ldg(grow + i);
+    const int n_src = load_neighbour_bins(sm, p, bin_off + tl.t * (size_t)(p.n_bins + 1), tl);
+    const int col0 = warp * tl.seg_w;
+    const int col1 = min(col0 + tl.seg_w, p.nx);
+
+    for (int c0 = 0; c0 < n_src; c0 += kChunk) {
+        gather_chunk(sm, p, atoms, atoms_px, tl, c0, n_src);
+        const int cnt = sm.seg_cnt[warp];
+        for (int j = 0; j < cnt; ++j) {
+            const int c = sm.seg_list[warp][j];
+            const int sp = sm.sp[c];
+            const float inv2s2 = sm.inv2s2[c], rc2 = sm.rc2[c];
+            const float sg = p.sigma[sp];
+            const float inv_s3 = 1.0f / (sg * sg * sg);
+            const float w = sm.w[c], dw = sm.dw[c];
+            float ga = 0.f, gs = 0.f;
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int col = col0 + lane + 32 * k;
+                if (col >= col1) continue;
+                const float dx2 = col_dist2(sm, p, c, col);
+                if (dx2 > rc2) continue;
+                const float gx = expf(-dx2 * inv2s2);
+#pragma unroll
+                for (int r = 0; r < kBandRows; ++r) {
+                    const float r2 = dx2 + sm.dy2[c][r];
+                    if (r2 <= rc2) {
+                        const float gp = gtile[r * p.nx + col] * gx * sm.gy[c][r];
+                        ga += gp;
+                        gs += gp * r2;
+                    }
+                }
+            }
+            // ga = sum g P, gs = sum g P rho^2  ->  (w ga, amp (gs w / s^3 + ga dw))
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                gs += __shfl_xor_sync(0xffffffffu, gs, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&tot[sp][0], (double)ga * (double)w);
+                atomicAdd(&tot[sp][1], (double)p.amp[sp] * ((double)gs * (double)w * (double)inv_s3 +
+                                                            (double)ga * (double)dw));
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (threadIdx.x < 2 * p.n_species)
+        partial[blk * 2 * p.n_species + threadIdx.x] = tot[threadIdx.x / 2][threadIdx.x % 2];
+}
+
+// out[i] = sum over blocks of partial[block][i], fixed order (one block per i).
+__global__ void __launch_bounds__(256)
+reduce_partials_kernel(const double* __restrict__ partial, size_t n_blocks, int n_vals,
+                       double* __restrict__ out) {
+    __shared__ double sh[256];
+    const int i = blockIdx.x;
+    double acc = 0.0;
+    for (size_t b = threadIdx.x; b < n_blocks; b += blockDim.x) acc += partial[b * n_vals + i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0];
 }
 
 struct PotWs {
@@ -415,6 +543,19 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
 
 }  // namespace
 
+static size_t pot_backward_blocks(const tacaw_grid& g, int n_t) {
+    return (size_t)((g.ny + kBandRows - 1) / kBandRows) * g.n_slices * n_t;
+}
+
+int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n_species, size_t* bytes) {
+    const int n_bins = g.n_slices * ((g.ny + kBandRows - 1) / kBandRows);
+    Carver cv(nullptr);
+    carve_pot(cv, n_t, n_atoms, n_bins);
+    cv.take<double>(pot_backward_blocks(g, n_t) * 2 * n_species);
+    *bytes = cv.bytes();
+    return TACAW_OK;
+}
+
 int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes) {
     const int n_bins = g.n_slices * ((g.ny + kBandRows - 1) / kBandRows);
     Carver cv(nullptr);
@@ -423,11 +564,7 @@ int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes)
     return TACAW_OK;
 }
 
-int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
-                  int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st) {
-    PotParams p;
-    int rc = make_params(g, n_atoms, n_species, amp_sigma, &p);
-    if (rc != TACAW_OK) return rc;
+static int check_tables(const tacaw_grid& g, const PotParams& p) {
     const size_t bin_smem = (size_t)p.n_bins * sizeof(int);
     TACAW_REQUIRE(bin_smem <= 200 * 1024, TACAW_EUNSUPPORTED,
                   "tacaw_potential: %d bins exceed the shared-memory histogram", p.n_bins);
@@ -438,12 +575,29 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
     TACAW_REQUIRE(n_nb <= kMaxNbBins, TACAW_EUNSUPPORTED,
                   "tacaw_potential: %d neighbouring bins per tile exceed %d (widths too large for "
                   "the slice thickness or pixel size)", n_nb, kMaxNbBins);
-    Carver cv(ws);
-    PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
+    return TACAW_OK;
+}
+
+static int run_binning(const PotParams& p, int n_t, const float* pos, const int* species, PotWs& w,
+                       cudaStream_t st) {
+    const size_t bin_smem = (size_t)p.n_bins * sizeof(int);
     TACAW_CUDA_CHECK(cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)bin_smem));
     bin_kernel<<<n_t, kBinThreads, bin_smem, st>>>(pos, species, p, w.bin_off, w.binned, w.binned_px);
     TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
+                  int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st) {
+    PotParams p;
+    int rc = make_params(g, n_atoms, n_species, amp_sigma, &p);
+    if (rc == TACAW_OK) rc = check_tables(g, p);
+    if (rc != TACAW_OK) return rc;
+    Carver cv(ws);
+    PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
+    rc = run_binning(p, n_t, pos, species, w, st);
+    if (rc != TACAW_OK) return rc;
     dim3 grid(p.n_bands, g.n_slices, n_t);
     const int cpl = ((g.nx + kSegs - 1) / kSegs + 31) / 32;
     if (cpl <= 1)
@@ -452,6 +606,38 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
         potential_kernel<2><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
     else
         potential_kernel<4><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+int potential_backward_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos,
+                           const int* species, int n_species, const float* amp_sigma, const float* dV,
+                           double* grad, void* ws, cudaStream_t st) {
+    PotParams p;
+    int rc = make_params(g, n_atoms, n_species, amp_sigma, &p);
+    if (rc == TACAW_OK) rc = check_tables(g, p);
+    if (rc != TACAW_OK) return rc;
+    Carver cv(ws);
+    PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
+    const size_t n_blocks = pot_backward_blocks(g, n_t);
+    double* partial = cv.take<double>(n_blocks * 2 * n_species);
+    rc = run_binning(p, n_t, pos, species, w, st);
+    if (rc != TACAW_OK) return rc;
+    dim3 grid(p.n_bands, g.n_slices, n_t);
+    const int cpl = ((g.nx + kSegs - 1) / kSegs + 31) / 32;
+    const int dsm = (int)(kBandRows * g.nx * sizeof(float));
+    if (cpl <= 1) {
+        TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_backward_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+        potential_backward_kernel<1><<<grid, kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px, p, dV, partial);
+    } else if (cpl == 2) {
+        TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_backward_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+        potential_backward_kernel<2><<<grid, kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px, p, dV, partial);
+    } else {
+        TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_backward_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+        potential_backward_kernel<4><<<grid, kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px, p, dV, partial);
+    }
+    TACAW_LAUNCH_CHECK();
+    reduce_partials_kernel<<<2 * n_species, 256, 0, st>>>(partial, n_blocks, 2 * n_species, grad);
     TACAW_LAUNCH_CHECK();
     return TACAW_OK;
 }

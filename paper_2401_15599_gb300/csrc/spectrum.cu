@@ -138,6 +138,126 @@ cgemm_power_kernel(const float2* __restrict__ a, const float2* __restrict__ e,
     }
 }
 
+// Adjoint, first half: Phi = sum_n A[n][q] E[n][k] as in cgemm_power_kernel, then
+// G[q][k] = (2 / T^2) dL/dI[q][k] Phi[q][k] (the gradient with respect to Phi).
+__global__ void __launch_bounds__(256)
+cgemm_gphi_kernel(const float2* __restrict__ a, const float2* __restrict__ e,
+                  const float* __restrict__ dldi, float2* __restrict__ gphi, int nq, int n_t, int n_w,
+                  float scale2) {
+    __shared__ float2 as[BK][BM];
+    __shared__ float2 es[BK][BN];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int w0 = blockIdx.x * BN, q0 = blockIdx.y * BM;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < n_t; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = threadIdx.x + 256 * i;
+            const int kk = idx / BM, mm = idx % BM;
+            const int n = k0 + kk;
+            as[kk][mm] = (n < n_t && q0 + mm < nq) ? __ldg(a + (size_t)n * nq + q0 + mm) : make_float2(0.f, 0.f);
+            es[kk][mm] = (n < n_t && w0 + mm < n_w) ? __ldg(e + (size_t)n * n_w + w0 + mm) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 av[4], ev[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = as[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ev[j] = es[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(av[i].x, ev[j].x, fmaf(-av[i].y, ev[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(av[i].x, ev[j].y, fmaf(av[i].y, ev[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int q = q0 + ty + 16 * i;
+        if (q >= nq) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = w0 + tx + 16 * j;
+            if (k >= n_w) continue;
+            const float f = scale2 * __ldg(dldi + (size_t)q * n_w + k);
+            gphi[(size_t)q * n_w + k] = make_float2(f * acc[i][j].x, f * acc[i][j].y);
+        }
+    }
+}
+
+// Adjoint, second half: gA[n][q] = sum_k conj(E[n][k]) G[q][k]  (both operands
+// contiguous in k), written time-major like the exit waves.
+__global__ void __launch_bounds__(256)
+cgemm_back_kernel(const float2* __restrict__ e, const float2* __restrict__ gphi, float2* __restrict__ ga,
+                  int nq, int n_t, int n_w) {
+    __shared__ float2 es[BK][BM + 1];   // [k][n]
+    __shared__ float2 gs[BK][BN + 1];   // [k][q]
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int q0 = blockIdx.x * BN, n0 = blockIdx.y * BM;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < n_w; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = threadIdx.x + 256 * i;
+            const int kk = idx % BK, rr = idx / BK;      // rr in [0, 64): row of the tile
+            const int k = k0 + kk;
+            const int n = n0 + rr, q = q0 + rr;
+            es[kk][rr] = (k < n_w && n < n_t) ? __ldg(e + (size_t)n * n_w + k) : make_float2(0.f, 0.f);
+            gs[kk][rr] = (k < n_w && q < nq) ? __ldg(gphi + (size_t)q * n_w + k) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 ev[4], gv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = es[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gv[j] = gs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {   // conj(e) * g
+                    acc[i][j].x = fmaf(ev[i].x, gv[j].x, fmaf(ev[i].y, gv[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(ev[i].x, gv[j].y, fmaf(-ev[i].y, gv[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int n = n0 + ty + 16 * i;
+        if (n >= n_t) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = q0 + tx + 16 * j;
+            if (q < nq) ga[(size_t)n * nq + q] = acc[i][j];
+        }
+    }
+}
+
+// g_psi = gA - (1/T) sum_n gA  (FP64 mean), in place.
+__global__ void centre_grad_kernel(float2* __restrict__ g, const double2* __restrict__ sum, int n_t, int nq) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (q >= nq) return;
+    const double2 s = sum[q];
+    const float2 v = g[(size_t)t * nq + q];
+    g[(size_t)t * nq + q] = make_float2((float)((double)v.x - s.x / n_t), (float)((double)v.y - s.y / n_t));
+}
+
 // Deterministic FP64 sum: fixed partition into blocks, fixed order inside.
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 1024;
@@ -244,6 +364,59 @@ int launch_normalize(float* out, size_t n, double* i_el_user, const double* i_el
     total_kernel<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, i_el, nq, total);
     TACAW_LAUNCH_CHECK();
     scale_kernel<<<1024, 256, 0, st>>>(out, n, i_el_user, nq, total);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+struct SpecBackWs {
+    double2* sum;
+    float2* a;
+    float2* e;
+    float2* gphi;
+    double2* gsum;
+};
+
+static SpecBackWs carve_spec_back(Carver& cv, int nq, int n_t, int n_w, bool need_sum) {
+    SpecBackWs w;
+    w.sum = need_sum ? cv.take<double2>(nq) : nullptr;
+    w.a = cv.take<float2>((size_t)n_t * nq);
+    w.e = cv.take<float2>((size_t)n_t * n_w);
+    w.gphi = cv.take<float2>((size_t)nq * n_w);
+    w.gsum = cv.take<double2>(nq);
+    return w;
+}
+
+size_t spectrum_backward_ws_bytes(int nq, int n_t, int n_w, bool have_sum) {
+    Carver cv(nullptr);
+    carve_spec_back(cv, nq, n_t, n_w, !have_sum);
+    return cv.bytes();
+}
+
+int spectrum_backward_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
+                          size_t ld, const double2* psi_sum, const float* dldi, float2* gpsi, void* ws,
+                          cudaStream_t st) {
+    Carver cv(ws);
+    SpecBackWs w = carve_spec_back(cv, nq, n_t, n_w, psi_sum == nullptr);
+    const double2* sum = psi_sum;
+    if (!sum) {
+        time_sum_kernel<<<(nq + 255) / 256, 256, 0, st>>>(psi, ld, w.sum, n_t, nq);
+        TACAW_LAUNCH_CHECK();
+        sum = w.sum;
+    }
+    centre_kernel<<<dim3((nq + 255) / 256, n_t), 256, 0, st>>>(psi, ld, sum, w.a, nullptr, n_t, nq);
+    TACAW_LAUNCH_CHECK();
+    dft_table_kernel<<<dim3((n_w + 127) / 128, n_t), 128, 0, st>>>(w.e, nullptr, omega, n_t, n_w, dt_fs, 0.0);
+    TACAW_LAUNCH_CHECK();
+    const float scale2 = (float)(2.0 / ((double)n_t * (double)n_t));
+    cgemm_gphi_kernel<<<dim3((n_w + BN - 1) / BN, (nq + BM - 1) / BM), 256, 0, st>>>(w.a, w.e, dldi, w.gphi, nq,
+                                                                                     n_t, n_w, scale2);
+    TACAW_LAUNCH_CHECK();
+    cgemm_back_kernel<<<dim3((nq + BN - 1) / BN, (n_t + BM - 1) / BM), 256, 0, st>>>(w.e, w.gphi, gpsi, nq, n_t,
+                                                                                     n_w);
+    TACAW_LAUNCH_CHECK();
+    time_sum_kernel<<<(nq + 255) / 256, 256, 0, st>>>(gpsi, nq, w.gsum, n_t, nq);
+    TACAW_LAUNCH_CHECK();
+    centre_grad_kernel<<<dim3((nq + 255) / 256, n_t), 256, 0, st>>>(gpsi, w.gsum, n_t, nq);
     TACAW_LAUNCH_CHECK();
     return TACAW_OK;
 }
