@@ -136,7 +136,7 @@ int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
  * psi_sum  in/out [ny][nx] double2 running sum over snapshots, or NULL; when
  *          given, sum_t psi_q(t) is ADDED to it in FP64 (snapshot order)
  * flags    0 (reserved)
- * Supported sizes: nx, ny in {64, 128, 256, 512, 1024}.
+ * Supported sizes: nx, ny in {64, 128, 256, 384, 512, 768, 1024}.
  */
 int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,
                      const void* psi_in, void* psi_q, void* psi_sum, int32_t flags,
@@ -202,6 +202,31 @@ int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_ome
                             const double* omega_meV, const void* psi, const void* psi_sum,
                             const float* dL_dI, void* dL_dpsi,
                             void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Many independent multislice jobs of uneven size in one call (independent
+ * trajectories, or segments of one trajectory, as the paper averages over).
+ * Each job is a tacaw_multislice call: its own grid (sizes as supported by
+ * tacaw_multislice), snapshot count, potentials, incident wave, exit waves
+ * and optional FP64 running sum.  Slice steps of jobs with the same grid
+ * size share kernel launches (at most TACAW_MAX_BATCH jobs and 65535
+ * snapshots per launch), so short and small jobs ride along with large ones;
+ * the call only enqueues kernels and is suited to CUDA graph capture (make
+ * one call outside capture first so per-kernel attributes are set).
+ * jobs: HOST array; the pointers inside are device pointers.
+ */
+#define TACAW_MAX_BATCH 64
+typedef struct tacaw_job {
+    tacaw_grid grid;
+    int32_t n_t;
+    const float* V;      /* [n_t][n_slices][ny][nx] */
+    const void* psi_in;  /* [ny][nx] float2 or NULL */
+    void* psi_q;         /* out [n_t][ny][nx] float2 */
+    void* psi_sum;       /* in/out [ny][nx] double2 or NULL */
+} tacaw_job;
+
+int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size_t* ws_bytes,
+                           void* stream);
 
 /*
  * Adjoint of tacaw_multislice for gradient-based fitting (PyTorch convention

@@ -24,6 +24,7 @@ TACAW_BF16X3 = 1
 TACAW_KUBO = 1
 TACAW_NORMALIZE = 2
 TACAW_MAX_SPECIES = 8
+TACAW_MAX_BATCH = 64
 
 ERRORS = {
     TACAW_EINVAL: "EINVAL", TACAW_ECUDA: "ECUDA", TACAW_ENOMEM: "ENOMEM",
@@ -38,6 +39,14 @@ class TacawGrid(ctypes.Structure):
         ("n_slices", ctypes.c_int32),
         ("dz", ctypes.c_double), ("z0", ctypes.c_double),
         ("kev", ctypes.c_double), ("bandlimit", ctypes.c_double),
+    ]
+
+
+class TacawJob(ctypes.Structure):
+    _fields_ = [
+        ("grid", TacawGrid), ("n_t", ctypes.c_int32),
+        ("V", ctypes.c_void_p), ("psi_in", ctypes.c_void_p),
+        ("psi_q", ctypes.c_void_p), ("psi_sum", ctypes.c_void_p),
     ]
 
 
@@ -60,6 +69,7 @@ SIGNATURES = {
                                         ctypes.c_int32, _P, _SZ, _P]),
     "tacaw_multislice_static": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,
                                                ctypes.c_int32, _P]),
+    "tacaw_multislice_batch": (ctypes.c_int, [ctypes.POINTER(TacawJob), ctypes.c_int32, _P, _SZ, _P]),
     "tacaw_spectrum": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P,
                                       _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                       _P, _SZ, _P]),

@@ -217,3 +217,37 @@ def potential_backward(grid, pos, species, amp_sigma, dl_dv, out=None, workspace
                                             amp_c, _ptr(dl_dv), _ptr(out), ws, nbytes, _stream(pos.device))
     _call_with_workspace("tacaw_potential_backward", call, pos.device, workspace)
     return out
+
+
+def multislice_batch(jobs, workspace=None):
+    """Run several multislice jobs of uneven size in one call.
+
+    jobs: sequence of dicts with keys grid, V [T, n_s, ny, nx] float32, out
+    [T, ny, nx] complex64 and optionally psi_in [ny, nx] complex64 and
+    psi_sum [ny, nx] complex128.  All tensors on the same CUDA device.
+    """
+    lib = L.load()
+    arr = (L.TacawJob * max(1, len(jobs)))()
+    dev = None
+    for i, j in enumerate(jobs):
+        V, out = j["V"], j["out"]
+        _need_cuda("V", V, torch.float32, 4)
+        _need_cuda("out", out, torch.complex64, 3)
+        g = j["grid"]
+        if tuple(V.shape[1:]) != (g.n_slices, g.ny, g.nx) or tuple(out.shape) != (V.shape[0], g.ny, g.nx):
+            raise ValueError(f"job {i}: V must be [T, n_slices, ny, nx] and out [T, ny, nx]")
+        psi_in, psi_sum = j.get("psi_in"), j.get("psi_sum")
+        if psi_in is not None:
+            _need_cuda("psi_in", psi_in, torch.complex64, 2)
+        if psi_sum is not None:
+            _need_cuda("psi_sum", psi_sum, torch.complex128)
+        arr[i] = L.TacawJob(L.make_grid(g), int(V.shape[0]), V.data_ptr(),
+                            psi_in.data_ptr() if psi_in is not None else None, out.data_ptr(),
+                            psi_sum.data_ptr() if psi_sum is not None else None)
+        dev = V.device
+    if dev is None:
+        return
+
+    def call(ws, nbytes):
+        return lib.tacaw_multislice_batch(arr, len(jobs), ws, nbytes, _stream(dev))
+    _call_with_workspace("tacaw_multislice_batch", call, dev, workspace)

@@ -48,6 +48,8 @@ int spectrum_backward_run(int nq, int n_t, double dt_fs, int n_w, const double* 
                           size_t ld, const double2* psi_sum, const float* dldi, float2* gpsi, void* ws,
                           cudaStream_t st);
 size_t multislice_backward_ws_bytes(const tacaw_grid& g, int n_t, int every);
+size_t multislice_batch_ws_bytes(const tacaw_job* jobs, int n_jobs);
+int multislice_batch_run(const tacaw_job* jobs, int n_jobs, void* ws, cudaStream_t st);
 int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
                             const float2* g_exit, float* dV, int every, void* ws, cudaStream_t st);
 int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n_species, size_t* bytes);
@@ -135,7 +137,7 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
     int rc = check_grid(grid, fn);
     if (rc) return rc;
     TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny),
-                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 512, 1024}", fn,
+                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
     TACAW_REQUIRE(flags == 0, TACAW_EINVAL, "%s: flags must be 0", fn);
@@ -146,6 +148,28 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
     TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
     return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
                           ws, (cudaStream_t)stream);
+}
+
+int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size_t* ws_bytes,
+                           void* stream) {
+    clear_error();
+    const char* fn = "tacaw_multislice_batch";
+    TACAW_REQUIRE(jobs != nullptr && n_jobs >= 0, TACAW_EINVAL, "%s: bad job list", fn);
+    for (int j = 0; j < n_jobs; ++j) {
+        int rc = check_grid(&jobs[j].grid, fn);
+        if (rc) return rc;
+        TACAW_REQUIRE(multislice_size_supported(jobs[j].grid.nx) && multislice_size_supported(jobs[j].grid.ny),
+                      TACAW_EUNSUPPORTED, "%s: job %d: nx = %d, ny = %d not supported", fn, j,
+                      jobs[j].grid.nx, jobs[j].grid.ny);
+        TACAW_REQUIRE(jobs[j].n_t >= 0 && jobs[j].n_t <= 65535, TACAW_EINVAL,
+                      "%s: job %d: n_t must be in [0, 65535]", fn, j);
+        TACAW_REQUIRE(jobs[j].n_t == 0 || (jobs[j].V && jobs[j].psi_q), TACAW_EINVAL,
+                      "%s: job %d: NULL array", fn, j);
+    }
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, multislice_batch_ws_bytes(jobs, n_jobs), fn, &query);
+    if (rc || query) return rc;
+    return multislice_batch_run(jobs, n_jobs, ws, (cudaStream_t)stream);
 }
 
 int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const double* omega_meV,
@@ -206,7 +230,7 @@ int tacaw_multislice_backward(const tacaw_grid* grid, int32_t n_t, const float* 
     int rc = check_grid(grid, fn);
     if (rc) return rc;
     TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny),
-                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 512, 1024}", fn,
+                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
     int every = ckpt_every;

@@ -51,6 +51,9 @@ struct Carver {
     size_t bytes() const { return (off + 255) / 256 * 256; }
 };
 
+// Raise a kernel's dynamic shared-memory limit once per device (multislice.cu).
+cudaError_t ensure_smem(const void* kernel, int bytes);
+
 // Beam constants (textbook relativistic values, CODATA 2018).
 void beam_constants(double kev, double* lambda_A, double* sigma_e);
 

@@ -123,6 +123,11 @@ template <>
 struct Plan<512> { static constexpr int E = 8; using R = Radices<8, 8, 8>; };
 template <>
 struct Plan<1024> { static constexpr int E = 8; using R = Radices<8, 8, 4, 4>; };
+// radix-3 sizes: 24 values per thread so that every radix divides E
+template <>
+struct Plan<384> { static constexpr int E = 24; using R = Radices<8, 8, 2, 3>; };
+template <>
+struct Plan<768> { static constexpr int E = 24; using R = Radices<8, 8, 4, 3>; };
 
 template <int A, int... Rest>
 struct First { static constexpr int value = A; };

@@ -12,10 +12,31 @@
 // Each pass reads and writes every point once (8 + 8 bytes per point), the
 // row pass also reads v_s (4 bytes per point): 36 bytes per point and slice.
 
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 #include "fft.cuh"
 
 namespace tacaw {
+
+// Raise a kernel's dynamic shared-memory limit once per device (later calls,
+// including calls made while a stream is being captured, skip the driver call).
+cudaError_t ensure_smem(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int& have = done[{kernel, dev}];
+    if (have >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
 
 namespace {
 
@@ -43,6 +64,8 @@ __device__ void fill_plan_twiddles(int n, float2* tw, int tid, int nthr) {
         case 256: fft::fill_twiddles<256>(tw, tid, nthr); break;
         case 512: fft::fill_twiddles<512>(tw, tid, nthr); break;
         case 1024: fft::fill_twiddles<1024>(tw, tid, nthr); break;
+        case 384: fft::fill_twiddles<384>(tw, tid, nthr); break;
+        case 768: fft::fill_twiddles<768>(tw, tid, nthr); break;
     }
 }
 
@@ -83,31 +106,16 @@ __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py
     }
 }
 
-// Row pass: ROWS rows of one snapshot per block.
-// mode 0: stored rows are (k_x, y) -> Fx^-1 first; 1: unit plane wave; 2: psi_in.
+// Row pass body for one row: (k_x, y) row -> Fx^-1 (mode 0; mode 1 starts from
+// the unit plane wave, mode 2 from psi_in) -> multiply by exp(i sigma v) -> Fx.
 template <int NX>
-__global__ void __launch_bounds__(kRowThreads)
-row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
-                const float2* __restrict__ psi_in, const float2* __restrict__ twx,
-                int ny, int n_slices, int s, float sigma, int mode) {
+__device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float* __restrict__ vrow,
+                                         const float2* __restrict__ inrow, int mode, float sigma,
+                                         float2* b0, float2* b1, const float2* tw, int t, int row) {
     using namespace fft;
     constexpr int E = Plan<NX>::E;
     constexpr int TPT = NX / E;
-    constexpr int ROWS = kRowThreads / TPT;
-    extern __shared__ float2 smem[];
-    float2* b0 = smem;
-    float2* b1 = smem + ROWS * NX;
-    float2* tw = smem + 2 * ROWS * NX;
-    stage_twiddles<NX>(tw, twx);
-
-    const int t = threadIdx.x % TPT;
-    const int row = threadIdx.x / TPT;
-    const int y = blockIdx.x * ROWS + row;
-    const size_t snap = blockIdx.y;
-    float2* rowp = psi + (snap * ny + y) * NX;
-    const float* vrow = V + ((snap * n_slices + s) * ny + y) * NX;
     const RowLayout lay{row * NX};
-
     float2 v[E];
     if (mode == 0) {
 #pragma unroll
@@ -118,7 +126,7 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
         for (int m = 0; m < E; ++m) v[m] = make_float2(1.f, 0.f);
     } else {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = psi_in[(size_t)y * NX + t + TPT * m];
+        for (int m = 0; m < E; ++m) v[m] = inrow[t + TPT * m];
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -131,40 +139,88 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
     for (int m = 0; m < E; ++m) rowp[t + TPT * m] = v[m];
 }
 
+// Row pass: ROWS rows of one snapshot per block.
+template <int NX>
+__global__ void __launch_bounds__(kRowThreads)
+row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
+                const float2* __restrict__ psi_in, const float2* __restrict__ twx,
+                int ny, int n_slices, int s, float sigma, int mode) {
+    constexpr int TPT = NX / fft::Plan<NX>::E;
+    constexpr int ROWS = kRowThreads / TPT;
+    extern __shared__ float2 smem[];
+    float2* tw = smem + 2 * ROWS * NX;
+    stage_twiddles<NX>(tw, twx);
+    const int t = threadIdx.x % TPT;
+    const int row = threadIdx.x / TPT;
+    const int y = blockIdx.x * ROWS + row;
+    const size_t snap = blockIdx.y;
+    row_body<NX>(psi + (snap * ny + y) * NX, V + ((snap * n_slices + s) * ny + y) * NX,
+                 psi_in ? psi_in + (size_t)y * NX : nullptr, mode, sigma, smem, smem + ROWS * NX, tw,
+                 t, row);
+}
+
+// Jobs of one batched launch (all of the same grid size): block row y of the
+// launch belongs to job j with start[j] <= blockIdx.y < start[j + 1].
+constexpr int kMaxBatch = 64;
+struct RowJobs {
+    int n;
+    int start[kMaxBatch + 1];
+    float2* psi[kMaxBatch];
+    const float* V[kMaxBatch];
+    const float2* psi_in[kMaxBatch];
+    int n_slices[kMaxBatch];
+    int mode[kMaxBatch];
+    float sigma[kMaxBatch];
+};
+
+__device__ __forceinline__ int find_job(const int* start, int n, int gy) {
+    int j = 0;
+    while (j + 1 < n && start[j + 1] <= gy) ++j;
+    return j;
+}
+
+template <int NX>
+__global__ void __launch_bounds__(kRowThreads)
+row_batch_kernel(const __grid_constant__ RowJobs jobs, const float2* __restrict__ twx, int ny, int s) {
+    constexpr int TPT = NX / fft::Plan<NX>::E;
+    constexpr int ROWS = kRowThreads / TPT;
+    extern __shared__ float2 smem[];
+    float2* tw = smem + 2 * ROWS * NX;
+    stage_twiddles<NX>(tw, twx);
+    const int t = threadIdx.x % TPT;
+    const int row = threadIdx.x / TPT;
+    const int y = blockIdx.x * ROWS + row;
+    const int j = find_job(jobs.start, jobs.n, blockIdx.y);
+    const size_t snap = blockIdx.y - jobs.start[j];
+    const float2* pin = jobs.psi_in[j];
+    row_body<NX>(jobs.psi[j] + (snap * ny + y) * NX, jobs.V[j] + ((snap * jobs.n_slices[j] + s) * ny + y) * NX,
+                 pin ? pin + (size_t)y * NX : nullptr, jobs.mode[j], jobs.sigma[j], smem, smem + ROWS * NX, tw,
+                 t, row);
+}
+
 template <int NY>
 struct ColCfg { static constexpr int W = (NY >= 512) ? 8 : 16; };
+// ny must be a multiple of the rows handled per row-pass block
+static_assert(kRowThreads / (384 / 24) == 16 && kRowThreads / (768 / 24) == 8, "row tiles");
 
-// Column pass: W adjacent columns of one snapshot per block.
+// Column pass body for W adjacent columns of one snapshot.
 //   forward  (CONJ = false, FFT_IN = true):  Fy -> x P BL / (nx ny) -> Fy^-1 (unless `last`)
 //   adjoint  (CONJ = true):  [Fy] -> x conj(P BL) / (nx ny) -> Fy^-1, where the leading
 //   Fy is skipped (FFT_IN = false) when the input is already in q-space.
 template <int NY, bool CONJ, bool FFT_IN>
-__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
-col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
-                const float2* __restrict__ px, const float2* __restrict__ py,
-                const int* __restrict__ kymax, int nx, int last) {
+__device__ __forceinline__ void col_body(float2* __restrict__ col, int nx, int kx,
+                                         const float2* __restrict__ px, const float2* __restrict__ py,
+                                         const int* __restrict__ kymax, int last, float2* b0, float2* b1,
+                                         const float2* tw, int t, int c) {
     using namespace fft;
     constexpr int E = Plan<NY>::E;
     constexpr int TPT = NY / E;
     constexpr int W = ColCfg<NY>::W;
-    extern __shared__ float2 smem[];
-    float2* b0 = smem;
-    float2* b1 = smem + W * NY;
-    float2* tw = smem + 2 * W * NY;
-    stage_twiddles<NY>(tw, twy);
-
-    const int c = threadIdx.x % W;
-    const int t = threadIdx.x / W;
-    const int kx = blockIdx.x * W + c;
-    const size_t snap = blockIdx.y;
-    float2* col = psi + snap * NY * (size_t)nx + kx;
     const ColLayout<W> lay{c};
-
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = col[(size_t)(t + TPT * m) * nx];
     if (FFT_IN) transform<NY, false>(v, b0, b1, t, tw, lay);
-
     const float2 pxv = __ldg(px + kx);
     const int kmax = __ldg(kymax + kx);
 #pragma unroll
@@ -177,6 +233,49 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     if (!last) transform<NY, true>(v, b0, b1, t, tw, lay);
 #pragma unroll
     for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
+}
+
+template <int NY, bool CONJ, bool FFT_IN>
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
+col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
+                const float2* __restrict__ px, const float2* __restrict__ py,
+                const int* __restrict__ kymax, int nx, int last) {
+    constexpr int W = ColCfg<NY>::W;
+    extern __shared__ float2 smem[];
+    float2* tw = smem + 2 * W * NY;
+    stage_twiddles<NY>(tw, twy);
+    const int c = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int kx = blockIdx.x * W + c;
+    const size_t snap = blockIdx.y;
+    col_body<NY, CONJ, FFT_IN>(psi + snap * NY * (size_t)nx + kx, nx, kx, px, py, kymax, last, smem,
+                               smem + W * NY, tw, t, c);
+}
+
+struct ColJobs {
+    int n;
+    int start[kMaxBatch + 1];
+    float2* psi[kMaxBatch];
+    const float2* px[kMaxBatch];
+    const float2* py[kMaxBatch];
+    const int* kymax[kMaxBatch];
+    int last[kMaxBatch];
+};
+
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
+col_batch_kernel(const __grid_constant__ ColJobs jobs, const float2* __restrict__ twy, int nx) {
+    constexpr int W = ColCfg<NY>::W;
+    extern __shared__ float2 smem[];
+    float2* tw = smem + 2 * W * NY;
+    stage_twiddles<NY>(tw, twy);
+    const int c = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int kx = blockIdx.x * W + c;
+    const int j = find_job(jobs.start, jobs.n, blockIdx.y);
+    const size_t snap = blockIdx.y - jobs.start[j];
+    col_body<NY, false, true>(jobs.psi[j] + snap * NY * (size_t)nx + kx, nx, kx, jobs.px[j], jobs.py[j],
+                              jobs.kymax[j], jobs.last[j], smem, smem + W * NY, tw, t, c);
 }
 
 // Adjoint row pass of slice s.  g holds the gradient (k_x, y) rows after the
@@ -264,8 +363,7 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<NX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void*)row_pass_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / ROWS, n_t);
     row_pass_kernel<NX><<<grid, kRowThreads, smem, st>>>(psi, V, psi_in, twx, ny, n_slices, s, sigma, mode);
@@ -302,8 +400,7 @@ cudaError_t launch_row_back(float2* g, const float2* state, const float* V, floa
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(row_back_kernel<NX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void*)row_back_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / ROWS, n_t);
     row_back_kernel<NX><<<grid, kRowThreads, smem, st>>>(g, state, V, dV, psi_in, twx, ny, n_slices, s,
@@ -319,6 +416,8 @@ cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_
         case 256: return launch_row<256>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
         case 512: return launch_row<512>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
         case 1024: return launch_row<1024>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+        case 384: return launch_row<384>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+        case 768: return launch_row<768>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -331,7 +430,54 @@ cudaError_t dispatch_col(int ny, float2* psi, const float2* twy, const float2* p
         case 256: return launch_col<256>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
         case 512: return launch_col<512>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
         case 1024: return launch_col<1024>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 384: return launch_col<384>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 768: return launch_col<768>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
     }
+    return cudaErrorInvalidValue;
+}
+
+template <int NX>
+cudaError_t launch_row_batch(const RowJobs& jobs, const float2* twx, int ny, int total, int s, cudaStream_t st) {
+    constexpr int TPT = NX / fft::Plan<NX>::E;
+    constexpr int ROWS = kRowThreads / TPT;
+    const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
+    cudaError_t e = ensure_smem((const void*)row_batch_kernel<NX>, (int)smem);
+    if (e != cudaSuccess) return e;
+    row_batch_kernel<NX><<<dim3(ny / ROWS, total), kRowThreads, smem, st>>>(jobs, twx, ny, s);
+    return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t launch_col_batch(const ColJobs& jobs, const float2* twy, int nx, int total, cudaStream_t st) {
+    constexpr int TPT = NY / fft::Plan<NY>::E;
+    constexpr int W = ColCfg<NY>::W;
+    const size_t smem = (2 * W * NY + fft::TwSize<NY>::value) * sizeof(float2);
+    cudaError_t e = ensure_smem((const void*)col_batch_kernel<NY>, (int)smem);
+    if (e != cudaSuccess) return e;
+    col_batch_kernel<NY><<<dim3(nx / W, total), W * TPT, smem, st>>>(jobs, twy, nx);
+    return cudaGetLastError();
+}
+
+#define TACAW_SIZE_SWITCH(n, CALL)                  \
+    switch (n) {                                    \
+        case 64: { constexpr int N_ = 64; CALL; }   \
+        case 128: { constexpr int N_ = 128; CALL; } \
+        case 256: { constexpr int N_ = 256; CALL; } \
+        case 384: { constexpr int N_ = 384; CALL; } \
+        case 512: { constexpr int N_ = 512; CALL; } \
+        case 768: { constexpr int N_ = 768; CALL; } \
+        case 1024: { constexpr int N_ = 1024; CALL; } \
+    }
+
+cudaError_t dispatch_row_batch(int nx, const RowJobs& jobs, const float2* twx, int ny, int total, int s,
+                               cudaStream_t st) {
+    TACAW_SIZE_SWITCH(nx, return launch_row_batch<N_>(jobs, twx, ny, total, s, st));
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_col_batch(int ny, const ColJobs& jobs, const float2* twy, int nx, int total,
+                               cudaStream_t st) {
+    TACAW_SIZE_SWITCH(ny, return launch_col_batch<N_>(jobs, twy, nx, total, st));
     return cudaErrorInvalidValue;
 }
 
@@ -344,6 +490,8 @@ cudaError_t dispatch_row_back(int nx, float2* g, const float2* state, const floa
         case 256: return launch_row_back<256>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
         case 512: return launch_row_back<512>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
         case 1024: return launch_row_back<1024>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
+        case 384: return launch_row_back<384>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
+        case 768: return launch_row_back<768>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -351,7 +499,7 @@ cudaError_t dispatch_row_back(int nx, float2* g, const float2* state, const floa
 }  // namespace
 
 bool multislice_size_supported(int n) {
-    return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+    return n == 64 || n == 128 || n == 256 || n == 384 || n == 512 || n == 768 || n == 1024;
 }
 
 struct MsTables {
@@ -398,6 +546,94 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
     if (psi_sum) {
         const size_t nq = (size_t)g.nx * g.ny;
         snapshot_sum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(psi_q, psi_sum, n_t, nq);
+        TACAW_LAUNCH_CHECK();
+    }
+    return TACAW_OK;
+}
+
+// ------------------------------------------------------------------ batch
+size_t multislice_batch_ws_bytes(const tacaw_job* jobs, int n_jobs) {
+    Carver cv(nullptr);
+    for (int j = 0; j < n_jobs; ++j) carve_ms(cv, jobs[j].grid);
+    return cv.bytes();
+}
+
+// Uneven jobs in one call: per-job set-up tables, then for every slice index
+// one row launch and one column launch per grid size covering all jobs of
+// that size that still have slices left (in chunks of at most kMaxBatch jobs
+// and 65535 snapshots), so small jobs share launches with large ones.
+int multislice_batch_run(const tacaw_job* jobs, int n_jobs, void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    std::vector<MsTables> tb(n_jobs);
+    std::vector<float> sigma(n_jobs);
+    int max_ns = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const tacaw_grid& g = jobs[j].grid;
+        tb[j] = carve_ms(cv, g);
+        double lam = 0.0, sig = 0.0;
+        beam_constants(g.kev, &lam, &sig);
+        sigma[j] = (float)sig;
+        const double qmax = g.bandlimit * fmin((double)g.nx / (2.0 * g.lx), (double)g.ny / (2.0 * g.ly));
+        const int nmax = g.nx > g.ny ? g.nx : g.ny;
+        ms_setup_kernel<<<(nmax + 127) / 128, 128, 0, st>>>(tb[j].twx, tb[j].twy, tb[j].px, tb[j].py,
+                                                           tb[j].kymax, g.nx, g.ny, g.lx, g.ly,
+                                                           lam * g.dz, qmax * qmax);
+        TACAW_LAUNCH_CHECK();
+        if (jobs[j].n_t > 0) max_ns = max_ns > g.n_slices ? max_ns : g.n_slices;
+    }
+    std::vector<char> used(n_jobs);
+    for (int s = 0; s < max_ns; ++s) {
+        std::fill(used.begin(), used.end(), 0);
+        for (int j0 = 0; j0 < n_jobs; ++j0) {
+            const tacaw_job& a = jobs[j0];
+            if (used[j0] || a.n_t <= 0 || s >= a.grid.n_slices) continue;
+            // all remaining jobs of this grid size with slice s to do, in chunks
+            std::vector<int> group;
+            for (int j = j0; j < n_jobs; ++j) {
+                const tacaw_job& b = jobs[j];
+                if (!used[j] && b.n_t > 0 && s < b.grid.n_slices && b.grid.nx == a.grid.nx &&
+                    b.grid.ny == a.grid.ny) {
+                    group.push_back(j);
+                    used[j] = 1;
+                }
+            }
+            size_t gi = 0;
+            while (gi < group.size()) {
+                RowJobs rj;
+                ColJobs cj;
+                rj.n = cj.n = 0;
+                int total = 0;
+                while (gi < group.size() && rj.n < kMaxBatch && total + jobs[group[gi]].n_t <= 65535) {
+                    const int j = group[gi++];
+                    const tacaw_job& b = jobs[j];
+                    const int k = rj.n++;
+                    cj.n = rj.n;
+                    rj.start[k] = cj.start[k] = total;
+                    rj.psi[k] = cj.psi[k] = (float2*)b.psi_q;
+                    rj.V[k] = b.V;
+                    rj.psi_in[k] = (const float2*)b.psi_in;
+                    rj.n_slices[k] = b.grid.n_slices;
+                    rj.mode[k] = s > 0 ? 0 : (b.psi_in ? 2 : 1);
+                    rj.sigma[k] = sigma[j];
+                    cj.px[k] = tb[j].px;
+                    cj.py[k] = tb[j].py;
+                    cj.kymax[k] = tb[j].kymax;
+                    cj.last[k] = (s + 1 == b.grid.n_slices) ? 1 : 0;
+                    total += b.n_t;
+                }
+                rj.start[rj.n] = cj.start[cj.n] = total;
+                const int first = group[0];
+                TACAW_CUDA_CHECK(dispatch_row_batch(a.grid.nx, rj, tb[first].twx, a.grid.ny, total, s, st));
+                TACAW_CUDA_CHECK(dispatch_col_batch(a.grid.ny, cj, tb[first].twy, a.grid.nx, total, st));
+            }
+        }
+    }
+    for (int j = 0; j < n_jobs; ++j) {
+        if (!jobs[j].psi_sum || jobs[j].n_t <= 0) continue;
+        const size_t nq = (size_t)jobs[j].grid.nx * jobs[j].grid.ny;
+        snapshot_sum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>((const float2*)jobs[j].psi_q,
+                                                                         (double2*)jobs[j].psi_sum,
+                                                                         jobs[j].n_t, nq);
         TACAW_LAUNCH_CHECK();
     }
     return TACAW_OK;

@@ -75,7 +75,7 @@ extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, cons
                       isfinite(grid->bandlimit),
                   TACAW_EINVAL, "%s: bad grid", fn);
     TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny),
-                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 512, 1024}", fn,
+                  TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     const size_t need = multislice_ws_bytes(*grid);
     TACAW_REQUIRE(need <= kStaticScratchBytes, TACAW_EINVAL,

@@ -581,8 +581,7 @@ static int check_tables(const tacaw_grid& g, const PotParams& p) {
 static int run_binning(const PotParams& p, int n_t, const float* pos, const int* species, PotWs& w,
                        cudaStream_t st) {
     const size_t bin_smem = (size_t)p.n_bins * sizeof(int);
-    TACAW_CUDA_CHECK(cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)bin_smem));
+    TACAW_CUDA_CHECK(ensure_smem((const void*)bin_kernel, (int)bin_smem));
     bin_kernel<<<n_t, kBinThreads, bin_smem, st>>>(pos, species, p, w.bin_off, w.binned, w.binned_px);
     TACAW_LAUNCH_CHECK();
     return TACAW_OK;
@@ -627,13 +626,13 @@ int potential_backward_run(const tacaw_grid& g, int n_t, int n_atoms, const floa
     const int cpl = ((g.nx + kSegs - 1) / kSegs + 31) / 32;
     const int dsm = (int)(kBandRows * g.nx * sizeof(float));
     if (cpl <= 1) {
-        TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_backward_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_backward_kernel<1>, dsm));
         potential_backward_kernel<1><<<grid, kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px, p, dV, partial);
     } else if (cpl == 2) {
-        TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_backward_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_backward_kernel<2>, dsm));
         potential_backward_kernel<2><<<grid, kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px, p, dV, partial);
     } else {
-        TACAW_CUDA_CHECK(cudaFuncSetAttribute(potential_backward_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_backward_kernel<4>, dsm));
         potential_backward_kernel<4><<<grid, kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px, p, dV, partial);
     }
     TACAW_LAUNCH_CHECK();

@@ -376,8 +376,7 @@ int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega,
     if (!rc) rc = make_map(&mbh, w.bhi, (size_t)g.n_ntiles * TN, g.k2, TN);
     if (!rc) rc = make_map(&mbl, w.blo, (size_t)g.n_ntiles * TN, g.k2, TN);
     if (rc) return rc;
-    TACAW_CUDA_CHECK(cudaFuncSetAttribute(tc_power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)TC_SMEM));
+    TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel, (int)TC_SMEM));
     const float scale = (float)(1.0 / ((double)n_t * (double)n_t));
     const unsigned blocks = (unsigned)(g.n_mtiles * g.n_ntiles);
     tc_power_kernel<<<blocks, TC_THREADS, TC_SMEM, st>>>(mah, mal, mbh, mbl, kubo ? w.kubo : nullptr, out, nq,

@@ -107,7 +107,7 @@ def _smooth_potential(g, n_t, seed):
 
 
 @pytest.mark.parametrize("nx,ny", [(64, 64), (128, 128), (256, 256), (512, 512), (1024, 1024),
-                                   (128, 64), (64, 256)])
+                                   (128, 64), (64, 256), (384, 384), (768, 768), (384, 128), (256, 768)])
 def test_multislice_matches_oracle(api, nx, ny):
     d = 0.25
     g = _grid(nx, ny, nx * d, ny * d, 3, 2.0, kev=100.0)

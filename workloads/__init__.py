@@ -20,5 +20,6 @@ from .configs import (  # noqa: F401
     Workload,
     GridSpec,
     WORKLOADS,
+    batching_jobs,
     build_inputs,
 )

@@ -110,6 +110,41 @@ WORKLOADS = {
 }
 
 
+def batching_jobs(n_jobs=64, seed0=1000, sizes=(128, 256, 384, 512, 768), slices=(10, 150),
+                  snapshots=(512, 4096), n_modes=40):
+    """Uneven independent trajectories (one Workload per job, seed seed0 + j).
+
+    Draw order from default_rng(seed): grid size N (uniform over `sizes`),
+    slice count, snapshot count (uniform integers, inclusive bounds), number of
+    species (1-3), then per species the amplitude U[10, 30] V*A and width
+    U[0.25, 0.40] A.  The fcc cell keeps the 0.158203125 A pixel of the
+    paper-scale grid (N / 25.6 cells of 4.05 A laterally), enough cells along z
+    to fill the slices; species are assigned per site in ``build_inputs``.
+    """
+    jobs = []
+    for j in range(n_jobs):
+        seed = seed0 + j
+        rng = np.random.default_rng(seed)
+        n = int(rng.choice(sizes))
+        n_s = int(rng.integers(slices[0], slices[1] + 1))
+        n_t = int(rng.integers(snapshots[0], snapshots[1] + 1))
+        n_sp = int(rng.integers(1, 4))
+        amp = rng.uniform(10.0, 30.0, n_sp)
+        sig = rng.uniform(0.25, 0.40, n_sp)
+        cells = int(round(n / 25.6))
+        cz = int(np.ceil(n_s * 2.0 / 4.05))
+        lx = cells * 4.05
+        jobs.append(Workload(
+            name=f"batch_job_{j}", lattice="fcc", ncell=(cells, cells, cz), a=4.05, mass_u=26.98,
+            grid=GridSpec(n, n, lx, lx, n_s, 2.0, 0.0, 200.0),
+            n_t=n_t, dt_fs=5.0, n_modes=n_modes, seed=seed + 100000,
+            amp_sigma=tuple((float(a), float(b)) for a, b in zip(amp, sig)),
+            n_lo=(-cells, -cells, -cz), n_hi=(cells, cells, cz),
+            extra={"n_species": n_sp},
+        ))
+    return jobs
+
+
 @dataclass
 class Inputs:
     workload: Workload
@@ -130,12 +165,14 @@ class Inputs:
 def build_inputs(w: Workload) -> Inputs:
     """Build the crystal and modes of a workload.
 
-    Draw order from default_rng(w.seed): mode energies (if not fixed), then
-    wave-vector indices, polarisations and phases (see ``draw_modes``).
+    Draw order from default_rng(w.seed): species per site (if several), mode
+    energies (if not fixed), then wave-vector indices, polarisations and
+    phases (see ``draw_modes``).
     """
     rng = np.random.default_rng(w.seed)
     maker = simple_cubic if w.lattice == "sc" else fcc
-    crystal = maker(w.ncell, w.a, w.mass_u)
+    n_species = int(w.extra.get("n_species", 1))
+    crystal = maker(w.ncell, w.a, w.mass_u, n_species=n_species, rng=rng if n_species > 1 else None)
     if w.mode_energies is not None:
         energies = np.asarray(w.mode_energies, dtype=np.float64)
     else:
