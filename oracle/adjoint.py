@@ -119,7 +119,8 @@ def potential_backward(g: Grid, pos, species, amp_sigma, g_v):
         ddx = np.mod(x - pos[a, 0] + g.lx / 2.0, g.lx) - g.lx / 2.0
         ddy = np.mod(y - pos[a, 1] + g.ly / 2.0, g.ly) - g.ly / 2.0
         r2 = ddx[None, :] ** 2 + ddy[:, None] ** 2
-        prof = np.exp(-r2 / (2.0 * sig * sig)) * (r2 <= (6.0 * sig) ** 2)
+        inside = (np.abs(ddx)[None, :] <= 6.0 * sig) & (np.abs(ddy)[:, None] <= 6.0 * sig)
+        prof = np.exp(-r2 / (2.0 * sig * sig)) * inside
         w = slice_weights(pos[a, 2], sig, g)
         dw = _dweight_dsigma(pos[a, 2], sig, g)
         gp = np.einsum("syx,yx->s", g_v, prof)                # sum_pixels g_v * profile

@@ -18,8 +18,8 @@ Readings taken where the paper is silent (each one listed in the design doc):
 
 * Atoms are isotropic 3-D Gaussians; ``amp`` is the peak of the z-projection
   (V*A), so the projected profile is amp*exp(-rho^2/(2 s^2)).  Laterally the
-  profile is truncated to the disc rho <= 6 s and summed with the minimum
-  periodic image.
+  profile is truncated to the square |dx|, |dy| <= 6 s (so that it stays
+  exactly separable in x and y) and summed with the minimum periodic image.
 * An atom is split over slices by the fraction of its z-Gaussian inside each
   slice (differences of erf); the first slice reaches -inf and the last +inf;
   slices that do not meet [z - 6 s, z + 6 s] get weight 0.
@@ -141,7 +141,7 @@ def projected_potential(g: Grid, pos, species, amp_sigma) -> np.ndarray:
     """Slice potentials v_s(x_i, y_j) in V*Angstrom, shape (n_slices, ny, nx).
 
     v_s(r) = sum_a amp_a exp(-|r - R_a|^2 / (2 s_a^2)) w_s(z_a) over atoms
-    whose minimum-image lateral distance is <= 6 s_a; pixel centres are
+    whose minimum-image offsets satisfy |dx|, |dy| <= 6 s_a; pixel centres are
     x_i = i * lx / nx, y_j = j * ly / ny.  Each atom is evaluated on the
     small window of pixels that can lie within its cut-off.
     """
@@ -166,7 +166,8 @@ def projected_potential(g: Grid, pos, species, amp_sigma) -> np.ndarray:
         ddx = ii * dx - p[:, 0:1]
         ddy = jj * dy - p[:, 1:2]
         r2 = ddx[:, None, :] ** 2 + ddy[:, :, None] ** 2               # (Na, wy, wx)
-        gauss = amp * np.exp(-r2 / (2.0 * sig * sig)) * (r2 <= rc * rc)
+        inside = (np.abs(ddx)[:, None, :] <= rc) & (np.abs(ddy)[:, :, None] <= rc)
+        gauss = amp * np.exp(-r2 / (2.0 * sig * sig)) * inside
         flat = (np.mod(jj, g.ny)[:, :, None] * g.nx + np.mod(ii, g.nx)[:, None, :])
         for s in np.nonzero(np.any(w != 0.0, axis=0))[0]:
             contrib = gauss * w[:, s][:, None, None]
@@ -186,7 +187,8 @@ def projected_potential_bruteforce(g: Grid, pos, species, amp_sigma) -> np.ndarr
         ddx = np.mod(x - pos[a, 0] + g.lx / 2.0, g.lx) - g.lx / 2.0
         ddy = np.mod(y - pos[a, 1] + g.ly / 2.0, g.ly) - g.ly / 2.0
         r2 = ddx[None, :] ** 2 + ddy[:, None] ** 2
-        prof = amp * np.exp(-r2 / (2.0 * sig * sig)) * (r2 <= (6.0 * sig) ** 2)
+        inside = (np.abs(ddx)[None, :] <= 6.0 * sig) & (np.abs(ddy)[:, None] <= 6.0 * sig)
+        prof = amp * np.exp(-r2 / (2.0 * sig * sig)) * inside
         w = slice_weights(pos[a, 2], sig, g)
         v += w[:, None, None] * prof[None]
     return v

@@ -70,7 +70,8 @@ def _pot_variant(width2=2.0, shift=0.0, swap=False):
             ddx = np.mod(x - px + g.lx / 2, g.lx) - g.lx / 2
             ddy = np.mod(y - py + g.ly / 2, g.ly) - g.ly / 2
             r2 = ddx[None, :] ** 2 + ddy[:, None] ** 2
-            prof = amp * np.exp(-r2 / (width2 * sig * sig)) * (r2 <= (6 * sig) ** 2)
+            inside = (np.abs(ddx)[None, :] <= 6 * sig) & (np.abs(ddy)[:, None] <= 6 * sig)
+            prof = amp * np.exp(-r2 / (width2 * sig * sig)) * inside
             v += T.slice_weights(pos[a, 2], sig, g)[:, None, None] * prof[None]
         return v
     return pot

@@ -188,8 +188,9 @@ def test_potential_integral_sum_rule():
     v = O.projected_potential(g, pos, species, amp_sigma)
     d2 = (g.lx / g.nx) * (g.ly / g.ny)
     ref = sum(amp_sigma[s, 0] * 2 * np.pi * amp_sigma[s, 1] ** 2 for s in species)
-    # the 6-sigma disc keeps 1 - exp(-18) of each Gaussian
-    assert v.sum() * d2 == pytest.approx(ref * (1 - np.exp(-18.0)), rel=1e-9)
+    # the 6-sigma square keeps erf(6/sqrt2)^2 of each Gaussian
+    from scipy.special import erf as _erf
+    assert v.sum() * d2 == pytest.approx(ref * _erf(6.0 / np.sqrt(2.0)) ** 2, rel=1e-9)
 
 
 def test_potential_fourier_transform_analytic():
