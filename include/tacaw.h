@@ -96,7 +96,7 @@ int tacaw_beam_constants(double kev, double* lambda_A, double* sigma_e);
  *
  *   v_s(r) = sum_a amp_a exp(-|r - R_a|^2 / (2 s_a^2)) w_s(z_a)
  *
- * over atoms whose minimum-image lateral distance is <= 6 s_a (each atom an
+ * over atoms whose minimum-image lateral offsets satisfy |dx|, |dy| <= 6 s_a (each atom an
  * isotropic 3-D Gaussian whose z-projection peaks at amp_a, in V*A), with
  * w_s(z) = (erf((z_{s+1} - z)/(sqrt2 s)) - erf((z_s - z)/(sqrt2 s))) / 2 the
  * fraction of the atom inside slice s (0 if the slice misses

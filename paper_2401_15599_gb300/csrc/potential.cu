@@ -5,7 +5,8 @@
 //   v_s(r) = sum_a amp_a exp(-|r - R_a|^2 / (2 s_a^2)) w_s(z_a)
 //   w_s(z) = (erf((z_{s+1} - z)/(sqrt2 s)) - erf((z_s - z)/(sqrt2 s))) / 2
 //
-// Laterally the Gaussian is cut at rho <= 6 s with the minimum periodic image;
+// Laterally the Gaussian is cut to the square |dx|, |dy| <= 6 s (minimum
+// periodic image), which keeps it separable in x and y;
 // slices that do not meet [z - 6 s, z + 6 s] get weight 0; the first slice
 // extends to -inf and the last to +inf.
 //
@@ -366,8 +367,8 @@ potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ bin
                 if (dx2 > rc2) continue;
                 const float gx = aw * expf(-dx2 * inv2s2);
 #pragma unroll
-                for (int r = 0; r < kBandRows; ++r)
-                    if (dx2 + sm.dy2[c][r] <= rc2) acc[k][r] += __float2int_rn(gx * sm.gy[c][r] * kFixScale);
+                for (int r = 0; r < kBandRows; ++r)   // square cut-off: |dx|, |dy| <= 6 s
+                    if (sm.dy2[c][r] <= rc2) acc[k][r] += __float2int_rn(gx * sm.gy[c][r] * kFixScale);
             }
         }
         __syncthreads();
@@ -436,7 +437,7 @@ potential_backward_kernel(const int* __restrict__ bin_off, const float4* __restr
 #pragma unroll
                 for (int r = 0; r < kBandRows; ++r) {
                     const float r2 = dx2 + sm.dy2[c][r];
-                    if (r2 <= rc2) {
+                    if (sm.dy2[c][r] <= rc2) {             // square cut-off: |dx|, |dy| <= 6 s
                         const float gp = gtile[r * p.nx + col] * gx * sm.gy[c][r];
                         ga += gp;
                         gs += gp * r2;
