@@ -76,4 +76,21 @@ __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
     return make_float2(a.x * s, a.y * s);
 }
 
+// exp(i x) = cos x + i sin x for the transmission phase sigma_e v.  The phase
+// is small in practice, so |x| <= 0.5 uses the Taylor series of sin to x^9
+// and of cos to x^10 (truncation below 2e-11, i.e. far under FP32 rounding),
+// evaluated by Horner's rule; larger phases fall back to sincosf.
+__device__ __forceinline__ void phase_sincos(float x, float* s, float* c) {
+    if (fabsf(x) <= 0.5f) {
+        const float x2 = x * x;
+        const float ps = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f),
+                                       -1.f / 6.f), 1.f);
+        *s = x * ps;
+        *c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f),
+                                        1.f / 24.f), -0.5f), 1.f);
+    } else {
+        sincosf(x, s, c);
+    }
+}
+
 }  // namespace tacaw

@@ -131,7 +131,7 @@ __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float*
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float sn, cs;
-        sincosf(sigma * __ldcs(vrow + t + TPT * m), &sn, &cs);
+        phase_sincos(sigma * __ldcs(vrow + t + TPT * m), &sn, &cs);
         v[m] = cmul(v[m], make_float2(cs, sn));
     }
     transform<NX, false>(v, b0, b1, t, tw, lay);
@@ -327,7 +327,7 @@ row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const 
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float sn, cs;
-        sincosf(sigma * __ldg(V + vrow_off + t + TPT * m), &sn, &cs);
+        phase_sincos(sigma * __ldg(V + vrow_off + t + TPT * m), &sn, &cs);
         const float2 tt = make_float2(cs, sn);
         const float2 chi = cmul(tt, sv[m]);
         const float2 gc = cmulc(gv[m], chi);            // g_chi conj(chi)
