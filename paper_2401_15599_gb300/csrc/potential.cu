@@ -11,15 +11,19 @@
 // extends to -inf and the last to +inf.
 //
 // Two kernels per call:
-//  1. bin_kernel (one block per snapshot): counting sort of the atoms into
-//     bins (slab of the atom centre) x (band of kBandRows grid rows).
-//  2. potential_kernel (one block per band, slice and snapshot): the block
-//     owns kBandRows x nx pixels in shared memory and adds the contributions
-//     of the atoms of the neighbouring bins.  Sums are kept in 64-bit fixed
-//     point (2^-32 V*A), so the result does not depend on the order in which
-//     atoms arrive: identical configurations give bit-identical potentials.
+//  1. bin_kernel (one block per snapshot): stable counting sort of the atoms
+//     into bins (slab of the atom centre) x (band of rows) x (tile of columns).
+//     Within a bin the atoms keep their input order, so the bins of identical
+//     configurations are identical.
+//  2. potential_tile_kernel (one block per 32 x 64 pixel tile, slice and
+//     snapshot): the separable Gaussian makes the tile a sum of outer products,
+//     V_tile = sum_a gy_a (x) gx_a, accumulated in FP32 registers over the
+//     candidate atoms in bin order (a fixed order: identical configurations give
+//     bit-identical potentials).
+// The adjoint (potential_backward_kernel) keeps one block per band of 8 rows.
 
 #include <math.h>
+#include <stdint.h>
 
 #include "common.cuh"
 
@@ -27,22 +31,19 @@ namespace tacaw {
 
 namespace {
 
-constexpr int kBandRows = 8;
+constexpr int kBandRows = 8;             // rows per band of the adjoint kernel
 constexpr int kBinThreads = 1024;
 constexpr int kPotThreads = 256;
-// Fixed point: each contribution is rounded to a multiple of 2^-20 V*A as a
-// 32-bit integer (so one contribution must stay below 2048 V*A; the host
-// checks the amplitudes) and summed exactly into a 64-bit accumulator.
-// 64-bit float<->int conversions are avoided on purpose: on this GPU they
-// run on the FP64 pipe.
-constexpr float kFixScale = 1048576.0f;              // 2^20
-constexpr float kFixInv = 9.5367431640625e-07f;      // 2^-20
+constexpr int kMaxBinInts = 48 * 1024;   // bins per snapshot held by the histogram (192 KiB)
 constexpr float kMaxAmp = 2000.0f;
 
 struct PotParams {
     int nx, ny, n_slices, n_atoms, n_species;
-    int n_bands, n_bins, slab_reach, band_reach;
-    float lx, ly, dx, dy, inv_dx, inv_lx, inv_ly, z0, dz, inv_dz, inv_band_h;
+    // bins: (slab, band of band_h rows, tile of ctile_w columns)
+    int n_bands, n_ctiles, n_bins, band_h, ctile_w;
+    int slab_reach, band_reach, ctile_reach;   // neighbouring bins that can reach a tile
+    int reach_x, reach_y;                      // ceil(6 s_max / d): pixels an atom reaches
+    float lx, ly, dx, dy, inv_dx, z0, dz, inv_dz;
     double dx_d, dy_d, inv_dx_d, inv_dy_d;
     float amp[TACAW_MAX_SPECIES], sigma[TACAW_MAX_SPECIES];
 };
@@ -50,9 +51,9 @@ struct PotParams {
 // An atom's position is split once, in FP64, into the pixel (ic, jc) that
 // holds it and a small offset (fx, fy) from that pixel, so that later
 // pixel-atom distances k*d - f carry no rounding from large coordinates.
-// Its band is the exact integer row band of jc; its slab comes from z with
-// explicit round-to-nearest operations (the bin is computed twice per atom,
-// count then scatter, and both passes must agree).
+// The binned copy keeps (ic, jc) wrapped into the box.
+// Its slab comes from z with explicit round-to-nearest operations (the bin is
+// computed twice per atom, count then scatter, and both passes must agree).
 struct Split {
     int ic, jc;
     float fx, fy;
@@ -71,15 +72,24 @@ __device__ __forceinline__ Split split_position(float x, float y, const PotParam
     return r;
 }
 
-__device__ __forceinline__ int atom_bin(int jc, float z, const PotParams& p) {
-    int jw = jc % p.ny;
-    if (jw < 0) jw += p.ny;
-    const int band = jw / kBandRows;
-    int slab = (int)floorf(__fmul_rn(__fsub_rn(z, p.z0), p.inv_dz));
-    slab = min(max(slab, 0), p.n_slices - 1);
-    return slab * p.n_bands + band;
+__device__ __forceinline__ int wrap(int k, int n) {
+    k %= n;
+    return k < 0 ? k + n : k;
 }
 
+__device__ __forceinline__ int atom_bin(const Split& sp, float z, const PotParams& p) {
+    const int band = wrap(sp.jc, p.ny) / p.band_h;
+    const int ct = wrap(sp.ic, p.nx) / p.ctile_w;
+    int slab = (int)floorf(__fmul_rn(__fsub_rn(z, p.z0), p.inv_dz));
+    slab = min(max(slab, 0), p.n_slices - 1);
+    return (slab * p.n_bands + band) * p.n_ctiles + ct;
+}
+
+// One block per snapshot.  Counts per bin (shared-memory histogram), an
+// exclusive scan into bin_off, then a stable scatter: atoms go in rounds of
+// one per thread; within a warp, atoms of the same bin take consecutive slots
+// by lane (match + popc), and the warps of a round claim their slots one after
+// the other, so every bin lists its atoms in input order.
 __global__ void __launch_bounds__(kBinThreads)
 bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotParams p,
            int* __restrict__ bin_off, float4* __restrict__ binned, int2* __restrict__ binned_px) {
@@ -91,7 +101,7 @@ bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotPa
     __syncthreads();
     for (int a = threadIdx.x; a < p.n_atoms; a += blockDim.x) {
         const Split sp = split_position(P[3 * a], P[3 * a + 1], p);
-        atomicAdd(&cnt[atom_bin(sp.jc, P[3 * a + 2], p)], 1);
+        atomicAdd(&cnt[atom_bin(sp, P[3 * a + 2], p)], 1);
     }
     __syncthreads();
 
@@ -134,21 +144,326 @@ bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotPa
 
     float4* out = binned + t * (size_t)p.n_atoms;
     int2* out_px = binned_px + t * (size_t)p.n_atoms;
-    for (int a = threadIdx.x; a < p.n_atoms; a += blockDim.x) {
-        const float z = P[3 * a + 2];
-        const Split sp = split_position(P[3 * a], P[3 * a + 1], p);
-        const int slot = atomicAdd(&cnt[atom_bin(sp.jc, z, p)], 1);
-        // a species of -1 marks an atom that is skipped (non-finite or absurd position)
-        const int spc = (sp.ok && fabsf(z) < 1e9f) ? __ldg(species + a) : -1;
-        out[slot] = make_float4(sp.fx, sp.fy, z, __int_as_float(spc));
-        out_px[slot] = make_int2(sp.ic, sp.jc);
+    const unsigned lt = (1u << lane) - 1u;
+    const int n_warps = blockDim.x / 32;
+    for (int base = 0; base < p.n_atoms; base += blockDim.x) {
+        const int a = base + threadIdx.x;
+        const bool valid = a < p.n_atoms;
+        float z = 0.f;
+        Split sp{0, 0, 0.f, 0.f, false};
+        int bin = -1;
+        if (valid) {
+            z = P[3 * a + 2];
+            sp = split_position(P[3 * a], P[3 * a + 1], p);
+            bin = atom_bin(sp, z, p);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        const int leader = __ffs(peers) - 1;
+        int slot = 0;
+        for (int w = 0; w < n_warps; ++w) {         // warps claim their slots in order
+            if (wid == w && valid && lane == leader) {
+                slot = cnt[bin];
+                cnt[bin] = slot + __popc(peers);
+            }
+            __syncthreads();
+        }
+        slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(peers & lt);
+        if (valid) {
+            // a species of -1 marks an atom that is skipped (non-finite or absurd position)
+            const int spc = (sp.ok && fabsf(z) < 1e9f) ? __ldg(species + a) : -1;
+            out[slot] = make_float4(sp.fx, sp.fy, z, __int_as_float(spc));
+            out_px[slot] = make_int2(wrap(sp.ic, p.nx), wrap(sp.jc, p.ny));
+        }
     }
 }
 
-// Candidate atoms of one block, gathered per chunk of source atoms.
+// Neighbouring bins of a tile (slabs s +- slab_reach, bands +- band_reach,
+// column tiles +- ctile_reach around the tile's own bin, each range cut to the
+// whole axis when it would wrap onto itself) as one flat list: warp 0 loads the
+// ranges and scans the counts into bin_start / bin_cum.  Returns the number of
+// source atoms (after a block barrier).
+constexpr int kMaxNbBins = 64;
+
+__device__ int load_bins(int* bin_start, int* bin_cum, const PotParams& p, const int* __restrict__ off,
+                         int s, int band, int ctile, int* n_nb_out) {
+    const int lane = threadIdx.x & 31;
+    const int slab0 = max(0, s - p.slab_reach), slab1 = min(p.n_slices - 1, s + p.slab_reach);
+    const bool all_b = 2 * p.band_reach + 1 >= p.n_bands;
+    const bool all_c = 2 * p.ctile_reach + 1 >= p.n_ctiles;
+    const int nb = all_b ? p.n_bands : 2 * p.band_reach + 1;
+    const int nc = all_c ? p.n_ctiles : 2 * p.ctile_reach + 1;
+    const int n_nb = nb * nc * (slab1 - slab0 + 1);
+    if (threadIdx.x < 32) {
+        int carry = 0;
+        for (int base = 0; base < n_nb; base += 32) {
+            const int i = base + lane;
+            int cnt = 0, start = 0;
+            if (i < n_nb) {
+                const int slab = slab0 + i / (nb * nc);
+                const int kb = (i / nc) % nb, kc = i % nc;
+                const int b = all_b ? kb : wrap(band - p.band_reach + kb, p.n_bands);
+                const int c = all_c ? kc : wrap(ctile - p.ctile_reach + kc, p.n_ctiles);
+                const int bin = (slab * p.n_bands + b) * p.n_ctiles + c;
+                start = __ldg(off + bin);
+                cnt = __ldg(off + bin + 1) - start;
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (i < n_nb) {
+                bin_start[i] = start;
+                bin_cum[i] = carry + incl - cnt;
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) bin_cum[n_nb] = carry;
+    }
+    __syncthreads();
+    *n_nb_out = n_nb;
+    return bin_cum[n_nb];
+}
+
+// Source index -> atom index through the scanned bin list: the last bin whose
+// running count is <= src (never an empty bin) holds it.
+__device__ __forceinline__ int source_atom(const int* bin_start, const int* bin_cum, int n_nb, int src) {
+    int lo = 0, hi = n_nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bin_cum[mid] <= src) lo = mid; else hi = mid - 1;
+    }
+    return bin_start[lo] + (src - bin_cum[lo]);
+}
+
+// Slice weight of an atom at height z with width sg in slice [lo, hi):
+// (erf((hi - z)/(sqrt2 sg)) - erf((lo - z)/(sqrt2 sg))) / 2, open at the first
+// and last slice; `dw` receives d(weight)/d(sigma).
+__device__ __forceinline__ float slice_weight(float z, float sg, float lo, float hi, bool first,
+                                              bool lastsl, float* dw) {
+    const float kz = 0.70710678118654752f / sg;
+    const float uh = (hi - z) * kz, ul = (lo - z) * kz;
+    const float fh = lastsl ? 0.5f : 0.5f * erff(uh);
+    const float fl = first ? -0.5f : 0.5f * erff(ul);
+    if (dw) {
+        // d/dsigma of erf(u)/2 with u = (edge - z)/(sqrt2 sigma): -(u/sigma) exp(-u^2)/sqrt(pi)
+        const float dh = lastsl ? 0.f : -(uh / sg) * expf(-uh * uh) * 0.56418958354775628f;
+        const float dl = first ? 0.f : -(ul / sg) * expf(-ul * ul) * 0.56418958354775628f;
+        *dw = dh - dl;
+    }
+    return fh - fl;
+}
+
+// Nearest periodic image of a pixel offset k in (-n, n).
+__device__ __forceinline__ int nearest_image(int k, int n) {
+    if (k >= (n + 1) / 2) k -= n;
+    if (k < -(n / 2)) k += n;
+    return k;
+}
+
+// Smallest distance |k d - f| (nearest images) from an atom in pixel c, at
+// offset f, to the pixels [a, a + len), with c and a in [0, n): 0 when the
+// atom's pixel is in the range, else the nearer end of the range (the offsets
+// k run monotonically away from the atom between the ends).
+__device__ __forceinline__ float range_gap(int c, float f, int a, int len, int n, float d) {
+    int u = c - a;
+    if (u < 0) u += n;
+    if (u < len) return 0.f;
+    const float d0 = fabsf((float)nearest_image(a - c, n) * d - f);
+    const float d1 = fabsf((float)nearest_image(a + len - 1 - c, n) * d - f);
+    return fminf(d0, d1);
+}
+
+// ------------------------------------------------------------------ forward
+// One block per (tile of kTR rows x kTC columns, slice, snapshot).  Lane l of
+// every warp owns tile row l; warp w owns the 8 columns [8w, 8w + 8), so each
+// thread accumulates 8 pixels in registers.  The block
+//  1. examines the sources of the neighbouring bins, one per thread, and keeps
+//     those that reach this slice and tile as candidates (compacted in source
+//     order);
+//  2. per group of kTCand candidates tabulates the row factors
+//     gy[r] = exp(-dy^2 / 2 s^2) over the tile rows and the column factors
+//     gx[c] = amp w_s exp(-dx^2 / 2 s^2) over the tile columns (0 outside
+//     |d| <= 6 s), one warp per candidate, with a mask of the 8-column groups
+//     the candidate touches;
+//  3. lets every warp run over the candidates that touch its columns, in order:
+//     acc += gy[lane] * gx[8w .. 8w + 7].
+constexpr int kTR = 32;
+constexpr int kTC = 64;
+constexpr int kTCand = 64;               // candidates tabulated at a time
+constexpr int kTWarps = kPotThreads / 32;
+static_assert(kTC == 8 * kTWarps && kTR == 32, "tile = 32 rows x 8 columns per warp");
+
+struct TileSmem {
+    float gy[kTCand][kTR];
+    float4 gx[kTCand][kTC / 4];
+    int wmask[kTCand];
+    unsigned char wlist[kTWarps][kTCand];
+    // candidates of one pass over the sources: nearest-image pixel offsets of the
+    // tile's first row / column from the atom, the atom's offset in its pixel,
+    // amp * w_s, log2(e) / (2 s^2) and the cut-off 6 s
+    int k0y[kPotThreads], k0x[kPotThreads];
+    float fx[kPotThreads], fy[kPotThreads], aw[kPotThreads], c2[kPotThreads], rc[kPotThreads];
+    int warp_cnt[kTWarps];
+    int bin_start[kMaxNbBins], bin_cum[kMaxNbBins + 1];
+};
+
+// Exact float of a small integer (|k| < 2^22) without a conversion instruction.
+__device__ __forceinline__ float small_int_to_float(int k) {
+    return __int_as_float(0x4B400000 + k) - 12582912.0f;
+}
+
+__global__ void __launch_bounds__(kPotThreads, 6)
+potential_tile_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                      const int2* __restrict__ binned_px, PotParams p, int n_tx, int vec_out,
+                      float* __restrict__ V) {
+    extern __shared__ __align__(16) unsigned char tile_smem_raw[];
+    TileSmem& sm = *reinterpret_cast<TileSmem*>(tile_smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int r0 = (blockIdx.x / n_tx) * kTR, c0 = (blockIdx.x % n_tx) * kTC;
+    const int s = blockIdx.y;
+    const size_t t = blockIdx.z;
+    const int nrows = min(kTR, p.ny - r0), ncols = min(kTC, p.nx - c0);
+    const int half_x = (p.nx + 1) / 2, half_y = (p.ny + 1) / 2;
+    const bool first = (s == 0), lastsl = (s == p.n_slices - 1);
+    const float lo = first ? -INFINITY : p.z0 + (float)s * p.dz;
+    const float hi = lastsl ? INFINITY : p.z0 + (float)(s + 1) * p.dz;
+    const float4* atoms = binned + t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
+    int n_nb;
+    const int n_src = load_bins(sm.bin_start, sm.bin_cum, p, bin_off + t * (size_t)(p.n_bins + 1), s,
+                                r0 / p.band_h, c0 / p.ctile_w, &n_nb);
+
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+
+    for (int sb = 0; sb < n_src; sb += kPotThreads) {
+        // 1. candidates among the sources [sb, sb + kPotThreads), in source order
+        bool ok = false;
+        float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
+        int icw = 0, jcw = 0, sp = 0;
+        float rc = 0.f;
+        if (sb + (int)threadIdx.x < n_src) {
+            const int ai = source_atom(sm.bin_start, sm.bin_cum, n_nb, sb + threadIdx.x);
+            at = atoms[ai];                              // (fx, fy, z, species)
+            const int2 px = atoms_px[ai];                // (ic, jc), wrapped
+            sp = __float_as_int(at.w);
+            ok = sp >= 0 && sp < p.n_species;
+            rc = 6.0f * (ok ? p.sigma[sp] : 1.f);
+            ok = ok && (hi > at.z - rc) && (lo < at.z + rc);
+            icw = px.x;
+            jcw = px.y;
+            ok = ok && range_gap(jcw, at.y, r0, nrows, p.ny, p.dy) <= rc &&
+                 range_gap(icw, at.x, c0, ncols, p.nx, p.dx) <= rc;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) sm.warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int n_cand = 0, my_off = 0;
+#pragma unroll
+        for (int w = 0; w < kTWarps; ++w) {
+            const int c = sm.warp_cnt[w];
+            if (w < warp) my_off += c;
+            n_cand += c;
+        }
+        if (ok) {
+            const int c = my_off + __popc(bal & lt);
+            const float sg = p.sigma[sp];
+            sm.k0y[c] = nearest_image(r0 - jcw, p.ny);
+            sm.k0x[c] = nearest_image(c0 - icw, p.nx);
+            sm.fx[c] = at.x;
+            sm.fy[c] = at.y;
+            sm.aw[c] = p.amp[sp] * slice_weight(at.z, sg, lo, hi, first, lastsl, nullptr);
+            sm.c2[c] = 1.4426950408889634f * (0.5f / (sg * sg));
+            sm.rc[c] = rc;
+        }
+        __syncthreads();
+
+        for (int cb = 0; cb < n_cand; cb += kTCand) {
+            const int nc = min(kTCand, n_cand - cb);
+            // 2. factors (square cut-off |dx|, |dy| <= 6 s): lane l gives row l and
+            //    columns l, l + 32; offsets from the atom's pixel by nearest image
+            for (int c = warp; c < nc; c += kTWarps) {
+                const int cc = cb + c;
+                const int k0y = sm.k0y[cc], k0x = sm.k0x[cc];
+                const float fx = sm.fx[cc], fy = sm.fy[cc], aw = sm.aw[cc], c2 = sm.c2[cc], rcc = sm.rc[cc];
+                float gyv = 0.f, g0 = 0.f, g1 = 0.f;
+                int ky = k0y + lane;
+                if (ky >= half_y) ky -= p.ny;
+                int kx0 = k0x + lane;
+                if (kx0 >= half_x) kx0 -= p.nx;
+                int kx1 = k0x + lane + 32;
+                if (kx1 >= half_x) kx1 -= p.nx;
+                const float dy_ = small_int_to_float(ky) * p.dy - fy;
+                const float dx0 = small_int_to_float(kx0) * p.dx - fx;
+                const float dx1 = small_int_to_float(kx1) * p.dx - fx;
+                if (lane < nrows && fabsf(dy_) <= rcc) gyv = exp2f(-(dy_ * dy_) * c2);
+                if (lane < ncols && fabsf(dx0) <= rcc) g0 = aw * exp2f(-(dx0 * dx0) * c2);
+                if (lane + 32 < ncols && fabsf(dx1) <= rcc) g1 = aw * exp2f(-(dx1 * dx1) * c2);
+                sm.gy[c][lane] = gyv;
+                float* gxr = reinterpret_cast<float*>(sm.gx[c]);
+                gxr[lane] = g0;
+                gxr[lane + 32] = g1;
+                const unsigned b0 = __ballot_sync(0xffffffffu, g0 != 0.f);
+                const unsigned b1 = __ballot_sync(0xffffffffu, g1 != 0.f);
+                const int q = lane & 7;                  // lane q < 8 reports column group q
+                const unsigned grp = (q < 4 ? b0 >> (8 * q) : b1 >> (8 * (q - 4))) & 0xffu;
+                const unsigned wm = __ballot_sync(0xffffffffu, lane < 8 && grp != 0u);
+                if (lane == 0) sm.wmask[c] = (int)wm;
+            }
+            __syncthreads();
+
+            // 3. this warp's candidates, in order, then the outer-product updates
+            int cnt = 0;
+            for (int base = 0; base < nc; base += 32) {
+                const int c = base + lane;
+                const bool has = c < nc && ((sm.wmask[c] >> warp) & 1);
+                const unsigned b = __ballot_sync(0xffffffffu, has);
+                if (has) sm.wlist[warp][cnt + __popc(b & lt)] = (unsigned char)c;
+                cnt += __popc(b);
+            }
+            __syncwarp();
+#pragma unroll 2
+            for (int j = 0; j < cnt; ++j) {
+                const int c = sm.wlist[warp][j];
+                const float gyv = sm.gy[c][lane];
+                const float4 a = sm.gx[c][2 * warp], b = sm.gx[c][2 * warp + 1];
+                acc[0] = fmaf(gyv, a.x, acc[0]);
+                acc[1] = fmaf(gyv, a.y, acc[1]);
+                acc[2] = fmaf(gyv, a.z, acc[2]);
+                acc[3] = fmaf(gyv, a.w, acc[3]);
+                acc[4] = fmaf(gyv, b.x, acc[4]);
+                acc[5] = fmaf(gyv, b.y, acc[5]);
+                acc[6] = fmaf(gyv, b.z, acc[6]);
+                acc[7] = fmaf(gyv, b.w, acc[7]);
+            }
+            __syncthreads();
+        }
+        __syncthreads();                                 // the next pass rewrites the candidates
+    }
+
+    if (lane < nrows) {
+        const int cw = 8 * warp;
+        float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + r0 + lane) * p.nx + c0 + cw;
+        if (vec_out && cw + 8 <= ncols) {
+            reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (cw + k < ncols) out[k] = acc[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+// Candidate atoms of one block of the adjoint kernel, gathered per chunk of
+// source atoms.
 constexpr int kChunk = kPotThreads;      // source atoms examined per chunk
 constexpr int kSegs = kPotThreads / 32;  // one column segment per warp
-constexpr int kMaxNbBins = 64;           // neighbouring bins scanned per block
 
 struct CandSmem {
     int ic[kChunk], jc[kChunk];                 // pixel index of the atom (wrapped into the box)
@@ -162,7 +477,6 @@ struct CandSmem {
     int seg_cnt[kSegs];
     int n_cand;
     int bin_start[kMaxNbBins], bin_cum[kMaxNbBins + 1];
-    int n_nb;
 };
 
 struct Tile {
@@ -188,63 +502,17 @@ __device__ __forceinline__ Tile make_tile(const PotParams& p) {
     return tl;
 }
 
-// Neighbouring bins (slabs s +- slab_reach, bands +- band_reach) as one flat
-// list: warp 0 loads the ranges and scans the counts.  Returns the number of
-// source atoms (after a block barrier).
-__device__ int load_neighbour_bins(CandSmem& sm, const PotParams& p, const int* __restrict__ off,
-                                   const Tile& tl) {
-    const int lane = threadIdx.x & 31;
-    const int slab0 = max(0, tl.s - p.slab_reach), slab1 = min(p.n_slices - 1, tl.s + p.slab_reach);
-    const bool all_bands = 2 * p.band_reach + 1 >= p.n_bands;
-    const int nb = all_bands ? p.n_bands : 2 * p.band_reach + 1;
-    const int n_nb = nb * (slab1 - slab0 + 1);
-    if (threadIdx.x < 32) {
-        int carry = 0;
-        for (int base = 0; base < n_nb; base += 32) {
-            const int i = base + lane;
-            int cnt = 0, start = 0;
-            if (i < n_nb) {
-                const int slab = slab0 + i / nb, k = i % nb;
-                int b = all_bands ? k : tl.band - p.band_reach + k;
-                b = ((b % p.n_bands) + p.n_bands) % p.n_bands;
-                const int bin = slab * p.n_bands + b;
-                start = __ldg(off + bin);
-                cnt = __ldg(off + bin + 1) - start;
-            }
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            if (i < n_nb) {
-                sm.bin_start[i] = start;
-                sm.bin_cum[i] = carry + incl - cnt;
-            }
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (lane == 0) {
-            sm.bin_cum[n_nb] = carry;
-            sm.n_nb = n_nb;
-        }
-    }
-    __syncthreads();
-    return sm.bin_cum[sm.n_nb];
-}
-
 // Candidates of one chunk of source atoms: the atoms that reach this slice
 // and band, listed in every column segment their window touches, with their
 // per-row Gaussian factors.  Ends with a block barrier.
 __device__ void gather_chunk(CandSmem& sm, const PotParams& p, const float4* __restrict__ atoms,
-                             const int2* __restrict__ atoms_px, const Tile& tl, int c0, int n_src) {
+                             const int2* __restrict__ atoms_px, const Tile& tl, int c0, int n_src, int n_nb) {
     if (threadIdx.x < kSegs) sm.seg_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) sm.n_cand = 0;
     __syncthreads();
     const int src = c0 + threadIdx.x;
     if (src < n_src) {
-        int bi = 0;
-        while (sm.bin_cum[bi + 1] <= src) ++bi;
-        const int ai = sm.bin_start[bi] + (src - sm.bin_cum[bi]);
+        const int ai = source_atom(sm.bin_start, sm.bin_cum, n_nb, src);
         const float4 at = atoms[ai];               // (fx, fy, z, species)
         const int2 px = atoms_px[ai];              // (ic, jc)
         const int sp = __float_as_int(at.w);
@@ -259,25 +527,18 @@ __device__ void gather_chunk(CandSmem& sm, const PotParams& p, const float4* __r
         const float d0 = (float)k0 * p.dy - at.y;
         ok = ok && (d0 <= rc) && (d0 + tl.band_span >= -rc);
         if (ok) {
-            const float kz = 0.70710678118654752f / sg;
-            const float uh = (tl.hi - at.z) * kz, ul = (tl.lo - at.z) * kz;
-            const float fh = tl.lastsl ? 0.5f : 0.5f * erff(uh);
-            const float fl = tl.first ? -0.5f : 0.5f * erff(ul);
-            // d/dsigma of erf(u)/2 with u = (edge - z)/(sqrt2 sigma): -(u/sigma) exp(-u^2)/sqrt(pi)
-            const float dh = tl.lastsl ? 0.f : -(uh / sg) * expf(-uh * uh) * 0.56418958354775628f;
-            const float dl = tl.first ? 0.f : -(ul / sg) * expf(-ul * ul) * 0.56418958354775628f;
+            float dw_ds;
+            const float w = slice_weight(at.z, sg, tl.lo, tl.hi, tl.first, tl.lastsl, &dw_ds);
             const int c = atomicAdd(&sm.n_cand, 1);
-            int icw = ic % p.nx, jcw = jc % p.ny;   // pixel indices wrapped into the box
-            if (icw < 0) icw += p.nx;
-            if (jcw < 0) jcw += p.ny;
+            const int icw = ic, jcw = jc;           // binned pixel indices are wrapped into the box
             sm.ic[c] = icw;
             sm.jc[c] = jcw;
             sm.fx[c] = at.x;
             sm.fy[c] = at.y;
             sm.sp[c] = sp;
-            sm.w[c] = fh - fl;
-            sm.dw[c] = dh - dl;
-            sm.aw[c] = p.amp[sp] * (fh - fl);
+            sm.w[c] = w;
+            sm.dw[c] = dw_ds;
+            sm.aw[c] = p.amp[sp] * w;
             sm.inv2s2[c] = 0.5f / (sg * sg);
             sm.rc2[c] = rc * rc;
             // columns within the cut-off lie in [i0, i0 + wx) (one spare column each side)
@@ -328,68 +589,6 @@ __device__ __forceinline__ float col_dist2(const CandSmem& sm, const PotParams& 
     return ddx * ddx;
 }
 
-// One block per (band of kBandRows rows, slice, snapshot).  Warp w owns the
-// column segment [w * seg_w, (w + 1) * seg_w) (CPL columns per lane) and keeps
-// the band's sums for those columns in 64-bit fixed-point registers: no
-// atomics on pixels, the Gaussian is evaluated separably (one row factor per
-// candidate and row, one column factor per candidate and column), and the
-// result does not depend on the order in which candidates arrive.
-template <int CPL>
-__global__ void __launch_bounds__(kPotThreads)
-potential_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
-                 const int2* __restrict__ binned_px, PotParams p, float* __restrict__ V) {
-    __shared__ CandSmem sm;
-    const Tile tl = make_tile(p);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float4* atoms = binned + tl.t * (size_t)p.n_atoms;
-    const int2* atoms_px = binned_px + tl.t * (size_t)p.n_atoms;
-    const int n_src = load_neighbour_bins(sm, p, bin_off + tl.t * (size_t)(p.n_bins + 1), tl);
-
-    long long acc[CPL][kBandRows];
-#pragma unroll
-    for (int k = 0; k < CPL; ++k)
-#pragma unroll
-        for (int r = 0; r < kBandRows; ++r) acc[k][r] = 0;
-    const int col0 = warp * tl.seg_w;
-    const int col1 = min(col0 + tl.seg_w, p.nx);
-
-    for (int c0 = 0; c0 < n_src; c0 += kChunk) {
-        gather_chunk(sm, p, atoms, atoms_px, tl, c0, n_src);
-        const int cnt = sm.seg_cnt[warp];
-        for (int j = 0; j < cnt; ++j) {
-            const int c = sm.seg_list[warp][j];
-            const float aw = sm.aw[c], inv2s2 = sm.inv2s2[c], rc2 = sm.rc2[c];
-#pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const int col = col0 + lane + 32 * k;
-                if (col >= col1) continue;
-                const float dx2 = col_dist2(sm, p, c, col);
-                if (dx2 > rc2) continue;
-                const float gx = aw * expf(-dx2 * inv2s2);
-#pragma unroll
-                for (int r = 0; r < kBandRows; ++r)   // square cut-off: |dx|, |dy| <= 6 s
-                    if (sm.dy2[c][r] <= rc2) acc[k][r] += __float2int_rn(gx * sm.gy[c][r] * kFixScale);
-            }
-        }
-        __syncthreads();
-    }
-    // write the band (lanes on consecutive columns)
-    float* out = V + ((tl.t * p.n_slices + tl.s) * (size_t)p.ny + tl.r0) * p.nx;
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-        const int col = col0 + lane + 32 * k;
-        if (col >= col1) continue;
-#pragma unroll
-        for (int r = 0; r < kBandRows; ++r)
-            if (r < tl.nrows) {
-                // sums below 2048 V*A fit in 32 bits: convert those without the FP64 pipe
-                const long long a = acc[k][r];
-                const float f = (a == (long long)(int)a) ? (float)(int)a : (float)a;
-                out[(size_t)r * p.nx + col] = f * kFixInv;
-            }
-    }
-}
-
 // Adjoint of the potential for the per-species Gaussian parameters: with
 // P = exp(-rho^2 / 2 s^2) inside the cut-off and g = dL/dv,
 //   dL/d amp += g P w,   dL/d s += g amp P (rho^2 / s^3 w + dw/ds).
@@ -412,12 +611,14 @@ potential_backward_kernel(const int* __restrict__ bin_off, const float4* __restr
     const float* grow = dV + ((tl.t * p.n_slices + tl.s) * (size_t)p.ny + tl.r0) * p.nx;
     for (int i = threadIdx.x; i < tl.nrows * p.nx; i += blockDim.x)
         gtile[i] = __ldg(grow + i);
-    const int n_src = load_neighbour_bins(sm, p, bin_off + tl.t * (size_t)(p.n_bins + 1), tl);
+    int n_nb;
+    const int n_src = load_bins(sm.bin_start, sm.bin_cum, p, bin_off + tl.t * (size_t)(p.n_bins + 1), tl.s,
+                                tl.band, 0, &n_nb);
     const int col0 = warp * tl.seg_w;
     const int col1 = min(col0 + tl.seg_w, p.nx);
 
     for (int c0 = 0; c0 < n_src; c0 += kChunk) {
-        gather_chunk(sm, p, atoms, atoms_px, tl, c0, n_src);
+        gather_chunk(sm, p, atoms, atoms_px, tl, c0, n_src, n_nb);
         const int cnt = sm.seg_cnt[warp];
         for (int j = 0; j < cnt; ++j) {
             const int c = sm.seg_list[warp][j];
@@ -481,6 +682,7 @@ reduce_partials_kernel(const double* __restrict__ partial, size_t n_blocks, int 
     if (threadIdx.x == 0) out[i] = sh[0];
 }
 
+
 struct PotWs {
     int* bin_off;
     float4* binned;
@@ -495,7 +697,33 @@ PotWs carve_pot(Carver& cv, int n_t, int n_atoms, int n_bins) {
     return w;
 }
 
-int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* amp_sigma,
+// Bin shapes: the forward kernel bins by (slab, 32-row band, 64-column tile),
+// coarsened along x, then y, while the histogram would exceed kMaxBinInts;
+// the adjoint bins by (slab, 8-row band).
+enum class BinLayout { Tiles, Bands };
+
+struct BinShape {
+    int band_h, ctile_w, n_bands, n_ctiles;
+    long long n_bins;
+};
+
+BinShape bin_shape(const tacaw_grid& g, BinLayout lay) {
+    BinShape b;
+    b.band_h = lay == BinLayout::Tiles ? kTR : kBandRows;
+    b.ctile_w = lay == BinLayout::Tiles ? kTC : g.nx;
+    for (;;) {
+        b.n_bands = (g.ny + b.band_h - 1) / b.band_h;
+        b.n_ctiles = (g.nx + b.ctile_w - 1) / b.ctile_w;
+        b.n_bins = (long long)g.n_slices * b.n_bands * b.n_ctiles;
+        if (b.n_bins <= kMaxBinInts || lay == BinLayout::Bands) break;
+        if (b.ctile_w < g.nx) b.ctile_w *= 2;
+        else if (b.band_h < g.ny) b.band_h *= 2;
+        else break;
+    }
+    return b;
+}
+
+int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* amp_sigma, BinLayout lay,
                 PotParams* p) {
     float smax = 0.f;
     for (int i = 0; i < n_species; ++i) {
@@ -512,33 +740,46 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
     const double rc = 6.0 * smax;
     TACAW_REQUIRE(2.0 * rc < g.lx && 2.0 * rc < g.ly, TACAW_EINVAL,
                   "tacaw_potential: cut-off 6 sigma = %g A must be below half the box", rc);
+    const BinShape b = bin_shape(g, lay);
+    TACAW_REQUIRE(b.n_bins <= kMaxBinInts, TACAW_EUNSUPPORTED,
+                  "tacaw_potential: %lld bins exceed the shared-memory histogram (too many slices)",
+                  b.n_bins);
     p->nx = g.nx;
     p->ny = g.ny;
     p->n_slices = g.n_slices;
     p->n_atoms = n_atoms;
     p->n_species = n_species;
-    p->n_bands = (g.ny + kBandRows - 1) / kBandRows;
-    p->n_bins = g.n_slices * p->n_bands;
-    const double dy = g.ly / g.ny;
-    // an atom in pixel row jc reaches rows jc - ceil(rc/dy) .. jc + 1 + ceil(rc/dy); the
-    // slab is assigned in float, so its reach gets a little slack
-    p->band_reach = (int)ceil((ceil(rc / dy) + 1.0) / kBandRows);
+    p->band_h = b.band_h;
+    p->ctile_w = b.ctile_w;
+    p->n_bands = b.n_bands;
+    p->n_ctiles = b.n_ctiles;
+    p->n_bins = (int)b.n_bins;
+    const double dx = g.lx / g.nx, dy = g.ly / g.ny;
+    // an atom in pixel (ic, jc) reaches columns ic - reach_x - 1 .. ic + reach_x + 1 (rows
+    // alike); the slab is assigned in float, so its reach gets a little slack
+    p->reach_x = (int)ceil(rc / dx);
+    p->reach_y = (int)ceil(rc / dy);
+    p->band_reach = (p->reach_y + 1 + p->band_h - 1) / p->band_h;
+    p->ctile_reach = (p->reach_x + 1 + p->ctile_w - 1) / p->ctile_w;
     p->slab_reach = (int)ceil((rc + 1e-4 * g.dz) / g.dz);
     p->lx = (float)g.lx;
     p->ly = (float)g.ly;
-    p->dx = (float)(g.lx / g.nx);
-    p->dy = (float)dy;
+    p->dx = (float)dx;
     p->inv_dx = (float)(g.nx / g.lx);
-    p->inv_lx = (float)(1.0 / g.lx);
-    p->dx_d = g.lx / g.nx;
-    p->dy_d = g.ly / g.ny;
+    p->dy = (float)dy;
+    p->dx_d = dx;
+    p->dy_d = dy;
     p->inv_dx_d = g.nx / g.lx;
     p->inv_dy_d = g.ny / g.ly;
-    p->inv_ly = (float)(1.0 / g.ly);
     p->z0 = (float)g.z0;
     p->dz = (float)g.dz;
     p->inv_dz = (float)(1.0 / g.dz);
-    p->inv_band_h = (float)(1.0 / (kBandRows * dy));
+    const int nb = (2 * p->band_reach + 1 >= p->n_bands) ? p->n_bands : 2 * p->band_reach + 1;
+    const int nc = (2 * p->ctile_reach + 1 >= p->n_ctiles) ? p->n_ctiles : 2 * p->ctile_reach + 1;
+    const int n_nb = nb * nc * (min(g.n_slices - 1, 2 * p->slab_reach) + 1);
+    TACAW_REQUIRE(n_nb <= kMaxNbBins, TACAW_EUNSUPPORTED,
+                  "tacaw_potential: %d neighbouring bins per tile exceed %d (widths too large for "
+                  "the slice thickness or pixel size)", n_nb, kMaxNbBins);
     return TACAW_OK;
 }
 
@@ -548,34 +789,20 @@ static size_t pot_backward_blocks(const tacaw_grid& g, int n_t) {
     return (size_t)((g.ny + kBandRows - 1) / kBandRows) * g.n_slices * n_t;
 }
 
+static long long clamp_bins(long long n) { return n < kMaxBinInts ? n : kMaxBinInts; }
+
 int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n_species, size_t* bytes) {
-    const int n_bins = g.n_slices * ((g.ny + kBandRows - 1) / kBandRows);
     Carver cv(nullptr);
-    carve_pot(cv, n_t, n_atoms, n_bins);
+    carve_pot(cv, n_t, n_atoms, (int)clamp_bins(bin_shape(g, BinLayout::Bands).n_bins));
     cv.take<double>(pot_backward_blocks(g, n_t) * 2 * n_species);
     *bytes = cv.bytes();
     return TACAW_OK;
 }
 
 int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes) {
-    const int n_bins = g.n_slices * ((g.ny + kBandRows - 1) / kBandRows);
     Carver cv(nullptr);
-    carve_pot(cv, n_t, n_atoms, n_bins);
+    carve_pot(cv, n_t, n_atoms, (int)clamp_bins(bin_shape(g, BinLayout::Tiles).n_bins));
     *bytes = cv.bytes();
-    return TACAW_OK;
-}
-
-static int check_tables(const tacaw_grid& g, const PotParams& p) {
-    const size_t bin_smem = (size_t)p.n_bins * sizeof(int);
-    TACAW_REQUIRE(bin_smem <= 200 * 1024, TACAW_EUNSUPPORTED,
-                  "tacaw_potential: %d bins exceed the shared-memory histogram", p.n_bins);
-    TACAW_REQUIRE(g.nx <= 4 * 32 * kSegs, TACAW_EUNSUPPORTED,
-                  "tacaw_potential: nx = %d above the supported %d", g.nx, 4 * 32 * kSegs);
-    const int nb = (2 * p.band_reach + 1 >= p.n_bands) ? p.n_bands : 2 * p.band_reach + 1;
-    const int n_nb = nb * (min(g.n_slices - 1, 2 * p.slab_reach) + 1);
-    TACAW_REQUIRE(n_nb <= kMaxNbBins, TACAW_EUNSUPPORTED,
-                  "tacaw_potential: %d neighbouring bins per tile exceed %d (widths too large for "
-                  "the slice thickness or pixel size)", n_nb, kMaxNbBins);
     return TACAW_OK;
 }
 
@@ -588,24 +815,28 @@ static int run_binning(const PotParams& p, int n_t, const float* pos, const int*
     return TACAW_OK;
 }
 
+static int check_launch_dims(const tacaw_grid& g, int n_t) {
+    TACAW_REQUIRE(g.n_slices <= 65535 && n_t <= 65535, TACAW_EUNSUPPORTED,
+                  "tacaw_potential: at most 65535 slices and 65535 snapshots per call");
+    return TACAW_OK;
+}
+
 int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
                   int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st) {
     PotParams p;
-    int rc = make_params(g, n_atoms, n_species, amp_sigma, &p);
-    if (rc == TACAW_OK) rc = check_tables(g, p);
+    int rc = make_params(g, n_atoms, n_species, amp_sigma, BinLayout::Tiles, &p);
+    if (rc == TACAW_OK) rc = check_launch_dims(g, n_t);
     if (rc != TACAW_OK) return rc;
     Carver cv(ws);
     PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
     rc = run_binning(p, n_t, pos, species, w, st);
     if (rc != TACAW_OK) return rc;
-    dim3 grid(p.n_bands, g.n_slices, n_t);
-    const int cpl = ((g.nx + kSegs - 1) / kSegs + 31) / 32;
-    if (cpl <= 1)
-        potential_kernel<1><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
-    else if (cpl == 2)
-        potential_kernel<2><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
-    else
-        potential_kernel<4><<<grid, kPotThreads, 0, st>>>(w.bin_off, w.binned, w.binned_px, p, V);
+    const int n_tx = (g.nx + kTC - 1) / kTC, n_ty = (g.ny + kTR - 1) / kTR;
+    const int vec_out = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
+    const int smem = (int)sizeof(TileSmem);
+    TACAW_CUDA_CHECK(ensure_smem((const void*)potential_tile_kernel, smem));
+    potential_tile_kernel<<<dim3(n_tx * n_ty, g.n_slices, n_t), kPotThreads, smem, st>>>(
+        w.bin_off, w.binned, w.binned_px, p, n_tx, vec_out, V);
     TACAW_LAUNCH_CHECK();
     return TACAW_OK;
 }
@@ -614,8 +845,11 @@ int potential_backward_run(const tacaw_grid& g, int n_t, int n_atoms, const floa
                            const int* species, int n_species, const float* amp_sigma, const float* dV,
                            double* grad, void* ws, cudaStream_t st) {
     PotParams p;
-    int rc = make_params(g, n_atoms, n_species, amp_sigma, &p);
-    if (rc == TACAW_OK) rc = check_tables(g, p);
+    int rc = make_params(g, n_atoms, n_species, amp_sigma, BinLayout::Bands, &p);
+    if (rc == TACAW_OK) rc = check_launch_dims(g, n_t);
+    if (rc == TACAW_OK)
+        TACAW_REQUIRE(g.nx <= 4 * 32 * kSegs, TACAW_EUNSUPPORTED,
+                      "tacaw_potential_backward: nx = %d above the supported %d", g.nx, 4 * 32 * kSegs);
     if (rc != TACAW_OK) return rc;
     Carver cv(ws);
     PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
