@@ -31,7 +31,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "multislice gridpt*slice*snapshot/s (time-to-spectrum)"
 UNIT = "gridpt*slice*snapshot/s"
-DESIGN_BYTES_PER_PT_SLICE = 36        # row pass 8+8+4, column pass 8+8
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS_SUSTAINED = 1700.0
 
@@ -199,6 +198,33 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def slice_step_bytes(g):
+    """Algorithmic DRAM bytes per grid point and slice of the slice step.
+
+    Row pass: v_s (4 B) plus the wave read and written (8 + 8 B) in the kept
+    columns only (|k_x| <= K, the columns the band limit keeps); column pass:
+    the wave read and written (8 + 8 B) in the column blocks that hold a kept
+    column.  K uses the same FP64 expressions as the device set-up kernel.
+    """
+    d = g.lx / g.nx
+    val = 1.0 / (g.nx * d)
+    qmax = g.bandlimit * min(g.nx / (2.0 * g.lx), g.ny / (2.0 * g.ly))
+    qmax2 = qmax * qmax
+    K = -1
+    for k in range(g.nx // 2 + 1):
+        q = k * val
+        if q * q <= qmax2:
+            K = k
+        else:
+            break
+    kept = [kx <= K or kx >= g.nx - K for kx in range(g.nx)]
+    w = 8 if g.ny >= 512 else 16                       # columns per column-pass block
+    blocks = [any(kept[b:b + w]) for b in range(0, g.nx, w)]
+    f_col = sum(kept) / g.nx
+    f_blk = sum(blocks) / len(blocks)
+    return 4.0 + 16.0 * f_col + 16.0 * f_blk
+
+
 def profiled_traffic(units_per_launch):
     """DRAM bytes of one slice step (row + column pass) from the committed ncu
     summary, scaled to the launch size, or None if absent or stale."""
@@ -308,14 +334,15 @@ def run_ours(args):
     ms_call = stage_ms("multislice")
     units_call = g.nx * g.ny * g.n_slices * tts.batch
     avg_call_ms = statistics.mean(ms_call)
-    achieved = DESIGN_BYTES_PER_PT_SLICE * units_call / (avg_call_ms * 1e-3) / 1e9
+    bytes_pt = slice_step_bytes(g)
+    achieved = bytes_pt * units_call / (avg_call_ms * 1e-3) / 1e9
     peak, peak_tf, peak_kind = load_peaks()
     traffic = profiled_traffic(units_call)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "multislice slice step (row pass + column pass kernels, all slices of one "
                           f"{tts.batch}-snapshot batch per call)",
-                "bytes_per_unit": DESIGN_BYTES_PER_PT_SLICE, "peak_kind": f"{peak_kind} hbm_gbs"}
+                "bytes_per_unit": round(bytes_pt, 3), "peak_kind": f"{peak_kind} hbm_gbs"}
     spec_ms = statistics.mean(stage_ms("spectrum"))
     nq = g.nx * g.ny
     complex_flop = 8.0 * nq * n_t * n_t                 # 8 real flop per q, snapshot, energy

@@ -45,7 +45,12 @@ constexpr int kRowThreads = 256;
 // Tables computed in FP64 on the device once per call (into the workspace):
 //   twx, twy: per-stage twiddle tables of the nx / ny FFT plans (rounded to float),
 //   px[kx] = exp(-i pi lambda dz qx^2), py[ky] = exp(-i pi lambda dz qy^2) / (nx ny),
-//   kymax[kx] = largest |ky| index with qx^2 + qy^2 <= qmax^2 (-1 if none).
+//   kymax[kx] = largest |ky| index with qx^2 + qy^2 <= qmax^2 (-1 if none),
+//   kymax[nx] = K, the largest |kx| index with qx^2 <= qmax^2: the columns
+//     kx <= K and kx >= nx - K are the ones the band limit keeps ("kept columns").
+// The band limit zeroes every other column of the hybrid (k_x, y) wave, so the
+// passes skip them: the row pass neither reads nor writes them, the column pass
+// does not transform them (it writes their zeros only into the exit wave).
 // q = k * (1 / (n * (L / n))) with k the signed FFT frequency index: the same
 // FP64 expression sequence as numpy.fft.fftfreq(n, d=L/n), evaluated without
 // FMA contraction so the band-limit decision is bit-identical to it.
@@ -97,6 +102,14 @@ __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py
         }
         kymax[i] = kmax;
     }
+    if (i == 0) {                        // K: the same FP64 test with q_y = 0
+        int kk = -1;
+        for (int k = 0; k <= nx / 2; ++k) {
+            const double q = fft_freq(k, nx, lx);
+            if (__dadd_rn(__dmul_rn(q, q), 0.0) <= qmax2) kk = k; else break;
+        }
+        kymax[nx] = kk;
+    }
     if (i < ny) {
         double s, c;
         const double qy = fft_freq(i, ny, ly);
@@ -108,9 +121,11 @@ __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py
 
 // Row pass body for one row: (k_x, y) row -> Fx^-1 (mode 0; mode 1 starts from
 // the unit plane wave, mode 2 from psi_in) -> multiply by exp(i sigma v) -> Fx.
+__device__ __forceinline__ bool kept_column(int kx, int nx, int K) { return kx <= K || kx >= nx - K; }
+
 template <int NX>
 __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float* __restrict__ vrow,
-                                         const float2* __restrict__ inrow, int mode, float sigma,
+                                         const float2* __restrict__ inrow, int mode, float sigma, int K,
                                          float2* b0, float2* b1, const float2* tw, int t, int row) {
     using namespace fft;
     constexpr int E = Plan<NX>::E;
@@ -119,7 +134,8 @@ __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float*
     float2 v[E];
     if (mode == 0) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = rowp[t + TPT * m];
+        for (int m = 0; m < E; ++m)
+            v[m] = kept_column(t + TPT * m, NX, K) ? rowp[t + TPT * m] : make_float2(0.f, 0.f);
         transform<NX, true>(v, b0, b1, t, tw, lay);
     } else if (mode == 1) {
 #pragma unroll
@@ -136,7 +152,8 @@ __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float*
     }
     transform<NX, false>(v, b0, b1, t, tw, lay);
 #pragma unroll
-    for (int m = 0; m < E; ++m) rowp[t + TPT * m] = v[m];
+    for (int m = 0; m < E; ++m)
+        if (kept_column(t + TPT * m, NX, K)) rowp[t + TPT * m] = v[m];
 }
 
 // Row pass: ROWS rows of one snapshot per block.
@@ -144,7 +161,7 @@ template <int NX>
 __global__ void __launch_bounds__(kRowThreads)
 row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
                 const float2* __restrict__ psi_in, const float2* __restrict__ twx,
-                int ny, int n_slices, int s, float sigma, int mode) {
+                const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int mode) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     extern __shared__ float2 smem[];
@@ -155,8 +172,8 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
     const int y = blockIdx.x * ROWS + row;
     const size_t snap = blockIdx.y;
     row_body<NX>(psi + (snap * ny + y) * NX, V + ((snap * n_slices + s) * ny + y) * NX,
-                 psi_in ? psi_in + (size_t)y * NX : nullptr, mode, sigma, smem, smem + ROWS * NX, tw,
-                 t, row);
+                 psi_in ? psi_in + (size_t)y * NX : nullptr, mode, sigma, __ldg(kymax + NX), smem,
+                 smem + ROWS * NX, tw, t, row);
 }
 
 // Jobs of one batched launch (all of the same grid size): block row y of the
@@ -168,6 +185,7 @@ struct RowJobs {
     float2* psi[kMaxBatch];
     const float* V[kMaxBatch];
     const float2* psi_in[kMaxBatch];
+    const int* kymax[kMaxBatch];
     int n_slices[kMaxBatch];
     int mode[kMaxBatch];
     float sigma[kMaxBatch];
@@ -194,8 +212,8 @@ row_batch_kernel(const __grid_constant__ RowJobs jobs, const float2* __restrict_
     const size_t snap = blockIdx.y - jobs.start[j];
     const float2* pin = jobs.psi_in[j];
     row_body<NX>(jobs.psi[j] + (snap * ny + y) * NX, jobs.V[j] + ((snap * jobs.n_slices[j] + s) * ny + y) * NX,
-                 pin ? pin + (size_t)y * NX : nullptr, jobs.mode[j], jobs.sigma[j], smem, smem + ROWS * NX, tw,
-                 t, row);
+                 pin ? pin + (size_t)y * NX : nullptr, jobs.mode[j], jobs.sigma[j], __ldg(jobs.kymax[j] + NX),
+                 smem, smem + ROWS * NX, tw, t, row);
 }
 
 template <int NY>
@@ -235,6 +253,22 @@ __device__ __forceinline__ void col_body(float2* __restrict__ col, int nx, int k
     for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
 }
 
+// A column block whose W columns the band limit all drops: nothing to
+// transform; after the last slice it writes their zeros into the exit wave.
+// Returns true when the block is done (uniform over the block).
+template <int NY>
+__device__ __forceinline__ bool dropped_block(float2* __restrict__ col, int nx, int kx0, int K, int last,
+                                              int t) {
+    constexpr int TPT = NY / fft::Plan<NY>::E;
+    constexpr int W = ColCfg<NY>::W;
+    if (kx0 <= K || kx0 + W - 1 >= nx - K) return false;
+    if (last) {
+#pragma unroll
+        for (int m = 0; m < fft::Plan<NY>::E; ++m) col[(size_t)(t + TPT * m) * nx] = make_float2(0.f, 0.f);
+    }
+    return true;
+}
+
 template <int NY, bool CONJ, bool FFT_IN>
 __global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
 col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
@@ -243,11 +277,13 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     constexpr int W = ColCfg<NY>::W;
     extern __shared__ float2 smem[];
     float2* tw = smem + 2 * W * NY;
-    stage_twiddles<NY>(tw, twy);
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int kx = blockIdx.x * W + c;
     const size_t snap = blockIdx.y;
+    if (dropped_block<NY>(psi + snap * NY * (size_t)nx + kx, nx, blockIdx.x * W, __ldg(kymax + nx), last, t))
+        return;
+    stage_twiddles<NY>(tw, twy);
     col_body<NY, CONJ, FFT_IN>(psi + snap * NY * (size_t)nx + kx, nx, kx, px, py, kymax, last, smem,
                                smem + W * NY, tw, t, c);
 }
@@ -268,12 +304,15 @@ col_batch_kernel(const __grid_constant__ ColJobs jobs, const float2* __restrict_
     constexpr int W = ColCfg<NY>::W;
     extern __shared__ float2 smem[];
     float2* tw = smem + 2 * W * NY;
-    stage_twiddles<NY>(tw, twy);
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int kx = blockIdx.x * W + c;
     const int j = find_job(jobs.start, jobs.n, blockIdx.y);
     const size_t snap = blockIdx.y - jobs.start[j];
+    if (dropped_block<NY>(jobs.psi[j] + snap * NY * (size_t)nx + kx, nx, blockIdx.x * W,
+                          __ldg(jobs.kymax[j] + nx), jobs.last[j], t))
+        return;
+    stage_twiddles<NY>(tw, twy);
     col_body<NY, false, true>(jobs.psi[j] + snap * NY * (size_t)nx + kx, nx, kx, jobs.px[j], jobs.py[j],
                               jobs.kymax[j], jobs.last[j], smem, smem + W * NY, tw, t, c);
 }
@@ -288,8 +327,8 @@ template <int NX>
 __global__ void __launch_bounds__(kRowThreads)
 row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const float* __restrict__ V,
                 float* __restrict__ dV, const float2* __restrict__ psi_in,
-                const float2* __restrict__ twx, int ny, int n_slices, int s, float sigma, int mode,
-                int fft_out) {
+                const float2* __restrict__ twx, const int* __restrict__ kymax, int ny, int n_slices, int s,
+                float sigma, int mode, int fft_out) {
     using namespace fft;
     constexpr int E = Plan<NX>::E;
     constexpr int TPT = NX / E;
@@ -308,14 +347,18 @@ row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const 
     const size_t vrow_off = ((snap * n_slices + s) * ny + y) * NX;
     const RowLayout lay{row * NX};
 
+    // g and the hybrid state hold data only in the kept columns
+    const int K = __ldg(kymax + NX);
     float2 gv[E], sv[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) gv[m] = grow[t + TPT * m];
+    for (int m = 0; m < E; ++m)
+        gv[m] = kept_column(t + TPT * m, NX, K) ? grow[t + TPT * m] : make_float2(0.f, 0.f);
     transform<NX, true>(gv, b0, b1, t, tw, lay);
     if (mode == 0) {
         const float2* srow = state + (snap * ny + y) * NX;
 #pragma unroll
-        for (int m = 0; m < E; ++m) sv[m] = srow[t + TPT * m];
+        for (int m = 0; m < E; ++m)
+            sv[m] = kept_column(t + TPT * m, NX, K) ? srow[t + TPT * m] : make_float2(0.f, 0.f);
         transform<NX, true>(sv, b0, b1, t, tw, lay);
     } else if (mode == 1) {
 #pragma unroll
@@ -336,7 +379,8 @@ row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const 
     }
     if (fft_out) transform<NX, false>(gv, b0, b1, t, tw, lay);
 #pragma unroll
-    for (int m = 0; m < E; ++m) grow[t + TPT * m] = gv[m];
+    for (int m = 0; m < E; ++m)
+        if (!fft_out || kept_column(t + TPT * m, NX, K)) grow[t + TPT * m] = gv[m];
 }
 
 // psi_sum[q] += sum_t psi[t][q], FP64, snapshots added in order.
@@ -358,7 +402,7 @@ __global__ void snapshot_sum_kernel(const float2* __restrict__ psi, double2* __r
 
 template <int NX>
 cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const float2* twx,
-                       int ny, int n_t, int n_slices, int s, float sigma, int mode,
+                       const int* kymax, int ny, int n_t, int n_slices, int s, float sigma, int mode,
                        cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
@@ -366,7 +410,8 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
     cudaError_t e = ensure_smem((const void*)row_pass_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / ROWS, n_t);
-    row_pass_kernel<NX><<<grid, kRowThreads, smem, st>>>(psi, V, psi_in, twx, ny, n_slices, s, sigma, mode);
+    row_pass_kernel<NX><<<grid, kRowThreads, smem, st>>>(psi, V, psi_in, twx, kymax, ny, n_slices, s, sigma,
+                                                          mode);
     return cudaGetLastError();
 }
 
@@ -395,30 +440,34 @@ cudaError_t launch_col(float2* psi, const float2* twy, const float2* px, const f
 
 template <int NX>
 cudaError_t launch_row_back(float2* g, const float2* state, const float* V, float* dV,
-                            const float2* psi_in, const float2* twx, int ny, int n_t, int n_slices,
-                            int s, float sigma, int mode, int fft_out, cudaStream_t st) {
+                            const float2* psi_in, const float2* twx, const int* kymax, int ny, int n_t,
+                            int n_slices, int s, float sigma, int mode, int fft_out, cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_back_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / ROWS, n_t);
-    row_back_kernel<NX><<<grid, kRowThreads, smem, st>>>(g, state, V, dV, psi_in, twx, ny, n_slices, s,
-                                                          sigma, mode, fft_out);
+    row_back_kernel<NX><<<grid, kRowThreads, smem, st>>>(g, state, V, dV, psi_in, twx, kymax, ny, n_slices,
+                                                          s, sigma, mode, fft_out);
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_in, const float2* twx,
-                         int ny, int n_t, int n_slices, int s, float sigma, int mode, cudaStream_t st) {
-    switch (nx) {
-        case 64: return launch_row<64>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
-        case 128: return launch_row<128>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
-        case 256: return launch_row<256>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
-        case 512: return launch_row<512>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
-        case 1024: return launch_row<1024>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
-        case 384: return launch_row<384>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
-        case 768: return launch_row<768>(psi, V, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, st);
+#define TACAW_SIZE_SWITCH(n, CALL)                  \
+    switch (n) {                                    \
+        case 64: { constexpr int N_ = 64; CALL; }   \
+        case 128: { constexpr int N_ = 128; CALL; } \
+        case 256: { constexpr int N_ = 256; CALL; } \
+        case 384: { constexpr int N_ = 384; CALL; } \
+        case 512: { constexpr int N_ = 512; CALL; } \
+        case 768: { constexpr int N_ = 768; CALL; } \
+        case 1024: { constexpr int N_ = 1024; CALL; } \
     }
+
+cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_in, const float2* twx,
+                         const int* kymax, int ny, int n_t, int n_slices, int s, float sigma, int mode,
+                         cudaStream_t st) {
+    TACAW_SIZE_SWITCH(nx, return launch_row<N_>(psi, V, psi_in, twx, kymax, ny, n_t, n_slices, s, sigma, mode, st));
     return cudaErrorInvalidValue;
 }
 
@@ -458,17 +507,6 @@ cudaError_t launch_col_batch(const ColJobs& jobs, const float2* twy, int nx, int
     return cudaGetLastError();
 }
 
-#define TACAW_SIZE_SWITCH(n, CALL)                  \
-    switch (n) {                                    \
-        case 64: { constexpr int N_ = 64; CALL; }   \
-        case 128: { constexpr int N_ = 128; CALL; } \
-        case 256: { constexpr int N_ = 256; CALL; } \
-        case 384: { constexpr int N_ = 384; CALL; } \
-        case 512: { constexpr int N_ = 512; CALL; } \
-        case 768: { constexpr int N_ = 768; CALL; } \
-        case 1024: { constexpr int N_ = 1024; CALL; } \
-    }
-
 cudaError_t dispatch_row_batch(int nx, const RowJobs& jobs, const float2* twx, int ny, int total, int s,
                                cudaStream_t st) {
     TACAW_SIZE_SWITCH(nx, return launch_row_batch<N_>(jobs, twx, ny, total, s, st));
@@ -482,17 +520,10 @@ cudaError_t dispatch_col_batch(int ny, const ColJobs& jobs, const float2* twy, i
 }
 
 cudaError_t dispatch_row_back(int nx, float2* g, const float2* state, const float* V, float* dV,
-                              const float2* psi_in, const float2* twx, int ny, int n_t, int n_slices,
-                              int s, float sigma, int mode, int fft_out, cudaStream_t st) {
-    switch (nx) {
-        case 64: return launch_row_back<64>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-        case 128: return launch_row_back<128>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-        case 256: return launch_row_back<256>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-        case 512: return launch_row_back<512>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-        case 1024: return launch_row_back<1024>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-        case 384: return launch_row_back<384>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-        case 768: return launch_row_back<768>(g, state, V, dV, psi_in, twx, ny, n_t, n_slices, s, sigma, mode, fft_out, st);
-    }
+                              const float2* psi_in, const float2* twx, const int* kymax, int ny, int n_t,
+                              int n_slices, int s, float sigma, int mode, int fft_out, cudaStream_t st) {
+    TACAW_SIZE_SWITCH(nx, return launch_row_back<N_>(g, state, V, dV, psi_in, twx, kymax, ny, n_t, n_slices, s,
+                                                     sigma, mode, fft_out, st));
     return cudaErrorInvalidValue;
 }
 
@@ -513,7 +544,7 @@ static MsTables carve_ms(Carver& cv, const tacaw_grid& g) {
     t.twy = cv.take<float2>(g.ny);
     t.px = cv.take<float2>(g.nx);
     t.py = cv.take<float2>(g.ny);
-    t.kymax = cv.take<int>(g.nx);
+    t.kymax = cv.take<int>(g.nx + 1);
     return t;
 }
 
@@ -538,7 +569,7 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
     const float sigma = (float)sig;
     for (int s = 0; s < g.n_slices; ++s) {
         const int mode = s > 0 ? 0 : (psi_in ? 2 : 1);
-        TACAW_CUDA_CHECK(dispatch_row(g.nx, psi_q, V, psi_in, tb.twx, g.ny, n_t, g.n_slices, s,
+        TACAW_CUDA_CHECK(dispatch_row(g.nx, psi_q, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s,
                                       sigma, mode, st));
         TACAW_CUDA_CHECK(dispatch_col(g.ny, psi_q, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t,
                                       s + 1 == g.n_slices, st));
@@ -612,6 +643,7 @@ int multislice_batch_run(const tacaw_job* jobs, int n_jobs, void* ws, cudaStream
                     rj.psi[k] = cj.psi[k] = (float2*)b.psi_q;
                     rj.V[k] = b.V;
                     rj.psi_in[k] = (const float2*)b.psi_in;
+                    rj.kymax[k] = tb[j].kymax;
                     rj.n_slices[k] = b.grid.n_slices;
                     rj.mode[k] = s > 0 ? 0 : (b.psi_in ? 2 : 1);
                     rj.sigma[k] = sigma[j];
@@ -692,7 +724,7 @@ int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const 
         if (s > 0 && s % every == 0)
             TACAW_CUDA_CHECK(cudaMemcpyAsync(b.ck + (size_t)(s / every) * wave, b.w, wave_bytes,
                                              cudaMemcpyDeviceToDevice, st));
-        TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, g.ny, n_t, g.n_slices, s, sigma,
+        TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s, sigma,
                                       s > 0 ? 0 : first_mode, st));
         TACAW_CUDA_CHECK(dispatch_col(g.ny, b.w, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st));
     }
@@ -711,7 +743,7 @@ int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const 
                 TACAW_CUDA_CHECK(cudaMemcpyAsync(b.w, b.ck + (size_t)c * wave, wave_bytes,
                                                  cudaMemcpyDeviceToDevice, st));
             for (int s = s0; s + 1 < s1; ++s) {
-                TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, g.ny, n_t, g.n_slices, s,
+                TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s,
                                               sigma, s > 0 ? 0 : first_mode, st));
                 TACAW_CUDA_CHECK(dispatch_col(g.ny, b.w, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st));
                 TACAW_CUDA_CHECK(cudaMemcpyAsync(b.seg + (size_t)(s + 1 - s0) * wave, b.w, wave_bytes,
@@ -724,7 +756,7 @@ int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const 
             first = false;
             const float2* state = (s == s0) ? (c > 0 ? b.ck + (size_t)c * wave : nullptr)
                                             : b.seg + (size_t)(s - s0) * wave;
-            TACAW_CUDA_CHECK(dispatch_row_back(g.nx, b.g, state, V, dV, psi_in, tb.twx, g.ny, n_t,
+            TACAW_CUDA_CHECK(dispatch_row_back(g.nx, b.g, state, V, dV, psi_in, tb.twx, tb.kymax, g.ny, n_t,
                                                g.n_slices, s, sigma, s > 0 ? 0 : first_mode, s > 0 ? 1 : 0,
                                                st));
         }
