@@ -76,6 +76,11 @@ __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
     return make_float2(a.x * s, a.y * s);
 }
 
+// L2 prefetch hint for [p, p + bytes): p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // exp(i x) = cos x + i sin x for the transmission phase sigma_e v.  The phase
 // is small in practice, so |x| <= 0.5 uses the Taylor series of sin to x^9
 // and of cos to x^10 (truncation below 2e-11, i.e. far under FP32 rounding),

@@ -12,8 +12,11 @@
 // Each pass reads and writes every point once (8 + 8 bytes per point), the
 // row pass also reads v_s (4 bytes per point): 36 bytes per point and slice.
 
+#include <stdint.h>
+
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -36,6 +39,29 @@ cudaError_t ensure_smem(const void* kernel, int bytes) {
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) have = bytes;
     return e;
+}
+
+// Blocks of `kernel` resident on the whole device at once (occupancy times
+// SM count), computed once per kernel, size and device.
+cudaError_t resident_blocks(const void* kernel, int threads, int smem, int* out) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, int>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(kernel, threads, smem, dev);
+    auto it = done.find(key);
+    if (it != done.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    int per_sm = 0, n_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *out = done[key] = per_sm * n_sm;
+    return cudaSuccess;
 }
 
 namespace {
@@ -156,16 +182,30 @@ __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float*
         if (kept_column(t + TPT * m, NX, K)) rowp[t + TPT * m] = v[m];
 }
 
-// Row pass: ROWS rows of one snapshot per block.
+// Row pass: ROWS rows of one snapshot per block.  With ahead > 0 (16-byte
+// aligned buffers) thread 0 first asks L2 for the block's potential rows and
+// for the rows of the block `ahead` places later in launch order (about one
+// wave of resident blocks later), so their loads find the data in L2.
 template <int NX>
 __global__ void __launch_bounds__(kRowThreads)
 row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
                 const float2* __restrict__ psi_in, const float2* __restrict__ twx,
-                const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int mode) {
+                const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int mode,
+                int ahead) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     extern __shared__ float2 smem[];
     float2* tw = smem + 2 * ROWS * NX;
+    if (ahead > 0 && threadIdx.x == 0) {
+        prefetch_l2_bulk(V + (((size_t)blockIdx.y * n_slices + s) * ny + (size_t)blockIdx.x * ROWS) * NX,
+                         ROWS * NX * sizeof(float));
+        const size_t nxt = (size_t)blockIdx.y * gridDim.x + blockIdx.x + ahead;
+        if (nxt < (size_t)gridDim.x * gridDim.y) {
+            const size_t by = nxt / gridDim.x, y0 = (nxt % gridDim.x) * ROWS;
+            prefetch_l2_bulk(V + ((by * n_slices + s) * ny + y0) * NX, ROWS * NX * sizeof(float));
+            if (mode == 0) prefetch_l2_bulk(psi + (by * ny + y0) * NX, ROWS * NX * sizeof(float2));
+        }
+    }
     stage_twiddles<NX>(tw, twx);
     const int t = threadIdx.x % TPT;
     const int row = threadIdx.x / TPT;
@@ -216,8 +256,13 @@ row_batch_kernel(const __grid_constant__ RowJobs jobs, const float2* __restrict_
                  smem, smem + ROWS * NX, tw, t, row);
 }
 
+// W columns per column-pass block and the blocks per SM the register budget
+// targets (three blocks of the 8-value plans would spill).
 template <int NY>
-struct ColCfg { static constexpr int W = (NY >= 512) ? 8 : 16; };
+struct ColCfg {
+    static constexpr int W = (NY >= 512) ? 8 : 16;
+    static constexpr int kMinBlocks = (NY >= 1024) ? 1 : 2;
+};
 // ny must be a multiple of the rows handled per row-pass block
 static_assert(kRowThreads / (384 / 24) == 16 && kRowThreads / (768 / 24) == 8, "row tiles");
 
@@ -269,8 +314,9 @@ __device__ __forceinline__ bool dropped_block(float2* __restrict__ col, int nx, 
     return true;
 }
 
+// Column pass: W columns of one snapshot per block.
 template <int NY, bool CONJ, bool FFT_IN>
-__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), ColCfg<NY>::kMinBlocks)
 col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
                 const float2* __restrict__ px, const float2* __restrict__ py,
                 const int* __restrict__ kymax, int nx, int last) {
@@ -281,7 +327,8 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
     const int t = threadIdx.x / W;
     const int kx = blockIdx.x * W + c;
     const size_t snap = blockIdx.y;
-    if (dropped_block<NY>(psi + snap * NY * (size_t)nx + kx, nx, blockIdx.x * W, __ldg(kymax + nx), last, t))
+    const int K = __ldg(kymax + nx);
+    if (dropped_block<NY>(psi + snap * NY * (size_t)nx + kx, nx, blockIdx.x * W, K, last, t))
         return;
     stage_twiddles<NY>(tw, twy);
     col_body<NY, CONJ, FFT_IN>(psi + snap * NY * (size_t)nx + kx, nx, kx, px, py, kymax, last, smem,
@@ -299,7 +346,7 @@ struct ColJobs {
 };
 
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), (NY >= 1024) ? 1 : 2)
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), ColCfg<NY>::kMinBlocks)
 col_batch_kernel(const __grid_constant__ ColJobs jobs, const float2* __restrict__ twy, int nx) {
     constexpr int W = ColCfg<NY>::W;
     extern __shared__ float2 smem[];
@@ -409,9 +456,14 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
     const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_pass_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
+    int ahead = 0;
+    if (reinterpret_cast<uintptr_t>(psi) % 16 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0) {
+        e = resident_blocks((const void*)row_pass_kernel<NX>, kRowThreads, (int)smem, &ahead);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid(ny / ROWS, n_t);
     row_pass_kernel<NX><<<grid, kRowThreads, smem, st>>>(psi, V, psi_in, twx, kymax, ny, n_slices, s, sigma,
-                                                          mode);
+                                                          mode, ahead);
     return cudaGetLastError();
 }
 
@@ -421,8 +473,7 @@ cudaError_t launch_col_t(float2* psi, const float2* twy, const float2* px, const
     constexpr int TPT = NY / fft::Plan<NY>::E;
     constexpr int W = ColCfg<NY>::W;
     const size_t smem = (2 * W * NY + fft::TwSize<NY>::value) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY, CONJ, FFT_IN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void*)col_pass_kernel<NY, CONJ, FFT_IN>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(nx / W, n_t);
     col_pass_kernel<NY, CONJ, FFT_IN><<<grid, W * TPT, smem, st>>>(psi, twy, px, py, kymax, nx, last);
