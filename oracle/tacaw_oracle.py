@@ -54,7 +54,7 @@ __all__ = [
     "spatial_frequencies", "bandlimit_mask", "propagator",
     "fft2_unitary", "ifft2_unitary", "multislice", "exit_waves",
     "natural_energies", "time_mean", "temporal_transform", "kubo_factor",
-    "spectrum",
+    "spectrum", "segment_count", "segment_starts", "segment_spectrum",
 ]
 
 # ---------------------------------------------------------------------------
@@ -331,6 +331,60 @@ def spectrum(psi, dt_fs: float, omega_meV=None, kubo=False, temperature_K=300.0,
     inten = np.abs(phi) ** 2 / float(n_t) ** 2
     energies = natural_energies(n_t, dt_fs) if omega_meV is None \
         else np.asarray(omega_meV, dtype=np.float64)
+    if kubo:
+        inten = inten * kubo_factor(energies, temperature_K)[None, :]
+    if normalize:
+        total = inten.sum() + i_el.sum()
+        inten = inten / total
+        i_el = i_el / total
+    return inten, i_el, energies
+
+
+# ---------------------------------------------------------------- segments
+def segment_count(n_t: int, seg_len: int, hop: int) -> int:
+    """Largest number of sets of seg_len consecutive snapshots, starts 0, hop, 2 hop, ..."""
+    if seg_len > n_t or seg_len < 1 or hop < 1:
+        return 0
+    return (n_t - seg_len) // hop + 1
+
+
+def segment_starts(n_t: int, seg_len: int, hop: int, n_sets=None) -> np.ndarray:
+    """First snapshot of each set: g * hop for g = 0 .. n_sets - 1 (all sets that fit
+    when n_sets is None)."""
+    most = segment_count(n_t, seg_len, hop)
+    n = most if n_sets is None else int(n_sets)
+    if n < 1 or n > most:
+        raise ValueError("need 1 <= n_sets <= the number of complete sets")
+    return np.arange(n) * hop
+
+
+def segment_spectrum(psi, dt_fs: float, seg_len: int, hop: int, n_sets=None, omega_meV=None,
+                     kubo=False, temperature_K=300.0, normalize=False):
+    """Spectrum averaged over sets of consecutive snapshots (the averaging over
+    trajectory segments the paper describes after Eq. (9) and applies with,
+    e.g., 79 sets of 100 snapshots offset by 50).
+
+    Set g holds snapshots g*hop .. g*hop + seg_len - 1 and is treated as a
+    trajectory of its own: its time mean m_g, elastic part |m_g|^2 and
+    I_g(q, E) = |sum_n (psi - m_g)(q, t_n) exp(-i E t_n / hbar)|^2 / seg_len^2
+    with t_n measured from the start of the set (the start time only adds a
+    phase).  I and I_el are the plain averages over the sets; the Kubo factor
+    and the normalisation then act on the averages as in ``spectrum``.
+    Natural grid (omega_meV None): E_k = h k / (seg_len dt).
+    Returns (I (nq, n_omega), I_el (nq,), E (n_omega,) in meV).
+    """
+    psi = np.asarray(psi, dtype=np.complex128)
+    n_t = psi.shape[0]
+    psi = psi.reshape(n_t, -1)
+    starts = segment_starts(n_t, seg_len, hop, n_sets)
+    inten = 0.0
+    i_el = 0.0
+    for g0 in starts:
+        i_g, iel_g, energies = spectrum(psi[g0:g0 + seg_len], dt_fs, omega_meV)
+        inten = inten + i_g
+        i_el = i_el + iel_g
+    inten = inten / len(starts)
+    i_el = i_el / len(starts)
     if kubo:
         inten = inten * kubo_factor(energies, temperature_K)[None, :]
     if normalize:

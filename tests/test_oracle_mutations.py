@@ -123,6 +123,33 @@ def _bl_max(g):
     return (q2 <= qmax * qmax).astype(float)
 
 
+def _segments_variant(stride_is_length=False, divide=True, global_mean=False):
+    def seg(psi, dt_fs, seg_len, hop, n_sets=None, omega_meV=None, kubo=False, temperature_K=300.0,
+            normalize=False):
+        psi = np.asarray(psi, complex).reshape(np.shape(psi)[0], -1)
+        if stride_is_length:        # offset confused with the overlap seg_len - hop
+            stride = seg_len - hop if seg_len > hop else seg_len
+            starts = T.segment_starts(psi.shape[0], seg_len, stride)
+        else:
+            starts = T.segment_starts(psi.shape[0], seg_len, hop, n_sets)
+        inten, iel = 0.0, 0.0
+        for s0 in starts:
+            part = psi[s0:s0 + seg_len]
+            if global_mean:
+                part = part - psi.mean(axis=0) + part.mean(axis=0)
+            i_g, iel_g, e = T.spectrum(part, dt_fs, omega_meV)
+            inten, iel = inten + i_g, iel + iel_g
+        if divide:
+            inten, iel = inten / len(starts), iel / len(starts)
+        if kubo:
+            inten = inten * T.kubo_factor(e, temperature_K)[None]
+        if normalize:
+            tot = inten.sum() + iel.sum()
+            inten, iel = inten / tot, iel / tot
+        return inten, iel, e
+    return seg
+
+
 MUTATIONS = {
     "fft_missing_1_over_N": ("fft2_unitary", lambda p: np.fft.fft2(p)),
     "ifft_with_1_over_N": ("ifft2_unitary", lambda p: np.fft.ifft2(p)),
@@ -149,6 +176,9 @@ MUTATIONS = {
     "sigma_without_gamma": ("interaction_constant",
                             lambda kev: 2 * np.pi * T.ME_KG * T.E_C * T.wavelength(kev) * 1e-10
                             / T.PLANCK_J_S ** 2 * 1e-10),
+    "segments_offset_as_overlap": ("segment_spectrum", _segments_variant(stride_is_length=True)),
+    "segments_summed_not_averaged": ("segment_spectrum", _segments_variant(divide=False)),
+    "segments_global_mean": ("segment_spectrum", _segments_variant(global_mean=True)),
     "wavelength_nonrelativistic": ("wavelength",
                                    lambda kev: T.PLANCK_J_S / np.sqrt(2 * T.ME_KG * kev * 1e3 * T.E_C)
                                    * 1e10),
@@ -175,6 +205,9 @@ PINS = [
     lambda: P.test_elastic_bin_zero_and_static_lattice(),
     lambda: P.test_kubo_factor_detailed_balance(),
     lambda: P.test_normalisation_sums_to_one(),
+    lambda: P.test_segment_sets_match_paper(),
+    lambda: P.test_segment_spectrum_bruteforce(),
+    lambda: P.test_segment_spectrum_parseval_over_tiling_sets(),
 ]
 
 

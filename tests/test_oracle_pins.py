@@ -418,3 +418,79 @@ def test_plain_small_inputs_are_seeded():
     u = inp.positions().astype(np.float64) - inp.crystal.positions[None]
     rms = np.sqrt(np.mean(np.sum(u**2, axis=-1)))
     assert rms == pytest.approx(0.05, rel=0.1)
+
+
+# ---------------------------------------------------------------------------
+# Spectra averaged over sets of consecutive snapshots
+# ---------------------------------------------------------------------------
+def test_segment_sets_match_paper():
+    # set counts and durations the paper prints for its three trajectories
+    for dt, n_t, seg, hop, n_sets, span_ps, all_fit in _golden("paper_segment_sets.txt"):
+        n_t, seg, hop, n_sets = int(n_t), int(seg), int(hop), int(n_sets)
+        most = O.segment_count(n_t, seg, hop)
+        if all_fit:
+            assert most == n_sets
+        else:
+            assert most >= n_sets
+        assert seg * dt / 1000.0 == pytest.approx(span_ps, abs=0.006)
+        starts = O.segment_starts(n_t, seg, hop, n_sets)
+        assert len(starts) == n_sets and starts[-1] + seg <= n_t
+    # Si: every snapshot is used twice except the first and the last 50
+    use = np.zeros(4000, int)
+    for s0 in O.segment_starts(4000, 100, 50):
+        use[s0:s0 + 100] += 1
+    assert np.all(use[50:-50] == 2) and np.all(use[:50] == 1) and np.all(use[-50:] == 1)
+
+
+def test_segment_spectrum_one_set_is_the_spectrum():
+    rng = np.random.default_rng(10)
+    psi = _waves(rng, 24, 5)
+    a = O.segment_spectrum(psi, 5.0, 24, 7)
+    b = O.spectrum(psi, 5.0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_segment_spectrum_bruteforce():
+    # 12 snapshots, sets of 6 offset by 2 (starts 0, 2, 4, 6): per-set means and
+    # DFT sums written out as plain loops
+    rng = np.random.default_rng(11)
+    t, seg, hop, dt = 12, 6, 2, 5.0
+    psi = _waves(rng, t, 2)
+    inten, iel, e = O.segment_spectrum(psi, dt, seg, hop)
+    starts = [0, 2, 4, 6]
+    for q in range(2):
+        ref_i = np.zeros(seg)
+        ref_el = 0.0
+        for s0 in starts:
+            m = sum(psi[s0 + n, q] for n in range(seg)) / seg
+            ref_el += abs(m) ** 2 / len(starts)
+            for k in range(seg):
+                ek = (k - seg // 2) * O.H_MEV_FS / (seg * dt)
+                phi = sum((psi[s0 + n, q] - m) * np.exp(-1j * ek * n * dt / O.HBAR_MEV_FS) for n in range(seg))
+                ref_i[k] += abs(phi) ** 2 / seg ** 2 / len(starts)
+        assert np.allclose(inten[q], ref_i, rtol=1e-12, atol=1e-18)
+        assert iel[q] == pytest.approx(ref_el, rel=1e-13)
+
+
+def test_segment_spectrum_parseval_over_tiling_sets():
+    # sets that tile the trajectory: I_el + sum_k I = mean over all snapshots of |psi|^2
+    rng = np.random.default_rng(12)
+    psi = _waves(rng, 32, 4)
+    inten, iel, _ = O.segment_spectrum(psi, 5.0, 8, 8)
+    assert np.allclose(iel + inten.sum(axis=1), np.mean(np.abs(psi) ** 2, axis=0), rtol=1e-13)
+    # with kubo and normalisation the averages still sum to one
+    inten, iel, _ = O.segment_spectrum(psi, 5.0, 8, 4, kubo=True, normalize=True)
+    assert inten.sum() + iel.sum() == pytest.approx(1.0, abs=1e-14)
+
+
+def test_segment_spectrum_single_mode_on_bin():
+    # a mode on bin 4 of 64 snapshots sits on bin 2 of every set of 32
+    psi, dt, _ = _single_mode_run(False, 4)
+    t = psi.shape[0]
+    inten, _, e = O.segment_spectrum(psi.reshape(t, -1), dt, 32, 16)
+    k = np.arange(32) - 16
+    harm = (k % 2) == 0
+    tot = inten.sum()
+    assert inten[:, ~harm].sum() < 1e-12 * tot
+    assert inten[:, k == 2].sum() > 1e-3 * tot and inten[:, k == -2].sum() > 1e-3 * tot
