@@ -55,6 +55,8 @@ __all__ = [
     "fft2_unitary", "ifft2_unitary", "multislice", "exit_waves",
     "natural_energies", "time_mean", "temporal_transform", "kubo_factor",
     "spectrum", "segment_count", "segment_starts", "segment_spectrum",
+    "qep_intensity", "energy_integral", "scattering_angles", "line_profile", "azimuthal_profile",
+    "relative_difference",
 ]
 
 # ---------------------------------------------------------------------------
@@ -392,3 +394,62 @@ def segment_spectrum(psi, dt_fs: float, seg_len: int, hop: int, n_sets=None, ome
         inten = inten / total
         i_el = i_el / total
     return inten, i_el, energies
+
+
+# ---------------------------------------------------------------- QEP by-products
+def qep_intensity(psi, t0: int = 0, stride: int = 1, n=None) -> np.ndarray:
+    """QEP diffraction pattern of a subset of snapshots (Eq. (4) with Eq. (3):
+    |psi|^2 averaged over configurations): (1/n) sum_j |psi(q, t0 + j stride)|^2.
+    psi has shape (T, ...); n None takes every snapshot t0, t0 + stride, ... < T."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    idx = np.arange(t0, psi.shape[0], stride)
+    if n is not None:
+        if n < 1 or n > len(idx):
+            raise ValueError("the snapshots do not fit")
+        idx = idx[:n]
+    return np.mean(np.abs(psi[idx]) ** 2, axis=0)
+
+
+def energy_integral(inten, i_el=None) -> np.ndarray:
+    """sum_k I(q, E_k) (+ I_el(q)): the energy integral of the spectrum."""
+    out = np.sum(np.asarray(inten, dtype=np.float64), axis=1)
+    return out if i_el is None else out + np.asarray(i_el, dtype=np.float64)
+
+
+def scattering_angles(nx: int, ny: int, lx: float, ly: float, lam: float) -> np.ndarray:
+    """theta = lambda |q| in mrad on the FFT-order grid (ny, nx)."""
+    qx = np.fft.fftfreq(nx, d=lx / nx)
+    qy = np.fft.fftfreq(ny, d=ly / ny)
+    return lam * np.sqrt(qx[None, :] ** 2 + qy[:, None] ** 2) * 1000.0
+
+
+def line_profile(values, lx: float, lam: float):
+    """Profile of values (ny, nx) (FFT order) along q_y = 0, in ascending
+    theta_x = lambda q_x; returns (line (nx,), theta_x (nx,) in mrad)."""
+    values = np.asarray(values, dtype=np.float64)
+    nx = values.shape[1]
+    order = np.fft.fftshift(np.arange(nx))
+    qx = np.fft.fftfreq(nx, d=lx / nx)
+    return values[0, order], lam * qx[order] * 1000.0
+
+
+def azimuthal_profile(values, lx: float, ly: float, lam: float, dtheta: float, n_bins: int):
+    """Mean of values (ny, nx) (FFT order) over the q with theta in
+    [b dtheta, (b+1) dtheta), b < n_bins (0 for an empty bin); returns
+    (profile (n_bins,), counts (n_bins,))."""
+    values = np.asarray(values, dtype=np.float64)
+    ny, nx = values.shape
+    b = np.floor(scattering_angles(nx, ny, lx, ly, lam) / dtheta).ravel()
+    keep = b < n_bins
+    counts = np.bincount(b[keep].astype(int), minlength=n_bins)
+    sums = np.bincount(b[keep].astype(int), weights=values.ravel()[keep], minlength=n_bins)
+    prof = np.where(counts > 0, sums / np.maximum(counts, 1), 0.0)
+    return prof, counts
+
+
+def relative_difference(a, b) -> np.ndarray:
+    """(a - b) / (a + b), 0 where a + b = 0 (the paper's difference divided by sum)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = a + b
+    return np.where(s != 0.0, (a - b) / np.where(s != 0.0, s, 1.0), 0.0)

@@ -150,6 +150,22 @@ def _segments_variant(stride_is_length=False, divide=True, global_mean=False):
     return seg
 
 
+def _line_unshifted(values, lx, lam):
+    values = np.asarray(values, float)
+    nx = values.shape[1]
+    return values[0], lam * np.fft.fftfreq(nx, d=lx / nx) * 1000.0
+
+
+def _azimuthal_rounded(values, lx, ly, lam, dtheta, n_bins):
+    values = np.asarray(values, float)
+    ny, nx = values.shape
+    b = np.round(T.scattering_angles(nx, ny, lx, ly, lam) / dtheta).ravel()
+    keep = b < n_bins
+    counts = np.bincount(b[keep].astype(int), minlength=n_bins)
+    sums = np.bincount(b[keep].astype(int), weights=values.ravel()[keep], minlength=n_bins)
+    return np.where(counts > 0, sums / np.maximum(counts, 1), 0.0), counts
+
+
 MUTATIONS = {
     "fft_missing_1_over_N": ("fft2_unitary", lambda p: np.fft.fft2(p)),
     "ifft_with_1_over_N": ("ifft2_unitary", lambda p: np.fft.ifft2(p)),
@@ -179,6 +195,12 @@ MUTATIONS = {
     "segments_offset_as_overlap": ("segment_spectrum", _segments_variant(stride_is_length=True)),
     "segments_summed_not_averaged": ("segment_spectrum", _segments_variant(divide=False)),
     "segments_global_mean": ("segment_spectrum", _segments_variant(global_mean=True)),
+    "qep_ignores_stride": ("qep_intensity",
+                           lambda psi, t0=0, stride=1, n=None: np.mean(np.abs(np.asarray(psi, complex)) ** 2, axis=0)),
+    "line_profile_fft_order": ("line_profile", _line_unshifted),
+    "azimuthal_rounded_bins": ("azimuthal_profile", _azimuthal_rounded),
+    "relative_difference_over_b": ("relative_difference",
+                                   lambda a, b: (np.asarray(a, float) - b) / np.where(np.asarray(b) != 0, b, 1.0)),
     "wavelength_nonrelativistic": ("wavelength",
                                    lambda kev: T.PLANCK_J_S / np.sqrt(2 * T.ME_KG * kev * 1e3 * T.E_C)
                                    * 1e10),
@@ -208,6 +230,11 @@ PINS = [
     lambda: P.test_segment_sets_match_paper(),
     lambda: P.test_segment_spectrum_bruteforce(),
     lambda: P.test_segment_spectrum_parseval_over_tiling_sets(),
+    lambda: P.test_qep_subset_of_the_si_trajectory(),
+    lambda: P.test_energy_integral_equals_qep_of_all_snapshots(),
+    lambda: P.test_line_profile_bragg_spots_of_a_static_crystal(),
+    lambda: P.test_azimuthal_profile_bruteforce(),
+    lambda: P.test_relative_difference_closed_forms(),
 ]
 
 

@@ -494,3 +494,70 @@ def test_segment_spectrum_single_mode_on_bin():
     tot = inten.sum()
     assert inten[:, ~harm].sum() < 1e-12 * tot
     assert inten[:, k == 2].sum() > 1e-3 * tot and inten[:, k == -2].sum() > 1e-3 * tot
+
+
+# ---------------------------------------------------------------------------
+# QEP by-products: patterns, energy integrals, line and azimuthal profiles
+# ---------------------------------------------------------------------------
+def test_qep_subset_of_the_si_trajectory():
+    # first figure: "QEP 100" takes 100 evenly spaced snapshots every 1 ps out of
+    # the 4000 snapshots at 25 fs, i.e. every 40th; with |psi(t)|^2 = t the
+    # pattern is the mean of 0, 40, ..., 3960 = 1980
+    psi = np.sqrt(np.arange(4000.0))[:, None] * np.ones((1, 3))
+    stride = int(round(1000.0 / 25.0))
+    assert len(np.arange(0, 4000, stride)) == 100
+    assert np.allclose(O.qep_intensity(psi, 0, stride), 1980.0, rtol=1e-15)
+    assert np.allclose(O.qep_intensity(psi, 10, stride, n=3), (10 + 50 + 90) / 3.0, rtol=1e-15)
+
+
+def test_energy_integral_equals_qep_of_all_snapshots():
+    rng = np.random.default_rng(13)
+    psi = _waves(rng, 40, 7)
+    inten, iel, _ = O.spectrum(psi, 5.0)
+    assert np.allclose(O.energy_integral(inten, iel), O.qep_intensity(psi), rtol=1e-13)
+
+
+def test_line_profile_bragg_spots_of_a_static_crystal():
+    # a crystal with period a = 8 pixels diffracts only into k_x = 8 h; along
+    # theta_y = 0 the pattern sits at theta_x = lambda h / a
+    g = _grid(nx=64, ny=64, lx=32.0, ly=32.0, n_slices=2, dz=4.0, z0=0.0, kev=100.0)
+    cr = W.simple_cubic((8, 8, 2), 4.0)
+    psi = O.exit_waves(g, cr.positions[None].astype(np.float64), cr.species, [[20.0, 0.3]], processes=1)
+    lam = O.wavelength(g.kev)
+    line, theta = O.line_profile(O.qep_intensity(psi), g.lx, lam)
+    k = np.arange(64) - 32
+    assert np.allclose(theta, lam * k / 32.0 * 1000.0, rtol=1e-14)
+    bragg = (k % 8) == 0
+    assert np.max(line[~bragg]) < 1e-20 * np.max(line)
+    for h in (-2, -1, 0, 1, 2):                                    # inside the 2/3 band limit
+        assert line[k == 8 * h][0] > 1e-8 * np.max(line)
+        assert theta[k == 8 * h][0] == pytest.approx(lam * h / 4.0 * 1000.0, rel=1e-14, abs=1e-14)
+
+
+def test_azimuthal_profile_bruteforce():
+    import math
+    rng = np.random.default_rng(14)
+    nx, ny, lx, ly, lam, dth, nb = 6, 5, 3.0, 2.5, 0.037, 7.3, 4
+    values = rng.random((ny, nx))
+    prof, counts = O.azimuthal_profile(values, lx, ly, lam, dth, nb)
+    ref_s, ref_c = np.zeros(nb), np.zeros(nb, int)
+    for j in range(ny):
+        for i in range(nx):
+            ki = i if i < (nx + 1) // 2 else i - nx
+            kj = j if j < (ny + 1) // 2 else j - ny
+            th = lam * math.hypot(ki / lx, kj / ly) * 1000.0
+            b = int(th // dth)
+            if b < nb:
+                ref_s[b] += values[j, i]
+                ref_c[b] += 1
+    assert np.array_equal(counts, ref_c) and counts.sum() > 0 and np.all(counts > 0)
+    assert np.allclose(prof, ref_s / ref_c, rtol=1e-14)
+
+
+def test_relative_difference_closed_forms():
+    a = np.array([3.0, 1.0, 0.0, 2.0, -1.0])
+    b = np.array([1.0, 3.0, 0.0, 2.0, 1.0])
+    r = O.relative_difference(a, b)
+    assert np.array_equal(r[:4], [0.5, -0.5, 0.0, 0.0])
+    assert r[4] == 0.0                                   # a + b = 0
+    assert np.array_equal(O.relative_difference(b, a)[:4], -r[:4])
