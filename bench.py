@@ -48,6 +48,8 @@ def parse_args():
     p.add_argument("--cpu-snapshots", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--seg", default="512,256",
+                   help="snapshots per set and offset for the set-averaged spectrum timing ('' = skip)")
     return p.parse_args()
 
 
@@ -370,6 +372,31 @@ def run_ours(args):
         fp32_ms = statistics.mean(stage_ms("spectrum"))
         tts.precision = args.precision
 
+    # spectra averaged over sets of consecutive snapshots, on the same exit waves
+    seg = None
+    if args.seg:
+        from paper_2401_15599_gb300 import api as A
+        seg_len, hop = (int(x) for x in args.seg.split(","))
+        if seg_len <= n_t:
+            psi2 = tts.psi.reshape(n_t, -1)
+            n_sets = (n_t - seg_len) // hop + 1
+            for _ in range(2):
+                A.spectrum_segments(psi2, w.dt_fs, seg_len, hop, precision=args.precision)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                A.spectrum_segments(psi2, w.dt_fs, seg_len, hop, precision=args.precision)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            seg_ms = statistics.mean(times)
+            flop = 8.0 * g.nx * g.ny * seg_len * seg_len * n_sets * (3 if args.precision == "bf16x3" else 1)
+            seg = {"seg_len": seg_len, "hop": hop, "n_sets": n_sets, "ms": seg_ms,
+                   "precision": args.precision, "tflops": flop / (seg_ms * 1e-3) / 1e12}
+
     # end to end: host positions in, host spectrum out, through the same C-ABI calls
     e2e = None
     if not args.no_e2e:
@@ -413,6 +440,7 @@ def run_ours(args):
             "plain_fp32_spectrum_ms": fp32_ms,
             "time_to_spectrum_plain_fp32_ms": (ms_step - stages["spectrum"] + fp32_ms) if fp32_ms else None,
             "roofline": roofline, "roofline_spectrum": roofline_spectrum,
+            "set_averaged_spectrum": seg,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clk,
         }

@@ -191,6 +191,80 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
                    double temperature_K, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * Spectrum averaged over sets of consecutive snapshots (the averaging over
+ * segments of one trajectory described after Eq. (9); the paper averages,
+ * e.g., 79 sets of 100 snapshots offset by 50).  Set g = 0 .. n_sets-1 holds
+ * snapshots g*hop .. g*hop + seg_len - 1 and is a trajectory of its own:
+ *
+ *   m_g(q)     = (1/seg_len) sum_n psi(q, t_{g hop + n})          (FP64)
+ *   I_g(q, E)  = |sum_n (psi - m_g)(q, t_{g hop + n}) exp(-i E n dt / hbar)|^2 / seg_len^2
+ *   I(q, E)    = (1/n_sets) sum_g I_g(q, E),   I_el(q) = (1/n_sets) sum_g |m_g(q)|^2
+ *
+ * (time measured from the start of each set: the start only adds a phase).
+ * TACAW_KUBO and TACAW_NORMALIZE act on the averages as in tacaw_spectrum.
+ *
+ * nq, dt_fs  as in tacaw_spectrum; psi [n_t][nq] float2 exit waves (DEVICE)
+ * seg_len    snapshots per set, 1 <= seg_len <= min(n_t, 65535)
+ * hop        offset between the first snapshots of consecutive sets, >= 1
+ * n_sets     number of sets, 1 .. (n_t - seg_len) / hop + 1; 0 = all that fit
+ * omega_meV  DEVICE [n_omega] energies, or NULL for the natural grid of one
+ *            set: n_omega == seg_len, E_k = h (k - seg_len/2) / (seg_len dt)
+ * I          out [nq][n_omega] float;  I_el out [nq] double, or NULL
+ * precision  TACAW_FP32 or TACAW_BF16X3 (the per-set transform); sums over
+ *            sets are FP64.
+ * Errors: TACAW_EINVAL for sizes, sets that do not fit, unknown flags or
+ * precision; TACAW_EUNSUPPORTED above 32640 energies with TACAW_BF16X3.
+ */
+int tacaw_spectrum_segments(int32_t nq, int32_t n_t, double dt_fs, int32_t seg_len, int32_t hop,
+                            int32_t n_sets, int32_t n_omega, const double* omega_meV, const void* psi,
+                            float* I, double* I_el, int32_t precision, int32_t flags,
+                            double temperature_K, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Quasi-elastic (QEP / frozen-phonon) by-products, the quantities the paper
+ * compares in its first figure (diffraction pattern of the time-averaged
+ * intensity, energy integral of the spectrum, line profiles along
+ * theta_y = 0, relative differences).  All arrays are DEVICE pointers; sums
+ * are FP64 in a fixed order, so results do not vary between runs.
+ *
+ * tacaw_qep_intensity: the QEP pattern of a subset of snapshots (Eq. (4) with
+ *   Eq. (3): |psi|^2 averaged over configurations), e.g. every 40th snapshot
+ *   for a "100 snapshots every 1 ps" QEP of a 25 fs trajectory:
+ *     qep[q] = (1/n) sum_{j < n} |psi(q, t0 + j stride)|^2
+ *   psi [n_t][nq] float2; n = 0 takes every snapshot t0, t0 + stride, ... < n_t.
+ *   TACAW_EINVAL when the snapshots do not fit.
+ *
+ * tacaw_energy_integral: out[q] = I_el[q] + sum_k I[q][k] (I [nq][n_omega]
+ *   float, I_el [nq] double or NULL).  On the natural grid it equals the QEP
+ *   pattern of all snapshots (Parseval).
+ *
+ * tacaw_line_profile: the profile along k_y = 0 of values [ny][nx] (FFT
+ *   order, double): line[i] = values[k_x(i)], k_x(i) = i - nx/2 (mod nx), in
+ *   ascending theta_x = lambda q_x; theta_mrad [nx] receives theta_x in mrad
+ *   (or NULL).  q_x = k/lx as numpy's fftfreq.
+ *
+ * tacaw_azimuthal_profile: mean of values [ny][nx] (FFT order, double) over
+ *   the q with theta = lambda |q| (mrad, FP64) in [b dtheta, (b+1) dtheta),
+ *   b = 0 .. n_bins-1 -> profile [n_bins] (0 for an empty bin); counts
+ *   [n_bins] int32 receives the number of q per bin (or NULL).  lambda_A is
+ *   given by the caller (e.g. from tacaw_beam_constants).  Workspace: one
+ *   int32 per q (query with ws == NULL).
+ *
+ * tacaw_relative_difference: out[i] = (a[i] - b[i]) / (a[i] + b[i]) (0 where
+ *   a + b = 0), the "difference divided by sum" of two profiles, n doubles.
+ */
+int tacaw_qep_intensity(int32_t nq, int32_t n_t, int32_t t0, int32_t stride, int32_t n, const void* psi,
+                        double* qep, void* stream);
+int tacaw_energy_integral(int32_t nq, int32_t n_omega, const float* I, const double* I_el, double* out,
+                          void* stream);
+int tacaw_line_profile(int32_t nx, int32_t ny, double lx, double lambda_A, const double* values,
+                       double* line, double* theta_mrad, void* stream);
+int tacaw_azimuthal_profile(int32_t nx, int32_t ny, double lx, double ly, double lambda_A,
+                            double dtheta_mrad, int32_t n_bins, const double* values, double* profile,
+                            int32_t* counts, void* ws, size_t* ws_bytes, void* stream);
+int tacaw_relative_difference(int64_t n, const double* a, const double* b, double* out, void* stream);
+
+/*
  * Adjoint of tacaw_spectrum (flags 0) for gradient-based fitting: given
  * dL/dI (real, [nq][n_omega]) returns the gradient with respect to psi in
  * the PyTorch convention for complex inputs (dL/dRe + i dL/dIm):

@@ -73,6 +73,17 @@ SIGNATURES = {
     "tacaw_spectrum": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P,
                                       _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                       _P, _SZ, _P]),
+    "tacaw_spectrum_segments": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _P, _SZ, _P]),
+    "tacaw_qep_intensity": (ctypes.c_int, [ctypes.c_int32] * 5 + [_P, _P, _P]),
+    "tacaw_energy_integral": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
+    "tacaw_line_profile": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                          _P, _P, _P, _P]),
+    "tacaw_azimuthal_profile": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P,
+                                               _SZ, _P]),
+    "tacaw_relative_difference": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P]),
     "tacaw_spectrum_backward": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                ctypes.c_int32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "tacaw_multislice_backward": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,

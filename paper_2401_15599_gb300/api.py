@@ -155,6 +155,112 @@ def _call_with_workspace(fn_name, call, device, workspace=None):
     L.check(fn_name, call(_ptr(workspace), ctypes.byref(nbytes)))
 
 
+def spectrum_segments(psi, dt_fs, seg_len, hop, n_sets=0, omega_meV=None, precision="fp32", kubo=False,
+                      temperature_K=300.0, normalize=False, out=None, i_el=None, workspace=None):
+    """I(q, E) [nq, n_omega] (float32) and I_el [nq] (float64) averaged over sets of
+    seg_len consecutive snapshots of psi [T, nq] offset by hop (n_sets = 0: all sets)."""
+    lib = L.load()
+    if psi.dim() > 2:
+        psi = psi.reshape(psi.shape[0], -1)
+    _need_cuda("psi", psi, torch.complex64, 2)
+    n_t, nq = psi.shape
+    dev = psi.device
+    if omega_meV is not None:
+        omega_meV = torch.as_tensor(omega_meV, dtype=torch.float64).to(dev).contiguous()
+    n_w = seg_len if omega_meV is None else omega_meV.numel()
+    if out is None:
+        out = torch.empty((nq, n_w), dtype=torch.float32, device=dev)
+    if i_el is None:
+        i_el = torch.empty(nq, dtype=torch.float64, device=dev)
+    _need_cuda("out", out, torch.float32, 2)
+    _need_cuda("i_el", i_el, torch.float64, 1)
+    flags = (L.TACAW_KUBO if kubo else 0) | (L.TACAW_NORMALIZE if normalize else 0)
+    prec = _PRECISION[precision]
+
+    def call(ws, nbytes):
+        return lib.tacaw_spectrum_segments(nq, n_t, float(dt_fs), int(seg_len), int(hop), int(n_sets), n_w,
+                                           _ptr(omega_meV), _ptr(psi), _ptr(out), _ptr(i_el), prec, flags,
+                                           float(temperature_K), ws, nbytes, _stream(dev))
+    _call_with_workspace("tacaw_spectrum_segments", call, dev, workspace)
+    return out, i_el
+
+
+def qep_intensity(psi, t0=0, stride=1, n=0, out=None):
+    """(1/n) sum_j |psi(q, t0 + j stride)|^2 [nq] (float64) from psi [T, nq] (complex64)."""
+    lib = L.load()
+    if psi.dim() > 2:
+        psi = psi.reshape(psi.shape[0], -1)
+    _need_cuda("psi", psi, torch.complex64, 2)
+    n_t, nq = psi.shape
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float64, device=psi.device)
+    _need_cuda("out", out, torch.float64, 1)
+    L.check("tacaw_qep_intensity", lib.tacaw_qep_intensity(nq, n_t, int(t0), int(stride), int(n), _ptr(psi),
+                                                           _ptr(out), _stream(psi.device)))
+    return out
+
+
+def energy_integral(inten, i_el=None, out=None):
+    """I_el[q] + sum_k I[q, k] [nq] (float64) from I [nq, n_omega] (float32)."""
+    lib = L.load()
+    _need_cuda("I", inten, torch.float32, 2)
+    nq, n_w = inten.shape
+    if i_el is not None:
+        _need_cuda("i_el", i_el, torch.float64, 1)
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float64, device=inten.device)
+    _need_cuda("out", out, torch.float64, 1)
+    L.check("tacaw_energy_integral", lib.tacaw_energy_integral(nq, n_w, _ptr(inten), _ptr(i_el), _ptr(out),
+                                                               _stream(inten.device)))
+    return out
+
+
+def line_profile(values, lx, lambda_A):
+    """Profile of values [ny, nx] (float64, FFT order) along k_y = 0 in ascending
+    theta_x = lambda q_x: returns (line [nx], theta_x [nx] in mrad)."""
+    lib = L.load()
+    _need_cuda("values", values, torch.float64, 2)
+    ny, nx = values.shape
+    line = torch.empty(nx, dtype=torch.float64, device=values.device)
+    theta = torch.empty(nx, dtype=torch.float64, device=values.device)
+    L.check("tacaw_line_profile", lib.tacaw_line_profile(nx, ny, float(lx), float(lambda_A), _ptr(values),
+                                                         _ptr(line), _ptr(theta), _stream(values.device)))
+    return line, theta
+
+
+def azimuthal_profile(values, lx, ly, lambda_A, dtheta_mrad, n_bins, workspace=None):
+    """Mean of values [ny, nx] (float64, FFT order) in bins of theta = lambda |q|
+    (mrad): returns (profile [n_bins] float64, counts [n_bins] int32)."""
+    lib = L.load()
+    _need_cuda("values", values, torch.float64, 2)
+    ny, nx = values.shape
+    dev = values.device
+    prof = torch.empty(int(n_bins), dtype=torch.float64, device=dev)
+    counts = torch.empty(int(n_bins), dtype=torch.int32, device=dev)
+
+    def call(ws, nbytes):
+        return lib.tacaw_azimuthal_profile(nx, ny, float(lx), float(ly), float(lambda_A), float(dtheta_mrad),
+                                           int(n_bins), _ptr(values), _ptr(prof), _ptr(counts), ws, nbytes,
+                                           _stream(dev))
+    _call_with_workspace("tacaw_azimuthal_profile", call, dev, workspace)
+    return prof, counts
+
+
+def relative_difference(a, b, out=None):
+    """(a - b) / (a + b) elementwise (0 where a + b = 0), float64 tensors of equal size."""
+    lib = L.load()
+    _need_cuda("a", a, torch.float64)
+    _need_cuda("b", b, torch.float64)
+    if a.numel() != b.numel():
+        raise ValueError("a and b must have the same size")
+    if out is None:
+        out = torch.empty_like(a)
+    _need_cuda("out", out, torch.float64)
+    L.check("tacaw_relative_difference", lib.tacaw_relative_difference(a.numel(), _ptr(a), _ptr(b), _ptr(out),
+                                                                       _stream(a.device)))
+    return out
+
+
 def spectrum_backward(psi, dt_fs, dl_di, omega_meV=None, psi_sum=None, out=None, workspace=None):
     """dL/dpsi [T, nq] (complex64) given dL/dI [nq, n_omega] (float32), FP32."""
     lib = L.load()

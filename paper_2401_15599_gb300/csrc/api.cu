@@ -60,6 +60,20 @@ int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, co
                  size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
                  int flags, double temperature_K, void* ws, cudaStream_t st);
 
+size_t spectrum_segments_ws_bytes(int nq, int seg_len, int n_w, int precision);
+int spectrum_segments_run(int nq, double dt_fs, int seg_len, int hop, int n_sets, int n_w,
+                          const double* omega, const float2* psi, float* out, double* i_el, int precision,
+                          int flags, double temperature_K, void* ws, cudaStream_t st);
+
+int qep_run(int nq, int t0, int stride, int n, const float2* psi, double* qep, cudaStream_t st);
+int energy_integral_run(int nq, int n_w, const float* I, const double* i_el, double* out, cudaStream_t st);
+int line_profile_run(int nx, int ny, double lx, double lam, const double* values, double* line, double* theta,
+                     cudaStream_t st);
+size_t azimuthal_ws_bytes(int nq);
+int azimuthal_run(int nx, int ny, double lx, double ly, double lam, double dtheta, int n_bins,
+                  const double* values, double* prof, int* counts, void* ws, cudaStream_t st);
+int rel_diff_run(size_t n, const double* a, const double* b, double* out, cudaStream_t st);
+
 static int check_grid(const tacaw_grid* g, const char* fn) {
     TACAW_REQUIRE(g != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
     TACAW_REQUIRE(g->nx > 0 && g->ny > 0 && g->n_slices > 0 && g->n_slices <= 65535, TACAW_EINVAL,
@@ -202,6 +216,37 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
                         (cudaStream_t)stream);
 }
 
+int tacaw_spectrum_segments(int32_t nq, int32_t n_t, double dt_fs, int32_t seg_len, int32_t hop,
+                            int32_t n_sets, int32_t n_omega, const double* omega_meV, const void* psi,
+                            float* I, double* I_el, int32_t precision, int32_t flags, double temperature_K,
+                            void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_spectrum_segments";
+    TACAW_REQUIRE(nq > 0 && n_omega > 0 && seg_len > 0 && seg_len <= 65535 && hop > 0 && seg_len <= n_t,
+                  TACAW_EINVAL, "%s: need nq, n_omega, hop > 0 and 1 <= seg_len <= min(T, 65535)", fn);
+    const long long most = ((long long)n_t - seg_len) / hop + 1;
+    const int sets = n_sets == 0 ? (int)(most < 0x7fffffff ? most : 0x7fffffff) : n_sets;
+    TACAW_REQUIRE(sets >= 1 && sets <= most, TACAW_EINVAL,
+                  "%s: n_sets = %d, but only %lld sets of %d snapshots offset by %d fit in %d", fn, n_sets,
+                  most, seg_len, hop, n_t);
+    TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
+    TACAW_REQUIRE(omega_meV != nullptr || n_omega == seg_len, TACAW_EINVAL,
+                  "%s: the natural grid (omega NULL) has n_omega == seg_len", fn);
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3, TACAW_EINVAL,
+                  "%s: unknown precision %d", fn, precision);
+    TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)), TACAW_EINVAL,
+                  "%s: the Kubo factor needs a positive temperature", fn);
+    TACAW_REQUIRE(precision != TACAW_BF16X3 || n_omega <= 32640, TACAW_EUNSUPPORTED,
+                  "%s: the tensor-core path takes at most 32640 energies", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, spectrum_segments_ws_bytes(nq, seg_len, n_omega, precision), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(psi && I, TACAW_EINVAL, "%s: NULL array", fn);
+    return spectrum_segments_run(nq, dt_fs, seg_len, hop, sets, n_omega, omega_meV, (const float2*)psi, I, I_el,
+                                 precision, flags, temperature_K, ws, (cudaStream_t)stream);
+}
+
 int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
                             const double* omega_meV, const void* psi, const void* psi_sum,
                             const float* dL_dI, void* dL_dpsi, void* ws, size_t* ws_bytes,
@@ -266,6 +311,66 @@ int tacaw_potential_backward(const tacaw_grid* grid, int32_t n_t, int32_t n_atom
                   "%s: NULL array", fn);
     return potential_backward_run(*grid, n_t, n_atoms, pos, species, n_species, amp_sigma, dL_dV,
                                   dL_damp_sigma, ws, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ QEP by-products
+int tacaw_qep_intensity(int32_t nq, int32_t n_t, int32_t t0, int32_t stride, int32_t n, const void* psi,
+                        double* qep, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_qep_intensity";
+    TACAW_REQUIRE(nq > 0 && n_t > 0 && t0 >= 0 && stride >= 1, TACAW_EINVAL,
+                  "%s: need nq, n_t > 0, t0 >= 0, stride >= 1", fn);
+    const long long most = t0 < n_t ? ((long long)n_t - 1 - t0) / stride + 1 : 0;
+    const long long use = n == 0 ? most : n;
+    TACAW_REQUIRE(use >= 1 && use <= most, TACAW_EINVAL,
+                  "%s: %d snapshots from %d every %d do not fit in %d", fn, n, t0, stride, n_t);
+    TACAW_REQUIRE(psi && qep, TACAW_EINVAL, "%s: NULL array", fn);
+    return qep_run(nq, t0, stride, (int)use, (const float2*)psi, qep, (cudaStream_t)stream);
+}
+
+int tacaw_energy_integral(int32_t nq, int32_t n_omega, const float* I, const double* I_el, double* out,
+                          void* stream) {
+    clear_error();
+    const char* fn = "tacaw_energy_integral";
+    TACAW_REQUIRE(nq > 0 && n_omega > 0, TACAW_EINVAL, "%s: nq and n_omega must be positive", fn);
+    TACAW_REQUIRE(I && out, TACAW_EINVAL, "%s: NULL array", fn);
+    return energy_integral_run(nq, n_omega, I, I_el, out, (cudaStream_t)stream);
+}
+
+int tacaw_line_profile(int32_t nx, int32_t ny, double lx, double lambda_A, const double* values, double* line,
+                       double* theta_mrad, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_line_profile";
+    TACAW_REQUIRE(nx > 0 && ny > 0 && lx > 0 && isfinite(lx) && lambda_A > 0 && isfinite(lambda_A), TACAW_EINVAL,
+                  "%s: need nx, ny, lx, lambda > 0", fn);
+    TACAW_REQUIRE(values && line, TACAW_EINVAL, "%s: NULL array", fn);
+    return line_profile_run(nx, ny, lx, lambda_A, values, line, theta_mrad, (cudaStream_t)stream);
+}
+
+int tacaw_azimuthal_profile(int32_t nx, int32_t ny, double lx, double ly, double lambda_A, double dtheta_mrad,
+                            int32_t n_bins, const double* values, double* profile, int32_t* counts, void* ws,
+                            size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_azimuthal_profile";
+    TACAW_REQUIRE(nx > 0 && ny > 0 && (long long)nx * ny <= 0x7fffffff && n_bins > 0 && lx > 0 && ly > 0 &&
+                      isfinite(lx) && isfinite(ly) && lambda_A > 0 && isfinite(lambda_A) && dtheta_mrad > 0 &&
+                      isfinite(dtheta_mrad),
+                  TACAW_EINVAL, "%s: need positive sizes, lengths, lambda and bin width", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, azimuthal_ws_bytes(nx * ny), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(values && profile, TACAW_EINVAL, "%s: NULL array", fn);
+    return azimuthal_run(nx, ny, lx, ly, lambda_A, dtheta_mrad, n_bins, values, profile, counts, ws,
+                         (cudaStream_t)stream);
+}
+
+int tacaw_relative_difference(int64_t n, const double* a, const double* b, double* out, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_relative_difference";
+    TACAW_REQUIRE(n >= 0, TACAW_EINVAL, "%s: n must be >= 0", fn);
+    if (n == 0) return TACAW_OK;
+    TACAW_REQUIRE(a && b && out, TACAW_EINVAL, "%s: NULL array", fn);
+    return rel_diff_run((size_t)n, a, b, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

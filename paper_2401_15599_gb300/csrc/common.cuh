@@ -37,6 +37,10 @@ void clear_error();
 #define TACAW_LAUNCH_CHECK() TACAW_CUDA_CHECK(cudaGetLastError())
 
 // Workspace carving: aligned sub-buffers of a caller-provided block.
+// Planck and Boltzmann constants in meV fs and meV / K (exact SI values).
+constexpr double kPlanckMeVfs = 6.62607015e-34 / 1.602176634e-19 * 1e3 * 1e15;
+constexpr double kBoltzmannMeVK = 1.380649e-23 / 1.602176634e-19 * 1e3;
+
 struct Carver {
     char* base;
     size_t off = 0;

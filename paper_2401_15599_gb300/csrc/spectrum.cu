@@ -18,8 +18,6 @@ namespace tacaw {
 namespace {
 
 // CODATA 2018: h in meV*fs and the Boltzmann constant in meV/K.
-constexpr double kPlanckMeVfs = 6.62607015e-34 / 1.602176634e-19 * 1e3 * 1e15;
-constexpr double kBoltzmannMeVK = 1.380649e-23 / 1.602176634e-19 * 1e3;
 
 __global__ void time_sum_kernel(const float2* __restrict__ psi, size_t ld, double2* __restrict__ sum,
                                 int n_t, int nq) {

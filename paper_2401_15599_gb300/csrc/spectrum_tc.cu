@@ -46,7 +46,6 @@ constexpr int GROUP_N = 8;                               // N tiles sharing an L
 constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 
 // CODATA 2018 Planck constant in meV*fs.
-constexpr double kPlanckMeVfs = 6.62607015e-34 / 1.602176634e-19 * 1e3 * 1e15;
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
     hi = __float2bfloat16_rn(x);
