@@ -56,7 +56,7 @@ __all__ = [
     "natural_energies", "time_mean", "temporal_transform", "kubo_factor",
     "spectrum", "segment_count", "segment_starts", "segment_spectrum",
     "qep_intensity", "energy_integral", "scattering_angles", "line_profile", "azimuthal_profile",
-    "relative_difference",
+    "relative_difference", "probe",
 ]
 
 # ---------------------------------------------------------------------------
@@ -453,3 +453,28 @@ def relative_difference(a, b) -> np.ndarray:
     b = np.asarray(b, dtype=np.float64)
     s = a + b
     return np.where(s != 0.0, (a - b) / np.where(s != 0.0, s, 1.0), 0.0)
+
+
+# ---------------------------------------------------------------- convergent probe
+def probe(g: Grid, alpha_mrad: float, defocus_A: float = 0.0, x0: float = 0.0, y0: float = 0.0) -> np.ndarray:
+    """Real-space incident wave of a convergent probe (the 1 mrad convergence
+    semi-angle set-up of the paper's Fe simulation), shape (ny, nx) complex128.
+
+    Psi(q) = exp(-i pi lambda defocus |q|^2) exp(-2 pi i q.r_p) / sqrt(N_ap)
+    for the N_ap grid points with theta = lambda |q| <= alpha (FP64, theta in
+    mrad as lambda * sqrt(qx^2 + qy^2) * 1000), 0 elsewhere; psi(r) is its
+    inverse transform without 1/N, so mean_r |psi|^2 = sum_q |Psi|^2 = 1 like
+    the unit plane wave.  A positive defocus equals free propagation by that
+    distance with the multislice propagator's sign.
+    """
+    qx, qy = spatial_frequencies(g)
+    lam = wavelength(g.kev)
+    theta = lam * np.sqrt(qx[None, :] ** 2 + qy[:, None] ** 2) * 1000.0
+    inside = theta <= alpha_mrad
+    n_ap = int(np.count_nonzero(inside))
+    if n_ap == 0:
+        raise ValueError("no grid point inside the aperture")
+    q2 = qx[None, :] ** 2 + qy[:, None] ** 2
+    phase = -np.pi * lam * defocus_A * q2 - 2.0 * np.pi * (qx[None, :] * x0 + qy[:, None] * y0)
+    psi_q = np.where(inside, np.exp(1j * phase), 0.0) / np.sqrt(n_ap)
+    return ifft2_unitary(psi_q)

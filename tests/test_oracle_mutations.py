@@ -166,6 +166,19 @@ def _azimuthal_rounded(values, lx, ly, lam, dtheta, n_bins):
     return np.where(counts > 0, sums / np.maximum(counts, 1), 0.0), counts
 
 
+def _probe_variant(defocus_sign=1.0, shift_sign=1.0, norm_power=0.5):
+    def probe(g, alpha_mrad, defocus_A=0.0, x0=0.0, y0=0.0):
+        qx, qy = T.spatial_frequencies(g)
+        lam = T.wavelength(g.kev)
+        inside = lam * np.sqrt(qx[None, :] ** 2 + qy[:, None] ** 2) * 1000.0 <= alpha_mrad
+        q2 = qx[None, :] ** 2 + qy[:, None] ** 2
+        phase = (-defocus_sign * np.pi * lam * defocus_A * q2
+                 - shift_sign * 2.0 * np.pi * (qx[None, :] * x0 + qy[:, None] * y0))
+        psi_q = np.where(inside, np.exp(1j * phase), 0.0) / np.count_nonzero(inside) ** norm_power
+        return T.ifft2_unitary(psi_q)
+    return probe
+
+
 MUTATIONS = {
     "fft_missing_1_over_N": ("fft2_unitary", lambda p: np.fft.fft2(p)),
     "ifft_with_1_over_N": ("ifft2_unitary", lambda p: np.fft.ifft2(p)),
@@ -201,6 +214,9 @@ MUTATIONS = {
     "azimuthal_rounded_bins": ("azimuthal_profile", _azimuthal_rounded),
     "relative_difference_over_b": ("relative_difference",
                                    lambda a, b: (np.asarray(a, float) - b) / np.where(np.asarray(b) != 0, b, 1.0)),
+    "probe_defocus_sign": ("probe", _probe_variant(defocus_sign=-1.0)),
+    "probe_shift_sign": ("probe", _probe_variant(shift_sign=-1.0)),
+    "probe_norm_not_sqrt": ("probe", _probe_variant(norm_power=1.0)),
     "wavelength_nonrelativistic": ("wavelength",
                                    lambda kev: T.PLANCK_J_S / np.sqrt(2 * T.ME_KG * kev * 1e3 * T.E_C)
                                    * 1e10),
@@ -235,6 +251,9 @@ PINS = [
     lambda: P.test_line_profile_bragg_spots_of_a_static_crystal(),
     lambda: P.test_azimuthal_profile_bruteforce(),
     lambda: P.test_relative_difference_closed_forms(),
+    lambda: P.test_probe_aperture_and_normalisation(),
+    lambda: P.test_probe_position_is_a_circular_shift(),
+    lambda: P.test_probe_defocus_is_free_propagation(),
 ]
 
 

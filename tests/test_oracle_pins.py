@@ -561,3 +561,51 @@ def test_relative_difference_closed_forms():
     assert np.array_equal(r[:4], [0.5, -0.5, 0.0, 0.0])
     assert r[4] == 0.0                                   # a + b = 0
     assert np.array_equal(O.relative_difference(b, a)[:4], -r[:4])
+
+
+# ---------------------------------------------------------------------------
+# Convergent probe
+# ---------------------------------------------------------------------------
+def test_probe_aperture_and_normalisation():
+    import math
+    g = _grid(nx=48, ny=40, lx=30.0, ly=25.0, n_slices=1, dz=2.0, kev=200.0)
+    lam = O.wavelength(g.kev)
+    alpha = 6.3                                        # mrad
+    psi = O.probe(g, alpha)
+    assert np.mean(np.abs(psi) ** 2) == pytest.approx(1.0, abs=1e-13)
+    psi_q = O.fft2_unitary(psi)
+    n_ap = 0
+    for j in range(g.ny):
+        for i in range(g.nx):
+            ki = i if i < (g.nx + 1) // 2 else i - g.nx
+            kj = j if j < (g.ny + 1) // 2 else j - g.ny
+            if lam * math.hypot(ki / g.lx, kj / g.ly) * 1000.0 <= alpha:
+                n_ap += 1
+                assert abs(psi_q[j, i]) == pytest.approx(1.0 / math.sqrt(n_ap_total(g, lam, alpha)), rel=1e-12)
+            else:
+                assert abs(psi_q[j, i]) < 1e-14
+    assert n_ap == n_ap_total(g, lam, alpha) and n_ap > 10
+    # an aperture that holds only q = 0 gives the unit plane wave
+    assert np.allclose(O.probe(g, 1e-3), 1.0, atol=1e-14)
+
+
+def n_ap_total(g, lam, alpha):
+    qx = np.fft.fftfreq(g.nx, d=g.lx / g.nx)
+    qy = np.fft.fftfreq(g.ny, d=g.ly / g.ny)
+    return int(np.count_nonzero(lam * np.hypot(qx[None, :], qy[:, None]) * 1000.0 <= alpha))
+
+
+def test_probe_position_is_a_circular_shift():
+    g = _grid(nx=64, ny=48, lx=32.0, ly=24.0, n_slices=1, dz=2.0, kev=200.0)
+    p0 = O.probe(g, 12.0, defocus_A=40.0)
+    p1 = O.probe(g, 12.0, defocus_A=40.0, x0=3 * g.lx / g.nx, y0=5 * g.ly / g.ny)
+    assert np.allclose(p1, np.roll(p0, (5, 3), axis=(0, 1)), atol=1e-12)
+    assert np.argmax(np.abs(O.probe(g, 12.0, x0=3 * g.lx / g.nx, y0=5 * g.ly / g.ny))) == 5 * g.nx + 3
+
+
+def test_probe_defocus_is_free_propagation():
+    # a probe defocused by f equals the focused probe propagated through f of vacuum
+    g = _grid(nx=64, ny=64, lx=32.0, ly=32.0, n_slices=2, dz=25.0, kev=200.0)
+    focused = O.probe(g, 15.0)
+    exit_q = O.multislice(g, np.zeros((2, 64, 64)), psi_in=focused)
+    assert np.allclose(exit_q, O.fft2_unitary(O.probe(g, 15.0, defocus_A=50.0)), atol=1e-13)
