@@ -265,6 +265,28 @@ int tacaw_azimuthal_profile(int32_t nx, int32_t ny, double lx, double ly, double
 int tacaw_relative_difference(int64_t n, const double* a, const double* b, double* out, void* stream);
 
 /*
+ * Convergent-probe incident wave for tacaw_multislice's psi_in (the paper's
+ * Fe set-up uses a 200 kV probe with a 1 mrad convergence semi-angle):
+ *
+ *   Psi(q) = exp(-i pi lambda f |q|^2) exp(-2 pi i q.r_p) / sqrt(N_ap)
+ *            for the N_ap grid points with theta = lambda |q| <= alpha, else 0
+ *   psi(r) = sum_q Psi(q) exp(2 pi i q.r)   (no 1/N, so mean |psi|^2 = 1 like
+ *            the unit plane wave)
+ *
+ * theta in mrad is evaluated in FP64 as lambda * sqrt(qx^2 + qy^2) * 1000 with
+ * q = k / l (numpy fftfreq order) and lambda from tacaw_beam_constants(kev).
+ * A positive defocus f (Angstrom) equals free propagation through f with the
+ * multislice propagator; r_p = (x0, y0) (Angstrom) is the probe position.
+ * The transform is a pruned FP64 DFT over the aperture's points, rounded to
+ * float once.  psi: out DEVICE [ny][nx] float2 (real space).  Workspace:
+ * query with ws == NULL.  TACAW_EINVAL for non-positive sizes or energy,
+ * alpha < 0 or non-finite values.
+ */
+int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double alpha_mrad,
+                double defocus_A, double x0_A, double y0_A, void* psi, void* ws, size_t* ws_bytes,
+                void* stream);
+
+/*
  * Adjoint of tacaw_spectrum (flags 0) for gradient-based fitting: given
  * dL/dI (real, [nq][n_omega]) returns the gradient with respect to psi in
  * the PyTorch convention for complex inputs (dL/dRe + i dL/dIm):

@@ -261,6 +261,23 @@ def relative_difference(a, b, out=None):
     return out
 
 
+def probe(grid, alpha_mrad, defocus_A=0.0, x0=0.0, y0=0.0, device="cuda", out=None, workspace=None):
+    """Convergent-probe incident wave [ny, nx] (complex64, real space) on the
+    grid's box at its beam energy, for multislice(..., psi_in=...)."""
+    lib = L.load()
+    dev = torch.device(device) if out is None else out.device
+    if out is None:
+        out = torch.empty((int(grid.ny), int(grid.nx)), dtype=torch.complex64, device=dev)
+    _need_cuda("out", out, torch.complex64, 2)
+
+    def call(ws, nbytes):
+        return lib.tacaw_probe(int(grid.nx), int(grid.ny), float(grid.lx), float(grid.ly), float(grid.kev),
+                               float(alpha_mrad), float(defocus_A), float(x0), float(y0), _ptr(out), ws, nbytes,
+                               _stream(dev))
+    _call_with_workspace("tacaw_probe", call, dev, workspace)
+    return out
+
+
 def spectrum_backward(psi, dt_fs, dl_di, omega_meV=None, psi_sum=None, out=None, workspace=None):
     """dL/dpsi [T, nq] (complex64) given dL/dI [nq, n_omega] (float32), FP32."""
     lib = L.load()

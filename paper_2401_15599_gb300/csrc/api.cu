@@ -74,6 +74,10 @@ int azimuthal_run(int nx, int ny, double lx, double ly, double lam, double dthet
                   const double* values, double* prof, int* counts, void* ws, cudaStream_t st);
 int rel_diff_run(size_t n, const double* a, const double* b, double* out, cudaStream_t st);
 
+size_t probe_ws_bytes(int nx, int ny, double lx, double ly, double lam, double alpha);
+int probe_run(int nx, int ny, double lx, double ly, double lam, double alpha, double defocus, double x0, double y0,
+              float2* psi, void* ws, cudaStream_t st);
+
 static int check_grid(const tacaw_grid* g, const char* fn) {
     TACAW_REQUIRE(g != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
     TACAW_REQUIRE(g->nx > 0 && g->ny > 0 && g->n_slices > 0 && g->n_slices <= 65535, TACAW_EINVAL,
@@ -371,6 +375,26 @@ int tacaw_relative_difference(int64_t n, const double* a, const double* b, doubl
     if (n == 0) return TACAW_OK;
     TACAW_REQUIRE(a && b && out, TACAW_EINVAL, "%s: NULL array", fn);
     return rel_diff_run((size_t)n, a, b, out, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ convergent probe
+int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double alpha_mrad, double defocus_A,
+                double x0_A, double y0_A, void* psi, void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_probe";
+    TACAW_REQUIRE(nx > 0 && ny > 0 && ny <= 65535 && lx > 0 && ly > 0 && isfinite(lx) && isfinite(ly), TACAW_EINVAL,
+                  "%s: need nx > 0, 0 < ny <= 65535 and positive lengths", fn);
+    TACAW_REQUIRE(kev > 0 && isfinite(kev) && alpha_mrad >= 0 && isfinite(alpha_mrad) && isfinite(defocus_A) &&
+                      isfinite(x0_A) && isfinite(y0_A),
+                  TACAW_EINVAL, "%s: need kev > 0, alpha >= 0 and finite defocus and position", fn);
+    double lam = 0.0, sig = 0.0;
+    beam_constants(kev, &lam, &sig);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, probe_ws_bytes(nx, ny, lx, ly, lam, alpha_mrad), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(psi, TACAW_EINVAL, "%s: NULL array", fn);
+    return probe_run(nx, ny, lx, ly, lam, alpha_mrad, defocus_A, x0_A, y0_A, (float2*)psi, ws,
+                     (cudaStream_t)stream);
 }
 
 }  // extern "C"
