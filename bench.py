@@ -43,7 +43,9 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="paper_scale")
     p.add_argument("--batch", type=int, default=32)
-    p.add_argument("--precision", choices=["bf16x3", "fp32"], default="bf16x3")
+    p.add_argument("--precision", choices=["fft32", "bf16x3", "fp32"], default="fft32",
+                   help="temporal transform: FP32 FFT over time (natural grid), split-BF16 tcgen05 GEMM, "
+                        "or FP32 SIMT GEMM")
     p.add_argument("--snapshots", type=int, default=0, help="override T (testing only)")
     p.add_argument("--cpu-snapshots", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -269,6 +271,8 @@ def run_ours(args):
     species = torch.from_numpy(inp.species).to(dev)
     pos = pos_host.to(dev, non_blocking=True)
     n_t, n_atoms = pos.shape[0], pos.shape[1]
+    if args.precision == "fft32" and n_t not in _lib.TIME_FFT_SIZES:
+        args.precision = "bf16x3"                 # no time-FFT plan for this T: the GEMM path
     tts = TimeToSpectrum(g, n_t, n_atoms, inp.amp_sigma, w.dt_fs, batch=args.batch, device=dev,
                          precision=args.precision)
     tts.prepare(None, None)
@@ -347,30 +351,46 @@ def run_ours(args):
                 "bytes_per_unit": round(bytes_pt, 3), "peak_kind": f"{peak_kind} hbm_gbs"}
     spec_ms = statistics.mean(stage_ms("spectrum"))
     nq = g.nx * g.ny
-    complex_flop = 8.0 * nq * n_t * n_t                 # 8 real flop per q, snapshot, energy
-    roofline_spectrum = None
-    if args.precision == "bf16x3":
-        tf = 3 * complex_flop / (spec_ms * 1e-3) / 1e12   # three BF16 products per complex flop
-        roofline_spectrum = {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
-                             "frac": tf / peak_tf, "traffic": None,
-                             "kernel": "tacaw_spectrum BF16X3 (split, centre, tcgen05 GEMM + |Phi|^2 epilogue)",
-                             "flop_per_unit": "3 x 8 real flop per q x snapshot x energy",
-                             "peak_kind": f"{peak_kind} bf16_tflops_sustained"}
     stages = {k: sum(stage_ms(k)) / args.steps for k in events}
 
-    # the plain FP32 form of the spectrum on the same exit waves, for comparison
-    fp32_ms = None
-    if args.precision != "fp32":
+    # the other forms of the temporal transform on the same exit waves, for comparison
+    spec_by_prec = {args.precision: spec_ms}
+    for prec in ("fft32", "bf16x3", "fp32"):
+        if prec == args.precision or (prec == "fft32" and n_t not in _lib.TIME_FFT_SIZES):
+            continue
         events["spectrum"].clear()
+        tts.precision = prec
         for _ in range(2):
-            tts.precision = "fp32"
             timed("spectrum", False, tts.spectrum)
         for _ in range(args.steps):
-            tts.precision = "fp32"
             timed("spectrum", True, tts.spectrum)
         torch.cuda.synchronize()
-        fp32_ms = statistics.mean(stage_ms("spectrum"))
-        tts.precision = args.precision
+        spec_by_prec[prec] = statistics.mean(stage_ms("spectrum"))
+    tts.precision = args.precision
+    fp32_ms = spec_by_prec.get("fp32")
+
+    def spectrum_roofline(prec):
+        ms = spec_by_prec.get(prec)
+        if ms is None:
+            return None
+        if prec == "fft32":
+            # one read of psi (8 B) and one write of I (4 B) per q and snapshot
+            gbs = 12.0 * nq * n_t / (ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "traffic": None, "kernel": "tacaw_spectrum FFT32 (time FFT + |Phi|^2, one kernel)",
+                    "bytes_per_unit": "8 B read + 4 B written per q x snapshot",
+                    "peak_kind": f"{peak_kind} hbm_gbs"}
+        if prec == "bf16x3":
+            tf = 3 * 8.0 * nq * n_t * n_t / (ms * 1e-3) / 1e12   # three BF16 products per complex flop
+            return {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf,
+                    "traffic": None,
+                    "kernel": "tacaw_spectrum BF16X3 (split, centre, tcgen05 GEMM + |Phi|^2 epilogue)",
+                    "flop_per_unit": "3 x 8 real flop per q x snapshot x energy",
+                    "peak_kind": f"{peak_kind} bf16_tflops_sustained"}
+        return None
+
+    roofline_spectrum = spectrum_roofline(args.precision)
+    roofline_spectrum_gemm = spectrum_roofline("bf16x3") if args.precision != "bf16x3" else None
 
     # spectra averaged over sets of consecutive snapshots, on the same exit waves
     seg = None
@@ -425,21 +445,24 @@ def run_ours(args):
                "d2h_bytes_per_step": int(i_host.numel() * 4 + el_host.numel() * 8)}
 
     n_batches = (n_t + tts.batch - 1) // tts.batch
-    spec_launches = 3 if args.precision == "bf16x3" else 3   # split A, split B, GEMM | centre, table, GEMM
+    # twiddles, FFT | split A, split B, GEMM | centre, table, GEMM
+    spec_launches = {"fft32": 2, "bf16x3": 3, "fp32": 3}[args.precision]
     launches = n_batches * (2 + 1 + 2 * g.n_slices + 1) + spec_launches
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+bf16x3",
+            "vs_baseline": None, "dtype": "f32+bf16x3" if args.precision == "bf16x3" else "f32",
             "data": "synthetic",
             "config": workload_config(w, {"batch": tts.batch, "spectrum_precision": args.precision,
                                           "parallelism": "replicas" if world > 1 else "single GPU"}),
             "time_to_spectrum_ms": ms_step,
             "stage_ms": stages,
             "plain_fp32_spectrum_ms": fp32_ms,
+            "spectrum_ms_by_precision": spec_by_prec,
             "time_to_spectrum_plain_fp32_ms": (ms_step - stages["spectrum"] + fp32_ms) if fp32_ms else None,
             "roofline": roofline, "roofline_spectrum": roofline_spectrum,
+            "roofline_spectrum_bf16x3_gemm": roofline_spectrum_gemm,
             "set_averaged_spectrum": seg,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clk,

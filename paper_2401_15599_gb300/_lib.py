@@ -21,6 +21,8 @@ TACAW_ETIMEOUT = -4
 TACAW_EUNSUPPORTED = -5
 TACAW_FP32 = 0
 TACAW_BF16X3 = 1
+TACAW_FFT32 = 2
+TIME_FFT_SIZES = (64, 128, 256, 384, 512, 768, 1024, 2048, 4096)   # T with a TACAW_FFT32 plan
 TACAW_KUBO = 1
 TACAW_NORMALIZE = 2
 TACAW_MAX_SPECIES = 8

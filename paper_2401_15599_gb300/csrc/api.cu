@@ -78,6 +78,8 @@ size_t probe_ws_bytes(int nx, int ny, double lx, double ly, double lam, double a
 int probe_run(int nx, int ny, double lx, double ly, double lam, double alpha, double defocus, double x0, double y0,
               float2* psi, void* ws, cudaStream_t st);
 
+bool time_fft_size_supported(int n);
+
 static int check_grid(const tacaw_grid* g, const char* fn) {
     TACAW_REQUIRE(g != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
     TACAW_REQUIRE(g->nx > 0 && g->ny > 0 && g->n_slices > 0 && g->n_slices <= 65535, TACAW_EINVAL,
@@ -200,7 +202,7 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
     TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
     TACAW_REQUIRE(omega_meV != nullptr || n_omega == n_t, TACAW_EINVAL,
                   "%s: the natural grid (omega NULL) has n_omega == T", fn);
-    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3, TACAW_EINVAL,
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_FFT32, TACAW_EINVAL,
                   "%s: unknown precision %d", fn, precision);
     TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags",
                   fn);
@@ -208,6 +210,10 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
                   TACAW_EINVAL, "%s: the Kubo factor needs a positive temperature", fn);
     TACAW_REQUIRE(precision != TACAW_BF16X3 || n_omega <= 32640, TACAW_EUNSUPPORTED,
                   "%s: the tensor-core path takes at most 32640 energies", fn);
+    TACAW_REQUIRE(precision != TACAW_FFT32 || omega_meV == nullptr, TACAW_EINVAL,
+                  "%s: TACAW_FFT32 computes the natural grid only (omega must be NULL)", fn);
+    TACAW_REQUIRE(precision != TACAW_FFT32 || time_fft_size_supported(n_t), TACAW_EUNSUPPORTED,
+                  "%s: TACAW_FFT32 has no plan for T = %d", fn, n_t);
     bool query = false;
     int rc = check_ws(ws, ws_bytes,
                       spectrum_ws_bytes(nq, n_t, n_omega, psi_sum != nullptr, I_el != nullptr,
@@ -236,13 +242,17 @@ int tacaw_spectrum_segments(int32_t nq, int32_t n_t, double dt_fs, int32_t seg_l
     TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
     TACAW_REQUIRE(omega_meV != nullptr || n_omega == seg_len, TACAW_EINVAL,
                   "%s: the natural grid (omega NULL) has n_omega == seg_len", fn);
-    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3, TACAW_EINVAL,
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_FFT32, TACAW_EINVAL,
                   "%s: unknown precision %d", fn, precision);
     TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)), TACAW_EINVAL,
                   "%s: the Kubo factor needs a positive temperature", fn);
     TACAW_REQUIRE(precision != TACAW_BF16X3 || n_omega <= 32640, TACAW_EUNSUPPORTED,
                   "%s: the tensor-core path takes at most 32640 energies", fn);
+    TACAW_REQUIRE(precision != TACAW_FFT32 || omega_meV == nullptr, TACAW_EINVAL,
+                  "%s: TACAW_FFT32 computes the natural grid only (omega must be NULL)", fn);
+    TACAW_REQUIRE(precision != TACAW_FFT32 || time_fft_size_supported(seg_len), TACAW_EUNSUPPORTED,
+                  "%s: TACAW_FFT32 has no plan for seg_len = %d", fn, seg_len);
     bool query = false;
     int rc = check_ws(ws, ws_bytes, spectrum_segments_ws_bytes(nq, seg_len, n_omega, precision), fn, &query);
     if (rc || query) return rc;

@@ -123,6 +123,11 @@ template <>
 struct Plan<512> { static constexpr int E = 8; using R = Radices<8, 8, 8>; };
 template <>
 struct Plan<1024> { static constexpr int E = 8; using R = Radices<8, 8, 4, 4>; };
+// long transforms (time axis): 16 values per thread
+template <>
+struct Plan<2048> { static constexpr int E = 16; using R = Radices<8, 8, 8, 4>; };
+template <>
+struct Plan<4096> { static constexpr int E = 16; using R = Radices<8, 8, 8, 8>; };
 // radix-3 sizes: 24 values per thread so that every radix divides E
 template <>
 struct Plan<384> { static constexpr int E = 24; using R = Radices<8, 8, 2, 3>; };
@@ -132,7 +137,8 @@ struct Plan<768> { static constexpr int E = 24; using R = Radices<8, 8, 4, 3>; }
 template <int A, int... Rest>
 struct First { static constexpr int value = A; };
 
-// Shared-memory layouts.  RowLayout: one transform per row, positions swizzled
+// Shared-memory layouts.  (Passing the same buffer as b0 and b1 to transform
+// runs it in one buffer with an extra barrier per exchange.)  RowLayout: one transform per row, positions swizzled
 // inside the row to spread 8-byte accesses over the banks.  ColLayout: W
 // transforms interleaved (position-major), lanes of a warp on adjacent
 // transforms, conflict free without a swizzle.
@@ -220,6 +226,7 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b
     if constexpr (sizeof...(Rest) > 0) {
         constexpr int RN = First<Rest...>::value;
         constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
+        if (b0 == b1) __syncthreads();   // one buffer: the previous exchange's reads come first
         write_out<N, E, R, NS>(v, b0, t, lay);
         __syncthreads();
         read_in<N, E, RN>(v, b0, t, lay);

@@ -424,8 +424,13 @@ int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega,
                     size_t ld, const double2* psi_sum, float* out, double* i_el, int flags,
                     double beta, void* ws, cudaStream_t st);
 
+size_t time_fft_ws_bytes(int nq, int n_t);
+int time_fft_spectrum_run(int nq, int n_t, double dt_fs, const float2* psi, size_t ld, const double2* psi_sum,
+                          float* out, double* i_el, int flags, double beta, void* ws, cudaStream_t st);
+
 size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int precision) {
     if (precision == TACAW_BF16X3) return spectrum_tc_ws_bytes(nq, n_t, n_w, have_sum, have_iel);
+    if (precision == TACAW_FFT32) return time_fft_ws_bytes(nq, n_t);
     Carver cv(nullptr);
     carve_spec(cv, nq, n_t, n_w, !have_sum, !have_iel);
     return cv.bytes();
@@ -437,6 +442,10 @@ int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, co
     if (precision == TACAW_BF16X3) {
         const double beta = (flags & TACAW_KUBO) ? 1.0 / (kBoltzmannMeVK * temperature_K) : 0.0;
         return spectrum_tc_run(nq, n_t, dt_fs, n_w, omega, psi, ld, psi_sum, out, i_el, flags, beta, ws, st);
+    }
+    if (precision == TACAW_FFT32) {
+        const double beta = (flags & TACAW_KUBO) ? 1.0 / (kBoltzmannMeVK * temperature_K) : 0.0;
+        return time_fft_spectrum_run(nq, n_t, dt_fs, psi, ld, psi_sum, out, i_el, flags, beta, ws, st);
     }
     Carver cv(ws);
     SpecWs w = carve_spec(cv, nq, n_t, n_w, psi_sum == nullptr, i_el == nullptr);

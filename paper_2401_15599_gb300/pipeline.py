@@ -85,7 +85,10 @@ class TimeToSpectrum:
         self._workspace("ms", n.value)
         n_w = self.n_t if self.omega is None else self.omega.numel()
         need = 0
-        for prec in (L.TACAW_FP32, L.TACAW_BF16X3):     # one workspace serves both precisions
+        precs = [L.TACAW_FP32, L.TACAW_BF16X3]
+        if self.omega is None and self.n_t in L.TIME_FFT_SIZES:
+            precs.append(L.TACAW_FFT32)
+        for prec in precs:                               # one workspace serves every precision
             L.check("tacaw_spectrum", lib.tacaw_spectrum(self.grid.nx * self.grid.ny, self.n_t, self.dt_fs, n_w,
                                                          null, null, ctypes.c_void_p(1), null, ctypes.c_void_p(1),
                                                          prec, 0, 300.0, null, ctypes.byref(n), null))
