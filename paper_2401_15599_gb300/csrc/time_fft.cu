@@ -7,8 +7,12 @@
 //   I(q, E_k)   = |Phi|^2 / T^2   (times the Kubo factor when asked).
 // One block takes W columns q of psi [T][nq] (time-major) and all T samples:
 //  1. loads them (thread (c, t) holds times t + TPT m of column c), forms the
-//     FP64 time mean m_q (fixed-order tree over the block), I_el = |m_q|^2 and
-//     A = psi - m_q in FP64 rounded to float;
+//     time mean m_q as an unevaluated sum hi + lo of two floats (pairwise
+//     two-sums over each thread's samples with their errors kept, then
+//     error-free sums in a fixed-order tree over the block: FP64 arithmetic
+//     would run on this GPU's slow FP64 pipe for every sample),
+//     I_el = |m_q|^2 in FP64 and A = (psi - m_hi) - m_lo, one rounding away from
+//     the exact difference;
 //  2. runs the length-T FP32 Stockham FFT (one shared buffer of W x T values);
 //  3. writes |Phi|^2 / T^2 in ascending energy through shared memory, so that
 //     each row I[q][.] is stored with coalesced writes.
@@ -26,6 +30,29 @@ int launch_normalize(float* out, size_t n, double* i_el_user, const double* i_el
 size_t normalize_ws_doubles();
 
 namespace {
+
+// Knuth's two-sum: s + e == a + b exactly (every operation an explicit
+// round-to-nearest, so no contraction changes it).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += (h2, l2) for unevaluated sums of two floats
+__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+    float s, e;
+    two_sum(hi, h2, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, l2));
+    two_sum(s, e, hi, lo);
+}
+
+// (hi + lo) / n as (qh, ql)
+__device__ __forceinline__ void df_div(float hi, float lo, float n, float& qh, float& ql) {
+    qh = __fdiv_rn(hi, n);
+    const float r = __fmaf_rn(-qh, n, hi);          // exact remainder hi - qh n
+    ql = __fdiv_rn(__fadd_rn(r, lo), n);
+}
 
 template <int T>
 struct TfCfg {
@@ -50,8 +77,8 @@ time_fft_power_kernel(const float2* __restrict__ psi, size_t ld, int nq, const d
     using Cfg = TfCfg<T>;
     constexpr int E = Cfg::E, TPT = Cfg::TPT, W = Cfg::W;
     extern __shared__ float2 smem[];
-    __shared__ double2 part[Cfg::WARPS][W];
-    __shared__ double2 mean[W];
+    __shared__ float4 part[Cfg::WARPS][W];          // (re hi, re lo, im hi, im lo)
+    __shared__ float4 mean[W];
     float2* buf = smem;
     float2* tw = smem + W * T;
     for (int i = threadIdx.x; i < fft::TwSize<T>::value; i += blockDim.x) tw[i] = __ldg(tw_g + i);
@@ -65,40 +92,62 @@ time_fft_power_kernel(const float2* __restrict__ psi, size_t ld, int nq, const d
     for (int m = 0; m < E; ++m)
         v[m] = valid ? __ldcs(psi + (size_t)(t + TPT * m) * ld + q) : make_float2(0.f, 0.f);
 
-    // FP64 time mean of each column: per thread, then the lanes of the same
-    // column in a warp (lane bits above log2 W), then the warps in order
+    // time mean of each column as hi + lo: per thread, then the lanes of the
+    // same column in a warp (lane bits above log2 W), then the warps in order
     if (psi_sum == nullptr) {
-        double re = 0.0, im = 0.0;
+        // the thread's own E samples by a pairwise tree of two-sums whose
+        // rounding errors are summed apart
+        float2 ps[E];
+        float er = 0.f, ei = 0.f;
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            re += (double)v[m].x;
-            im += (double)v[m].y;
-        }
+        for (int m = 0; m < E; ++m) ps[m] = v[m];
+#pragma unroll
+        for (int n = E; n > 1; n = (n + 1) / 2)
+#pragma unroll
+            for (int m = 0; m < n / 2; ++m) {
+                float e;
+                two_sum(ps[m].x, ps[m + (n + 1) / 2].x, ps[m].x, e);
+                er = __fadd_rn(er, e);
+                two_sum(ps[m].y, ps[m + (n + 1) / 2].y, ps[m].y, e);
+                ei = __fadd_rn(ei, e);
+            }
+        float rh, rl, ih, il;
+        two_sum(ps[0].x, er, rh, rl);
+        two_sum(ps[0].y, ei, ih, il);
 #pragma unroll
         for (int o = 16; o >= W; o >>= 1) {
-            re += __shfl_xor_sync(0xffffffffu, re, o);
-            im += __shfl_xor_sync(0xffffffffu, im, o);
+            df_add(rh, rl, __shfl_xor_sync(0xffffffffu, rh, o), __shfl_xor_sync(0xffffffffu, rl, o));
+            df_add(ih, il, __shfl_xor_sync(0xffffffffu, ih, o), __shfl_xor_sync(0xffffffffu, il, o));
         }
-        if ((threadIdx.x & 31) < W) part[threadIdx.x >> 5][c] = make_double2(re, im);
+        if ((threadIdx.x & 31) < W) part[threadIdx.x >> 5][c] = make_float4(rh, rl, ih, il);
         __syncthreads();
         if (threadIdx.x < W) {
-            double sr = 0.0, si = 0.0;
-            for (int w = 0; w < Cfg::WARPS; ++w) {
-                sr += part[w][threadIdx.x].x;
-                si += part[w][threadIdx.x].y;
+            float4 a = part[0][threadIdx.x];
+            for (int w = 1; w < Cfg::WARPS; ++w) {
+                const float4 b = part[w][threadIdx.x];
+                df_add(a.x, a.y, b.x, b.y);
+                df_add(a.z, a.w, b.z, b.w);
             }
-            mean[threadIdx.x] = make_double2(sr / T, si / T);
+            float4 mm;
+            df_div(a.x, a.y, (float)T, mm.x, mm.y);
+            df_div(a.z, a.w, (float)T, mm.z, mm.w);
+            mean[threadIdx.x] = mm;
         }
     } else if (threadIdx.x < W) {
         const double2 s = q0 + (int)threadIdx.x < nq ? psi_sum[q0 + threadIdx.x] : make_double2(0.0, 0.0);
-        mean[threadIdx.x] = make_double2(s.x / T, s.y / T);
+        const double mr = s.x / T, mi = s.y / T;
+        const float rh = (float)mr, ih = (float)mi;
+        mean[threadIdx.x] = make_float4(rh, (float)(mr - rh), ih, (float)(mi - ih));
     }
     __syncthreads();
-    const double2 mq = mean[c];
-    if (t == 0 && valid && i_el) i_el[q] = mq.x * mq.x + mq.y * mq.y;
+    const float4 mq = mean[c];
+    if (t == 0 && valid && i_el) {
+        const double mr = (double)mq.x + (double)mq.y, mi = (double)mq.z + (double)mq.w;
+        i_el[q] = mr * mr + mi * mi;
+    }
 #pragma unroll
     for (int m = 0; m < E; ++m)
-        v[m] = make_float2((float)((double)v[m].x - mq.x), (float)((double)v[m].y - mq.y));
+        v[m] = make_float2(__fsub_rn(__fsub_rn(v[m].x, mq.x), mq.y), __fsub_rn(__fsub_rn(v[m].y, mq.z), mq.w));
 
     fft::transform<T, false>(v, buf, buf, t, tw, fft::ColLayout<W>{c});
 

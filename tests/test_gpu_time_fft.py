@@ -2,7 +2,8 @@
 (precision "fft32", through the C-ABI) against the FP64 oracle spectrum.
 
 FP32 FFT rounding grows like log2(T) ulps of the spectrum's norm, well under
-the 2e-5 relative-L2 bound of the spectra; I_el comes from an FP64 mean.
+the 2e-5 relative-L2 bound of the spectra; the time mean is kept as a sum of
+two floats (about 48 bits), so I_el agrees with the FP64 oracle to 1e-12.
 """
 
 import numpy as np
@@ -49,7 +50,7 @@ def test_time_fft_natural_grid(api, n_t, nq):
     inten, iel = api.spectrum(_dev(psi), 5.0, precision="fft32")
     ref, ref_el, _ = O.spectrum(psi.astype(np.complex128), 5.0)
     assert rel_l2(inten.cpu().numpy(), ref) < SPEC_TOL
-    assert rel_l2(iel.cpu().numpy(), ref_el) < 1e-13
+    assert rel_l2(iel.cpu().numpy(), ref_el) < 1e-12      # two-float mean, about 48 bits
     # the E = 0 bin of the mean-free signal is (numerically) empty
     assert float(inten[:, n_t // 2].abs().max()) < 1e-10 * float(inten.max())
 
