@@ -50,6 +50,9 @@ def parse_args():
     p.add_argument("--cpu-snapshots", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--spectrum-only", default="",
+                   help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
+                        "(a kernel micro-benchmark; not the benchmark line)")
     p.add_argument("--seg", default="512,256",
                    help="snapshots per set and offset for the set-averaged spectrum timing ('' = skip)")
     return p.parse_args()
@@ -473,10 +476,38 @@ def run_ours(args):
     return 0
 
 
+def run_spectrum_only(args):
+    """Temporal transform alone on seeded synthetic exit waves, through the
+    public spectrum call: prints one JSON line with the mean time and the
+    achieved bandwidth of one read of psi and one write of I."""
+    import torch
+    from paper_2401_15599_gb300 import api
+    n_t, nq = (int(x) for x in args.spectrum_only.split(","))
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    psi = 1 + 0.05 * torch.randn(n_t, nq, dtype=torch.complex64, device="cuda", generator=gen)
+    out, el = api.spectrum(psi, 5.0, precision=args.precision)
+    for _ in range(max(args.warmup - 1, 0)):
+        api.spectrum(psi, 5.0, precision=args.precision, out=out, i_el=el)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        api.spectrum(psi, 5.0, precision=args.precision, out=out, i_el=el)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"spectrum_only": {"T": n_t, "nq": nq, "precision": args.precision, "ms": ms,
+                                        "gbs_psi_read_I_write": 12.0 * n_t * nq / (ms * 1e-3) / 1e9}}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.spectrum_only:
+        return run_spectrum_only(args)
     return run_ours(args)
 
 
