@@ -50,6 +50,9 @@ def parse_args():
     p.add_argument("--cpu-snapshots", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the further measurements (explicit grid, plain cuFFT slice step, batched "
+                        "jobs, adjoint)")
     p.add_argument("--spectrum-only", default="",
                    help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
                         "(a kernel micro-benchmark; not the benchmark line)")
@@ -420,6 +423,16 @@ def run_ours(args):
             seg = {"seg_len": seg_len, "hop": hop, "n_sets": n_sets, "ms": seg_ms,
                    "precision": args.precision, "tflops": flop / (seg_ms * 1e-3) / 1e12}
 
+    further = None
+    if rank == 0 and not args.no_extras:
+        further = {
+            "explicit_grid_1024_bins": explicit_grid_comparison(tts, w, args.steps, stream),
+            "plain_cufft_multislice_call": plain_cufft_slice_step(tts, g, args.steps, stream),
+            "batched_jobs": batched_jobs_sample(args.steps, stream),
+            "adjoint": adjoint_sample(args.steps, stream),
+        }
+        torch.cuda.synchronize()
+
     # end to end: host positions in, host spectrum out, through the same C-ABI calls
     e2e = None
     if not args.no_e2e:
@@ -467,6 +480,7 @@ def run_ours(args):
             "roofline": roofline, "roofline_spectrum": roofline_spectrum,
             "roofline_spectrum_bf16x3_gemm": roofline_spectrum_gemm,
             "set_averaged_spectrum": seg,
+            "further": further,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clk,
         }
@@ -474,6 +488,153 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------ further measurements
+def _events_ms(fn, reps, stream):
+    """Mean device time of fn() over reps calls (CUDA events on the stream)."""
+    import torch
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times)
+
+
+def explicit_grid_comparison(tts, w, reps, stream):
+    """The explicit energy grid of 1024 bins over [-200, 200) meV on the benchmark's
+    exit waves: two- and three-term split-BF16 tcgen05 GEMMs against the FP32 SIMT
+    GEMM, times and relative L2 differences per 50 meV band (the FP64 comparison
+    is a GPU test)."""
+    import torch
+    from paper_2401_15599_gb300 import api
+    n_t = tts.n_t
+    psi = tts.psi.reshape(n_t, -1)
+    omega = torch.arange(1024, dtype=torch.float64, device=psi.device) * (400.0 / 1024) - 200.0
+    out = {}
+    res = {}
+    for prec in ("bf16x3", "bf16x6", "fp32"):
+        buf = torch.empty((psi.shape[1], 1024), dtype=torch.float32, device=psi.device)
+        el = torch.empty(psi.shape[1], dtype=torch.float64, device=psi.device)
+        call = lambda: api.spectrum(psi, w.dt_fs, omega_meV=omega, psi_sum=tts.psi_sum.reshape(-1),
+                                    precision=prec, out=buf, i_el=el)
+        call()
+        out[prec + "_ms"] = _events_ms(call, reps, stream)
+        res[prec] = buf
+    bands = []
+    e = omega.cpu().numpy()
+    bands6 = []
+    for lo in range(-200, 200, 50):
+        sel = torch.from_numpy(((e >= lo) & (e < lo + 50))).to(psi.device)
+        a, a6, b = res["bf16x3"][:, sel].double(), res["bf16x6"][:, sel].double(), res["fp32"][:, sel].double()
+        bands.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
+        bands6.append(float(torch.linalg.norm(a6 - b) / torch.linalg.norm(b)))
+    out["band_rel_l2_bf16x3_vs_fp32"] = bands
+    out["band_rel_l2_bf16x6_vs_fp32"] = bands6
+    out["bands_meV"] = [[lo, lo + 50] for lo in range(-200, 200, 50)]
+    return out
+
+
+def plain_cufft_slice_step(tts, g, reps, stream):
+    """The unfused form of one multislice call for timing: transmission,
+    cuFFT 2-D transforms (torch.fft) and the band-limited propagator as separate
+    elementwise launches, on the benchmark's last batch of potentials."""
+    import numpy as np
+    import torch
+    from paper_2401_15599_gb300 import _lib as L
+    import ctypes
+    lib = L.load()
+    lam, sig = ctypes.c_double(0), ctypes.c_double(0)
+    L.check("tacaw_beam_constants", lib.tacaw_beam_constants(float(g.kev), ctypes.byref(lam), ctypes.byref(sig)))
+    qx = np.fft.fftfreq(g.nx, d=g.lx / g.nx)
+    qy = np.fft.fftfreq(g.ny, d=g.ly / g.ny)
+    q2 = qx[None, :] ** 2 + qy[:, None] ** 2
+    qmax = g.bandlimit * min(g.nx / (2 * g.lx), g.ny / (2 * g.ly))
+    prop = np.exp(-1j * np.pi * lam.value * g.dz * q2) * (q2 <= qmax * qmax)
+    prop = torch.from_numpy(prop.astype(np.complex64)).to(tts.V.device)
+    V = tts.V
+    sigma = float(sig.value)
+
+    def run():
+        psi = torch.ones((V.shape[0], g.ny, g.nx), dtype=torch.complex64, device=V.device)
+        for s in range(g.n_slices):
+            psi = psi * torch.polar(torch.ones_like(V[:, s]), sigma * V[:, s])
+            psi = torch.fft.fft2(psi, norm="forward") * prop
+            if s + 1 < g.n_slices:
+                psi = torch.fft.ifft2(psi, norm="forward")
+        return psi
+
+    ref = run()
+    ours = torch.empty_like(ref)
+    from paper_2401_15599_gb300 import api
+    api.multislice(g, V, out=ours)
+    diff = float(torch.linalg.norm(ours - ref) / torch.linalg.norm(ref))
+    ms = _events_ms(run, reps, stream)
+    ours_ms = _events_ms(lambda: api.multislice(g, V, out=ours), reps, stream)
+    return {"snapshots": int(V.shape[0]), "plain_cufft_ms": ms, "ours_ms": ours_ms,
+            "speedup": ms / ours_ms, "rel_l2_difference": diff}
+
+
+def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=32):
+    """The 64 uneven seeded jobs (grids 128-768, 10-150 slices, 1-3 species), each
+    cut to its first `snapshots` snapshots, through the batched path: eager run and
+    CUDA-graph replay, in grid point * slice * snapshot per second."""
+    import torch
+    import workloads as W
+    from paper_2401_15599_gb300.batch import BatchTimeToSpectrum, Job
+    jobs, units = [], 0
+    for wj in W.batching_jobs(n_jobs=n_jobs):
+        inp = W.build_inputs(wj)
+        n = min(snapshots, wj.n_t)
+        pos = torch.from_numpy(inp.positions(snapshots=list(range(n)))).cuda()
+        jobs.append(Job(wj.grid, pos, torch.from_numpy(inp.species).cuda(), inp.amp_sigma, wj.dt_fs))
+        units += wj.grid.nx * wj.grid.ny * wj.grid.n_slices * n
+    run = BatchTimeToSpectrum(jobs, window=8, precision="fft32")
+    run.capture()
+    eager_ms = _events_ms(run.run, reps, stream)
+    graph_ms = _events_ms(run.replay, reps, stream)
+    return {"jobs": n_jobs, "snapshots_per_job": snapshots, "window": 8, "units": units,
+            "eager_ms": eager_ms, "graph_ms": graph_ms,
+            "value_graph": units / (graph_ms * 1e-3), "unit": UNIT}
+
+
+def adjoint_sample(reps, stream, snapshots=64):
+    """Forward and backward of the spectrum-mismatch loss on the differentiation
+    workload (256^2, 50 slices, fcc 10x10x25), first `snapshots` snapshots:
+    gradients with respect to the per-species (amp, sigma)."""
+    import torch
+    import workloads as W
+    from paper_2401_15599_gb300.autograd import spectrum_from_atoms
+    w = W.WORKLOADS["differentiation"]
+    inp = W.build_inputs(w)
+    pos = torch.from_numpy(inp.positions(snapshots=list(range(snapshots)))).cuda()
+    species = torch.from_numpy(inp.species).cuda()
+    amp = torch.tensor(inp.amp_sigma, dtype=torch.float64, device="cuda")
+    target = spectrum_from_atoms(amp * torch.tensor([1.05, 1.0], device="cuda", dtype=torch.float64), pos,
+                                 species, w.grid, w.dt_fs).detach()
+
+    def fwd():
+        a = amp.clone().requires_grad_(True)
+        inten = spectrum_from_atoms(a, pos, species, w.grid, w.dt_fs)
+        return a, ((inten - target) ** 2).sum() / (target ** 2).sum()
+
+    def fwd_bwd():
+        a, loss = fwd()
+        loss.backward()
+
+    fwd_bwd()
+    f_ms = _events_ms(lambda: fwd(), reps, stream)
+    fb_ms = _events_ms(fwd_bwd, reps, stream)
+    g = w.grid
+    units = g.nx * g.ny * g.n_slices * snapshots
+    return {"workload": "differentiation, first %d snapshots" % snapshots, "forward_ms": f_ms,
+            "forward_backward_ms": fb_ms, "backward_over_forward": (fb_ms - f_ms) / f_ms,
+            "value_forward_backward": units / (fb_ms * 1e-3), "unit": UNIT}
 
 
 def run_spectrum_only(args):

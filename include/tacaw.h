@@ -55,6 +55,7 @@ extern "C" {
 #define TACAW_BF16X3 1          /* split BF16 (hi+lo), 3 products, FP32 accumulation */
 #define TACAW_FFT32 2           /* natural grid only: FP32 FFT over time (T in 64..1024 as for
                                    tacaw_multislice, or 2048, 4096) */
+#define TACAW_BF16X6 3          /* split BF16 (three terms), 6 products, FP32 accumulation */
 
 /* flags of tacaw_spectrum */
 #define TACAW_KUBO 1            /* multiply by beta E / (1 - exp(-beta E)), Eq. (8) */
@@ -184,7 +185,9 @@ int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, const float* V,
  * omega_meV  DEVICE [n_omega] double energies in meV, or NULL for the natural grid
  * I          out [nq][n_omega] float
  * I_el       out [nq] double, or NULL
- * precision  TACAW_FP32, TACAW_BF16X3, or TACAW_FFT32 (natural grid only, T in
+ * precision  TACAW_FP32, TACAW_BF16X3, TACAW_BF16X6 (three-term split, for the
+ *            bands where the two-term split's ~2^-16 relative error matters), or
+ *            TACAW_FFT32 (natural grid only, T in
  *            {64, 128, 256, 384, 512, 768, 1024, 2048, 4096}: one FP32 FFT over
  *            time per q instead of the DFT-matrix GEMM; with it psi_sum, when
  *            given, supplies the mean, else the mean is an FP64 block sum)
@@ -215,7 +218,7 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
  * omega_meV  DEVICE [n_omega] energies, or NULL for the natural grid of one
  *            set: n_omega == seg_len, E_k = h (k - seg_len/2) / (seg_len dt)
  * I          out [nq][n_omega] float;  I_el out [nq] double, or NULL
- * precision  TACAW_FP32, TACAW_BF16X3 or TACAW_FFT32 (the per-set transform); sums over
+ * precision  TACAW_FP32, TACAW_BF16X3, TACAW_BF16X6 or TACAW_FFT32 (the per-set transform); sums over
  *            sets are FP64.
  * Errors: TACAW_EINVAL for sizes, sets that do not fit, unknown flags or
  * precision; TACAW_EUNSUPPORTED above 32640 energies with TACAW_BF16X3.

@@ -22,6 +22,7 @@ TACAW_EUNSUPPORTED = -5
 TACAW_FP32 = 0
 TACAW_BF16X3 = 1
 TACAW_FFT32 = 2
+TACAW_BF16X6 = 3
 TIME_FFT_SIZES = (64, 128, 256, 384, 512, 768, 1024, 2048, 4096)   # T with a TACAW_FFT32 plan
 TACAW_KUBO = 1
 TACAW_NORMALIZE = 2

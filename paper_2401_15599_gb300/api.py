@@ -104,7 +104,7 @@ def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None):
     return out
 
 
-_PRECISION = {"fp32": L.TACAW_FP32, "bf16x3": L.TACAW_BF16X3, "fft32": L.TACAW_FFT32}
+_PRECISION = {"fp32": L.TACAW_FP32, "bf16x3": L.TACAW_BF16X3, "fft32": L.TACAW_FFT32, "bf16x6": L.TACAW_BF16X6}
 
 
 def spectrum(psi, dt_fs, omega_meV=None, psi_sum=None, precision="fp32", kubo=False,

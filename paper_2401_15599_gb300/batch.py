@@ -90,7 +90,8 @@ class BatchTimeToSpectrum:
             st["ws_pot"] = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
             n_t = j.pos.shape[0]
             n_w = st["I"].shape[1]
-            prec = {"fp32": L.TACAW_FP32, "bf16x3": L.TACAW_BF16X3}[self.precision]
+            prec = {"fp32": L.TACAW_FP32, "bf16x3": L.TACAW_BF16X3, "fft32": L.TACAW_FFT32,
+                    "bf16x6": L.TACAW_BF16X6}[self.precision]
             L.check("tacaw_spectrum", lib.tacaw_spectrum(j.grid.nx * j.grid.ny, n_t, float(j.dt_fs), n_w,
                                                          ctypes.c_void_p(1) if st["omega"] is not None else null,
                                                          null, ctypes.c_void_p(1), null, ctypes.c_void_p(1), prec, 0,

@@ -202,13 +202,14 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
     TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
     TACAW_REQUIRE(omega_meV != nullptr || n_omega == n_t, TACAW_EINVAL,
                   "%s: the natural grid (omega NULL) has n_omega == T", fn);
-    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_FFT32, TACAW_EINVAL,
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_BF16X6 ||
+                      precision == TACAW_FFT32, TACAW_EINVAL,
                   "%s: unknown precision %d", fn, precision);
     TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags",
                   fn);
     TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)),
                   TACAW_EINVAL, "%s: the Kubo factor needs a positive temperature", fn);
-    TACAW_REQUIRE(precision != TACAW_BF16X3 || n_omega <= 32640, TACAW_EUNSUPPORTED,
+    TACAW_REQUIRE((precision != TACAW_BF16X3 && precision != TACAW_BF16X6) || n_omega <= 32640, TACAW_EUNSUPPORTED,
                   "%s: the tensor-core path takes at most 32640 energies", fn);
     TACAW_REQUIRE(precision != TACAW_FFT32 || omega_meV == nullptr, TACAW_EINVAL,
                   "%s: TACAW_FFT32 computes the natural grid only (omega must be NULL)", fn);
@@ -242,12 +243,13 @@ int tacaw_spectrum_segments(int32_t nq, int32_t n_t, double dt_fs, int32_t seg_l
     TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
     TACAW_REQUIRE(omega_meV != nullptr || n_omega == seg_len, TACAW_EINVAL,
                   "%s: the natural grid (omega NULL) has n_omega == seg_len", fn);
-    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_FFT32, TACAW_EINVAL,
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_BF16X6 ||
+                      precision == TACAW_FFT32, TACAW_EINVAL,
                   "%s: unknown precision %d", fn, precision);
     TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)), TACAW_EINVAL,
                   "%s: the Kubo factor needs a positive temperature", fn);
-    TACAW_REQUIRE(precision != TACAW_BF16X3 || n_omega <= 32640, TACAW_EUNSUPPORTED,
+    TACAW_REQUIRE((precision != TACAW_BF16X3 && precision != TACAW_BF16X6) || n_omega <= 32640, TACAW_EUNSUPPORTED,
                   "%s: the tensor-core path takes at most 32640 energies", fn);
     TACAW_REQUIRE(precision != TACAW_FFT32 || omega_meV == nullptr, TACAW_EINVAL,
                   "%s: TACAW_FFT32 computes the natural grid only (omega must be NULL)", fn);

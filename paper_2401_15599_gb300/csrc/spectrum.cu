@@ -419,17 +419,18 @@ int spectrum_backward_run(int nq, int n_t, double dt_fs, int n_w, const double* 
     return TACAW_OK;
 }
 
-size_t spectrum_tc_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel);
+size_t spectrum_tc_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int terms);
 int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
                     size_t ld, const double2* psi_sum, float* out, double* i_el, int flags,
-                    double beta, void* ws, cudaStream_t st);
+                    double beta, int terms, void* ws, cudaStream_t st);
 
 size_t time_fft_ws_bytes(int nq, int n_t);
 int time_fft_spectrum_run(int nq, int n_t, double dt_fs, const float2* psi, size_t ld, const double2* psi_sum,
                           float* out, double* i_el, int flags, double beta, void* ws, cudaStream_t st);
 
 size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int precision) {
-    if (precision == TACAW_BF16X3) return spectrum_tc_ws_bytes(nq, n_t, n_w, have_sum, have_iel);
+    if (precision == TACAW_BF16X3) return spectrum_tc_ws_bytes(nq, n_t, n_w, have_sum, have_iel, 2);
+    if (precision == TACAW_BF16X6) return spectrum_tc_ws_bytes(nq, n_t, n_w, have_sum, have_iel, 3);
     if (precision == TACAW_FFT32) return time_fft_ws_bytes(nq, n_t);
     Carver cv(nullptr);
     carve_spec(cv, nq, n_t, n_w, !have_sum, !have_iel);
@@ -439,9 +440,10 @@ size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel,
 int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
                  size_t ld, const double2* psi_sum, float* out, double* i_el, int precision,
                  int flags, double temperature_K, void* ws, cudaStream_t st) {
-    if (precision == TACAW_BF16X3) {
+    if (precision == TACAW_BF16X3 || precision == TACAW_BF16X6) {
         const double beta = (flags & TACAW_KUBO) ? 1.0 / (kBoltzmannMeVK * temperature_K) : 0.0;
-        return spectrum_tc_run(nq, n_t, dt_fs, n_w, omega, psi, ld, psi_sum, out, i_el, flags, beta, ws, st);
+        return spectrum_tc_run(nq, n_t, dt_fs, n_w, omega, psi, ld, psi_sum, out, i_el, flags, beta,
+                               precision == TACAW_BF16X3 ? 2 : 3, ws, st);
     }
     if (precision == TACAW_FFT32) {
         const double beta = (flags & TACAW_KUBO) ? 1.0 / (kBoltzmannMeVK * temperature_K) : 0.0;

@@ -7,16 +7,28 @@
 // 256 columns of each N tile hold, for 128 energies, first the columns giving
 // Re Phi (B'[2n] = Re e, B'[2n+1] = -Im e) and then those giving Im Phi
 // (B'[2n] = Im e, B'[2n+1] = Re e), so the epilogue finds Re and Im of one
-// energy 128 TMEM columns apart.  Every operand x is split as
-// x = hi + lo (both BF16) and three products hi*hi + hi*lo + lo*hi are
-// accumulated in FP32 (the lo*lo term, ~2^-16 relative, is dropped).
+// energy TN/2 TMEM columns apart.  Every operand x is split into BF16 terms:
+//  * BF16X3: x = x0 + x1, products x0 y0 + x0 y1 + x1 y0 (the x1 y1 term and
+//    the split residual, ~2^-16 relative, are dropped), three-stage ring;
+//  * BF16X6: x = x0 + x1 + x2, products x0 y0 + x0 y1 + x1 y0 + x0 y2 + x1 y1 +
+//    x2 y0 (dropped terms ~2^-24 relative), two-stage ring.
+// The tensor cores' FP32 accumulation into TMEM does not round to nearest: its
+// error is a bias that grows with the number of MMAs into one accumulator and
+// with the accumulator's size (measured: -4.8e-5 relative on I at T = 4096 when
+// one accumulator took the whole K).  So the leading product x0 y0 and the
+// small products go to separate accumulators that restart every CHUNK K blocks
+// (two TMEM buffers, double-buffered), and four epilogue warps add each chunk
+// into FP32 registers with round-to-nearest adds.
 //
 // Prologue kernels: the FP64 time mean and centring with the hi/lo split
 // (written K-major, i.e. transposed from the time-major exit waves), and the
 // split DFT matrix built in FP64.  Main kernel per 128 x 256 output tile:
-// TMA (128-byte swizzle) into a 2-stage ring, one thread issues the MMAs,
-// tcgen05.commit frees ring stages, four warps read the accumulator from
-// TMEM and write |Phi|^2 / T^2 (times the Kubo factor).
+// TMA (128-byte swizzle) into a 2- or 3-stage ring (warp 4), one thread of
+// warp 5 issues the MMAs, tcgen05.commit frees ring stages and hands finished
+// chunks to warps 0-3, which accumulate them and finally write |Phi|^2 / T^2
+// (times the Kubo factor).  N tiles are 128 wide: 64 energies, Re then Im.
+
+#include <string.h>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -36,20 +48,30 @@ size_t normalize_ws_doubles();
 
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 64;     // tile; TK BF16 = 128 bytes per row
-constexpr int STAGES = 2;
+constexpr int TM = 128, TN = 128, TK = 64;     // tile; TK BF16 = 128 bytes per row
 constexpr int A_BYTES = TM * TK * 2;
-constexpr int B_BYTES = TN * TK * 2;
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KiB
-constexpr int TC_THREADS = 128;
-constexpr int GROUP_N = 8;                               // N tiles sharing an L2 panel of B'
-constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int B_BYTES_ = TN * TK * 2;
+constexpr int EPI_WARPS = 4;                   // warps 0-3: TMEM lanes 0-127, the epilogue
+constexpr int LOAD_WARP = 4, MMA_WARP = 5;
+constexpr int TC_THREADS = 6 * 32;
+constexpr int GROUP_N = 8;                     // N tiles sharing an L2 panel of B'
+constexpr int CHUNK = 2;                       // K blocks summed in TMEM before the FP32 drain
+constexpr uint32_t TMEM_COLS = 4 * TN;         // two buffers x (big, small) accumulators
 
-// CODATA 2018 Planck constant in meV*fs.
+template <int NT>                              // BF16 terms per operand: 2 or 3
+struct TcCfg {
+    static constexpr int STAGES = NT == 2 ? 3 : 2;
+    static constexpr int B_BYTES = B_BYTES_;
+    static constexpr int STAGE_BYTES = NT * (A_BYTES + B_BYTES);   // 64 or 96 KiB
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+};
 
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+// x -> BF16 terms t0 + t1 (+ t2); every residual is exact in FP32
+__device__ __forceinline__ void split_bf16(float x, int nt, __nv_bfloat16* t) {
+    t[0] = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(t[0]);
+    t[1] = __float2bfloat16_rn(r1);
+    if (nt == 3) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(t[1]));
 }
 
 // A'_hi / A'_lo [nq_pad][2 t_pad]: (q, 2n) = Re(psi(q, t_n) - m_q), (q, 2n+1) = Im(...);
@@ -57,8 +79,8 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 // 32 (time) x 32 (q) tile through shared memory; also writes I_el = |m_q|^2.
 __global__ void __launch_bounds__(256)
 split_a_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restrict__ sum, int n_t,
-               int nq, int t_pad, __nv_bfloat16* __restrict__ ahi, __nv_bfloat16* __restrict__ alo,
-               double* __restrict__ i_el) {
+               int nq, int t_pad, __nv_bfloat16* __restrict__ a0, __nv_bfloat16* __restrict__ a1,
+               __nv_bfloat16* __restrict__ a2, double* __restrict__ i_el) {
     __shared__ float2 tile[32][33];
     const int q0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
@@ -87,28 +109,31 @@ split_a_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restr
     for (int r = ty; r < 32; r += 8) {               // r: q within the tile, tx: time
         const int q = q0 + r, t = t0 + tx;
         const float2 a = tile[tx][r];
-        __nv_bfloat16 h0, l0, h1, l1;
-        split_bf16(a.x, h0, l0);
-        split_bf16(a.y, h1, l1);
-        __nv_bfloat162 hh, ll;
-        hh.x = h0; hh.y = h1;
-        ll.x = l0; ll.y = l1;
-        reinterpret_cast<__nv_bfloat162*>(ahi + (size_t)q * k2)[t] = hh;
-        reinterpret_cast<__nv_bfloat162*>(alo + (size_t)q * k2)[t] = ll;
+        const int nt = a2 ? 3 : 2;
+        __nv_bfloat16 re[3], im[3];
+        split_bf16(a.x, nt, re);
+        split_bf16(a.y, nt, im);
+        __nv_bfloat16* dst[3] = {a0, a1, a2};
+        for (int i = 0; i < nt; ++i) {
+            __nv_bfloat162 v;
+            v.x = re[i];
+            v.y = im[i];
+            reinterpret_cast<__nv_bfloat162*>(dst[i] + (size_t)q * k2)[t] = v;
+        }
     }
 }
 
-// B'_hi / B'_lo [n_tiles * 256][2 t_pad], see the file comment; e = exp(-i E_k t_n / hbar)
+// B' terms [n_tiles * tn][2 t_pad], see the file comment; e = exp(-i E_k t_n / hbar)
 // computed in FP64 (exact integer phase on the natural grid), zero beyond n_w / T.
 __global__ void __launch_bounds__(128)
-split_b_kernel(const double* __restrict__ omega, int n_t, int n_w, int t_pad, double dt,
-               __nv_bfloat16* __restrict__ bhi, __nv_bfloat16* __restrict__ blo) {
+split_b_kernel(const double* __restrict__ omega, int n_t, int n_w, int t_pad, double dt, int tn,
+               __nv_bfloat16* __restrict__ b0, __nv_bfloat16* __restrict__ b1, __nv_bfloat16* __restrict__ b2) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;   // time index
     const int j = blockIdx.y;                              // B' row
     if (n >= t_pad) return;
-    const int tile = j / TN, c = j % TN;
-    const int k = tile * (TN / 2) + (c & (TN / 2 - 1));
-    const bool imag_row = c >= TN / 2;
+    const int tile = j / tn, c = j % tn;
+    const int k = tile * (tn / 2) + (c & (tn / 2 - 1));
+    const bool imag_row = c >= tn / 2;
     float er = 0.f, ei = 0.f;
     if (k < n_w && n < n_t) {
         double s, co;
@@ -126,28 +151,41 @@ split_b_kernel(const double* __restrict__ omega, int n_t, int n_w, int t_pad, do
     }
     const float x0 = imag_row ? ei : er;
     const float x1 = imag_row ? er : -ei;
-    __nv_bfloat16 h0, l0, h1, l1;
-    split_bf16(x0, h0, l0);
-    split_bf16(x1, h1, l1);
-    __nv_bfloat162 hh, ll;
-    hh.x = h0; hh.y = h1;
-    ll.x = l0; ll.y = l1;
+    const int nt = b2 ? 3 : 2;
+    __nv_bfloat16 s0[3], s1[3];
+    split_bf16(x0, nt, s0);
+    split_bf16(x1, nt, s1);
+    __nv_bfloat16* dst[3] = {b0, b1, b2};
     const size_t k2 = 2 * (size_t)t_pad;
-    reinterpret_cast<__nv_bfloat162*>(bhi + (size_t)j * k2)[n] = hh;
-    reinterpret_cast<__nv_bfloat162*>(blo + (size_t)j * k2)[n] = ll;
+    for (int i = 0; i < nt; ++i) {
+        __nv_bfloat162 v;
+        v.x = s0[i];
+        v.y = s1[i];
+        reinterpret_cast<__nv_bfloat162*>(dst[i] + (size_t)j * k2)[n] = v;
+    }
 }
 
+// Operand tensor maps of one launch: A' and B' terms 0 .. NT-1.
+struct TcMaps {
+    CUtensorMap a[3], b[3];
+};
+
+template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-tc_power_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
-                const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
-                const float* __restrict__ kubo, float* __restrict__ out, int nq, int n_w,
-                int n_kblocks, int n_mtiles, int n_ntiles, float scale, int* __restrict__ err) {
+tc_power_kernel(const __grid_constant__ TcMaps maps, const float* __restrict__ kubo, float* __restrict__ out,
+                int nq, int n_w, int n_kblocks, int n_mtiles, int n_ntiles, float scale, int* __restrict__ err) {
+    using Cfg = TcCfg<NT>;
+    constexpr int STAGES = Cfg::STAGES;
+    constexpr int B_BYTES = Cfg::B_BYTES;
+    constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accum = empty + STAGES;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    uint64_t* acc_full = empty + STAGES;     // [2]: a chunk's partial sums are complete in TMEM
+    uint64_t* acc_empty = acc_full + 2;      // [2]: the epilogue warps have read them
+    uint64_t* done = acc_empty + 2;          // every MMA of the block has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     int* consumed = reinterpret_cast<int*>(tmem_slot + 1);
 
     // tile order: groups of GROUP_N N tiles; inside a group, N fastest, then M
@@ -156,6 +194,7 @@ tc_power_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_consta
     const int g = b / gfull, rem = b % gfull;
     const int gw = min(GROUP_N, n_ntiles - g * GROUP_N);
     const int mt = rem / gw, nt = g * GROUP_N + rem % gw;
+    const int n_chunks = (n_kblocks + CHUNK - 1) / CHUNK;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -163,12 +202,16 @@ tc_power_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_consta
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(accum, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], EPI_WARPS);
+        }
+        tc::mbar_init(done, 1);
         *consumed = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, TN);
+    if (warp == MMA_WARP) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -177,66 +220,96 @@ tc_power_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_consta
     const uint32_t tmem = *tmem_slot;
 
     int issued = 0;
-    if (warp == 0 && lane == 0) {
-        // producer: TMA loads of the four operand tiles of each K block
+    if (warp == LOAD_WARP && lane == 0) {
+        // producer: TMA loads of the operand terms of each K block
         for (int kb = 0; kb < n_kblocks; ++kb) {
             const int s = kb % STAGES, u = kb / STAGES;
             if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, err)) break;
             uint8_t* st = base + s * STAGE_BYTES;
             tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-            tc::tma_load_2d(st, &map_ahi, &full[s], kb * TK, mt * TM);
-            tc::tma_load_2d(st + A_BYTES, &map_alo, &full[s], kb * TK, mt * TM);
-            tc::tma_load_2d(st + 2 * A_BYTES, &map_bhi, &full[s], kb * TK, nt * TN);
-            tc::tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_blo, &full[s], kb * TK, nt * TN);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                tc::tma_load_2d(st + i * A_BYTES, &maps.a[i], &full[s], kb * TK, mt * TM);
+                tc::tma_load_2d(st + NT * A_BYTES + i * B_BYTES, &maps.b[i], &full[s], kb * TK, nt * TN);
+            }
             issued = kb + 1;
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+    } else if (warp == MMA_WARP && lane == 0) {
+        // MMA issuer.  Chunk c (CHUNK K blocks) accumulates into TMEM buffer c & 1:
+        // the leading product x0 y0 into its "big" half, every other product into
+        // its "small" half, both starting from zero.
         constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, TN);
         int kb = 0;
-        for (; kb < n_kblocks; ++kb) {
+        bool ok = true;
+        for (; kb < n_kblocks && ok; ++kb) {
+            const int c = kb / CHUNK, buf = c & 1;
+            const bool kfirst = (kb % CHUNK) == 0;
+            if (kfirst && c >= 2 && !tc::mbar_wait(&acc_empty[buf], ((c >> 1) - 1) & 1, err)) break;
             const int s = kb % STAGES, u = kb / STAGES;
             if (!tc::mbar_wait(&full[s], u & 1, err)) break;
             tc::fence_after_sync();
+            const uint32_t big = tmem + buf * 2 * TN, small = big + TN;
             const uint32_t sa = tc::smem_u32(base + s * STAGE_BYTES);
-            const uint32_t ahi = sa, alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES,
-                           blo = sa + 2 * A_BYTES + B_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TK / 16; ++kk) {
                 const uint32_t off = kk * 32;   // 16 BF16 along K inside the swizzled row
-                const uint64_t dah = tc::desc_kmajor_sw128(ahi + off);
-                const uint64_t dal = tc::desc_kmajor_sw128(alo + off);
-                const uint64_t dbh = tc::desc_kmajor_sw128(bhi + off);
-                const uint64_t dbl = tc::desc_kmajor_sw128(blo + off);
-                tc::mma_bf16(tmem, dah, dbh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
-                tc::mma_bf16(tmem, dal, dbh, idesc, 1u);
+                uint64_t da[NT], db[NT];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    da[i] = tc::desc_kmajor_sw128(sa + i * A_BYTES + off);
+                    db[i] = tc::desc_kmajor_sw128(sa + NT * A_BYTES + i * B_BYTES + off);
+                }
+                const uint32_t acc = (kfirst && kk == 0) ? 0u : 1u;
+                tc::mma_bf16(big, da[0], db[0], idesc, acc);
+                tc::mma_bf16(small, da[0], db[1], idesc, acc);
+                tc::mma_bf16(small, da[1], db[0], idesc, 1u);
+                if constexpr (NT == 3) {
+                    tc::mma_bf16(small, da[0], db[2], idesc, 1u);
+                    tc::mma_bf16(small, da[1], db[1], idesc, 1u);
+                    tc::mma_bf16(small, da[2], db[0], idesc, 1u);
+                }
             }
             tc::mma_commit(&empty[s]);
+            if ((kb % CHUNK) == CHUNK - 1 || kb == n_kblocks - 1) tc::mma_commit(&acc_full[buf]);
         }
         *consumed = kb;
-        tc::mma_commit(accum);
-    }
-    __syncwarp();
-
-    // epilogue: warp w owns TMEM lanes 32w .. 32w + 31 (rows of the tile)
-    const bool ok = tc::mbar_wait(accum, 0, err);
-    tc::fence_after_sync();
-    if (ok && !*(volatile int*)err) {
-        const int row = mt * TM + warp * 32 + lane;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        float* orow = out + (size_t)row * n_w;
-#pragma unroll 1
-        for (int c0 = 0; c0 < TN / 2; c0 += 32) {
-            float re[32], im[32];
-            tc::tmem_ld_32cols(lane_addr + c0, re);
-            tc::tmem_ld_32cols(lane_addr + TN / 2 + c0, im);
-            if (row < nq) {
+        tc::mma_commit(done);
+    } else if (warp < EPI_WARPS) {
+        // epilogue warps: warp w owns TMEM lanes 32w .. 32w + 31 (rows of the tile) and
+        // adds each chunk's partial sums into FP32 registers with round-to-nearest
+        float acc[TN];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int k = nt * (TN / 2) + c0 + i;
+        for (int i = 0; i < TN; ++i) acc[i] = 0.f;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        bool ok = true;
+        for (int c = 0; c < n_chunks; ++c) {
+            const int buf = c & 1;
+            if (!tc::mbar_wait(&acc_full[buf], (c >> 1) & 1, err)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int c0 = 0; c0 < TN; c0 += 32) {
+                float vb[32], vs[32];
+                tc::tmem_ld_32cols(lane_addr + buf * 2 * TN + c0, vb);
+                tc::tmem_ld_32cols(lane_addr + buf * 2 * TN + TN + c0, vs);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[c0 + i] = __fadd_rn(__fadd_rn(acc[c0 + i], vb[i]), vs[i]);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+        }
+        if (ok && !*(volatile int*)err) {
+            const int row = mt * TM + warp * 32 + lane;
+            if (row < nq) {
+                float* orow = out + (size_t)row * n_w;
+#pragma unroll
+                for (int i = 0; i < TN / 2; ++i) {
+                    const int k = nt * (TN / 2) + i;
                     if (k < n_w) {
-                        float v = (re[i] * re[i] + im[i] * im[i]) * scale;
+                        float v = (acc[i] * acc[i] + acc[TN / 2 + i] * acc[TN / 2 + i]) * scale;
                         if (kubo) v *= __ldg(kubo + k);
                         orow[k] = v;
                     }
@@ -244,17 +317,20 @@ tc_power_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_consta
             }
         }
     }
-    // On a timeout, wait (bounded) for loads that were issued but never consumed
-    // so no TMA write lands after the block has exited.
+    __syncwarp();
+    // Before TMEM is freed: every MMA has completed (bounded wait), and after a
+    // timeout the loads that were issued but never consumed have landed.
     __syncthreads();
-    if (warp == 0 && lane == 0 && *(volatile int*)err) {
-        for (int kb = *consumed; kb < issued; ++kb)
-            tc::mbar_wait_quiet(&full[kb % STAGES], (kb / STAGES) & 1, 1u << 20);
+    if (warp == LOAD_WARP && lane == 0) {
+        tc::mbar_wait_quiet(done, 0, 1u << 22);
+        if (*(volatile int*)err)
+            for (int kb = *consumed; kb < issued; ++kb)
+                tc::mbar_wait_quiet(&full[kb % STAGES], (kb / STAGES) & 1, 1u << 20);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 1) tc::tmem_dealloc(tmem, TN);
+    if (warp == MMA_WARP) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -291,16 +367,18 @@ int make_map(CUtensorMap* map, const void* ptr, size_t rows, size_t k2, int box_
 }
 
 struct TcGeom {
-    int t_pad, nq_pad, n_mtiles, n_ntiles, n_kblocks;
+    int nt, tn, t_pad, nq_pad, n_mtiles, n_ntiles, n_kblocks;
     size_t k2;
 };
 
-TcGeom geom(int nq, int n_t, int n_w) {
+TcGeom geom(int nq, int n_t, int n_w, int nt) {
     TcGeom g;
+    g.nt = nt;
+    g.tn = TN;
     g.t_pad = (n_t + TK / 2 - 1) / (TK / 2) * (TK / 2);     // 2 t_pad multiple of TK
     g.nq_pad = (nq + TM - 1) / TM * TM;
     g.n_mtiles = g.nq_pad / TM;
-    g.n_ntiles = (n_w + TN / 2 - 1) / (TN / 2);
+    g.n_ntiles = (n_w + g.tn / 2 - 1) / (g.tn / 2);
     g.k2 = 2 * (size_t)g.t_pad;
     g.n_kblocks = (int)(g.k2 / TK);
     return g;
@@ -308,21 +386,21 @@ TcGeom geom(int nq, int n_t, int n_w) {
 
 struct TcWs {
     double2* sum;
-    __nv_bfloat16 *ahi, *alo, *bhi, *blo;
+    __nv_bfloat16 *a[3], *b[3];
     float* kubo;
     double* red;
     double* i_el;
     int* err;
 };
 
-TcWs carve_tc(Carver& cv, int nq, int n_t, int n_w, bool need_sum, bool need_iel) {
-    const TcGeom g = geom(nq, n_t, n_w);
+TcWs carve_tc(Carver& cv, int nq, int n_t, int n_w, bool need_sum, bool need_iel, int nt) {
+    const TcGeom g = geom(nq, n_t, n_w, nt);
     TcWs w;
     w.sum = need_sum ? cv.take<double2>(nq) : nullptr;
-    w.ahi = cv.take<__nv_bfloat16>((size_t)g.nq_pad * g.k2, 1024);
-    w.alo = cv.take<__nv_bfloat16>((size_t)g.nq_pad * g.k2, 1024);
-    w.bhi = cv.take<__nv_bfloat16>((size_t)g.n_ntiles * TN * g.k2, 1024);
-    w.blo = cv.take<__nv_bfloat16>((size_t)g.n_ntiles * TN * g.k2, 1024);
+    for (int i = 0; i < 3; ++i) {
+        w.a[i] = i < nt ? cv.take<__nv_bfloat16>((size_t)g.nq_pad * g.k2, 1024) : nullptr;
+        w.b[i] = i < nt ? cv.take<__nv_bfloat16>((size_t)g.n_ntiles * g.tn * g.k2, 1024) : nullptr;
+    }
     w.kubo = cv.take<float>(n_w);
     w.red = cv.take<double>(normalize_ws_doubles());
     w.i_el = need_iel ? cv.take<double>(nq) : nullptr;
@@ -332,18 +410,19 @@ TcWs carve_tc(Carver& cv, int nq, int n_t, int n_w, bool need_sum, bool need_iel
 
 }  // namespace
 
-size_t spectrum_tc_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel) {
+size_t spectrum_tc_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int terms) {
     Carver cv(nullptr);
-    carve_tc(cv, nq, n_t, n_w, !have_sum, !have_iel);
+    carve_tc(cv, nq, n_t, n_w, !have_sum, !have_iel, terms);
     return cv.bytes();
 }
 
+// terms = 2 (BF16X3) or 3 (BF16X6)
 int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* psi,
                     size_t ld, const double2* psi_sum, float* out, double* i_el, int flags,
-                    double beta, void* ws, cudaStream_t st) {
+                    double beta, int terms, void* ws, cudaStream_t st) {
     Carver cv(ws);
-    TcWs w = carve_tc(cv, nq, n_t, n_w, psi_sum == nullptr, i_el == nullptr);
-    const TcGeom g = geom(nq, n_t, n_w);
+    TcWs w = carve_tc(cv, nq, n_t, n_w, psi_sum == nullptr, i_el == nullptr, terms);
+    const TcGeom g = geom(nq, n_t, n_w, terms);
     TACAW_REQUIRE((size_t)g.n_mtiles * g.n_ntiles <= 0x7fffffffu, TACAW_EUNSUPPORTED,
                   "tacaw_spectrum: too many output tiles");
     const double2* sum = psi_sum;
@@ -356,12 +435,12 @@ int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega,
     TACAW_CUDA_CHECK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     {
         dim3 grid(g.nq_pad / 32, g.t_pad / 32);
-        split_a_kernel<<<grid, 256, 0, st>>>(psi, ld, sum, n_t, nq, g.t_pad, w.ahi, w.alo, iel);
+        split_a_kernel<<<grid, 256, 0, st>>>(psi, ld, sum, n_t, nq, g.t_pad, w.a[0], w.a[1], w.a[2], iel);
         TACAW_LAUNCH_CHECK();
     }
     {
-        dim3 grid((g.t_pad + 127) / 128, g.n_ntiles * TN);
-        split_b_kernel<<<grid, 128, 0, st>>>(omega, n_t, n_w, g.t_pad, dt_fs, w.bhi, w.blo);
+        dim3 grid((g.t_pad + 127) / 128, g.n_ntiles * g.tn);
+        split_b_kernel<<<grid, 128, 0, st>>>(omega, n_t, n_w, g.t_pad, dt_fs, g.tn, w.b[0], w.b[1], w.b[2]);
         TACAW_LAUNCH_CHECK();
     }
     const bool kubo = (flags & TACAW_KUBO) != 0;
@@ -369,18 +448,27 @@ int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega,
         int rc = launch_kubo(w.kubo, omega, n_t, n_w, dt_fs, beta, st);
         if (rc) return rc;
     }
-    CUtensorMap mah, mal, mbh, mbl;
-    int rc = make_map(&mah, w.ahi, g.nq_pad, g.k2, TM);
-    if (!rc) rc = make_map(&mal, w.alo, g.nq_pad, g.k2, TM);
-    if (!rc) rc = make_map(&mbh, w.bhi, (size_t)g.n_ntiles * TN, g.k2, TN);
-    if (!rc) rc = make_map(&mbl, w.blo, (size_t)g.n_ntiles * TN, g.k2, TN);
+    TcMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    int rc = TACAW_OK;
+    for (int i = 0; i < terms && !rc; ++i) {
+        rc = make_map(&maps.a[i], w.a[i], g.nq_pad, g.k2, TM);
+        if (!rc) rc = make_map(&maps.b[i], w.b[i], (size_t)g.n_ntiles * g.tn, g.k2, g.tn);
+    }
     if (rc) return rc;
-    TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel, (int)TC_SMEM));
     const float scale = (float)(1.0 / ((double)n_t * (double)n_t));
     const unsigned blocks = (unsigned)(g.n_mtiles * g.n_ntiles);
-    tc_power_kernel<<<blocks, TC_THREADS, TC_SMEM, st>>>(mah, mal, mbh, mbl, kubo ? w.kubo : nullptr, out, nq,
-                                                         n_w, g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
-                                                         w.err);
+    if (terms == 2) {
+        TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<2>, (int)TcCfg<2>::SMEM));
+        tc_power_kernel<2><<<blocks, TC_THREADS, TcCfg<2>::SMEM, st>>>(maps, kubo ? w.kubo : nullptr, out, nq, n_w,
+                                                                      g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
+                                                                      w.err);
+    } else {
+        TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<3>, (int)TcCfg<3>::SMEM));
+        tc_power_kernel<3><<<blocks, TC_THREADS, TcCfg<3>::SMEM, st>>>(maps, kubo ? w.kubo : nullptr, out, nq, n_w,
+                                                                      g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
+                                                                      w.err);
+    }
     TACAW_LAUNCH_CHECK();
     if (flags & TACAW_NORMALIZE) {
         rc = launch_normalize(out, (size_t)nq * n_w, i_el, iel, nq, w.red, w.red + normalize_ws_doubles() - 1, st);

@@ -88,6 +88,8 @@ class TimeToSpectrum:
         precs = [L.TACAW_FP32, L.TACAW_BF16X3]
         if self.omega is None and self.n_t in L.TIME_FFT_SIZES:
             precs.append(L.TACAW_FFT32)
+        if self.precision == "bf16x6":
+            precs.append(L.TACAW_BF16X6)
         for prec in precs:                               # one workspace serves every precision
             L.check("tacaw_spectrum", lib.tacaw_spectrum(self.grid.nx * self.grid.ny, self.n_t, self.dt_fs, n_w,
                                                          null, null, ctypes.c_void_p(1), null, ctypes.c_void_p(1),
