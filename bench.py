@@ -580,7 +580,7 @@ def plain_cufft_slice_step(tts, g, reps, stream):
             "speedup": ms / ours_ms, "rel_l2_difference": diff}
 
 
-def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=32):
+def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=64):
     """The 64 uneven seeded jobs (grids 128-768, 10-150 slices, 1-3 species), each
     cut to its first `snapshots` snapshots, through the batched path: eager run and
     CUDA-graph replay, in grid point * slice * snapshot per second."""
