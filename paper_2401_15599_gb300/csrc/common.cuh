@@ -85,6 +85,22 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this block's shared memory, completing on `bar`
+// (an mbarrier in shared memory that expects the bytes).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(bytes), "r"(static_cast<uint32_t>(__cvta_generic_to_shared(bar)))
+                 : "memory");
+}
+
+// Orders this thread's (and, after a block barrier, the block's) earlier
+// ordinary shared-memory accesses before later asynchronous-proxy writes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // exp(i x) = cos x + i sin x for the transmission phase sigma_e v.  The phase
 // is small in practice, so |x| <= 0.5 uses the Taylor series of sin to x^9
 // and of cos to x^10 (truncation below 2e-11, i.e. far under FP32 rounding),

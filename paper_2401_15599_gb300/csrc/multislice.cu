@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "tc.cuh"
 
 namespace tacaw {
 
@@ -73,7 +74,8 @@ constexpr int kRowThreads = 256;
 //   px[kx] = exp(-i pi lambda dz qx^2), py[ky] = exp(-i pi lambda dz qy^2) / (nx ny),
 //   kymax[kx] = largest |ky| index with qx^2 + qy^2 <= qmax^2 (-1 if none),
 //   kymax[nx] = K, the largest |kx| index with qx^2 <= qmax^2: the columns
-//     kx <= K and kx >= nx - K are the ones the band limit keeps ("kept columns").
+//     kx <= K and kx >= nx - K are the ones the band limit keeps ("kept columns");
+//   kymax[nx + 1] = 0: set to 1 by the staged row pass if a bounded wait gives up.
 // The band limit zeroes every other column of the hybrid (k_x, y) wave, so the
 // passes skip them: the row pass neither reads nor writes them, the column pass
 // does not transform them (it writes their zeros only into the exit wave).
@@ -135,6 +137,7 @@ __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py
             if (__dadd_rn(__dmul_rn(q, q), 0.0) <= qmax2) kk = k; else break;
         }
         kymax[nx] = kk;
+        kymax[nx + 1] = 0;               // error flag of the staged row pass
     }
     if (i < ny) {
         double s, c;
@@ -214,6 +217,100 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
     row_body<NX>(psi + (snap * ny + y) * NX, V + ((snap * n_slices + s) * ny + y) * NX,
                  psi_in ? psi_in + (size_t)y * NX : nullptr, mode, sigma, __ldg(kymax + NX), smem,
                  smem + ROWS * NX, tw, t, row);
+}
+
+
+// Staged row pass for slices after the first (hybrid (k_x, y) input): a
+// persistent grid in which each block walks row groups (ROWS rows of one
+// snapshot) and, while it transforms one group, has bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier) bring the kept columns of the next
+// group's wave rows and its potential rows into the other half of a two-stage
+// shared-memory ring.  The stage being transformed doubles as the FFT's
+// exchange buffer (one-buffer mode).  Same arithmetic as row_body, so the
+// results are identical; the waits are bounded and set *err on a timeout.
+template <int NX>
+__global__ void __launch_bounds__(kRowThreads)
+row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, const float2* __restrict__ twx,
+                       const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int n_groups,
+                       int* __restrict__ err) {
+    using namespace fft;
+    constexpr int E = Plan<NX>::E;
+    constexpr int TPT = NX / E;
+    constexpr int ROWS = kRowThreads / TPT;
+    constexpr int PSI_BYTES = ROWS * NX * (int)sizeof(float2);
+    constexpr int V_BYTES = ROWS * NX * (int)sizeof(float);
+    constexpr int STAGE = PSI_BYTES + V_BYTES;
+    extern __shared__ __align__(128) unsigned char stage_raw[];
+    float2* tw = reinterpret_cast<float2*>(stage_raw + 2 * STAGE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(stage_raw + 2 * STAGE + TwSize<NX>::value * sizeof(float2));
+    const int groups_per_snap = ny / ROWS;
+    const int K = __ldg(kymax + NX);
+    // kept columns [0, a) and [b, NX), both ends even so every copy is 16-byte aligned
+    int a = K + 1;
+    a += a & 1;
+    if (a > NX) a = NX;
+    int b = NX - K;
+    b -= b & 1;
+    if (b < a) b = a;
+    const uint32_t tx_bytes = (uint32_t)(ROWS * (a + NX - b) * (int)sizeof(float2) + V_BYTES);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::fence_mbar_init();
+    }
+    stage_twiddles<NX>(tw, twx);
+    __syncthreads();
+    auto issue = [&](int g, int st) {              // thread 0
+        const int snap = g / groups_per_snap, y0 = (g % groups_per_snap) * ROWS;
+        unsigned char* dst = stage_raw + st * STAGE;
+        fence_proxy_async_smem();                  // the stage was FFT scratch two groups ago
+        tc::mbar_arrive_expect_tx(&bar[st], tx_bytes);
+        const float2* src = psi + ((size_t)snap * ny + y0) * NX;
+        for (int r = 0; r < ROWS; ++r) {
+            bulk_copy_g2s(dst + (size_t)r * NX * sizeof(float2), src + (size_t)r * NX, a * sizeof(float2), &bar[st]);
+            if (b < NX)
+                bulk_copy_g2s(dst + ((size_t)r * NX + b) * sizeof(float2), src + (size_t)r * NX + b,
+                              (NX - b) * sizeof(float2), &bar[st]);
+        }
+        bulk_copy_g2s(dst + PSI_BYTES, V + (((size_t)snap * n_slices + s) * ny + y0) * NX, V_BYTES, &bar[st]);
+    };
+    const int t = threadIdx.x % TPT;
+    const int row = threadIdx.x / TPT;
+    if (threadIdx.x == 0 && (int)blockIdx.x < n_groups) issue(blockIdx.x, 0);
+    int it = 0, pending = -1;                      // stage with a copy in flight at a break
+    for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++it) {
+        const int st = it & 1;
+        const int gn = g + gridDim.x;
+        if (threadIdx.x == 0 && gn < n_groups) issue(gn, st ^ 1);
+        const bool ok = tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 24);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            pending = gn < n_groups ? st ^ 1 : -1;
+            break;
+        }
+        float2* buf = reinterpret_cast<float2*>(stage_raw + st * STAGE);
+        const float* vrow = reinterpret_cast<const float*>(stage_raw + st * STAGE + PSI_BYTES) + row * NX;
+        const RowLayout lay{row * NX};
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * NX + t + TPT * m] : make_float2(0.f, 0.f);
+        transform<NX, true>(v, buf, buf, t, tw, lay);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            float sn, cs;
+            phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
+            v[m] = cmul(v[m], make_float2(cs, sn));
+        }
+        transform<NX, false>(v, buf, buf, t, tw, lay);
+        const int snap = g / groups_per_snap, y = (g % groups_per_snap) * ROWS + row;
+        float2* rowp = psi + ((size_t)snap * ny + y) * NX;
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            if (kept_column(t + TPT * m, NX, K)) rowp[t + TPT * m] = v[m];
+        __syncthreads();                           // this stage is refilled two groups later
+    }
+    if (threadIdx.x == 0 && pending >= 0) tc::mbar_wait_quiet(&bar[pending], ((it + 1) >> 1) & 1, 1u << 24);
 }
 
 // Jobs of one batched launch (all of the same grid size): block row y of the
@@ -453,6 +550,24 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
                        cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
+    if (mode == 0 && fft::Plan<NX>::E == 8 && reinterpret_cast<uintptr_t>(psi) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(V) % 16 == 0) {
+        const size_t smem = 2 * (size_t)ROWS * NX * (sizeof(float2) + sizeof(float)) +
+                            fft::TwSize<NX>::value * sizeof(float2) + 2 * sizeof(uint64_t);
+        cudaError_t e = ensure_smem((const void*)row_pass_staged_kernel<NX>, (int)smem);
+        if (e != cudaSuccess) return e;
+        int resident = 0;
+        e = resident_blocks((const void*)row_pass_staged_kernel<NX>, kRowThreads, (int)smem, &resident);
+        if (e != cudaSuccess) return e;
+        const long long groups = (long long)(ny / ROWS) * n_t;
+        if (groups <= 0x7fffffffLL) {
+            const int n_groups = (int)groups;
+            const int blocks = resident < n_groups ? resident : n_groups;
+            row_pass_staged_kernel<NX><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
+                                                                         n_groups, const_cast<int*>(kymax) + NX + 1);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_pass_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
@@ -595,7 +710,7 @@ static MsTables carve_ms(Carver& cv, const tacaw_grid& g) {
     t.twy = cv.take<float2>(g.ny);
     t.px = cv.take<float2>(g.nx);
     t.py = cv.take<float2>(g.ny);
-    t.kymax = cv.take<int>(g.nx + 1);
+    t.kymax = cv.take<int>(g.nx + 2);   // + K and an error flag (see ms_setup_kernel)
     return t;
 }
 
