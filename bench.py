@@ -42,7 +42,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="paper_scale")
-    p.add_argument("--batch", type=int, default=32)
+    p.add_argument("--batch", default="auto",
+                   help="snapshots per multislice call, or 'auto' (tuned per grid and GPU, cached in JSON)")
     p.add_argument("--precision", choices=["fft32", "bf16x3", "fp32"], default="fft32",
                    help="temporal transform: FP32 FFT over time (natural grid), split-BF16 tcgen05 GEMM, "
                         "or FP32 SIMT GEMM")

@@ -295,6 +295,24 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
                 void* stream);
 
 /*
+ * Autotuning of the snapshot batch (the paper has no counterpart; it serves
+ * the batched and long-trajectory drivers).  Times tacaw_multislice with a
+ * plane wave on the caller's potentials V [max_batch][n_slices][ny][nx] (DEVICE)
+ * into psi_q [max_batch][ny][nx] (DEVICE, overwritten) for n_candidates
+ * snapshot batches candidates[i] (HOST, each in [1, max_batch]): one warm-up
+ * call, then `reps` timed calls per candidate (CUDA events on `stream`).
+ * ms_per_snapshot [n_candidates] (HOST out) receives the device time per
+ * snapshot of each; *best_batch (HOST out) the fastest candidate.  Blocks the
+ * calling thread until the timings are read (not for stream capture).
+ * Workspace as tacaw_multislice (query with ws == NULL).  TACAW_EINVAL for bad
+ * sizes, TACAW_EUNSUPPORTED for grid sizes tacaw_multislice does not take.
+ */
+int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float* V, void* psi_q,
+                          const int32_t* candidates, int32_t n_candidates, int32_t reps,
+                          float* ms_per_snapshot, int32_t* best_batch, void* ws, size_t* ws_bytes,
+                          void* stream);
+
+/*
  * Adjoint of tacaw_spectrum (flags 0) for gradient-based fitting: given
  * dL/dI (real, [nq][n_omega]) returns the gradient with respect to psi in
  * the PyTorch convention for complex inputs (dL/dRe + i dL/dIm):

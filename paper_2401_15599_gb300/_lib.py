@@ -88,6 +88,8 @@ SIGNATURES = {
                                                _SZ, _P]),
     "tacaw_relative_difference": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P]),
     "tacaw_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32] + [ctypes.c_double] * 7 + [_P, _P, _SZ, _P]),
+    "tacaw_tune_multislice": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
+                                             ctypes.c_int32, _P, _P, _P, _SZ, _P]),
     "tacaw_spectrum_backward": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                ctypes.c_int32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "tacaw_multislice_backward": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,

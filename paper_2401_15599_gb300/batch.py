@@ -30,6 +30,10 @@ class Job:
 class BatchTimeToSpectrum:
     def __init__(self, jobs, window=8, precision="bf16x3", device="cuda"):
         self.jobs = list(jobs)
+        if window == "auto":                    # tuned for the largest grid of the jobs (tuning.py)
+            from .tuning import best_multislice_batch
+            big = max(self.jobs, key=lambda j: j.grid.nx * j.grid.ny * j.grid.n_slices)
+            window = best_multislice_batch(big.grid, device=device)
         self.window = int(window)
         self.precision = precision
         self.device = torch.device(device)

@@ -80,6 +80,9 @@ int probe_run(int nx, int ny, double lx, double ly, double lam, double alpha, do
 
 bool time_fft_size_supported(int n);
 
+int tune_multislice_run(const tacaw_grid& g, const float* V, float2* psi_q, const int* cand, int n_cand,
+                        int reps, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st);
+
 static int check_grid(const tacaw_grid* g, const char* fn) {
     TACAW_REQUIRE(g != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
     TACAW_REQUIRE(g->nx > 0 && g->ny > 0 && g->n_slices > 0 && g->n_slices <= 65535, TACAW_EINVAL,
@@ -407,6 +410,29 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
     TACAW_REQUIRE(psi, TACAW_EINVAL, "%s: NULL array", fn);
     return probe_run(nx, ny, lx, ly, lam, alpha_mrad, defocus_A, x0_A, y0_A, (float2*)psi, ws,
                      (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ autotuning
+int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float* V, void* psi_q,
+                          const int32_t* candidates, int32_t n_candidates, int32_t reps, float* ms_per_snapshot,
+                          int32_t* best_batch, void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_tune_multislice";
+    int rc = check_grid(grid, fn);
+    if (rc) return rc;
+    TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny), TACAW_EUNSUPPORTED,
+                  "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn, grid->nx, grid->ny);
+    TACAW_REQUIRE(max_batch >= 1 && max_batch <= 65535 && n_candidates >= 1 && reps >= 1 && reps <= 1000,
+                  TACAW_EINVAL, "%s: need 1 <= max_batch <= 65535, n_candidates >= 1, 1 <= reps <= 1000", fn);
+    bool query = false;
+    rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(V && psi_q && candidates && ms_per_snapshot && best_batch, TACAW_EINVAL, "%s: NULL array", fn);
+    for (int i = 0; i < n_candidates; ++i)
+        TACAW_REQUIRE(candidates[i] >= 1 && candidates[i] <= max_batch, TACAW_EINVAL,
+                      "%s: candidate %d = %d outside [1, max_batch = %d]", fn, i, candidates[i], max_batch);
+    return tune_multislice_run(*grid, V, (float2*)psi_q, candidates, n_candidates, reps, ms_per_snapshot,
+                               best_batch, ws, (cudaStream_t)stream);
 }
 
 }  // extern "C"

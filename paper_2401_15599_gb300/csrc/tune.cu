@@ -1,0 +1,53 @@
+// Autotuning of the snapshot batch of the multislice: how many snapshots one
+// tacaw_multislice call advances together.  The slice step is two passes over
+// the batch's waves, so the batch sets how much of the wave stays in L2 between
+// the row and the column pass (32 snapshots of 512^2 are 64 MB) and how many
+// blocks each launch has.  The tuner times the real entry point on the
+// caller's buffers for each candidate and reports the device time per snapshot.
+
+#include "common.cuh"
+
+namespace tacaw {
+
+size_t multislice_ws_bytes(const tacaw_grid& g);
+int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st);
+
+int tune_multislice_run(const tacaw_grid& g, const float* V, float2* psi_q, const int* cand, int n_cand,
+                        int reps, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TACAW_CUDA_CHECK(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        TACAW_CUDA_CHECK(ce);
+    }
+    int rc = TACAW_OK;
+    float best_ms = 0.f;
+    for (int i = 0; i < n_cand && rc == TACAW_OK; ++i) {
+        rc = multislice_run(g, cand[i], V, nullptr, psi_q, nullptr, ws, st);     // warm-up
+        if (rc) break;
+        ce = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rc == TACAW_OK && ce == cudaSuccess; ++r)
+            rc = multislice_run(g, cand[i], V, nullptr, psi_q, nullptr, ws, st);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+            set_error("tacaw_tune_multislice: %s", cudaGetErrorString(ce));
+            rc = TACAW_ECUDA;
+            break;
+        }
+        ms_per_snapshot[i] = ms / ((float)reps * (float)cand[i]);
+        if (i == 0 || ms_per_snapshot[i] < best_ms) {
+            best_ms = ms_per_snapshot[i];
+            *best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace tacaw

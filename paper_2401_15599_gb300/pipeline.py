@@ -23,6 +23,9 @@ class TimeToSpectrum:
         self.n_atoms = int(n_atoms)
         self.amp_sigma = amp_sigma
         self.dt_fs = float(dt_fs)
+        if batch == "auto":                     # tuned per grid and GPU, cached (tuning.py)
+            from .tuning import best_multislice_batch
+            batch = best_multislice_batch(grid, device=device)
         self.batch = max(1, min(int(batch), self.n_t))
         self.precision = precision
         self.kubo = kubo

@@ -1,0 +1,101 @@
+"""Snapshot-batch autotuning with a JSON cache.
+
+``best_multislice_batch(grid)`` returns how many snapshots one multislice call
+should advance together on this GPU for this grid (candidates whose potentials
+would exceed MAX_TUNING_BYTES are skipped).  On a cache miss it times
+the candidates with the library's ``tacaw_tune_multislice`` (random slice
+potentials: the transform cost does not depend on the values) and stores the
+result under the key "<device name>|<nx>x<ny>x<n_slices>".
+
+The cache file is ``$TACAW_TUNE_CACHE`` when set, else
+``~/.cache/tacaw/tune.json``.  Entries hold the batch and the measured
+milliseconds per snapshot of every candidate.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import tempfile
+
+import torch
+
+from . import _lib as L
+
+DEFAULT_CANDIDATES = (8, 16, 32, 64, 128)
+MAX_TUNING_BYTES = 16 << 30         # potentials allocated for the largest candidate
+
+
+def cache_path() -> str:
+    return os.environ.get("TACAW_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "tacaw",
+                                                               "tune.json")
+
+
+def load_cache(path=None) -> dict:
+    try:
+        with open(path or cache_path()) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store_cache(entries: dict, path=None) -> None:
+    """Merge entries into the cache file (written atomically)."""
+    path = path or cache_path()
+    data = load_cache(path)
+    data.update(entries)
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=os.path.dirname(os.path.abspath(path)), suffix=".tmp")
+    with os.fdopen(fd, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def cache_key(grid, device_name: str) -> str:
+    return f"{device_name}|{int(grid.nx)}x{int(grid.ny)}x{int(grid.n_slices)}"
+
+
+def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, device="cuda"):
+    """Time every candidate batch on this device: {batch: ms per snapshot}."""
+    lib = L.load()
+    dev = torch.device(device)
+    per_snapshot = 4 * int(grid.n_slices) * int(grid.ny) * int(grid.nx)
+    cap = max(1, MAX_TUNING_BYTES // per_snapshot)
+    cand = sorted({int(c) for c in candidates if 1 <= int(c) <= cap}) or [min(int(c) for c in candidates)]
+    top = max(cand)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    V = torch.rand((top, grid.n_slices, grid.ny, grid.nx), generator=gen, device=dev) * 30.0
+    psi = torch.empty((top, grid.ny, grid.nx), dtype=torch.complex64, device=dev)
+    g = L.make_grid(grid)
+    c_arr = (ctypes.c_int32 * len(cand))(*cand)
+    ms = (ctypes.c_float * len(cand))()
+    best = ctypes.c_int32(0)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+    def call(ws, nbytes):
+        return lib.tacaw_tune_multislice(ctypes.byref(g), top, ctypes.c_void_p(V.data_ptr()),
+                                         ctypes.c_void_p(psi.data_ptr()), c_arr, len(cand), int(reps), ms,
+                                         ctypes.byref(best), ws, nbytes, stream)
+
+    nbytes = ctypes.c_size_t(0)
+    L.check("tacaw_tune_multislice", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    nbytes = ctypes.c_size_t(ws.numel())
+    L.check("tacaw_tune_multislice", call(ctypes.c_void_p(ws.data_ptr()), ctypes.byref(nbytes)))
+    return {c: float(m) for c, m in zip(cand, ms)}, int(best.value)
+
+
+def best_multislice_batch(grid, candidates=DEFAULT_CANDIDATES, device="cuda", path=None, measure=None):
+    """Cached best snapshot batch for this grid on this device (tuned on a miss).
+    ``measure`` replaces the timing function (tests)."""
+    dev = torch.device(device)
+    name = torch.cuda.get_device_name(dev) if measure is None else "test-device"
+    key = cache_key(grid, name)
+    entry = load_cache(path).get(key)
+    if entry and int(entry.get("batch", 0)) >= 1:
+        return int(entry["batch"])
+    timings, best = (measure or measure_multislice_batches)(grid, candidates, device=device)
+    store_cache({key: {"batch": int(best), "ms_per_snapshot": {str(k): v for k, v in timings.items()}}}, path)
+    return int(best)

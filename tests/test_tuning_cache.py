@@ -1,0 +1,45 @@
+"""The snapshot-batch tuner's JSON cache (host logic, CPU): a miss measures
+and stores, a hit does not measure again, entries of other grids survive, a
+corrupt file counts as empty."""
+
+import json
+
+from paper_2401_15599_gb300 import tuning
+import workloads as W
+
+
+def _grid(n=256, ns=10):
+    return W.GridSpec(n, n, n * 0.158203125, n * 0.158203125, ns, 2.0, 0.0, 200.0)
+
+
+def test_miss_measures_and_hit_reuses(tmp_path):
+    path = str(tmp_path / "tune.json")
+    calls = []
+
+    def fake(grid, candidates, device="cuda"):
+        calls.append((grid.nx, tuple(candidates)))
+        t = {c: 1.0 / c + (0.5 if c == 32 else 0.0) for c in candidates}
+        return t, min(t, key=t.get)
+
+    b1 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
+    assert b1 == 64 and len(calls) == 1
+    b2 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
+    assert b2 == 64 and len(calls) == 1                     # from the cache
+    tuning.best_multislice_batch(_grid(512, 101), candidates=(8, 16), path=path, measure=fake)
+    data = json.load(open(path))
+    assert len(calls) == 2 and len(data) == 2
+    entry = data["test-device|256x256x10"]
+    assert entry["batch"] == 64 and set(entry["ms_per_snapshot"]) == {"8", "16", "32", "64"}
+
+
+def test_corrupt_cache_is_ignored(tmp_path):
+    path = tmp_path / "tune.json"
+    path.write_text("{not json")
+    b = tuning.best_multislice_batch(_grid(), candidates=(4, 8), path=str(path),
+                                     measure=lambda g, c, device="cuda": ({4: 2.0, 8: 1.0}, 8))
+    assert b == 8 and json.load(open(path))["test-device|256x256x10"]["batch"] == 8
+
+
+def test_cache_path_follows_environment(monkeypatch, tmp_path):
+    monkeypatch.setenv("TACAW_TUNE_CACHE", str(tmp_path / "x.json"))
+    assert tuning.cache_path() == str(tmp_path / "x.json")
