@@ -138,18 +138,23 @@ template <int A, int... Rest>
 struct First { static constexpr int value = A; };
 
 // Shared-memory layouts.  (Passing the same buffer as b0 and b1 to transform
-// runs it in one buffer with an extra barrier per exchange.)  RowLayout: one transform per row, positions swizzled
-// inside the row to spread 8-byte accesses over the banks.  ColLayout: W
-// transforms interleaved (position-major), lanes of a warp on adjacent
-// transforms, conflict free without a swizzle.
+// runs it in one buffer with an extra barrier per exchange.)  RowLayout: one
+// transform per row, positions swizzled inside the row to spread 8-byte
+// accesses over the banks.  ColLayout: W transforms interleaved
+// (position-major), lanes of a warp on adjacent transforms.
 struct RowLayout {
     int base;  // row * N
     __device__ __forceinline__ int operator()(int p) const { return base + (p ^ ((p >> 4) & 15)); }
 };
+// ColLayout: a position row of W float2 covers 2W of the 32 banks, so 16/W rows
+// share the banks; the first exchange writes positions 8j + r, whose low bits
+// are the same for every lane, so the position is XORed with (p >> 3) in its
+// low log2(16/W) bits to spread those lanes over all bank groups.
 template <int W>
 struct ColLayout {
     int c;
-    __device__ __forceinline__ int operator()(int p) const { return p * W + c; }
+    static constexpr int kGroups = 16 / W > 1 ? 16 / W : 1;
+    __device__ __forceinline__ int operator()(int p) const { return (p ^ ((p >> 3) & (kGroups - 1))) * W + c; }
 };
 
 // Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
