@@ -20,6 +20,9 @@
 //     V_tile = sum_a gy_a (x) gx_a, accumulated in FP32 registers over the
 //     candidate atoms in bin order (a fixed order: identical configurations give
 //     bit-identical potentials).
+//     When 6 s <= dz for every species, potential_depth_kernel takes its place:
+//     one block per tile and snapshot walks the slices and tabulates each slab's
+//     lateral factors once for the three slices they reach.
 // The adjoint (potential_backward_kernel) keeps one block per band of 8 rows.
 
 #include <math.h>
@@ -41,7 +44,8 @@ struct PotParams {
     int nx, ny, n_slices, n_atoms, n_species;
     // bins: (slab, band of band_h rows, tile of ctile_w columns)
     int n_bands, n_ctiles, n_bins, band_h, ctile_w;
-    int slab_reach, band_reach, ctile_reach;   // neighbouring bins that can reach a tile
+    int slab_reach;                            // neighbouring slabs that can reach a slice
+    int nb_max, nc_max;                        // most bands / column tiles any tile needs
     int reach_x, reach_y;                      // ceil(6 s_max / d): pixels an atom reaches
     float lx, ly, dx, dy, inv_dx, z0, dz, inv_dz;
     double dx_d, dy_d, inv_dx_d, inv_dy_d;
@@ -75,6 +79,33 @@ __device__ __forceinline__ Split split_position(float x, float y, const PotParam
 __device__ __forceinline__ int wrap(int k, int n) {
     k %= n;
     return k < 0 ? k + n : k;
+}
+
+// Bins along one periodic axis (bands of w rows or column tiles of w columns,
+// the last one shorter when w does not divide n) holding a pixel within R of
+// bin `bin`'s pixels, through the wrap: `count` bins from `first` on, modulo
+// n_axis.  Counted from pixel intervals, not from whole bins, because across a
+// short last bin a pixel R away can lie two or more bins over.
+struct AxisRange {
+    int first, count;
+};
+
+__host__ __device__ __forceinline__ AxisRange axis_range(int bin, int w, int n, int n_axis, int R) {
+    const int t0 = bin * w, len = (n - t0 < w) ? n - t0 : w;
+    AxisRange a;
+    a.first = 0;
+    a.count = n_axis;
+    if (len + 2 * R >= n) return a;                  // the interval covers the axis
+    const int lo = t0 - R, hi = t0 + len - 1 + R;   // -n < lo, hi < 2n
+    const int bf = (lo < 0 ? lo + n : lo) / w, bl = (hi >= n ? hi - n : hi) / w;
+    if (lo >= 0 && hi < n) {
+        a.first = bf;
+        a.count = bl - bf + 1;
+    } else if (bl < bf) {                            // wraps without meeting itself
+        a.first = bf;
+        a.count = n_axis - bf + bl + 1;
+    }
+    return a;
 }
 
 __device__ __forceinline__ int atom_bin(const Split& sp, float z, const PotParams& p) {
@@ -177,21 +208,18 @@ bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotPa
     }
 }
 
-// Neighbouring bins of a tile (slabs s +- slab_reach, bands +- band_reach,
-// column tiles +- ctile_reach around the tile's own bin, each range cut to the
-// whole axis when it would wrap onto itself) as one flat list: warp 0 loads the
-// ranges and scans the counts into bin_start / bin_cum.  Returns the number of
-// source atoms (after a block barrier).
-constexpr int kMaxNbBins = 64;
+// Neighbouring bins of a tile (slabs slab0 .. slab1; the bands and column
+// tiles holding a pixel within reach + 1 of the tile, from axis_range) as one
+// flat list: warp 0 loads the ranges and scans the counts into bin_start /
+// bin_cum.  Returns the number of source atoms (after a block barrier).
+constexpr int kMaxNbBins = 128;
 
-__device__ int load_bins(int* bin_start, int* bin_cum, const PotParams& p, const int* __restrict__ off,
-                         int s, int band, int ctile, int* n_nb_out) {
+__device__ int load_bins_slabs(int* bin_start, int* bin_cum, const PotParams& p, const int* __restrict__ off,
+                               int slab0, int slab1, int band, int ctile, int* n_nb_out) {
     const int lane = threadIdx.x & 31;
-    const int slab0 = max(0, s - p.slab_reach), slab1 = min(p.n_slices - 1, s + p.slab_reach);
-    const bool all_b = 2 * p.band_reach + 1 >= p.n_bands;
-    const bool all_c = 2 * p.ctile_reach + 1 >= p.n_ctiles;
-    const int nb = all_b ? p.n_bands : 2 * p.band_reach + 1;
-    const int nc = all_c ? p.n_ctiles : 2 * p.ctile_reach + 1;
+    const AxisRange rb = axis_range(band, p.band_h, p.ny, p.n_bands, p.reach_y + 1);
+    const AxisRange rx = axis_range(ctile, p.ctile_w, p.nx, p.n_ctiles, p.reach_x + 1);
+    const int nb = rb.count, nc = rx.count;
     const int n_nb = nb * nc * (slab1 - slab0 + 1);
     if (threadIdx.x < 32) {
         int carry = 0;
@@ -201,8 +229,8 @@ __device__ int load_bins(int* bin_start, int* bin_cum, const PotParams& p, const
             if (i < n_nb) {
                 const int slab = slab0 + i / (nb * nc);
                 const int kb = (i / nc) % nb, kc = i % nc;
-                const int b = all_b ? kb : wrap(band - p.band_reach + kb, p.n_bands);
-                const int c = all_c ? kc : wrap(ctile - p.ctile_reach + kc, p.n_ctiles);
+                const int b = (rb.first + kb) % p.n_bands;
+                const int c = (rx.first + kc) % p.n_ctiles;
                 const int bin = (slab * p.n_bands + b) * p.n_ctiles + c;
                 start = __ldg(off + bin);
                 cnt = __ldg(off + bin + 1) - start;
@@ -224,6 +252,12 @@ __device__ int load_bins(int* bin_start, int* bin_cum, const PotParams& p, const
     __syncthreads();
     *n_nb_out = n_nb;
     return bin_cum[n_nb];
+}
+
+__device__ int load_bins(int* bin_start, int* bin_cum, const PotParams& p, const int* __restrict__ off,
+                         int s, int band, int ctile, int* n_nb_out) {
+    return load_bins_slabs(bin_start, bin_cum, p, off, max(0, s - p.slab_reach),
+                           min(p.n_slices - 1, s + p.slab_reach), band, ctile, n_nb_out);
 }
 
 // Source index -> atom index through the scanned bin list: the last bin whose
@@ -456,6 +490,249 @@ potential_tile_kernel(const int* __restrict__ bin_off, const float4* __restrict_
             for (int k = 0; k < 8; ++k)
                 if (cw + k < ncols) out[k] = acc[k];
         }
+    }
+}
+
+// ------------------------------------------------------------------ forward, depth walk
+// One block per (tile, snapshot) walks the slices in order.  The lateral
+// factors of an atom do not depend on the slice, and an atom of slab k reaches
+// only slices k-1 .. k+1 when 6 s <= dz (slab_reach 1), so each slab's
+// candidates are selected and tabulated once, when the slab enters the window,
+// into one of three slots (slab k -> slot k mod 3) and reused by the three
+// slices; per slice only the weights amp w_s(z) and the outer products are
+// new.  A slot holds kDCap candidates; the rest of a crowded slab ("overflow")
+// is re-selected and tabulated in chunks for every slice, so any input is
+// handled.  Order of the sums: slab s-1, s, s+1, each in source order (cached
+// candidates, then overflow chunks): fixed by the configuration.
+constexpr int kDCap = 24;                 // cached candidates per slab slot
+constexpr int kDSlots = 4;                // three slabs + one overflow scratch slot
+constexpr int kDBins = 24;                // bins per slab neighbourhood (<= 3 x 3 here)
+
+struct DepthSmem {
+    float gy[kDSlots][kDCap][kTR];
+    float4 gx[kDSlots][kDCap][kTC / 4];
+    int k0y[kDSlots][kDCap], k0x[kDSlots][kDCap], wmask[kDSlots][kDCap], spc[kDSlots][kDCap];
+    float fx[kDSlots][kDCap], fy[kDSlots][kDCap], z[kDSlots][kDCap], aw[kDSlots][kDCap];
+    int n_cand[kDSlots], resume[kDSlots];      // candidates held; source index where the slab continues
+    int bin_start[kDSlots][kDBins], bin_cum[kDSlots][kDBins + 1], n_nb[kDSlots], n_src[kDSlots];
+    int warp_cnt[kTWarps];
+    unsigned char wlist[kTWarps][kDCap];
+};
+
+struct DepthTile {
+    int r0, c0, nrows, ncols, half_x, half_y;
+};
+
+// Candidates of slab `slab` from source index `from` on: accept (valid species,
+// window reaches the tile), keep the first kDCap in `slot`, record where the
+// slab continues (its n_src when all fitted), then tabulate their lateral
+// factors and warp masks.  Uniform over the block; ends with a barrier.
+__device__ void depth_gather(DepthSmem& sm, const PotParams& p, const DepthTile& dt, const float4* __restrict__ atoms,
+                             const int2* __restrict__ atoms_px, int slot, int bslot, int from) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int n_src = sm.n_src[bslot];
+    if (threadIdx.x == 0) {
+        sm.n_cand[slot] = 0;
+        sm.resume[slot] = n_src;
+    }
+    __syncthreads();
+    for (int sb = from; sb < n_src; sb += kPotThreads) {
+        if (sm.n_cand[slot] >= kDCap) {             // uniform: read after a barrier
+            // full exactly at the end of the previous pass: continue at this one
+            if (threadIdx.x == 0 && sm.resume[slot] == n_src) sm.resume[slot] = sb;
+            break;
+        }
+        const int src = sb + (int)threadIdx.x;
+        bool ok = false;
+        float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
+        int2 px = make_int2(0, 0);
+        int sp = 0;
+        if (src < n_src) {
+            const int ai = source_atom(sm.bin_start[bslot], sm.bin_cum[bslot], sm.n_nb[bslot], src);
+            at = atoms[ai];
+            px = atoms_px[ai];
+            sp = __float_as_int(at.w);
+            ok = sp >= 0 && sp < p.n_species;
+            const float rc = 6.0f * (ok ? p.sigma[sp] : 1.f);
+            ok = ok && range_gap(px.y, at.y, dt.r0, dt.nrows, p.ny, p.dy) <= rc &&
+                 range_gap(px.x, at.x, dt.c0, dt.ncols, p.nx, p.dx) <= rc;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) sm.warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = sm.n_cand[slot], my_off = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kTWarps; ++w) {
+            const int c = sm.warp_cnt[w];
+            if (w < warp) my_off += c;
+            total += c;
+        }
+        const int rank = before + my_off + __popc(bal & lt);
+        if (ok && rank < kDCap) {
+            sm.k0y[slot][rank] = nearest_image(dt.r0 - px.y, p.ny);
+            sm.k0x[slot][rank] = nearest_image(dt.c0 - px.x, p.nx);
+            sm.fx[slot][rank] = at.x;
+            sm.fy[slot][rank] = at.y;
+            sm.z[slot][rank] = at.z;
+            sm.spc[slot][rank] = sp;
+        }
+        if (ok && rank == kDCap) sm.resume[slot] = src;  // first candidate that did not fit
+        __syncthreads();
+        if (threadIdx.x == 0) sm.n_cand[slot] = min(before + total, kDCap);
+        __syncthreads();
+    }
+    __syncthreads();
+    // lateral factors (square cut-off |dx|, |dy| <= 6 s), one warp per candidate
+    const int nc = sm.n_cand[slot];
+    for (int c = warp; c < nc; c += kTWarps) {
+        const float sg = p.sigma[sm.spc[slot][c]];
+        const float c2 = 1.4426950408889634f * (0.5f / (sg * sg));
+        const float rcc = 6.0f * sg;
+        const int k0y = sm.k0y[slot][c], k0x = sm.k0x[slot][c];
+        const float fx = sm.fx[slot][c], fy = sm.fy[slot][c];
+        float gyv = 0.f, g0 = 0.f, g1 = 0.f;
+        int ky = k0y + lane;
+        if (ky >= dt.half_y) ky -= p.ny;
+        int kx0 = k0x + lane;
+        if (kx0 >= dt.half_x) kx0 -= p.nx;
+        int kx1 = k0x + lane + 32;
+        if (kx1 >= dt.half_x) kx1 -= p.nx;
+        const float dy_ = small_int_to_float(ky) * p.dy - fy;
+        const float dx0 = small_int_to_float(kx0) * p.dx - fx;
+        const float dx1 = small_int_to_float(kx1) * p.dx - fx;
+        if (lane < dt.nrows && fabsf(dy_) <= rcc) gyv = exp2f(-(dy_ * dy_) * c2);
+        if (lane < dt.ncols && fabsf(dx0) <= rcc) g0 = exp2f(-(dx0 * dx0) * c2);
+        if (lane + 32 < dt.ncols && fabsf(dx1) <= rcc) g1 = exp2f(-(dx1 * dx1) * c2);
+        sm.gy[slot][c][lane] = gyv;
+        float* gxr = reinterpret_cast<float*>(sm.gx[slot][c]);
+        gxr[lane] = g0;
+        gxr[lane + 32] = g1;
+        const unsigned b0 = __ballot_sync(0xffffffffu, g0 != 0.f);
+        const unsigned b1 = __ballot_sync(0xffffffffu, g1 != 0.f);
+        const int q = lane & 7;
+        const unsigned grp = (q < 4 ? b0 >> (8 * q) : b1 >> (8 * (q - 4))) & 0xffu;
+        const unsigned wm = __ballot_sync(0xffffffffu, lane < 8 && grp != 0u);
+        if (lane == 0) sm.wmask[slot][c] = (int)wm;
+    }
+    __syncthreads();
+}
+
+// amp_sp w_s(z) of every candidate in `slot` for the slice [lo, hi) (0 outside
+// the z cut-off), one thread per candidate.  No barrier.
+__device__ __forceinline__ void depth_weights(DepthSmem& sm, const PotParams& p, int slot, float lo, float hi,
+                                              bool first, bool lastsl, int tid) {
+    if (tid < sm.n_cand[slot]) {
+        const int sp = sm.spc[slot][tid];
+        const float sg = p.sigma[sp], rc = 6.0f * sg, z = sm.z[slot][tid];
+        sm.aw[slot][tid] = ((hi > z - rc) && (lo < z + rc))
+                               ? p.amp[sp] * slice_weight(z, sg, lo, hi, first, lastsl, nullptr) : 0.f;
+    }
+}
+
+// acc += outer products of this warp's candidates in `slot` (no barrier)
+__device__ __forceinline__ void depth_accumulate(DepthSmem& sm, int slot, float (&acc)[8]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nc = sm.n_cand[slot];
+    const bool has = lane < nc && sm.aw[slot][lane] != 0.f && ((sm.wmask[slot][lane] >> warp) & 1);
+    const unsigned b = __ballot_sync(0xffffffffu, has);
+    if (has) sm.wlist[warp][__popc(b & lt)] = (unsigned char)lane;
+    __syncwarp();
+    const int cnt = __popc(b);
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+        const int c = sm.wlist[warp][j];
+        const float gyv = sm.gy[slot][c][lane] * sm.aw[slot][c];
+        const float4 a = sm.gx[slot][c][2 * warp], bq = sm.gx[slot][c][2 * warp + 1];
+        acc[0] = fmaf(gyv, a.x, acc[0]);
+        acc[1] = fmaf(gyv, a.y, acc[1]);
+        acc[2] = fmaf(gyv, a.z, acc[2]);
+        acc[3] = fmaf(gyv, a.w, acc[3]);
+        acc[4] = fmaf(gyv, bq.x, acc[4]);
+        acc[5] = fmaf(gyv, bq.y, acc[5]);
+        acc[6] = fmaf(gyv, bq.z, acc[6]);
+        acc[7] = fmaf(gyv, bq.w, acc[7]);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kPotThreads)
+potential_depth_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                       const int2* __restrict__ binned_px, PotParams p, int n_tx, int vec_out,
+                       float* __restrict__ V) {
+    static_assert(kDCap <= 32, "one weight thread / list lane per cached candidate");
+    extern __shared__ __align__(16) unsigned char depth_smem_raw[];
+    DepthSmem& sm = *reinterpret_cast<DepthSmem*>(depth_smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    DepthTile dt;
+    dt.r0 = (blockIdx.x / n_tx) * kTR;
+    dt.c0 = (blockIdx.x % n_tx) * kTC;
+    dt.nrows = min(kTR, p.ny - dt.r0);
+    dt.ncols = min(kTC, p.nx - dt.c0);
+    dt.half_x = (p.nx + 1) / 2;
+    dt.half_y = (p.ny + 1) / 2;
+    const size_t t = blockIdx.y;
+    const float4* atoms = binned + t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
+    const int* off = bin_off + t * (size_t)(p.n_bins + 1);
+    const int band = dt.r0 / p.band_h, ctile = dt.c0 / p.ctile_w;
+
+    // slab k enters: its bins, then its cached candidates
+    auto enter = [&](int k) {
+        const int slot = k % 3;
+        int nnb;
+        const int ns = load_bins_slabs(sm.bin_start[slot], sm.bin_cum[slot], p, off, k, k, band, ctile, &nnb);
+        if (threadIdx.x == 0) {
+            sm.n_nb[slot] = nnb;
+            sm.n_src[slot] = ns;
+        }
+        __syncthreads();
+        depth_gather(sm, p, dt, atoms, atoms_px, slot, slot, 0);
+    };
+    enter(0);
+    if (p.n_slices > 1) enter(1);
+
+    for (int s = 0; s < p.n_slices; ++s) {
+        if (s > 0 && s + 1 < p.n_slices) enter(s + 1);
+        const bool first = (s == 0), lastsl = (s == p.n_slices - 1);
+        const float lo = first ? -INFINITY : p.z0 + (float)s * p.dz;
+        const float hi = lastsl ? INFINITY : p.z0 + (float)(s + 1) * p.dz;
+        const int k_lo = max(0, s - 1), k_hi = min(p.n_slices - 1, s + 1);
+        // weights of the cached candidates of the three slabs: warp w takes slab k_lo + w
+        if (warp <= k_hi - k_lo) depth_weights(sm, p, (k_lo + warp) % 3, lo, hi, first, lastsl, lane);
+        __syncthreads();
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+        for (int k = k_lo; k <= k_hi; ++k) {
+            const int slot = k % 3;
+            depth_accumulate(sm, slot, acc);
+            // the rest of a crowded slab, chunk by chunk, for this slice only
+            int from = sm.resume[slot];
+            while (from < sm.n_src[slot]) {             // uniform (shared values)
+                __syncthreads();
+                depth_gather(sm, p, dt, atoms, atoms_px, 3, slot, from);
+                if (warp == 0) depth_weights(sm, p, 3, lo, hi, first, lastsl, lane);
+                __syncthreads();
+                depth_accumulate(sm, 3, acc);
+                from = sm.resume[3];
+                __syncthreads();
+            }
+        }
+        if (lane < dt.nrows) {
+            const int cw = 8 * warp;
+            float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + dt.r0 + lane) * p.nx + dt.c0 + cw;
+            if (vec_out && cw + 8 <= dt.ncols) {
+                reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (cw + k < dt.ncols) out[k] = acc[k];
+            }
+        }
+        __syncthreads();                                // slot (s - 1) % 3 is refilled next
     }
 }
 
@@ -759,8 +1036,15 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
     // alike); the slab is assigned in float, so its reach gets a little slack
     p->reach_x = (int)ceil(rc / dx);
     p->reach_y = (int)ceil(rc / dy);
-    p->band_reach = (p->reach_y + 1 + p->band_h - 1) / p->band_h;
-    p->ctile_reach = (p->reach_x + 1 + p->ctile_w - 1) / p->ctile_w;
+    p->nb_max = p->nc_max = 0;
+    for (int b = 0; b < p->n_bands; ++b) {
+        const int c = axis_range(b, p->band_h, g.ny, p->n_bands, p->reach_y + 1).count;
+        p->nb_max = c > p->nb_max ? c : p->nb_max;
+    }
+    for (int b = 0; b < p->n_ctiles; ++b) {
+        const int c = axis_range(b, p->ctile_w, g.nx, p->n_ctiles, p->reach_x + 1).count;
+        p->nc_max = c > p->nc_max ? c : p->nc_max;
+    }
     p->slab_reach = (int)ceil((rc + 1e-4 * g.dz) / g.dz);
     p->lx = (float)g.lx;
     p->ly = (float)g.ly;
@@ -774,9 +1058,7 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
     p->z0 = (float)g.z0;
     p->dz = (float)g.dz;
     p->inv_dz = (float)(1.0 / g.dz);
-    const int nb = (2 * p->band_reach + 1 >= p->n_bands) ? p->n_bands : 2 * p->band_reach + 1;
-    const int nc = (2 * p->ctile_reach + 1 >= p->n_ctiles) ? p->n_ctiles : 2 * p->ctile_reach + 1;
-    const int n_nb = nb * nc * (min(g.n_slices - 1, 2 * p->slab_reach) + 1);
+    const int n_nb = p->nb_max * p->nc_max * (min(g.n_slices - 1, 2 * p->slab_reach) + 1);
     TACAW_REQUIRE(n_nb <= kMaxNbBins, TACAW_EUNSUPPORTED,
                   "tacaw_potential: %d neighbouring bins per tile exceed %d (widths too large for "
                   "the slice thickness or pixel size)", n_nb, kMaxNbBins);
@@ -833,6 +1115,15 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
     if (rc != TACAW_OK) return rc;
     const int n_tx = (g.nx + kTC - 1) / kTC, n_ty = (g.ny + kTR - 1) / kTR;
     const int vec_out = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
+    if (p.slab_reach <= 1 && p.nb_max * p.nc_max <= kDBins) {
+        // atoms reach at most the neighbouring slices: walk the depth once per tile
+        const int dsm = (int)sizeof(DepthSmem);
+        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_depth_kernel, dsm));
+        potential_depth_kernel<<<dim3(n_tx * n_ty, n_t), kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px,
+                                                                               p, n_tx, vec_out, V);
+        TACAW_LAUNCH_CHECK();
+        return TACAW_OK;
+    }
     const int smem = (int)sizeof(TileSmem);
     TACAW_CUDA_CHECK(ensure_smem((const void*)potential_tile_kernel, smem));
     potential_tile_kernel<<<dim3(n_tx * n_ty, g.n_slices, n_t), kPotThreads, smem, st>>>(

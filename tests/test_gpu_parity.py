@@ -98,6 +98,24 @@ def test_potential_edge_cases(api):
     assert np.max(np.abs(v - ref)) <= 2e-6 * ref.max()
 
 
+@pytest.mark.parametrize("dz", [2.5, 2.0])     # 6 s = 2.46 A: neighbouring slices only / two either side
+def test_potential_reach_across_a_short_last_tile(api, dz):
+    # 200 x 136 pixels: the last column tile is 8 wide and the last band 8 high, so
+    # atoms in column / row 0 reach pixels two tiles over through the periodic wrap
+    g = _grid(200, 136, 40.0, 27.0, 3, dz, z0=0.5)
+    rng = np.random.default_rng(31)
+    n = 120
+    x, y, z = rng.uniform(0.0, 40.0, n), rng.uniform(0.0, 27.0, n), rng.uniform(0.5, 0.5 + 3 * dz, n)
+    x[:n // 2] = rng.uniform(0.0, 40.0 / 200, n // 2)              # column 0
+    y[n // 2:] = rng.uniform(0.0, 27.0 / 136, n - n // 2)          # row 0
+    pos = np.stack([x, y, z], axis=1).astype(np.float32)
+    species = np.zeros(n, np.int32)
+    amp_sigma = [[27.0, 0.41]]
+    v = api.potential(g, _dev(pos[None]), _dev(species), amp_sigma).cpu().numpy()[0]
+    ref = O.projected_potential(g, pos.astype(np.float64), species, np.asarray(amp_sigma, np.float64))
+    assert np.max(np.abs(v - ref)) <= 2e-6 * np.max(np.abs(ref)) + 1e-6
+
+
 # ---------------------------------------------------------------- multislice
 def _smooth_potential(g, n_t, seed):
     rng = np.random.default_rng(seed)
