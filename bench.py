@@ -48,6 +48,8 @@ def parse_args():
                    help="temporal transform: FP32 FFT over time (natural grid), split-BF16 tcgen05 GEMM, "
                         "or FP32 SIMT GEMM")
     p.add_argument("--snapshots", type=int, default=0, help="override T (testing only)")
+    p.add_argument("--slices", type=int, default=0,
+                   help="override the slice count, with as many cells along z as fill it (profiling only)")
     p.add_argument("--cpu-snapshots", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -72,6 +74,13 @@ def workload(args):
     w = W.WORKLOADS[args.workload]
     if args.snapshots:
         w = w.with_(n_t=args.snapshots)
+    if args.slices:
+        import dataclasses
+        import math
+        g = w.grid
+        nz = max(1, math.ceil(args.slices * g.dz / w.a))
+        w = w.with_(grid=dataclasses.replace(g, n_slices=args.slices), ncell=(w.ncell[0], w.ncell[1], nz),
+                    n_lo=(w.n_lo[0], w.n_lo[1], -(nz // 2)), n_hi=(w.n_hi[0], w.n_hi[1], max(1, nz // 2)))
     return w
 
 
