@@ -20,9 +20,9 @@
 //     V_tile = sum_a gy_a (x) gx_a, accumulated in FP32 registers over the
 //     candidate atoms in bin order (a fixed order: identical configurations give
 //     bit-identical potentials).
-//     When 6 s <= dz for every species, potential_depth_kernel takes its place:
-//     one block per tile and snapshot walks the slices and tabulates each slab's
-//     lateral factors once for the three slices they reach.
+//     When 6 s <= dz for every species, potential_slab_kernel takes its place:
+//     one block per tile and snapshot walks the slabs, tabulating each slab's
+//     candidates once and accumulating them into the three slices they reach.
 // The adjoint (potential_backward_kernel) keeps one block per band of 8 rows.
 
 #include <math.h>
@@ -50,6 +50,8 @@ struct PotParams {
     float lx, ly, dx, dy, inv_dx, z0, dz, inv_dz;
     double dx_d, dy_d, inv_dx_d, inv_dy_d;
     float amp[TACAW_MAX_SPECIES], sigma[TACAW_MAX_SPECIES];
+    // per species: log2(e) / (2 s^2), 6 s and 1 / (sqrt2 s), rounded once on the host
+    float c2[TACAW_MAX_SPECIES], rc[TACAW_MAX_SPECIES], kz[TACAW_MAX_SPECIES];
 };
 
 // An atom's position is split once, in FP64, into the pixel (ic, jc) that
@@ -493,247 +495,307 @@ potential_tile_kernel(const int* __restrict__ bin_off, const float4* __restrict_
     }
 }
 
-// ------------------------------------------------------------------ forward, depth walk
-// One block per (tile, snapshot) walks the slices in order.  The lateral
-// factors of an atom do not depend on the slice, and an atom of slab k reaches
-// only slices k-1 .. k+1 when 6 s <= dz (slab_reach 1), so each slab's
-// candidates are selected and tabulated once, when the slab enters the window,
-// into one of three slots (slab k -> slot k mod 3) and reused by the three
-// slices; per slice only the weights amp w_s(z) and the outer products are
-// new.  A slot holds kDCap candidates; the rest of a crowded slab ("overflow")
-// is re-selected and tabulated in chunks for every slice, so any input is
-// handled.  Order of the sums: slab s-1, s, s+1, each in source order (cached
-// candidates, then overflow chunks): fixed by the configuration.
-constexpr int kDCap = 24;                 // cached candidates per slab slot
-constexpr int kDSlots = 4;                // three slabs + one overflow scratch slot
-constexpr int kDBins = 24;                // bins per slab neighbourhood (<= 3 x 3 here)
+// ------------------------------------------------------------------ forward, slab walk
+// One block per (tile, snapshot) walks the slabs in order.  When 6 s <= dz an
+// atom of slab k reaches only slices k-1, k and k+1, so each candidate of slab
+// k is selected, tabulated and accumulated once, into three running slices
+// held in registers (acc_m, acc_c, acc_p for slices k-1, k, k+1); slice k-1
+// is complete after slab k and is written then.  The weights amp w_s(z) of
+// the three slices come from the erf at the four slice boundaries around the
+// slab.  Per slice the sum runs over slabs s-1, s, s+1, each in source order,
+// as in the tile kernel: fixed by the configuration.
+// Global-memory latency is taken off the slab-to-slab path: the tile's bin
+// ranges of up to kTabInts / (2 n_nb + 1) slabs are loaded at once into a
+// table, and while slab k is tabulated and accumulated the atom records of
+// slab k+1 (its first kPotThreads sources) are copied into shared memory with
+// cp.async.
+constexpr int kSCand = 32;                // candidates tabulated at a time
+constexpr int kSBins = 32;                // bins per slab neighbourhood (one warp scans them)
+constexpr int kTabInts = 4096;            // bin table: per slab n_nb starts, n_nb + 1 running counts
 
-struct DepthSmem {
-    float gy[kDSlots][kDCap][kTR];
-    float4 gx[kDSlots][kDCap][kTC / 4];
-    int k0y[kDSlots][kDCap], k0x[kDSlots][kDCap], wmask[kDSlots][kDCap], spc[kDSlots][kDCap];
-    float fx[kDSlots][kDCap], fy[kDSlots][kDCap], z[kDSlots][kDCap], aw[kDSlots][kDCap];
-    int n_cand[kDSlots], resume[kDSlots];      // candidates held; source index where the slab continues
-    int bin_start[kDSlots][kDBins], bin_cum[kDSlots][kDBins + 1], n_nb[kDSlots], n_src[kDSlots];
+struct SlabSmem {
+    float gy[kSCand][kTR];
+    float4 gx[kSCand][kTC / 4];
+    float4 w[kSCand];                     // amp w_{k-1}, amp w_k, amp w_{k+1}, 0
+    float4 st_at[2][kPotThreads];         // staged atom records of the next slab, by source index
+    int2 st_px[2][kPotThreads];
+    int wmask[kSCand];
+    // candidates of one pass over the sources (see TileSmem)
+    int k0y[kPotThreads], k0x[kPotThreads], spc[kPotThreads];
+    float fx[kPotThreads], fy[kPotThreads], z[kPotThreads];
+    int tab[kTabInts];
     int warp_cnt[kTWarps];
-    unsigned char wlist[kTWarps][kDCap];
+    unsigned char wlist[kTWarps][kSCand];
 };
 
-struct DepthTile {
-    int r0, c0, nrows, ncols, half_x, half_y;
-};
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Candidates of slab `slab` from source index `from` on: accept (valid species,
-// window reaches the tile), keep the first kDCap in `slot`, record where the
-// slab continues (its n_src when all fitted), then tabulate their lateral
-// factors and warp masks.  Uniform over the block; ends with a barrier.
-__device__ void depth_gather(DepthSmem& sm, const PotParams& p, const DepthTile& dt, const float4* __restrict__ atoms,
-                             const int2* __restrict__ atoms_px, int slot, int bslot, int from) {
+// Bin table of slabs [k0, k0 + n_k): for slab k0 + j at tab + j (2 n_nb + 1):
+// n_nb bin starts, then the n_nb + 1 running counts (the last = the slab's
+// sources).  All threads load, one warp per slab scans; ends with a barrier.
+__device__ void load_bin_table(int* tab, const PotParams& p, const int* __restrict__ off, int k0, int n_k,
+                               AxisRange rb, AxisRange rx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int n_src = sm.n_src[bslot];
-    if (threadIdx.x == 0) {
-        sm.n_cand[slot] = 0;
-        sm.resume[slot] = n_src;
+    const int nc = rx.count, n_nb = rb.count * rx.count, stride = 2 * n_nb + 1;
+    for (int e = threadIdx.x; e < n_k * n_nb; e += kPotThreads) {
+        const int j = e / n_nb, i = e - j * n_nb;
+        const int kb = i / nc, kc = i - kb * nc;
+        const int b = (rb.first + kb) % p.n_bands, c = (rx.first + kc) % p.n_ctiles;
+        const int bin = ((k0 + j) * p.n_bands + b) * p.n_ctiles + c;
+        const int s0 = __ldg(off + bin);
+        tab[j * stride + i] = s0;
+        tab[j * stride + n_nb + i] = __ldg(off + bin + 1) - s0;
     }
     __syncthreads();
-    for (int sb = from; sb < n_src; sb += kPotThreads) {
-        if (sm.n_cand[slot] >= kDCap) {             // uniform: read after a barrier
-            // full exactly at the end of the previous pass: continue at this one
-            if (threadIdx.x == 0 && sm.resume[slot] == n_src) sm.resume[slot] = sb;
-            break;
-        }
-        const int src = sb + (int)threadIdx.x;
-        bool ok = false;
-        float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
-        int2 px = make_int2(0, 0);
-        int sp = 0;
-        if (src < n_src) {
-            const int ai = source_atom(sm.bin_start[bslot], sm.bin_cum[bslot], sm.n_nb[bslot], src);
-            at = atoms[ai];
-            px = atoms_px[ai];
-            sp = __float_as_int(at.w);
-            ok = sp >= 0 && sp < p.n_species;
-            const float rc = 6.0f * (ok ? p.sigma[sp] : 1.f);
-            ok = ok && range_gap(px.y, at.y, dt.r0, dt.nrows, p.ny, p.dy) <= rc &&
-                 range_gap(px.x, at.x, dt.c0, dt.ncols, p.nx, p.dx) <= rc;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (lane == 0) sm.warp_cnt[warp] = __popc(bal);
-        __syncthreads();
-        int before = sm.n_cand[slot], my_off = 0, total = 0;
+    for (int j = warp; j < n_k; j += kTWarps) {
+        int* cum = tab + j * stride + n_nb;
+        const int cnt = lane < n_nb ? cum[lane] : 0;
+        int incl = cnt;
 #pragma unroll
-        for (int w = 0; w < kTWarps; ++w) {
-            const int c = sm.warp_cnt[w];
-            if (w < warp) my_off += c;
-            total += c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        const int rank = before + my_off + __popc(bal & lt);
-        if (ok && rank < kDCap) {
-            sm.k0y[slot][rank] = nearest_image(dt.r0 - px.y, p.ny);
-            sm.k0x[slot][rank] = nearest_image(dt.c0 - px.x, p.nx);
-            sm.fx[slot][rank] = at.x;
-            sm.fy[slot][rank] = at.y;
-            sm.z[slot][rank] = at.z;
-            sm.spc[slot][rank] = sp;
-        }
-        if (ok && rank == kDCap) sm.resume[slot] = src;  // first candidate that did not fit
-        __syncthreads();
-        if (threadIdx.x == 0) sm.n_cand[slot] = min(before + total, kDCap);
-        __syncthreads();
-    }
-    __syncthreads();
-    // lateral factors (square cut-off |dx|, |dy| <= 6 s), one warp per candidate
-    const int nc = sm.n_cand[slot];
-    for (int c = warp; c < nc; c += kTWarps) {
-        const float sg = p.sigma[sm.spc[slot][c]];
-        const float c2 = 1.4426950408889634f * (0.5f / (sg * sg));
-        const float rcc = 6.0f * sg;
-        const int k0y = sm.k0y[slot][c], k0x = sm.k0x[slot][c];
-        const float fx = sm.fx[slot][c], fy = sm.fy[slot][c];
-        float gyv = 0.f, g0 = 0.f, g1 = 0.f;
-        int ky = k0y + lane;
-        if (ky >= dt.half_y) ky -= p.ny;
-        int kx0 = k0x + lane;
-        if (kx0 >= dt.half_x) kx0 -= p.nx;
-        int kx1 = k0x + lane + 32;
-        if (kx1 >= dt.half_x) kx1 -= p.nx;
-        const float dy_ = small_int_to_float(ky) * p.dy - fy;
-        const float dx0 = small_int_to_float(kx0) * p.dx - fx;
-        const float dx1 = small_int_to_float(kx1) * p.dx - fx;
-        if (lane < dt.nrows && fabsf(dy_) <= rcc) gyv = exp2f(-(dy_ * dy_) * c2);
-        if (lane < dt.ncols && fabsf(dx0) <= rcc) g0 = exp2f(-(dx0 * dx0) * c2);
-        if (lane + 32 < dt.ncols && fabsf(dx1) <= rcc) g1 = exp2f(-(dx1 * dx1) * c2);
-        sm.gy[slot][c][lane] = gyv;
-        float* gxr = reinterpret_cast<float*>(sm.gx[slot][c]);
-        gxr[lane] = g0;
-        gxr[lane + 32] = g1;
-        const unsigned b0 = __ballot_sync(0xffffffffu, g0 != 0.f);
-        const unsigned b1 = __ballot_sync(0xffffffffu, g1 != 0.f);
-        const int q = lane & 7;
-        const unsigned grp = (q < 4 ? b0 >> (8 * q) : b1 >> (8 * (q - 4))) & 0xffu;
-        const unsigned wm = __ballot_sync(0xffffffffu, lane < 8 && grp != 0u);
-        if (lane == 0) sm.wmask[slot][c] = (int)wm;
+        if (lane < n_nb) cum[lane] = incl - cnt;
+        if (lane == 31) cum[n_nb] = incl;
     }
     __syncthreads();
 }
 
-// amp_sp w_s(z) of every candidate in `slot` for the slice [lo, hi) (0 outside
-// the z cut-off), one thread per candidate.  No barrier.
-__device__ __forceinline__ void depth_weights(DepthSmem& sm, const PotParams& p, int slot, float lo, float hi,
-                                              bool first, bool lastsl, int tid) {
-    if (tid < sm.n_cand[slot]) {
-        const int sp = sm.spc[slot][tid];
-        const float sg = p.sigma[sp], rc = 6.0f * sg, z = sm.z[slot][tid];
-        sm.aw[slot][tid] = ((hi > z - rc) && (lo < z + rc))
-                               ? p.amp[sp] * slice_weight(z, sg, lo, hi, first, lastsl, nullptr) : 0.f;
+// Height of slice boundary j: the first slice is open below, the last above.
+__device__ __forceinline__ float slice_boundary(const PotParams& p, int j) {
+    return j <= 0 ? -INFINITY : (j >= p.n_slices ? INFINITY : p.z0 + (float)j * p.dz);
+}
+
+__device__ __forceinline__ void store_tile_row(const PotParams& p, float* __restrict__ V, size_t t, int s, int r0,
+                                               int c0, int nrows, int ncols, int vec_out, const float (&acc)[8]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < nrows) {
+        const int cw = 8 * warp;
+        float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + r0 + lane) * p.nx + c0 + cw;
+        if (vec_out && cw + 8 <= ncols) {
+            reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (cw + k < ncols) out[k] = acc[k];
+        }
     }
 }
 
-// acc += outer products of this warp's candidates in `slot` (no barrier)
-__device__ __forceinline__ void depth_accumulate(DepthSmem& sm, int slot, float (&acc)[8]) {
+__global__ void __launch_bounds__(kPotThreads, 4)
+potential_slab_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                      const int2* __restrict__ binned_px, PotParams p, int n_tx, int vec_out,
+                      float* __restrict__ V) {
+    static_assert(kSCand == 32 && kSBins <= 32, "one list lane per tabulated candidate, one scan lane per bin");
+    extern __shared__ __align__(16) unsigned char slab_smem_raw[];
+    SlabSmem& sm = *reinterpret_cast<SlabSmem*>(slab_smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const int nc = sm.n_cand[slot];
-    const bool has = lane < nc && sm.aw[slot][lane] != 0.f && ((sm.wmask[slot][lane] >> warp) & 1);
-    const unsigned b = __ballot_sync(0xffffffffu, has);
-    if (has) sm.wlist[warp][__popc(b & lt)] = (unsigned char)lane;
-    __syncwarp();
-    const int cnt = __popc(b);
-#pragma unroll 2
-    for (int j = 0; j < cnt; ++j) {
-        const int c = sm.wlist[warp][j];
-        const float gyv = sm.gy[slot][c][lane] * sm.aw[slot][c];
-        const float4 a = sm.gx[slot][c][2 * warp], bq = sm.gx[slot][c][2 * warp + 1];
-        acc[0] = fmaf(gyv, a.x, acc[0]);
-        acc[1] = fmaf(gyv, a.y, acc[1]);
-        acc[2] = fmaf(gyv, a.z, acc[2]);
-        acc[3] = fmaf(gyv, a.w, acc[3]);
-        acc[4] = fmaf(gyv, bq.x, acc[4]);
-        acc[5] = fmaf(gyv, bq.y, acc[5]);
-        acc[6] = fmaf(gyv, bq.z, acc[6]);
-        acc[7] = fmaf(gyv, bq.w, acc[7]);
-    }
-    __syncwarp();
-}
-
-__global__ void __launch_bounds__(kPotThreads)
-potential_depth_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
-                       const int2* __restrict__ binned_px, PotParams p, int n_tx, int vec_out,
-                       float* __restrict__ V) {
-    static_assert(kDCap <= 32, "one weight thread / list lane per cached candidate");
-    extern __shared__ __align__(16) unsigned char depth_smem_raw[];
-    DepthSmem& sm = *reinterpret_cast<DepthSmem*>(depth_smem_raw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    DepthTile dt;
-    dt.r0 = (blockIdx.x / n_tx) * kTR;
-    dt.c0 = (blockIdx.x % n_tx) * kTC;
-    dt.nrows = min(kTR, p.ny - dt.r0);
-    dt.ncols = min(kTC, p.nx - dt.c0);
-    dt.half_x = (p.nx + 1) / 2;
-    dt.half_y = (p.ny + 1) / 2;
+    const int r0 = (blockIdx.x / n_tx) * kTR, c0 = (blockIdx.x % n_tx) * kTC;
+    const int nrows = min(kTR, p.ny - r0), ncols = min(kTC, p.nx - c0);
+    const int half_x = (p.nx + 1) / 2, half_y = (p.ny + 1) / 2;
     const size_t t = blockIdx.y;
     const float4* atoms = binned + t * (size_t)p.n_atoms;
     const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
     const int* off = bin_off + t * (size_t)(p.n_bins + 1);
-    const int band = dt.r0 / p.band_h, ctile = dt.c0 / p.ctile_w;
+    const AxisRange rb = axis_range(r0 / p.band_h, p.band_h, p.ny, p.n_bands, p.reach_y + 1);
+    const AxisRange rx = axis_range(c0 / p.ctile_w, p.ctile_w, p.nx, p.n_ctiles, p.reach_x + 1);
+    const int n_nb = rb.count * rx.count, stride = 2 * n_nb + 1;
+    const int chunk = kTabInts / stride;         // slabs per table load (>= 49 with n_nb <= 32)
 
-    // slab k enters: its bins, then its cached candidates
-    auto enter = [&](int k) {
-        const int slot = k % 3;
-        int nnb;
-        const int ns = load_bins_slabs(sm.bin_start[slot], sm.bin_cum[slot], p, off, k, k, band, ctile, &nnb);
-        if (threadIdx.x == 0) {
-            sm.n_nb[slot] = nnb;
-            sm.n_src[slot] = ns;
-        }
-        __syncthreads();
-        depth_gather(sm, p, dt, atoms, atoms_px, slot, slot, 0);
-    };
-    enter(0);
-    if (p.n_slices > 1) enter(1);
-
-    for (int s = 0; s < p.n_slices; ++s) {
-        if (s > 0 && s + 1 < p.n_slices) enter(s + 1);
-        const bool first = (s == 0), lastsl = (s == p.n_slices - 1);
-        const float lo = first ? -INFINITY : p.z0 + (float)s * p.dz;
-        const float hi = lastsl ? INFINITY : p.z0 + (float)(s + 1) * p.dz;
-        const int k_lo = max(0, s - 1), k_hi = min(p.n_slices - 1, s + 1);
-        // weights of the cached candidates of the three slabs: warp w takes slab k_lo + w
-        if (warp <= k_hi - k_lo) depth_weights(sm, p, (k_lo + warp) % 3, lo, hi, first, lastsl, lane);
-        __syncthreads();
-        float acc[8];
+    float acc_m[8], acc_c[8], acc_p[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-        for (int k = k_lo; k <= k_hi; ++k) {
-            const int slot = k % 3;
-            depth_accumulate(sm, slot, acc);
-            // the rest of a crowded slab, chunk by chunk, for this slice only
-            int from = sm.resume[slot];
-            while (from < sm.n_src[slot]) {             // uniform (shared values)
+    for (int i = 0; i < 8; ++i) acc_m[i] = acc_c[i] = acc_p[i] = 0.f;
+
+    int k0 = 0, n_staged = 0;                    // first slab of the table; sources staged for slab k
+    for (int k = 0; k < p.n_slices; ++k) {
+        if (k == 0 || k == k0 + chunk) {
+            if (k > 0) k0 = k;
+            load_bin_table(sm.tab, p, off, k0, min(chunk, p.n_slices - k0), rb, rx);
+            n_staged = 0;                        // the first slab of a table is read directly
+        }
+        const int* bstart = sm.tab + (k - k0) * stride;
+        const int* bcum = bstart + n_nb;
+        const int n_src = bcum[n_nb];
+        const int buf = k & 1;
+        const float bm = slice_boundary(p, k - 1), b0 = slice_boundary(p, k), b1 = slice_boundary(p, k + 1),
+                    b2 = slice_boundary(p, k + 2);
+        const bool has_m = k >= 1, has_p = k + 1 < p.n_slices;
+
+        for (int sb = 0; sb < n_src; sb += kPotThreads) {
+            // 1. candidates among the sources [sb, sb + kPotThreads), in source order
+            const int src = sb + (int)threadIdx.x;
+            bool ok = false;
+            float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
+            int2 px = make_int2(0, 0);
+            int sp = 0;
+            if (src < n_src) {
+                if (src < n_staged) {
+                    at = sm.st_at[buf][src];
+                    px = sm.st_px[buf][src];
+                } else {
+                    const int ai = source_atom(bstart, bcum, n_nb, src);
+                    at = atoms[ai];                      // (fx, fy, z, species)
+                    px = atoms_px[ai];                   // (ic, jc), wrapped
+                }
+                sp = __float_as_int(at.w);
+                ok = sp >= 0 && sp < p.n_species;
+                const float rc = 6.0f * (ok ? p.sigma[sp] : 1.f);
+                ok = ok && range_gap(px.y, at.y, r0, nrows, p.ny, p.dy) <= rc &&
+                     range_gap(px.x, at.x, c0, ncols, p.nx, p.dx) <= rc;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) sm.warp_cnt[warp] = __popc(bal);
+            __syncthreads();
+            int n_cand = 0, my_off = 0;
+#pragma unroll
+            for (int w = 0; w < kTWarps; ++w) {
+                const int c = sm.warp_cnt[w];
+                if (w < warp) my_off += c;
+                n_cand += c;
+            }
+            if (ok) {
+                const int c = my_off + __popc(bal & lt);
+                sm.k0y[c] = nearest_image(r0 - px.y, p.ny);
+                sm.k0x[c] = nearest_image(c0 - px.x, p.nx);
+                sm.fx[c] = at.x;
+                sm.fy[c] = at.y;
+                sm.z[c] = at.z;
+                sm.spc[c] = sp;
+            }
+            if (sb == 0 && k + 1 < p.n_slices && k + 1 < k0 + chunk) {
+                // stage the next slab's first sources while this one is worked on
+                // (the other buffer was last read before this slab's first barrier)
+                const int* nstart = bstart + stride;
+                const int n1 = nstart[2 * n_nb];
+                if ((int)threadIdx.x < n1) {
+                    const int ai = source_atom(nstart, nstart + n_nb, n_nb, threadIdx.x);
+                    cp_async_16(&sm.st_at[buf ^ 1][threadIdx.x], atoms + ai);
+                    cp_async_8(&sm.st_px[buf ^ 1][threadIdx.x], atoms_px + ai);
+                }
+                cp_async_commit();
+            }
+            __syncthreads();
+
+            for (int cb = 0; cb < n_cand; cb += kSCand) {
+                const int nc = min(kSCand, n_cand - cb);
+                // 2. factors, in tasks of 8 values: task (c, g) for g < 4 tabulates rows
+                //    8g .. 8g + 7 of gy and erf/2 at slice boundary k - 1 + g; task (c, g)
+                //    for g < 8 of the column tasks tabulates columns 8g .. 8g + 7 of gx (the
+                //    columns of warp g).  Square cut-off |dx|, |dy| <= 6 s; rows and columns
+                //    outside the tile are 0.  Row tasks of a candidate are 4 aligned lanes,
+                //    column tasks 8 aligned lanes (column tasks start at a multiple of 8).
+                const int n_rt = 4 * nc, col0 = (n_rt + 7) & ~7, n_task = col0 + 8 * nc;
+                for (int ib = 0; ib < n_task; ib += kPotThreads) {
+                    const int i = ib + (int)threadIdx.x;
+                    const bool row_task = i < n_rt, col_task = i >= col0 && i < n_task;
+                    const int c = row_task ? (i >> 2) : (col_task ? (i - col0) >> 3 : 0);
+                    const int g = row_task ? (i & 3) : (i & 7);
+                    const int cc = cb + c;
+                    const int csp = sm.spc[cc];
+                    const float c2 = p.c2[csp], rcc = p.rc[csp];
+                    bool nz = false;
+                    if (row_task || col_task) {
+                        // rows: offsets k0y + r from the atom's pixel, limit nrows; columns alike
+                        const int k0 = row_task ? sm.k0y[cc] : sm.k0x[cc];
+                        const float f = row_task ? sm.fy[cc] : sm.fx[cc];
+                        const int n = row_task ? p.ny : p.nx, half = row_task ? half_y : half_x;
+                        const int lim = row_task ? nrows : ncols;
+                        const float dd = row_task ? p.dy : p.dx;
+                        float4* dst = row_task ? reinterpret_cast<float4*>(&sm.gy[c][8 * g]) : &sm.gx[c][2 * g];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float v[4];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const int o = 8 * g + 4 * h + r;
+                                int kk = k0 + o;
+                                if (kk >= half) kk -= n;
+                                const float d = small_int_to_float(kk) * dd - f;
+                                v[r] = (o < lim && fabsf(d) <= rcc) ? exp2f(-(d * d) * c2) : 0.f;
+                                nz = nz || v[r] != 0.f;
+                            }
+                            dst[h] = make_float4(v[0], v[1], v[2], v[3]);
+                        }
+                    }
+                    // erf(.)/2 at boundary k - 1 + g (open ends -1/2, +1/2), gathered per row group
+                    const float bj = slice_boundary(p, k - 1 + g);
+                    const float zc = sm.z[cc];
+                    const float e = bj == -INFINITY ? -0.5f
+                                                    : (bj == INFINITY ? 0.5f : 0.5f * erff((bj - zc) * p.kz[csp]));
+                    const int l4 = lane & ~3;
+                    const float e0 = __shfl_sync(0xffffffffu, e, l4), e1 = __shfl_sync(0xffffffffu, e, l4 + 1);
+                    const float e2 = __shfl_sync(0xffffffffu, e, l4 + 2), e3 = __shfl_sync(0xffffffffu, e, l4 + 3);
+                    const unsigned nzb = __ballot_sync(0xffffffffu, col_task && nz);
+                    if (row_task && g == 0) {
+                        const float amp = p.amp[csp];
+                        const float lo_z = zc - rcc, hi_z = zc + rcc;
+                        const float wm_ = (has_m && b0 > lo_z && bm < hi_z) ? amp * (e1 - e0) : 0.f;
+                        const float wc_ = (b1 > lo_z && b0 < hi_z) ? amp * (e2 - e1) : 0.f;
+                        const float wp_ = (has_p && b2 > lo_z && b1 < hi_z) ? amp * (e3 - e2) : 0.f;
+                        sm.w[c] = make_float4(wm_, wc_, wp_, 0.f);
+                    }
+                    if (col_task && g == 0) sm.wmask[c] = (int)((nzb >> (lane & 24)) & 0xffu);
+                }
                 __syncthreads();
-                depth_gather(sm, p, dt, atoms, atoms_px, 3, slot, from);
-                if (warp == 0) depth_weights(sm, p, 3, lo, hi, first, lastsl, lane);
-                __syncthreads();
-                depth_accumulate(sm, 3, acc);
-                from = sm.resume[3];
-                __syncthreads();
+
+                // 3. this warp's candidates, in order, then the outer-product updates of
+                //    the three running slices
+                bool has = lane < nc && ((sm.wmask[lane] >> warp) & 1);
+                if (has) {
+                    const float4 wv = sm.w[lane];
+                    has = wv.x != 0.f || wv.y != 0.f || wv.z != 0.f;
+                }
+                const unsigned hb = __ballot_sync(0xffffffffu, has);
+                if (has) sm.wlist[warp][__popc(hb & lt)] = (unsigned char)lane;
+                __syncwarp();
+                const int cnt = __popc(hb);
+                for (int j = 0; j < cnt; ++j) {
+                    const int c = sm.wlist[warp][j];
+                    const float gyv = sm.gy[c][lane];
+                    const float4 wv = sm.w[c];
+                    const float ym = gyv * wv.x, yc = gyv * wv.y, yp = gyv * wv.z;
+                    const float4 a = sm.gx[c][2 * warp], b = sm.gx[c][2 * warp + 1];
+                    const float g[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        acc_m[i] = fmaf(ym, g[i], acc_m[i]);
+                        acc_c[i] = fmaf(yc, g[i], acc_c[i]);
+                        acc_p[i] = fmaf(yp, g[i], acc_p[i]);
+                    }
+                }
+                __syncthreads();                         // the next chunk rewrites the table
             }
         }
-        if (lane < dt.nrows) {
-            const int cw = 8 * warp;
-            float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + dt.r0 + lane) * p.nx + dt.c0 + cw;
-            if (vec_out && cw + 8 <= dt.ncols) {
-                reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-            } else {
+        // slice k-1 has all its slabs (k-2 .. k): write it, then move the window up
+        if (has_m) store_tile_row(p, V, t, k - 1, r0, c0, nrows, ncols, vec_out, acc_m);
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (cw + k < dt.ncols) out[k] = acc[k];
-            }
+        for (int i = 0; i < 8; ++i) {
+            acc_m[i] = acc_c[i];
+            acc_c[i] = acc_p[i];
+            acc_p[i] = 0.f;
         }
-        __syncthreads();                                // slot (s - 1) % 3 is refilled next
+        const bool staged_next = n_src > 0 && k + 1 < p.n_slices && k + 1 < k0 + chunk;
+        if (staged_next) {
+            cp_async_wait_all();
+            n_staged = min(bcum[n_nb + stride], kPotThreads);
+        } else {
+            n_staged = 0;
+        }
+        __syncthreads();                                 // staged records visible; candidates reusable
     }
+    store_tile_row(p, V, t, p.n_slices - 1, r0, c0, nrows, ncols, vec_out, acc_m);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1011,9 +1073,13 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
                       (double)kMaxAmp);
         p->amp[i] = amp_sigma[2 * i];
         p->sigma[i] = amp_sigma[2 * i + 1];
+        const float sg = p->sigma[i];
+        p->c2[i] = 1.4426950408889634f * (0.5f / (sg * sg));
+        p->rc[i] = 6.0f * sg;
+        p->kz[i] = 0.70710678118654752f / sg;
         smax = fmaxf(smax, amp_sigma[2 * i + 1]);
     }
-    for (int i = n_species; i < TACAW_MAX_SPECIES; ++i) p->amp[i] = p->sigma[i] = 0.f;
+    for (int i = n_species; i < TACAW_MAX_SPECIES; ++i) p->amp[i] = p->sigma[i] = p->c2[i] = p->rc[i] = p->kz[i] = 0.f;
     const double rc = 6.0 * smax;
     TACAW_REQUIRE(2.0 * rc < g.lx && 2.0 * rc < g.ly, TACAW_EINVAL,
                   "tacaw_potential: cut-off 6 sigma = %g A must be below half the box", rc);
@@ -1115,12 +1181,12 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
     if (rc != TACAW_OK) return rc;
     const int n_tx = (g.nx + kTC - 1) / kTC, n_ty = (g.ny + kTR - 1) / kTR;
     const int vec_out = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
-    if (p.slab_reach <= 1 && p.nb_max * p.nc_max <= kDBins) {
-        // atoms reach at most the neighbouring slices: walk the depth once per tile
-        const int dsm = (int)sizeof(DepthSmem);
-        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_depth_kernel, dsm));
-        potential_depth_kernel<<<dim3(n_tx * n_ty, n_t), kPotThreads, dsm, st>>>(w.bin_off, w.binned, w.binned_px,
-                                                                               p, n_tx, vec_out, V);
+    if (p.slab_reach <= 1 && p.nb_max * p.nc_max <= kSBins) {
+        // atoms reach at most the neighbouring slices: walk the slabs once per tile
+        const int ssm = (int)sizeof(SlabSmem);
+        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_slab_kernel, ssm));
+        potential_slab_kernel<<<dim3(n_tx * n_ty, n_t), kPotThreads, ssm, st>>>(w.bin_off, w.binned, w.binned_px,
+                                                                              p, n_tx, vec_out, V);
         TACAW_LAUNCH_CHECK();
         return TACAW_OK;
     }

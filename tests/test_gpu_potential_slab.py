@@ -1,10 +1,11 @@
-"""GPU parity of the depth-walking slice-potential builder (used when every
-atom's z cut-off 6 s stays within one slice thickness, so an atom reaches at
-most the neighbouring slices) against the FP64 oracle: ragged grids, one and
-two slices, atoms beyond both ends of the stack and across the periodic
-edges, several species, and crowded slabs that overflow the per-slab cache.
-Bound as for the other potential tests: 2e-6 of the peak; identical
-configurations give bit-identical potentials."""
+"""GPU parity of the slab-walking slice-potential builder (used when every
+atom's z cut-off 6 s stays within one slice thickness, so an atom of slab k
+reaches only slices k-1, k and k+1) against the FP64 oracle: ragged grids, one
+and two slices, atoms beyond both ends of the stack and across the periodic
+edges, several species, and crowded slabs with more candidates than one
+tabulation chunk and more sources than one staged pass.  Bound as for the
+other potential tests: 2e-6 of the peak; identical configurations give
+bit-identical potentials."""
 
 import numpy as np
 import pytest
@@ -41,7 +42,7 @@ def _check(api, g, pos, species, amp_sigma):
 @pytest.mark.parametrize("shape", [(64, 64, 32.0, 32.0, 5, 2.0), (96, 40, 24.0, 10.0, 3, 2.5),
                                    (512, 512, 81.0, 81.0, 7, 2.0), (200, 136, 40.0, 27.0, 1, 2.0),
                                    (128, 128, 40.5, 40.5, 2, 2.0)])
-def test_depth_walk_matches_oracle(api, shape):
+def test_slab_walk_matches_oracle(api, shape):
     nx, ny, lx, ly, ns, dz = shape
     g = O.Grid(nx, ny, lx, ly, ns, dz, 0.5, 200.0, 2.0 / 3.0)
     rng = np.random.default_rng(nx * 3 + ny + ns)
@@ -53,8 +54,8 @@ def test_depth_walk_matches_oracle(api, shape):
     _check(api, g, pos.astype(np.float32), species, amp_sigma)
 
 
-def test_crowded_slabs_overflow_the_cache(api):
-    # 2000 atoms in a 6 A x 6 A x 4 A corner: hundreds of candidates per slab and tile
+def test_crowded_slabs(api):
+    # 2000 atoms in a 6 A x 6 A x 4 A corner: hundreds of sources and candidates per slab and tile
     g = O.Grid(128, 128, 40.0, 40.0, 4, 2.0, 0.0, 200.0, 2.0 / 3.0)
     rng = np.random.default_rng(77)
     n = 2000
@@ -63,7 +64,18 @@ def test_crowded_slabs_overflow_the_cache(api):
     _check(api, g, pos[None].astype(np.float32), species, [[20.0, 0.3], [15.0, 0.28]])
 
 
-def test_depth_walk_is_deterministic(api):
+def test_many_slices_reload_the_bin_table(api):
+    # 400 slices of 0.5 A: the bin ranges of 6 bins per slab fill the table after 315
+    # slabs, so the walk reloads it part-way (no staged records for that slab)
+    g = O.Grid(128, 128, 20.0, 20.0, 400, 0.5, 0.0, 200.0, 2.0 / 3.0)
+    rng = np.random.default_rng(9)
+    n = 1500
+    pos = np.stack([rng.uniform(-0.5, 20.5, n), rng.uniform(-0.5, 20.5, n), rng.uniform(-1.0, 201.0, n)], axis=1)
+    species = rng.integers(0, 2, n).astype(np.int32)
+    _check(api, g, pos[None].astype(np.float32), species, [[20.0, 0.08], [12.0, 0.07]])
+
+
+def test_slab_walk_is_deterministic(api):
     g = O.Grid(256, 256, 40.5, 40.5, 10, 2.0, 0.0, 200.0, 2.0 / 3.0)
     rng = np.random.default_rng(5)
     n = 4000
