@@ -43,6 +43,8 @@ class TimeToSpectrum:
         self.I = torch.empty((nq, n_w), dtype=torch.float32, device=self.device)
         self.I_el = torch.empty(nq, dtype=torch.float64, device=self.device)
         self._ws = {}
+        self._copy_stream = None                # host-input path (run_host): H2D copies
+        self._pos_stage = None                  # [2][batch][Na][3] device staging of host positions
 
     def _workspace(self, key, nbytes):
         ws = self._ws.get(key)
@@ -103,3 +105,61 @@ class TimeToSpectrum:
     def run(self, pos, species):
         self.exit_waves(pos, species)
         return self.spectrum()
+
+    def run_host(self, pos_host, species, out=None, out_el=None):
+        """Host positions pos_host [T, Na, 3] (float32, CPU; pinned for asynchronous
+        copies) -> I(q, E) and I_el in host memory.
+
+        The positions travel to the device one snapshot batch at a time on a copy
+        stream, into two staging buffers, so that the copy of batch b + 1 overlaps
+        the potential and multislice of batch b; then the temporal transform, and
+        I and I_el are copied into `out` / `out_el` (host tensors, allocated pinned
+        if None).  Everything is enqueued on the current stream: synchronize it
+        before reading the outputs."""
+        if pos_host.device.type != "cpu" or pos_host.dtype != torch.float32 or not pos_host.is_contiguous():
+            raise ValueError("pos_host must be a contiguous float32 CPU tensor")
+        if tuple(pos_host.shape) != (self.n_t, self.n_atoms, 3):
+            raise ValueError(f"pos_host must be [{self.n_t}, {self.n_atoms}, 3]")
+        comp = torch.cuda.current_stream(self.device)
+        if self._copy_stream is None:
+            self._copy_stream = torch.cuda.Stream(self.device)
+        if self._pos_stage is None:
+            self._pos_stage = torch.empty((2, self.batch, self.n_atoms, 3), dtype=torch.float32, device=self.device)
+        cs = self._copy_stream
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        free = [torch.cuda.Event(), torch.cuda.Event()]
+        starts = list(range(0, self.n_t, self.batch))
+        cs.wait_stream(comp)                    # earlier work may still read the staging buffers
+
+        def issue(i):
+            t0 = starts[i]
+            t1 = min(self.n_t, t0 + self.batch)
+            slot = i % 2
+            with torch.cuda.stream(cs):
+                if i >= 2:
+                    cs.wait_event(free[slot])   # the potential of batch i - 2 has read it
+                self._pos_stage[slot, : t1 - t0].copy_(pos_host[t0:t1], non_blocking=True)
+                ready[slot].record(cs)
+
+        issue(0)
+        self.psi_sum.zero_()
+        for i, t0 in enumerate(starts):
+            if i + 1 < len(starts):
+                issue(i + 1)
+            t1 = min(self.n_t, t0 + self.batch)
+            slot = i % 2
+            comp.wait_event(ready[slot])
+            v = self.V[: t1 - t0]
+            api.potential(self.grid, self._pos_stage[slot, : t1 - t0], species, self.amp_sigma, out=v,
+                          workspace=self._ws.get("pot"))
+            free[slot].record(comp)
+            api.multislice(self.grid, v, out=self.psi[t0:t1], psi_sum=self.psi_sum,
+                           workspace=self._ws.get("ms"))
+        self.spectrum()
+        if out is None:
+            out = torch.empty(self.I.shape, dtype=self.I.dtype).pin_memory()
+        if out_el is None:
+            out_el = torch.empty(self.I_el.shape, dtype=self.I_el.dtype).pin_memory()
+        out.copy_(self.I, non_blocking=True)
+        out_el.copy_(self.I_el, non_blocking=True)
+        return out, out_el

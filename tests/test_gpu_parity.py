@@ -247,6 +247,28 @@ def test_end_to_end_plain_small(api, precision):
     assert rel_l2(iel, ref_el) < 1e-6
 
 
+def test_host_input_path_matches_device_path(api):
+    # run_host: positions from pinned host memory in batches on a copy stream,
+    # I(q, E) back to host memory; same kernels and inputs as run(), so the
+    # outputs are bit-identical (uneven last batch: 48 snapshots in batches of 20)
+    from paper_2401_15599_gb300.pipeline import TimeToSpectrum
+    w = W.WORKLOADS["plain_small"].with_(n_t=48)
+    inp = W.build_inputs(w)
+    pos = inp.positions()
+    tts = TimeToSpectrum(w.grid, 48, pos.shape[1], inp.amp_sigma, w.dt_fs, batch=20)
+    tts.prepare(None, None)
+    sp = _dev(inp.species)
+    inten, iel = tts.run(_dev(pos), sp)
+    inten, iel = inten.cpu(), iel.cpu()
+    pos_host = torch.from_numpy(pos).pin_memory()
+    for _ in range(2):                                   # the staging buffers are reused
+        out, out_el = tts.run_host(pos_host, sp)
+        torch.cuda.synchronize()
+        assert torch.equal(out, inten) and torch.equal(out_el, iel)
+    with pytest.raises(ValueError):
+        tts.run_host(pos_host[:10], sp)
+
+
 def test_static_lattice_gives_exactly_zero(api):
     w = W.WORKLOADS["plain_small"].with_(n_t=16)
     from paper_2401_15599_gb300.pipeline import TimeToSpectrum
