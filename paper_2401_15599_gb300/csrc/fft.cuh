@@ -224,30 +224,47 @@ __device__ __forceinline__ void stage_to_canon(float2 (&v)[E]) {
     for (int m = 0; m < E; ++m) v[m] = tmp[m];
 }
 
-template <int N, int E, bool INV, int NS, int OFF, class L, int R, int... Rest>
+// Barrier of the threads that share a transform's exchange buffer: the whole
+// block, one named barrier (ids 1 .. 15, `count` threads, a multiple of 32)
+// per group of transforms whose buffers no other threads touch, or the warp.
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct NamedSync {
+    int id, count;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+    }
+};
+// Transforms whose threads all lie in one warp.
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+template <int N, int E, bool INV, int NS, int OFF, class L, class S, int R, int... Rest>
 __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
-                                           const float2* tw, L lay) {
+                                           const float2* tw, L lay, S sync) {
     stage<N, E, R, NS, OFF, INV>(v, t, tw);
     if constexpr (sizeof...(Rest) > 0) {
         constexpr int RN = First<Rest...>::value;
         constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
-        if (b0 == b1) __syncthreads();   // one buffer: the previous exchange's reads come first
+        if (b0 == b1) sync();            // one buffer: the previous exchange's reads come first
         write_out<N, E, R, NS>(v, b0, t, lay);
-        __syncthreads();
+        sync();
         read_in<N, E, RN>(v, b0, t, lay);
-        run_stages<N, E, INV, NS * R, NEXT_OFF, L, Rest...>(v, b1, b0, t, tw, lay);
+        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, Rest...>(v, b1, b0, t, tw, lay, sync);
     } else {
         stage_to_canon<E, R>(v);
     }
 }
 
-template <int N, bool INV, class L, int R0, int... Rs>
+template <int N, bool INV, class L, class S, int R0, int... Rs>
 __device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[Plan<N>::E],
                                                float2* b0, float2* b1, int t, const float2* tw,
-                                               L lay) {
+                                               L lay, S sync) {
     constexpr int E = Plan<N>::E;
     canon_to_stage<E, R0>(v);
-    run_stages<N, E, INV, 1, 0, L, R0, Rs...>(v, b0, b1, t, tw, lay);
+    run_stages<N, E, INV, 1, 0, L, S, R0, Rs...>(v, b0, b1, t, tw, lay, sync);
 }
 
 // Size of the per-stage twiddle table of a plan.
@@ -287,16 +304,17 @@ __device__ void fill_twiddles(float2* tw, int tid, int nthr) {
 
 // Full length-N transform of the values held in canonical order by the TPT
 // threads of one transform.  Every thread of the block must call it the same
-// number of times (it contains __syncthreads).  tw: the plan's per-stage
+// number of times (it contains barriers: __syncthreads, or the named barrier
+// `sync` of the threads sharing the buffers).  tw: the plan's per-stage
 // twiddle table (TwSize<N> entries), normally staged in shared memory.
 // The leading barrier separates the last shared-memory reads of a previous
 // transform from the first writes of this one (plans with one exchange would
 // otherwise reuse a buffer without a barrier in between).
-template <int N, bool INV, class L>
+template <int N, bool INV, class L, class S = BlockSync>
 __device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, float2* b1, int t,
-                                          const float2* tw, L lay) {
-    __syncthreads();
-    transform_impl<N, INV, L>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay);
+                                          const float2* tw, L lay, S sync = S{}) {
+    sync();
+    transform_impl<N, INV, L, S>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync);
 }
 
 }  // namespace fft

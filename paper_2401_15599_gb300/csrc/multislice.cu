@@ -228,6 +228,15 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
 // shared-memory ring.  The stage being transformed doubles as the FFT's
 // exchange buffer (one-buffer mode).  Same arithmetic as row_body, so the
 // results are identical; the waits are bounded and set *err on a timeout.
+// The barrier of one row's transform threads: a named barrier per row when a
+// row spans several warps, the warp itself when it spans one or part of one.
+template <int TPT>
+__device__ __forceinline__ auto row_sync_of(int row) {
+    static_assert(TPT <= 32 || (TPT % 32 == 0 && kRowThreads / TPT <= 15), "named barrier per row");
+    if constexpr (TPT >= 64) return fft::NamedSync{1 + row, TPT};
+    else return fft::WarpSync{};
+}
+
 template <int NX>
 __global__ void __launch_bounds__(kRowThreads)
 row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, const float2* __restrict__ twx,
@@ -295,14 +304,15 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
 #pragma unroll
         for (int m = 0; m < E; ++m)
             v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * NX + t + TPT * m] : make_float2(0.f, 0.f);
-        transform<NX, true>(v, buf, buf, t, tw, lay);
+        const auto row_sync = row_sync_of<TPT>(row);   // a row's transforms touch only its own row
+        transform<NX, true>(v, buf, buf, t, tw, lay, row_sync);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             float sn, cs;
             phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
             v[m] = cmul(v[m], make_float2(cs, sn));
         }
-        transform<NX, false>(v, buf, buf, t, tw, lay);
+        transform<NX, false>(v, buf, buf, t, tw, lay, row_sync);
         const int snap = g / groups_per_snap, y = (g % groups_per_snap) * ROWS + row;
         float2* rowp = psi + ((size_t)snap * ny + y) * NX;
 #pragma unroll
