@@ -364,11 +364,13 @@ row_batch_kernel(const __grid_constant__ RowJobs jobs, const float2* __restrict_
 }
 
 // W columns per column-pass block and the blocks per SM the register budget
-// targets (three blocks of the 8-value plans would spill).
+// targets.  At 512 rows four 256-thread blocks of 4 columns per SM ran faster
+// than two 512-thread blocks of 8 (narrower barriers; fewer band-limited
+// columns transformed) and than eight blocks of 2 (half-sector loads, spills).
 template <int NY>
 struct ColCfg {
-    static constexpr int W = (NY >= 512) ? 8 : 16;
-    static constexpr int kMinBlocks = (NY >= 1024) ? 1 : 2;
+    static constexpr int W = (NY >= 1024) ? 8 : (NY >= 512 ? 4 : 16);
+    static constexpr int kMinBlocks = (NY >= 1024) ? 1 : (NY >= 512 ? 4 : 2);
 };
 // ny must be a multiple of the rows handled per row-pass block
 static_assert(kRowThreads / (384 / 24) == 16 && kRowThreads / (768 / 24) == 8, "row tiles");
