@@ -238,7 +238,7 @@ def slice_step_bytes(g):
         else:
             break
     kept = [kx <= K or kx >= g.nx - K for kx in range(g.nx)]
-    w = 8 if g.ny >= 512 else 16                       # columns per column-pass block
+    w = 8 if g.ny >= 1024 else (4 if g.ny >= 512 else 16)   # columns per column-pass block
     blocks = [any(kept[b:b + w]) for b in range(0, g.nx, w)]
     f_col = sum(kept) / g.nx
     f_blk = sum(blocks) / len(blocks)

@@ -729,24 +729,30 @@ potential_slab_kernel(const int* __restrict__ bin_off, const float4* __restrict_
                             dst[h] = make_float4(v[0], v[1], v[2], v[3]);
                         }
                     }
-                    // erf(.)/2 at boundary k - 1 + g (open ends -1/2, +1/2), gathered per row group
-                    const float bj = slice_boundary(p, k - 1 + g);
-                    const float zc = sm.z[cc];
-                    const float e = bj == -INFINITY ? -0.5f
-                                                    : (bj == INFINITY ? 0.5f : 0.5f * erff((bj - zc) * p.kz[csp]));
-                    const int l4 = lane & ~3;
-                    const float e0 = __shfl_sync(0xffffffffu, e, l4), e1 = __shfl_sync(0xffffffffu, e, l4 + 1);
-                    const float e2 = __shfl_sync(0xffffffffu, e, l4 + 2), e3 = __shfl_sync(0xffffffffu, e, l4 + 3);
-                    const unsigned nzb = __ballot_sync(0xffffffffu, col_task && nz);
-                    if (row_task && g == 0) {
-                        const float amp = p.amp[csp];
-                        const float lo_z = zc - rcc, hi_z = zc + rcc;
-                        const float wm_ = (has_m && b0 > lo_z && bm < hi_z) ? amp * (e1 - e0) : 0.f;
-                        const float wc_ = (b1 > lo_z && b0 < hi_z) ? amp * (e2 - e1) : 0.f;
-                        const float wp_ = (has_p && b2 > lo_z && b1 < hi_z) ? amp * (e3 - e2) : 0.f;
-                        sm.w[c] = make_float4(wm_, wc_, wp_, 0.f);
+                    // erf(.)/2 at boundary k - 1 + g (open ends -1/2, +1/2), gathered per row
+                    // group; only warps that hold row tasks (resp. column tasks) take part
+                    const int wi0 = ib + 32 * warp;      // this warp's first task index
+                    if (wi0 < n_rt) {
+                        const float bj = slice_boundary(p, k - 1 + g);
+                        const float zc = sm.z[cc];
+                        const float e = bj == -INFINITY ? -0.5f
+                                        : (bj == INFINITY ? 0.5f : 0.5f * erff((bj - zc) * p.kz[csp]));
+                        const int l4 = lane & ~3;
+                        const float e0 = __shfl_sync(0xffffffffu, e, l4), e1 = __shfl_sync(0xffffffffu, e, l4 + 1);
+                        const float e2 = __shfl_sync(0xffffffffu, e, l4 + 2), e3 = __shfl_sync(0xffffffffu, e, l4 + 3);
+                        if (row_task && g == 0) {
+                            const float amp = p.amp[csp];
+                            const float lo_z = zc - rcc, hi_z = zc + rcc;
+                            const float wm_ = (has_m && b0 > lo_z && bm < hi_z) ? amp * (e1 - e0) : 0.f;
+                            const float wc_ = (b1 > lo_z && b0 < hi_z) ? amp * (e2 - e1) : 0.f;
+                            const float wp_ = (has_p && b2 > lo_z && b1 < hi_z) ? amp * (e3 - e2) : 0.f;
+                            sm.w[c] = make_float4(wm_, wc_, wp_, 0.f);
+                        }
                     }
-                    if (col_task && g == 0) sm.wmask[c] = (int)((nzb >> (lane & 24)) & 0xffu);
+                    if (wi0 + 31 >= col0 && wi0 < n_task) {
+                        const unsigned nzb = __ballot_sync(0xffffffffu, col_task && nz);
+                        if (col_task && g == 0) sm.wmask[c] = (int)((nzb >> (lane & 24)) & 0xffu);
+                    }
                 }
                 __syncthreads();
 
