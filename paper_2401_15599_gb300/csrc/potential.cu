@@ -781,7 +781,10 @@ potential_slab_kernel(const int* __restrict__ bin_off, const float4* __restrict_
                         acc_p[i] = fmaf(yp, g[i], acc_p[i]);
                     }
                 }
-                __syncthreads();                         // the next chunk rewrites the table
+                // the next chunk rewrites the table; after a slab's last chunk the
+                // end-of-slab barrier comes first (the next writes follow the next
+                // slab's selection barriers)
+                if (cb + kSCand < n_cand || sb + kPotThreads < n_src) __syncthreads();
             }
         }
         // slice k-1 has all its slabs (k-2 .. k): write it, then move the window up
