@@ -358,6 +358,7 @@ def run_ours(args):
         el_host = torch.empty(tts.I_el.shape, dtype=torch.float64).pin_memory()
         tts.precision = args.precision
         tts.run_host(pos_host, species, out=i_host, out_el=el_host)
+        tts.wait_host()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -368,6 +369,7 @@ def run_ours(args):
         s2.record(stream)
         for _ in range(args.steps):
             tts.run_host(pos_host, species, out=i_host, out_el=el_host)
+        tts.wait_host()                       # the last step's outputs are in host memory
         e2.record(stream)
         torch.cuda.synchronize()
         clk_e2e = clocks_e2e.stop()

@@ -45,6 +45,10 @@ class TimeToSpectrum:
         self._ws = {}
         self._copy_stream = None                # host-input path (run_host): H2D copies
         self._pos_stage = None                  # [2][batch][Na][3] device staging of host positions
+        self._d2h_stream = None                 # run_host: D2H copies of I, I_el
+        self._d2h_done = None                   # event: the last run_host's outputs are in host memory
+        self._graph = None                      # CUDA graph of run() on self._graph_args
+        self._graph_args = None
 
     def _workspace(self, key, nbytes):
         ws = self._ws.get(key)
@@ -106,6 +110,26 @@ class TimeToSpectrum:
         self.exit_waves(pos, species)
         return self.spectrum()
 
+    def capture(self, pos, species):
+        """Record run(pos, species) into a CUDA graph (after one eager run that
+        fills the workspace cache); replay() then re-runs it on the same device
+        buffers with one launch.  The buffers must stay alive and in place."""
+        self.prepare(None, None)
+        self.run(pos, species)
+        torch.cuda.synchronize(self.device)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run(pos, species)
+        self._graph, self._graph_args = graph, (pos, species)
+        return graph
+
+    def replay(self):
+        """Re-run the captured run() (positions read from the captured buffer)."""
+        if self._graph is None:
+            raise RuntimeError("capture() first")
+        self._graph.replay()
+        return self.I, self.I_el
+
     def run_host(self, pos_host, species, out=None, out_el=None):
         """Host positions pos_host [T, Na, 3] (float32, CPU; pinned for asynchronous
         copies) -> I(q, E) and I_el in host memory.
@@ -114,7 +138,9 @@ class TimeToSpectrum:
         stream, into two staging buffers, so that the copy of batch b + 1 overlaps
         the potential and multislice of batch b; then the temporal transform, and
         I and I_el are copied into `out` / `out_el` (host tensors, allocated pinned
-        if None).  Everything is enqueued on the current stream: synchronize it
+        if None) on a stream of their own, so that those copies overlap the next
+        call's work (whose temporal transform waits for them).  Nothing blocks the
+        host: call wait_host() and synchronize the current stream (or the device)
         before reading the outputs."""
         if pos_host.device.type != "cpu" or pos_host.dtype != torch.float32 or not pos_host.is_contiguous():
             raise ValueError("pos_host must be a contiguous float32 CPU tensor")
@@ -155,11 +181,26 @@ class TimeToSpectrum:
             free[slot].record(comp)
             api.multislice(self.grid, v, out=self.psi[t0:t1], psi_sum=self.psi_sum,
                            workspace=self._ws.get("ms"))
+        if self._d2h_done is not None:
+            comp.wait_event(self._d2h_done)     # the previous call's outputs have left I, I_el
         self.spectrum()
         if out is None:
             out = torch.empty(self.I.shape, dtype=self.I.dtype).pin_memory()
         if out_el is None:
             out_el = torch.empty(self.I_el.shape, dtype=self.I_el.dtype).pin_memory()
-        out.copy_(self.I, non_blocking=True)
-        out_el.copy_(self.I_el, non_blocking=True)
+        if self._d2h_stream is None:
+            self._d2h_stream = torch.cuda.Stream(self.device)
+            self._d2h_done = torch.cuda.Event()
+        d2h = self._d2h_stream
+        d2h.wait_stream(comp)
+        with torch.cuda.stream(d2h):
+            out.copy_(self.I, non_blocking=True)
+            out_el.copy_(self.I_el, non_blocking=True)
+        self._d2h_done.record(d2h)
         return out, out_el
+
+    def wait_host(self):
+        """Make the current stream wait until the last run_host's outputs are in
+        host memory."""
+        if self._d2h_done is not None:
+            torch.cuda.current_stream(self.device).wait_event(self._d2h_done)

@@ -263,8 +263,22 @@ def test_host_input_path_matches_device_path(api):
     pos_host = torch.from_numpy(pos).pin_memory()
     for _ in range(2):                                   # the staging buffers are reused
         out, out_el = tts.run_host(pos_host, sp)
-        torch.cuda.synchronize()
+        tts.wait_host()
+        torch.cuda.current_stream().synchronize()
         assert torch.equal(out, inten) and torch.equal(out_el, iel)
+    # back-to-back calls into the same host buffers: each call's transform waits for
+    # the previous call's copies; a captured run() replays bit-identically
+    o1, e1 = tts.run_host(pos_host, sp)
+    o1, e1 = tts.run_host(pos_host, sp, out=o1, out_el=e1)
+    tts.wait_host()
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(o1, inten) and torch.equal(e1, iel)
+    pos_dev = _dev(pos)
+    tts.capture(pos_dev, sp)
+    tts.I.zero_()
+    i2, el2 = tts.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(i2.cpu(), inten) and torch.equal(el2.cpu(), iel)
     with pytest.raises(ValueError):
         tts.run_host(pos_host[:10], sp)
 
