@@ -23,8 +23,8 @@ import torch
 
 from . import _lib as L
 
-DEFAULT_CANDIDATES = (8, 16, 32, 64, 128)
-MAX_TUNING_BYTES = 16 << 30         # potentials allocated for the largest candidate
+DEFAULT_CANDIDATES = (8, 16, 32, 64, 128, 256, 512)
+MAX_TUNING_BYTES = 64 << 30         # potentials allocated for the largest candidate (HBM: 288 GB)
 
 
 def cache_path() -> str:
