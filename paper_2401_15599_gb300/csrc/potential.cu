@@ -118,11 +118,33 @@ __device__ __forceinline__ int atom_bin(const Split& sp, float z, const PotParam
     return (slab * p.n_bands + band) * p.n_ctiles + ct;
 }
 
+// Shell sort (Knuth's gaps) of one bin's records by atom index (key.x): bins
+// hold a handful of atoms, so this is an insertion sort in practice, and any
+// crowded bin still ends in input order.
+__device__ void sort_bin_by_index(float4* __restrict__ rec, int2* __restrict__ key, int n) {
+    int h = 1;
+    while (h < n / 3) h = 3 * h + 1;
+    for (; h >= 1; h /= 3) {
+        for (int i = h; i < n; ++i) {
+            const int2 kk = key[i];
+            const float4 rr = rec[i];
+            int j = i;
+            while (j >= h && key[j - h].x > kk.x) {
+                key[j] = key[j - h];
+                rec[j] = rec[j - h];
+                j -= h;
+            }
+            key[j] = kk;
+            rec[j] = rr;
+        }
+    }
+}
+
 // One block per snapshot.  Counts per bin (shared-memory histogram), an
-// exclusive scan into bin_off, then a stable scatter: atoms go in rounds of
-// one per thread; within a warp, atoms of the same bin take consecutive slots
-// by lane (match + popc), and the warps of a round claim their slots one after
-// the other, so every bin lists its atoms in input order.
+// exclusive scan into bin_off, a scatter whose slots come from shared-memory
+// atomics (any order; the atom index and the packed pixel ride along in the
+// pixel array), then every bin sorted back into input order and its pixels
+// unpacked, so every bin lists its atoms in input order.
 __global__ void __launch_bounds__(kBinThreads)
 bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotParams p,
            int* __restrict__ bin_off, float4* __restrict__ binned, int2* __restrict__ binned_px) {
@@ -177,35 +199,22 @@ bin_kernel(const float* __restrict__ pos, const int* __restrict__ species, PotPa
 
     float4* out = binned + t * (size_t)p.n_atoms;
     int2* out_px = binned_px + t * (size_t)p.n_atoms;
-    const unsigned lt = (1u << lane) - 1u;
-    const int n_warps = blockDim.x / 32;
-    for (int base = 0; base < p.n_atoms; base += blockDim.x) {
-        const int a = base + threadIdx.x;
-        const bool valid = a < p.n_atoms;
-        float z = 0.f;
-        Split sp{0, 0, 0.f, 0.f, false};
-        int bin = -1;
-        if (valid) {
-            z = P[3 * a + 2];
-            sp = split_position(P[3 * a], P[3 * a + 1], p);
-            bin = atom_bin(sp, z, p);
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        const int leader = __ffs(peers) - 1;
-        int slot = 0;
-        for (int w = 0; w < n_warps; ++w) {         // warps claim their slots in order
-            if (wid == w && valid && lane == leader) {
-                slot = cnt[bin];
-                cnt[bin] = slot + __popc(peers);
-            }
-            __syncthreads();
-        }
-        slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(peers & lt);
-        if (valid) {
-            // a species of -1 marks an atom that is skipped (non-finite or absurd position)
-            const int spc = (sp.ok && fabsf(z) < 1e9f) ? __ldg(species + a) : -1;
-            out[slot] = make_float4(sp.fx, sp.fy, z, __int_as_float(spc));
-            out_px[slot] = make_int2(wrap(sp.ic, p.nx), wrap(sp.jc, p.ny));
+    for (int a = threadIdx.x; a < p.n_atoms; a += blockDim.x) {
+        const float z = P[3 * a + 2];
+        const Split sp = split_position(P[3 * a], P[3 * a + 1], p);
+        const int slot = atomicAdd(&cnt[atom_bin(sp, z, p)], 1);
+        // a species of -1 marks an atom that is skipped (non-finite or absurd position)
+        const int spc = (sp.ok && fabsf(z) < 1e9f) ? __ldg(species + a) : -1;
+        out[slot] = make_float4(sp.fx, sp.fy, z, __int_as_float(spc));
+        out_px[slot] = make_int2(a, (int)((unsigned)wrap(sp.ic, p.nx) | ((unsigned)wrap(sp.jc, p.ny) << 16)));
+    }
+    __syncthreads();                               // cnt[b] is now the end of bin b
+    for (int b = threadIdx.x; b < p.n_bins; b += blockDim.x) {
+        const int s0 = b ? cnt[b - 1] : 0, s1 = cnt[b];
+        sort_bin_by_index(out + s0, out_px + s0, s1 - s0);
+        for (int i = s0; i < s1; ++i) {
+            const unsigned pk = (unsigned)out_px[i].y;
+            out_px[i] = make_int2((int)(pk & 0xffffu), (int)(pk >> 16));
         }
     }
 }
@@ -1089,6 +1098,8 @@ int make_params(const tacaw_grid& g, int n_atoms, int n_species, const float* am
         smax = fmaxf(smax, amp_sigma[2 * i + 1]);
     }
     for (int i = n_species; i < TACAW_MAX_SPECIES; ++i) p->amp[i] = p->sigma[i] = p->c2[i] = p->rc[i] = p->kz[i] = 0.f;
+    TACAW_REQUIRE(g.nx <= 65535 && g.ny <= 65535, TACAW_EUNSUPPORTED,
+                  "tacaw_potential: nx and ny must be at most 65535");
     const double rc = 6.0 * smax;
     TACAW_REQUIRE(2.0 * rc < g.lx && 2.0 * rc < g.ly, TACAW_EINVAL,
                   "tacaw_potential: cut-off 6 sigma = %g A must be below half the box", rc);
