@@ -11,9 +11,9 @@
 // extends to -inf and the last to +inf.
 //
 // Two kernels per call:
-//  1. bin_kernel (one block per snapshot): stable counting sort of the atoms
-//     into bins (slab of the atom centre) x (band of rows) x (tile of columns).
-//     Within a bin the atoms keep their input order, so the bins of identical
+//  1. bin_kernel (one block per snapshot): counting sort of the atoms into
+//     bins (slab of the atom centre) x (band of rows) x (tile of columns); each
+//     bin is sorted back into input order, so the bins of identical
 //     configurations are identical.
 //  2. potential_tile_kernel (one block per 32 x 64 pixel tile, slice and
 //     snapshot): the separable Gaussian makes the tile a sum of outer products,
