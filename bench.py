@@ -69,6 +69,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x, device):
+    """The largest x over the ranks of the process group (the slowest rank's
+    time); x itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, ms_step):
+    """Whole-job throughput: the units of all ranks over the slowest rank's step time."""
+    return units_per_rank * world / (ms_step * 1e-3)
+
+
 def workload(args):
     import workloads as W
     w = W.WORKLOADS[args.workload]
@@ -341,13 +358,9 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms_total = start.elapsed_time(end)
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dev)
     units_step = g.nx * g.ny * g.n_slices * n_t
-    value = units_step * world / (ms_step * 1e-3)
+    value = aggregate_rate(units_step, world, ms_step)
 
     # end to end through the public host-input call: pinned host positions in (copied batch by
     # batch on a copy stream, overlapping the work on the previous batch), host I(q, E) out;
@@ -373,12 +386,8 @@ def run_ours(args):
         e2.record(stream)
         torch.cuda.synchronize()
         clk_e2e = clocks_e2e.stop()
-        e2e_ms = s2.elapsed_time(e2) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": units_step * world / (e2e_ms * 1e-3), "unit": UNIT,
+        e2e_ms = max_over_ranks(s2.elapsed_time(e2) / args.steps, dev)
+        e2e = {"value": aggregate_rate(units_step, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(pos_host.numel() * 4),
                "d2h_bytes_per_step": int(i_host.numel() * 4 + el_host.numel() * 8),
                "ms_per_step": e2e_ms, "call": "TimeToSpectrum.run_host", "clocks": clk_e2e}
