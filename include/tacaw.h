@@ -111,11 +111,14 @@ int tacaw_beam_constants(double kev, double* lambda_A, double* sigma_e);
  * amp_sigma HOST [n_species][2] float: amplitude (V*A), width s (A);
  *           n_species <= TACAW_MAX_SPECIES
  * V         out [T][n_slices][ny][nx] float, V*A
- * Deterministic: identical configurations give bit-identical V (per-pixel
- * sums are accumulated in 64-bit fixed point, 2^-32 V*A, so the order in
- * which atoms are added does not matter).
- * Errors: EINVAL for bad sizes or pointers, EUNSUPPORTED if the binning
- * tables exceed shared memory, ENOMEM for a short workspace.
+ * Deterministic: identical configurations give bit-identical V (each pixel
+ * is an FP32 sum over the atoms in a fixed order: by slab, then by bin, then
+ * in input order); listing the same atoms in another order changes only that
+ * rounding order.
+ * Errors: EINVAL for bad sizes or pointers; EUNSUPPORTED for nx or ny above
+ * 65535, or when the binning tables exceed shared memory (too many slices, or
+ * more than 128 neighbouring bins per tile: widths too large for the slice
+ * thickness or the pixel size); ENOMEM for a short workspace.
  */
 #define TACAW_MAX_SPECIES 8
 int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
