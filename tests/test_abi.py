@@ -97,6 +97,18 @@ def test_host_side_argument_errors(lib):
                                ctypes.byref(ctypes.c_size_t(1 << 30)), null) == L.TACAW_EINVAL
     assert lib.tacaw_potential(ctypes.byref(g), 1, 1, fake, fake, 9, amp, fake, fake,
                                ctypes.byref(ctypes.c_size_t(1 << 30)), null) == L.TACAW_EINVAL
+    # pixel pairs are packed in 16 + 16 bits while binning
+    amp = (ctypes.c_float * 2)(20.0, 0.3)
+    wide = _grid(nx=70000)
+    assert lib.tacaw_potential(ctypes.byref(wide), 1, 1, fake, fake, 1, amp, fake, fake,
+                               ctypes.byref(ctypes.c_size_t(1 << 40)), null) == L.TACAW_EUNSUPPORTED
+    assert b"65535" in lib.tacaw_last_error()
+    # a width reaching 192 pixels and 3 slabs either side: too many neighbouring bins per tile
+    fine = _grid(nx=512, ny=512)
+    amp = (ctypes.c_float * 2)(20.0, 2.0)
+    assert lib.tacaw_potential(ctypes.byref(fine), 1, 1, fake, fake, 1, amp, fake, fake,
+                               ctypes.byref(ctypes.c_size_t(1 << 40)), null) == L.TACAW_EUNSUPPORTED
+    assert b"neighbouring bins" in lib.tacaw_last_error()
     # spectrum: natural grid needs n_omega == T; Kubo needs a temperature
     assert lib.tacaw_spectrum(16, 8, 5.0, 9, null, fake, null, fake, null, 0, 0, 300.0, null,
                               ctypes.byref(n), null) == L.TACAW_EINVAL
