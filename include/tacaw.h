@@ -47,12 +47,15 @@ extern "C" {
 #define TACAW_EINVAL (-1)       /* bad argument (detected on the host) */
 #define TACAW_ECUDA (-2)        /* a CUDA runtime call or launch failed */
 #define TACAW_ENOMEM (-3)       /* workspace smaller than required */
-#define TACAW_ETIMEOUT (-4)     /* a bounded device wait gave up */
+#define TACAW_ETIMEOUT (-4)     /* a bounded device wait gave up (reported by tacaw_status) */
 #define TACAW_EUNSUPPORTED (-5) /* size or option not supported by this build */
 
 /* precision of the temporal transform (tacaw_spectrum) */
 #define TACAW_FP32 0            /* FP32 SIMT complex GEMM */
-#define TACAW_BF16X3 1          /* split BF16 (hi+lo), 3 products, FP32 accumulation */
+#define TACAW_BF16X3 1          /* split BF16 (hi+lo), 3 products, FP32 accumulation: for timing
+                                   comparisons only -- its ~2^-16 error relative to sum |A||e|
+                                   exceeds 2e-5 of I in the weak outer energy bands; use
+                                   TACAW_BF16X6 for explicit energy grids */
 #define TACAW_FFT32 2           /* natural grid only: FP32 FFT over time (T in 64..1024 as for
                                    tacaw_multislice, or 2048, 4096) */
 #define TACAW_BF16X6 3          /* split BF16 (three terms), 6 products, FP32 accumulation */
@@ -82,6 +85,38 @@ const char* tacaw_last_error(void);
 
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t tacaw_version(void);
+
+/*
+ * Bounded device waits and their status (the paper has no counterpart: this
+ * is the library's failure reporting).  Kernels that wait on the GPU for
+ * asynchronous copies or tensor-core work (the multislice row pass after the
+ * first slice, the split-BF16 temporal transform) give up after a bounded
+ * number of polls instead of spinning forever; they then stop, leave their
+ * outputs incomplete and set a per-device status flag.  Calls return before
+ * their kernels run, so the flag cannot be their return value:
+ *
+ * tacaw_status(stream): waits for `stream` (NULL: the legacy default stream),
+ *   reads the flag of the current device and clears it.  Returns TACAW_OK, or
+ *   TACAW_ETIMEOUT if any bounded wait gave up since the flag was last read
+ *   (the outputs of the calls enqueued since then are incomplete);
+ *   TACAW_ECUDA if the device cannot be reached.  Blocks the calling thread:
+ *   not for use during stream capture.
+ *
+ * tacaw_set_wait_limit(polls): polls >= 0 sets the number of polls of every
+ *   bounded data wait of the multislice row pass enqueued afterwards in this
+ *   process (0 gives up at once: for tests of the timeout path); polls < 0
+ *   restores the default (about a second).  A CUDA graph keeps the limit
+ *   that was in force when it was captured.  Always returns TACAW_OK.
+ *
+ * Host-side fault injection for tests: the environment variable TACAW_FAULT
+ * (comma-separated) makes "launch" fail every computing entry point with
+ * TACAW_ECUDA just before it would enqueue work, "symbol" fail the lookup of
+ * the library's device variables (TACAW_ECUDA), and "timeout" make
+ * tacaw_status return TACAW_ETIMEOUT without touching the device.  It is read
+ * on every call.
+ */
+int tacaw_status(void* stream);
+int tacaw_set_wait_limit(int64_t polls);
 
 /*
  * Relativistic wavelength lambda (Angstrom) and interaction constant sigma_e
@@ -159,10 +194,11 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,
  *
  * Scratch lives in one fixed 64 KiB device array inside the library (enough
  * for every supported grid, up to 1024 x 1024); each GPU that loads the
- * library holds it until the process exits.  A grid needing more is rejected
- * with TACAW_EINVAL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls on a device share the array and
+ * library holds it until the process exits (the tables of the largest grid,
+ * 1024 x 1024, take 37120 bytes).  A grid needing more is rejected with
+ * TACAW_EINVAL.  The first call in a CUDA context looks up the array's device
+ * address there (cudaGetSymbolAddress) and keeps it for that context; make
+ * that first call before any stream capture, and again after a device reset.  All calls on a device share the array and
  * rewrite it at the start of each call: calls whose kernels overlap on the GPU
  * (concurrent streams or graph replays) race and must be serialised.
  */

@@ -14,7 +14,7 @@ What it computes (arXiv 2401.15599, the two-step procedure after Eq. (9)):
    the Kubo detailed-balance factor (Eq. (8)) and the fractional-intensity
    normalisation (the unnumbered equation after Eq. (9)).
 
-Readings taken where the paper is silent (each one listed in the design doc):
+Readings taken where the paper is silent:
 
 * Atoms are isotropic 3-D Gaussians; ``amp`` is the peak of the z-projection
   (V*A), so the projected profile is amp*exp(-rho^2/(2 s^2)).  Laterally the

@@ -64,6 +64,8 @@ _SZ = ctypes.POINTER(ctypes.c_size_t)
 SIGNATURES = {
     "tacaw_last_error": (ctypes.c_char_p, []),
     "tacaw_version": (ctypes.c_int32, []),
+    "tacaw_status": (ctypes.c_int, [_P]),
+    "tacaw_set_wait_limit": (ctypes.c_int, [ctypes.c_int64]),
     "tacaw_beam_constants": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]),
     "tacaw_potential": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, ctypes.c_int32, _P, _P,

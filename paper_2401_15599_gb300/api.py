@@ -40,6 +40,21 @@ def _workspace(query, device):
     return ws, nbytes
 
 
+def status(device=None):
+    """Wait for the current stream, then raise TacawError (ETIMEOUT) if a bounded
+    device wait of an earlier call gave up since the last status check (its
+    outputs are incomplete); the flag is cleared by reading it."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    L.check("tacaw_status", L.load().tacaw_status(_stream(dev)))
+
+
+def set_wait_limit(polls):
+    """Polls of the multislice row pass's bounded waits for calls enqueued from
+    now on (0 gives up at once, for tests); None or a negative value restores
+    the default."""
+    L.check("tacaw_set_wait_limit", L.load().tacaw_set_wait_limit(-1 if polls is None else int(polls)))
+
+
 def beam_constants(kev: float):
     lam, sig = ctypes.c_double(), ctypes.c_double()
     L.check("tacaw_beam_constants", L.load().tacaw_beam_constants(kev, ctypes.byref(lam), ctypes.byref(sig)))

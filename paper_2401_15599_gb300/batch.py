@@ -28,7 +28,7 @@ class Job:
 
 
 class BatchTimeToSpectrum:
-    def __init__(self, jobs, window=8, precision="bf16x3", device="cuda"):
+    def __init__(self, jobs, window=8, precision="bf16x6", device="cuda"):
         self.jobs = list(jobs)
         if window == "auto":                    # tuned for the largest grid of the jobs (tuning.py)
             from .tuning import best_multislice_batch

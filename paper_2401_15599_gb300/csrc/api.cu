@@ -148,6 +148,10 @@ int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms, const 
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V != nullptr && (n_atoms == 0 || (pos && species)), TACAW_EINVAL,
                   "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return potential_run(*grid, n_t, n_atoms, pos, species, n_species, amp_sigma, V, ws,
                          (cudaStream_t)stream);
 }
@@ -169,6 +173,10 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
     if (rc || query) return rc;
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
                           ws, (cudaStream_t)stream);
 }
@@ -192,6 +200,10 @@ int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size
     bool query = false;
     int rc = check_ws(ws, ws_bytes, multislice_batch_ws_bytes(jobs, n_jobs), fn, &query);
     if (rc || query) return rc;
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return multislice_batch_run(jobs, n_jobs, ws, (cudaStream_t)stream);
 }
 
@@ -225,6 +237,10 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
                       fn, &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(psi && I, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return spectrum_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
                         (const double2*)psi_sum, I, I_el, precision, flags, temperature_K, ws,
                         (cudaStream_t)stream);
@@ -262,6 +278,10 @@ int tacaw_spectrum_segments(int32_t nq, int32_t n_t, double dt_fs, int32_t seg_l
     int rc = check_ws(ws, ws_bytes, spectrum_segments_ws_bytes(nq, seg_len, n_omega, precision), fn, &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(psi && I, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return spectrum_segments_run(nq, dt_fs, seg_len, hop, sets, n_omega, omega_meV, (const float2*)psi, I, I_el,
                                  precision, flags, temperature_K, ws, (cudaStream_t)stream);
 }
@@ -282,6 +302,10 @@ int tacaw_spectrum_backward(int32_t nq, int32_t n_t, double dt_fs, int32_t n_ome
                       &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(psi && dL_dI && dL_dpsi, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return spectrum_backward_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
                                  (const double2*)psi_sum, dL_dI, (float2*)dL_dpsi, ws, (cudaStream_t)stream);
 }
@@ -305,6 +329,10 @@ int tacaw_multislice_backward(const tacaw_grid* grid, int32_t n_t, const float* 
     if (rc || query) return rc;
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V && dL_dpsi_q && dL_dV, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return multislice_backward_run(*grid, n_t, V, (const float2*)psi_in, (const float2*)dL_dpsi_q, dL_dV,
                                    every, ws, (cudaStream_t)stream);
 }
@@ -328,6 +356,10 @@ int tacaw_potential_backward(const tacaw_grid* grid, int32_t n_t, int32_t n_atom
     if (rc || query) return rc;
     TACAW_REQUIRE(dL_dV && dL_damp_sigma && (n_atoms == 0 || (pos && species)), TACAW_EINVAL,
                   "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return potential_backward_run(*grid, n_t, n_atoms, pos, species, n_species, amp_sigma, dL_dV,
                                   dL_damp_sigma, ws, (cudaStream_t)stream);
 }
@@ -344,6 +376,10 @@ int tacaw_qep_intensity(int32_t nq, int32_t n_t, int32_t t0, int32_t stride, int
     TACAW_REQUIRE(use >= 1 && use <= most, TACAW_EINVAL,
                   "%s: %d snapshots from %d every %d do not fit in %d", fn, n, t0, stride, n_t);
     TACAW_REQUIRE(psi && qep, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return qep_run(nq, t0, stride, (int)use, (const float2*)psi, qep, (cudaStream_t)stream);
 }
 
@@ -353,6 +389,10 @@ int tacaw_energy_integral(int32_t nq, int32_t n_omega, const float* I, const dou
     const char* fn = "tacaw_energy_integral";
     TACAW_REQUIRE(nq > 0 && n_omega > 0, TACAW_EINVAL, "%s: nq and n_omega must be positive", fn);
     TACAW_REQUIRE(I && out, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return energy_integral_run(nq, n_omega, I, I_el, out, (cudaStream_t)stream);
 }
 
@@ -363,6 +403,10 @@ int tacaw_line_profile(int32_t nx, int32_t ny, double lx, double lambda_A, const
     TACAW_REQUIRE(nx > 0 && ny > 0 && lx > 0 && isfinite(lx) && lambda_A > 0 && isfinite(lambda_A), TACAW_EINVAL,
                   "%s: need nx, ny, lx, lambda > 0", fn);
     TACAW_REQUIRE(values && line, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return line_profile_run(nx, ny, lx, lambda_A, values, line, theta_mrad, (cudaStream_t)stream);
 }
 
@@ -379,6 +423,10 @@ int tacaw_azimuthal_profile(int32_t nx, int32_t ny, double lx, double ly, double
     int rc = check_ws(ws, ws_bytes, azimuthal_ws_bytes(nx * ny), fn, &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(values && profile, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return azimuthal_run(nx, ny, lx, ly, lambda_A, dtheta_mrad, n_bins, values, profile, counts, ws,
                          (cudaStream_t)stream);
 }
@@ -389,6 +437,10 @@ int tacaw_relative_difference(int64_t n, const double* a, const double* b, doubl
     TACAW_REQUIRE(n >= 0, TACAW_EINVAL, "%s: n must be >= 0", fn);
     if (n == 0) return TACAW_OK;
     TACAW_REQUIRE(a && b && out, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return rel_diff_run((size_t)n, a, b, out, (cudaStream_t)stream);
 }
 
@@ -408,6 +460,10 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
     int rc = check_ws(ws, ws_bytes, probe_ws_bytes(nx, ny, lx, ly, lam, alpha_mrad), fn, &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(psi, TACAW_EINVAL, "%s: NULL array", fn);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return probe_run(nx, ny, lx, ly, lam, alpha_mrad, defocus_A, x0_A, y0_A, (float2*)psi, ws,
                      (cudaStream_t)stream);
 }
@@ -431,6 +487,10 @@ int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float
     for (int i = 0; i < n_candidates; ++i)
         TACAW_REQUIRE(candidates[i] >= 1 && candidates[i] <= max_batch, TACAW_EINVAL,
                       "%s: candidate %d = %d outside [1, max_batch = %d]", fn, i, candidates[i], max_batch);
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
     return tune_multislice_run(*grid, V, (float2*)psi_q, candidates, n_candidates, reps, ms_per_snapshot,
                                best_batch, ws, (cudaStream_t)stream);
 }

@@ -36,6 +36,28 @@ void clear_error();
 
 #define TACAW_LAUNCH_CHECK() TACAW_CUDA_CHECK(cudaGetLastError())
 
+// Device status (status.cu).  fault_injected(kind): `kind` is listed in the
+// comma-separated environment variable TACAW_FAULT (host-side fault injection
+// for tests: "launch" fails every entry point before its first enqueue,
+// "symbol" fails device-symbol lookups, "timeout" makes tacaw_status report a
+// timeout); inject_launch_fault returns TACAW_ECUDA with a message when
+// "launch" is set.  device_symbol: device address of a __device__ variable in
+// the current context.  timeout_flag: address of the sticky flag that bounded
+// device waits set when they give up.  wait_polls: the poll limit of bounded
+// waits set by tacaw_set_wait_limit, or `dflt`.
+bool fault_injected(const char* kind);
+int inject_launch_fault(const char* fn);
+int device_symbol(const void* symbol, void** out, const char* fn);
+int timeout_flag(int** out, const char* fn);
+uint32_t wait_polls(uint32_t dflt);
+
+// A kernel's bounded waits: the status flag to set when one gives up, and the
+// number of polls before it does.
+struct WaitCtl {
+    int* flag;
+    uint32_t polls;
+};
+
 // Workspace carving: aligned sub-buffers of a caller-provided block.
 // Planck and Boltzmann constants in meV fs and meV / K (exact SI values).
 constexpr double kPlanckMeVfs = 6.62607015e-34 / 1.602176634e-19 * 1e3 * 1e15;

@@ -10,7 +10,11 @@
 // pass starts from the real-space incident wave (no inverse transform); the
 // last column pass skips Fy^-1 and leaves the exit wave in q-space.
 // Each pass reads and writes every point once (8 + 8 bytes per point), the
-// row pass also reads v_s (4 bytes per point): 36 bytes per point and slice.
+// row pass also reads v_s (4 bytes per point): 36 bytes per point and slice
+// for a dense wave.  The band limit zeroes a third of the k_x columns, which
+// neither pass reads or writes, so at 512^2 with the 2/3 limit the passes
+// move 4 + 16 f_col + 16 f_blk = 25.4 bytes per point and slice (f_col: kept
+// columns, f_blk: column-pass blocks holding a kept column).
 
 #include <stdint.h>
 
@@ -74,8 +78,7 @@ constexpr int kRowThreads = 256;
 //   px[kx] = exp(-i pi lambda dz qx^2), py[ky] = exp(-i pi lambda dz qy^2) / (nx ny),
 //   kymax[kx] = largest |ky| index with qx^2 + qy^2 <= qmax^2 (-1 if none),
 //   kymax[nx] = K, the largest |kx| index with qx^2 <= qmax^2: the columns
-//     kx <= K and kx >= nx - K are the ones the band limit keeps ("kept columns");
-//   kymax[nx + 1] = 0: set to 1 by the staged row pass if a bounded wait gives up.
+//     kx <= K and kx >= nx - K are the ones the band limit keeps ("kept columns").
 // The band limit zeroes every other column of the hybrid (k_x, y) wave, so the
 // passes skip them: the row pass neither reads nor writes them, the column pass
 // does not transform them (it writes their zeros only into the exit wave).
@@ -137,7 +140,6 @@ __global__ void ms_setup_kernel(float2* twx, float2* twy, float2* px, float2* py
             if (__dadd_rn(__dmul_rn(q, q), 0.0) <= qmax2) kk = k; else break;
         }
         kymax[nx] = kk;
-        kymax[nx + 1] = 0;               // error flag of the staged row pass
     }
     if (i < ny) {
         double s, c;
@@ -227,7 +229,10 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
 // group's wave rows and its potential rows into the other half of a two-stage
 // shared-memory ring.  The stage being transformed doubles as the FFT's
 // exchange buffer (one-buffer mode).  Same arithmetic as row_body, so the
-// results are identical; the waits are bounded and set *err on a timeout.
+// results are identical.  The waits for a group's data give up after
+// `polls` polls: the block then sets the status flag *err, stops, and waits
+// (with a fixed long bound) for the copies it has issued into both stages,
+// so no copy lands in shared memory after the block has exited.
 // The barrier of one row's transform threads: a named barrier per row when a
 // row spans several warps, the warp itself when it spans one or part of one.
 template <int TPT>
@@ -241,7 +246,7 @@ template <int NX>
 __global__ void __launch_bounds__(kRowThreads)
 row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, const float2* __restrict__ twx,
                        const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int n_groups,
-                       int* __restrict__ err) {
+                       int* __restrict__ err, uint32_t polls) {
     using namespace fft;
     constexpr int E = Plan<NX>::E;
     constexpr int TPT = NX / E;
@@ -286,15 +291,16 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     const int t = threadIdx.x % TPT;
     const int row = threadIdx.x / TPT;
     if (threadIdx.x == 0 && (int)blockIdx.x < n_groups) issue(blockIdx.x, 0);
-    int it = 0, pending = -1;                      // stage with a copy in flight at a break
+    int it = 0;
+    bool timed_out = false, next_issued = false;   // at a timeout: copies in flight into st and st ^ 1
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++it) {
         const int st = it & 1;
         const int gn = g + gridDim.x;
         if (threadIdx.x == 0 && gn < n_groups) issue(gn, st ^ 1);
-        const bool ok = tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 24);
+        const bool ok = tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, polls);
         if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicExch(err, 1);
-            pending = gn < n_groups ? st ^ 1 : -1;
+            timed_out = true;
+            next_issued = gn < n_groups;
             break;
         }
         float2* buf = reinterpret_cast<float2*>(stage_raw + st * STAGE);
@@ -320,7 +326,17 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
             if (kept_column(t + TPT * m, NX, K)) rowp[t + TPT * m] = v[m];
         __syncthreads();                           // this stage is refilled two groups later
     }
-    if (threadIdx.x == 0 && pending >= 0) tc::mbar_wait_quiet(&bar[pending], ((it + 1) >> 1) & 1, 1u << 24);
+    if (timed_out && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        // drain: the copy into stage it & 1 (whose wait gave up) and, if issued,
+        // the one into the other stage; each completes once its bytes land
+        const int st = it & 1;
+        for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 20); ++k) {
+        }
+        if (next_issued)
+            for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st ^ 1], ((it + 1) >> 1) & 1, 1u << 20); ++k) {
+            }
+    }
 }
 
 // Jobs of one batched launch (all of the same grid size): block row y of the
@@ -559,7 +575,7 @@ __global__ void snapshot_sum_kernel(const float2* __restrict__ psi, double2* __r
 template <int NX>
 cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const float2* twx,
                        const int* kymax, int ny, int n_t, int n_slices, int s, float sigma, int mode,
-                       cudaStream_t st) {
+                       WaitCtl wc, cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     if (mode == 0 && fft::Plan<NX>::E == 8 && reinterpret_cast<uintptr_t>(psi) % 16 == 0 &&
@@ -576,7 +592,7 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
             const int n_groups = (int)groups;
             const int blocks = resident < n_groups ? resident : n_groups;
             row_pass_staged_kernel<NX><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
-                                                                         n_groups, const_cast<int*>(kymax) + NX + 1);
+                                                                         n_groups, wc.flag, wc.polls);
             return cudaGetLastError();
         }
     }
@@ -644,8 +660,9 @@ cudaError_t launch_row_back(float2* g, const float2* state, const float* V, floa
 
 cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_in, const float2* twx,
                          const int* kymax, int ny, int n_t, int n_slices, int s, float sigma, int mode,
-                         cudaStream_t st) {
-    TACAW_SIZE_SWITCH(nx, return launch_row<N_>(psi, V, psi_in, twx, kymax, ny, n_t, n_slices, s, sigma, mode, st));
+                         WaitCtl wc, cudaStream_t st) {
+    TACAW_SIZE_SWITCH(nx, return launch_row<N_>(psi, V, psi_in, twx, kymax, ny, n_t, n_slices, s, sigma, mode, wc,
+                                                st));
     return cudaErrorInvalidValue;
 }
 
@@ -722,7 +739,7 @@ static MsTables carve_ms(Carver& cv, const tacaw_grid& g) {
     t.twy = cv.take<float2>(g.ny);
     t.px = cv.take<float2>(g.nx);
     t.py = cv.take<float2>(g.ny);
-    t.kymax = cv.take<int>(g.nx + 2);   // + K and an error flag (see ms_setup_kernel)
+    t.kymax = cv.take<int>(g.nx + 1);   // + K (see ms_setup_kernel)
     return t;
 }
 
@@ -732,10 +749,16 @@ size_t multislice_ws_bytes(const tacaw_grid& g) {
     return cv.bytes();
 }
 
+// Default poll limit of the staged row pass's waits (about a second or more).
+constexpr uint32_t kRowWaitPolls = 1u << 24;
+
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
                    float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st) {
     Carver cv(ws);
     MsTables tb = carve_ms(cv, g);
+    WaitCtl wc{nullptr, wait_polls(kRowWaitPolls)};
+    int rc = timeout_flag(&wc.flag, "tacaw_multislice");
+    if (rc) return rc;
     double lam = 0.0, sig = 0.0;
     beam_constants(g.kev, &lam, &sig);
     const double qmax = g.bandlimit * fmin((double)g.nx / (2.0 * g.lx), (double)g.ny / (2.0 * g.ly));
@@ -748,7 +771,7 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
     for (int s = 0; s < g.n_slices; ++s) {
         const int mode = s > 0 ? 0 : (psi_in ? 2 : 1);
         TACAW_CUDA_CHECK(dispatch_row(g.nx, psi_q, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s,
-                                      sigma, mode, st));
+                                      sigma, mode, wc, st));
         TACAW_CUDA_CHECK(dispatch_col(g.ny, psi_q, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t,
                                       s + 1 == g.n_slices, st));
     }
@@ -884,6 +907,9 @@ int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const 
     Carver cv(ws);
     MsBackWs b = carve_ms_back(cv, g, n_t, every);
     const MsTables& tb = b.tb;
+    WaitCtl wc{nullptr, wait_polls(kRowWaitPolls)};
+    int rc = timeout_flag(&wc.flag, "tacaw_multislice_backward");
+    if (rc) return rc;
     double lam = 0.0, sig = 0.0;
     beam_constants(g.kev, &lam, &sig);
     const double qmax = g.bandlimit * fmin((double)g.nx / (2.0 * g.lx), (double)g.ny / (2.0 * g.ly));
@@ -903,7 +929,7 @@ int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const 
             TACAW_CUDA_CHECK(cudaMemcpyAsync(b.ck + (size_t)(s / every) * wave, b.w, wave_bytes,
                                              cudaMemcpyDeviceToDevice, st));
         TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s, sigma,
-                                      s > 0 ? 0 : first_mode, st));
+                                      s > 0 ? 0 : first_mode, wc, st));
         TACAW_CUDA_CHECK(dispatch_col(g.ny, b.w, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st));
     }
     if (n_ck > 1 && (n_ck - 1) * every < g.n_slices)
@@ -922,7 +948,7 @@ int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const 
                                                  cudaMemcpyDeviceToDevice, st));
             for (int s = s0; s + 1 < s1; ++s) {
                 TACAW_CUDA_CHECK(dispatch_row(g.nx, b.w, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s,
-                                              sigma, s > 0 ? 0 : first_mode, st));
+                                              sigma, s > 0 ? 0 : first_mode, wc, st));
                 TACAW_CUDA_CHECK(dispatch_col(g.ny, b.w, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t, 0, st));
                 TACAW_CUDA_CHECK(cudaMemcpyAsync(b.seg + (size_t)(s + 1 - s0) * wave, b.w, wave_bytes,
                                                  cudaMemcpyDeviceToDevice, st));

@@ -6,12 +6,11 @@
 // can neither call cudaMalloc nor hand over a workspace buffer.
 //
 // The scratch holds only the per-call tables of the slice step (twiddles,
-// separable propagator factors, band-limit extents): at most 36 KiB for the
-// largest supported grid, so kStaticScratchBytes = 64 KiB covers every
-// supported size.  Every GPU that loads the library keeps this array until
-// the process exits.
-
-#include <mutex>
+// separable propagator factors, band-limit extents): 37120 bytes for the
+// largest supported grid, 1024 x 1024 (four 8192-byte float2 tables and
+// 1025 ints, each table starting on a 256-byte boundary), so
+// kStaticScratchBytes = 64 KiB covers every supported size.  Every GPU that
+// loads the library keeps this array until the process exits.
 
 #include "common.cuh"
 
@@ -25,36 +24,20 @@ bool multislice_size_supported(int n);
 namespace {
 
 constexpr size_t kStaticScratchBytes = 64 * 1024;
-constexpr int kMaxDevices = 64;
+constexpr size_t kLargestTablesBytes = 37120;   // multislice_ws_bytes at 1024 x 1024
+static_assert(kLargestTablesBytes <= kStaticScratchBytes, "the fixed scratch must hold the largest grid's tables");
 
 // One shared scratch block per device.  All calls on a device reuse it, so
 // two calls whose kernels overlap on the GPU (different streams, or graphs
 // replayed concurrently) overwrite each other's tables and race.
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// In host code g_static_scratch names a host-side shadow, not device memory;
-// the device address is looked up once per device with that device current.
+// In host code g_static_scratch names a host-side shadow, not device memory.
+// Its device address belongs to the current CUDA context; device_symbol looks
+// it up with that context current and caches it under the context's unique
+// id, so a context made after a device reset is looked up afresh.
 int static_scratch(void** out) {
-    int dev = -1;
-    TACAW_CUDA_CHECK(cudaGetDevice(&dev));
-    TACAW_REQUIRE(dev >= 0 && dev < kMaxDevices, TACAW_EUNSUPPORTED,
-                  "tacaw_multislice_static: device ordinal %d beyond %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            set_error("tacaw_multislice_static: cudaGetSymbolAddress failed: %s",
-                      cudaGetErrorString(e));
-            return TACAW_ECUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return TACAW_OK;
+    return device_symbol((const void*)g_static_scratch, out, "tacaw_multislice_static");
 }
 
 }  // namespace
@@ -78,6 +61,11 @@ extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, cons
                   TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     const size_t need = multislice_ws_bytes(*grid);
+    if (grid->nx == 1024 && grid->ny == 1024 && need != kLargestTablesBytes) {
+        set_error("%s: the tables of a 1024 x 1024 grid take %zu bytes, not the %zu this file states", fn, need,
+                  kLargestTablesBytes);
+        return TACAW_EUNSUPPORTED;
+    }
     TACAW_REQUIRE(need <= kStaticScratchBytes, TACAW_EINVAL,
                   "%s: this grid needs %zu bytes of scratch, more than the fixed %zu", fn, need,
                   kStaticScratchBytes);
@@ -85,8 +73,10 @@ extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, cons
     TACAW_REQUIRE(flags == 0, TACAW_EINVAL, "%s: flags must be 0", fn);
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
+    int rc = inject_launch_fault(fn);
+    if (rc) return rc;
     void* scratch = nullptr;
-    int rc = static_scratch(&scratch);
+    rc = static_scratch(&scratch);
     if (rc != TACAW_OK) return rc;
     // The tables are rewritten in full at the start of every call, so no part
     // of the shared array has to start at zero.

@@ -173,7 +173,8 @@ struct TcMaps {
 template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_power_kernel(const __grid_constant__ TcMaps maps, const float* __restrict__ kubo, float* __restrict__ out,
-                int nq, int n_w, int n_kblocks, int n_mtiles, int n_ntiles, float scale, int* __restrict__ err) {
+                int nq, int n_w, int n_kblocks, int n_mtiles, int n_ntiles, float scale, int* __restrict__ err,
+                int* __restrict__ status) {
     using Cfg = TcCfg<NT>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr int B_BYTES = Cfg::B_BYTES;
@@ -331,6 +332,9 @@ tc_power_kernel(const __grid_constant__ TcMaps maps, const float* __restrict__ k
     __syncthreads();
     tc::fence_after_sync();
     if (warp == MMA_WARP) tc::tmem_dealloc(tmem, TMEM_COLS);
+    // a role gave up: the launch's flag coordinated the roles; the sticky
+    // status flag reports it to the host (tacaw_status)
+    if (threadIdx.x == 0 && *(volatile int*)err) atomicExch(status, 1);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -458,16 +462,19 @@ int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega,
     if (rc) return rc;
     const float scale = (float)(1.0 / ((double)n_t * (double)n_t));
     const unsigned blocks = (unsigned)(g.n_mtiles * g.n_ntiles);
+    int* status = nullptr;
+    rc = timeout_flag(&status, "tacaw_spectrum");
+    if (rc) return rc;
     if (terms == 2) {
         TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<2>, (int)TcCfg<2>::SMEM));
         tc_power_kernel<2><<<blocks, TC_THREADS, TcCfg<2>::SMEM, st>>>(maps, kubo ? w.kubo : nullptr, out, nq, n_w,
                                                                       g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
-                                                                      w.err);
+                                                                      w.err, status);
     } else {
         TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<3>, (int)TcCfg<3>::SMEM));
         tc_power_kernel<3><<<blocks, TC_THREADS, TcCfg<3>::SMEM, st>>>(maps, kubo ? w.kubo : nullptr, out, nq, n_w,
                                                                       g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
-                                                                      w.err);
+                                                                      w.err, status);
     }
     TACAW_LAUNCH_CHECK();
     if (flags & TACAW_NORMALIZE) {

@@ -23,3 +23,4 @@ from .configs import (  # noqa: F401
     batching_jobs,
     build_inputs,
 )
+from .series import modulated_waves  # noqa: F401
