@@ -358,7 +358,8 @@ def run_ours(args):
             timed("potential", record, lambda: api.potential(
                 g, pos[t0:t1], species, inp.amp_sigma, out=v, workspace=tts._ws.get("pot")))
             timed("multislice", record, lambda: api.multislice(
-                g, v, out=tts.psi[t0:t1], psi_sum=tts.psi_sum, workspace=tts._ws.get("ms")))
+                g, v, out=tts.psi[t0:t1], psi_sum=tts.psi_sum, workspace=tts._ws.get("ms"),
+                warp_rows=tts.warp_rows))
         tts.precision = precision
         return timed("spectrum", record, tts.spectrum)
 
@@ -520,7 +521,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+bf16x3" if args.precision == "bf16x3" else "f32",
             "data": "synthetic",
-            "config": workload_config(w, {"batch": tts.batch, "spectrum_precision": args.precision,
+            "config": workload_config(w, {"batch": tts.batch, "warp_rows": tts.warp_rows,
+                                          "spectrum_precision": args.precision,
                                           "parallelism": "replicas" if world > 1 else "single GPU"}),
             "time_to_spectrum_ms": ms_step,
             "stage_ms": stages,
@@ -622,10 +624,10 @@ def plain_cufft_slice_step(tts, g, reps, stream):
     ref = run()
     ours = torch.empty_like(ref)
     from paper_2401_15599_gb300 import api
-    api.multislice(g, V, out=ours)
+    api.multislice(g, V, out=ours, warp_rows=tts.warp_rows)
     diff = float(torch.linalg.norm(ours - ref) / torch.linalg.norm(ref))
     ms = _events_ms(run, reps, stream)
-    ours_ms = _events_ms(lambda: api.multislice(g, V, out=ours), reps, stream)
+    ours_ms = _events_ms(lambda: api.multislice(g, V, out=ours, warp_rows=tts.warp_rows), reps, stream)
     return {"snapshots": int(V.shape[0]), "plain_cufft_ms": ms, "ours_ms": ours_ms,
             "speedup": ms / ours_ms, "rel_l2_difference": diff}
 

@@ -60,6 +60,11 @@ extern "C" {
                                    tacaw_multislice, or 2048, 4096) */
 #define TACAW_BF16X6 3          /* split BF16 (three terms), 6 products, FP32 accumulation */
 
+/* flags of tacaw_multislice */
+#define TACAW_MS_WARP_ROWS 1    /* 512-point rows: row pass with one warp per row (16 values per
+                                   thread) instead of two; same results to rounding, chosen by
+                                   the autotuner where faster; ignored for other sizes */
+
 /* flags of tacaw_spectrum */
 #define TACAW_KUBO 1            /* multiply by beta E / (1 - exp(-beta E)), Eq. (8) */
 #define TACAW_NORMALIZE 2       /* scale I and I_el so sum I + sum I_el = 1 */
@@ -176,7 +181,7 @@ int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
  *          used as the working buffer (no other scratch for the waves)
  * psi_sum  in/out [ny][nx] double2 running sum over snapshots, or NULL; when
  *          given, sum_t psi_q(t) is ADDED to it in FP64 (snapshot order)
- * flags    0 (reserved)
+ * flags    0 or TACAW_MS_WARP_ROWS (a variant of the row pass's thread layout)
  * Supported sizes: nx, ny in {64, 128, 256, 384, 512, 768, 1024}.
  */
 int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,
@@ -339,7 +344,9 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
  * plane wave on the caller's potentials V [max_batch][n_slices][ny][nx] (DEVICE)
  * into psi_q [max_batch][ny][nx] (DEVICE, overwritten) for n_candidates
  * snapshot batches candidates[i] (HOST, each in [1, max_batch]): one warm-up
- * call, then `reps` timed calls per candidate (CUDA events on `stream`).
+ * call, then `reps` timed calls per candidate (CUDA events on `stream`), every
+ * call with the tacaw_multislice `flags` given (so the caller can compare the
+ * row-pass variants as well).
  * ms_per_snapshot [n_candidates] (HOST out) receives the device time per
  * snapshot of each; *best_batch (HOST out) the fastest candidate.  Blocks the
  * calling thread until the timings are read (not for stream capture).
@@ -347,7 +354,7 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
  * sizes, TACAW_EUNSUPPORTED for grid sizes tacaw_multislice does not take.
  */
 int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float* V, void* psi_q,
-                          const int32_t* candidates, int32_t n_candidates, int32_t reps,
+                          const int32_t* candidates, int32_t n_candidates, int32_t reps, int32_t flags,
                           float* ms_per_snapshot, int32_t* best_batch, void* ws, size_t* ws_bytes,
                           void* stream);
 

@@ -28,6 +28,7 @@ TACAW_KUBO = 1
 TACAW_NORMALIZE = 2
 TACAW_MAX_SPECIES = 8
 TACAW_MAX_BATCH = 64
+TACAW_MS_WARP_ROWS = 1
 
 ERRORS = {
     TACAW_EINVAL: "EINVAL", TACAW_ECUDA: "ECUDA", TACAW_ENOMEM: "ENOMEM",
@@ -91,7 +92,7 @@ SIGNATURES = {
     "tacaw_relative_difference": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P]),
     "tacaw_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32] + [ctypes.c_double] * 7 + [_P, _P, _SZ, _P]),
     "tacaw_tune_multislice": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
-                                             ctypes.c_int32, _P, _P, _P, _SZ, _P]),
+                                             ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _SZ, _P]),
     "tacaw_spectrum_backward": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                ctypes.c_int32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "tacaw_multislice_backward": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,

@@ -90,8 +90,9 @@ def potential(grid, pos, species, amp_sigma, out=None, workspace=None):
     return out
 
 
-def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None):
-    """Exit waves psi_q [T, ny, nx] (complex64, q-space, FFT order) for potentials V."""
+def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None, warp_rows=False):
+    """Exit waves psi_q [T, ny, nx] (complex64, q-space, FFT order) for potentials V.
+    warp_rows: the row-pass variant with one warp per 512-point row (TACAW_MS_WARP_ROWS)."""
     lib = L.load()
     _need_cuda("V", V, torch.float32, 4)
     n_t = V.shape[0]
@@ -108,7 +109,7 @@ def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None):
 
     def call(ws, nbytes):
         return lib.tacaw_multislice(ctypes.byref(g), n_t, _ptr(V), _ptr(psi_in), _ptr(out), _ptr(psi_sum),
-                                    0, ws, nbytes, _stream(V.device))
+                                    L.TACAW_MS_WARP_ROWS if warp_rows else 0, ws, nbytes, _stream(V.device))
 
     nbytes = ctypes.c_size_t(0)
     L.check("tacaw_multislice", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))

@@ -38,7 +38,7 @@ void beam_constants(double kev, double* lambda_A, double* sigma_e) {
 bool multislice_size_supported(int n);
 size_t multislice_ws_bytes(const tacaw_grid& g);
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
-                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st);
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st, int flags);
 int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes);
 int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
                   int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st);
@@ -81,7 +81,7 @@ int probe_run(int nx, int ny, double lx, double ly, double lam, double alpha, do
 bool time_fft_size_supported(int n);
 
 int tune_multislice_run(const tacaw_grid& g, const float* V, float2* psi_q, const int* cand, int n_cand,
-                        int reps, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st);
+                        int reps, int flags, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st);
 
 static int check_grid(const tacaw_grid* g, const char* fn) {
     TACAW_REQUIRE(g != nullptr, TACAW_EINVAL, "%s: grid is NULL", fn);
@@ -167,7 +167,7 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
                   TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
-    TACAW_REQUIRE(flags == 0, TACAW_EINVAL, "%s: flags must be 0", fn);
+    TACAW_REQUIRE((flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     bool query = false;
     rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
     if (rc || query) return rc;
@@ -178,7 +178,7 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
         if (frc) return frc;
     }
     return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
-                          ws, (cudaStream_t)stream);
+                          ws, (cudaStream_t)stream, flags);
 }
 
 int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size_t* ws_bytes,
@@ -470,8 +470,8 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
 
 // ------------------------------------------------------------------ autotuning
 int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float* V, void* psi_q,
-                          const int32_t* candidates, int32_t n_candidates, int32_t reps, float* ms_per_snapshot,
-                          int32_t* best_batch, void* ws, size_t* ws_bytes, void* stream) {
+                          const int32_t* candidates, int32_t n_candidates, int32_t reps, int32_t flags,
+                          float* ms_per_snapshot, int32_t* best_batch, void* ws, size_t* ws_bytes, void* stream) {
     clear_error();
     const char* fn = "tacaw_tune_multislice";
     int rc = check_grid(grid, fn);
@@ -480,6 +480,7 @@ int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float
                   "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn, grid->nx, grid->ny);
     TACAW_REQUIRE(max_batch >= 1 && max_batch <= 65535 && n_candidates >= 1 && reps >= 1 && reps <= 1000,
                   TACAW_EINVAL, "%s: need 1 <= max_batch <= 65535, n_candidates >= 1, 1 <= reps <= 1000", fn);
+    TACAW_REQUIRE((flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     bool query = false;
     rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
     if (rc || query) return rc;
@@ -491,7 +492,7 @@ int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float
         const int frc = inject_launch_fault(fn);
         if (frc) return frc;
     }
-    return tune_multislice_run(*grid, V, (float2*)psi_q, candidates, n_candidates, reps, ms_per_snapshot,
+    return tune_multislice_run(*grid, V, (float2*)psi_q, candidates, n_candidates, reps, flags, ms_per_snapshot,
                                best_batch, ws, (cudaStream_t)stream);
 }
 

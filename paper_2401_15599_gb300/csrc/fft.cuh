@@ -134,6 +134,14 @@ struct Plan<384> { static constexpr int E = 24; using R = Radices<8, 8, 2, 3>; }
 template <>
 struct Plan<768> { static constexpr int E = 24; using R = Radices<8, 8, 4, 3>; };
 
+// Warp-per-row plans: one transform held by the 32 lanes of one warp, so
+// every exchange needs only __syncwarp.  512 points = 16 values per thread,
+// three radix-8 stages (two butterflies per thread per stage).
+template <int N>
+struct WarpPlan;
+template <>
+struct WarpPlan<512> { static constexpr int E = 16; using R = Radices<8, 8, 8>; };
+
 template <int A, int... Rest>
 struct First { static constexpr int value = A; };
 
@@ -258,11 +266,10 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b
     }
 }
 
-template <int N, bool INV, class L, class S, int R0, int... Rs>
-__device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[Plan<N>::E],
+template <int N, int E, bool INV, class L, class S, int R0, int... Rs>
+__device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[E],
                                                float2* b0, float2* b1, int t, const float2* tw,
                                                L lay, S sync) {
-    constexpr int E = Plan<N>::E;
     canon_to_stage<E, R0>(v);
     run_stages<N, E, INV, 1, 0, L, S, R0, Rs...>(v, b0, b1, t, tw, lay, sync);
 }
@@ -314,7 +321,16 @@ template <int N, bool INV, class L, class S = BlockSync>
 __device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, float2* b1, int t,
                                           const float2* tw, L lay, S sync = S{}) {
     sync();
-    transform_impl<N, INV, L, S>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync);
+    transform_impl<N, Plan<N>::E, INV, L, S>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync);
+}
+
+// The same with an explicit plan P (P::E values per thread, radices P::R; its
+// twiddle table is that of Plan<N> when the radices agree).
+template <class P, int N, bool INV, class L, class S>
+__device__ __forceinline__ void transform_plan(float2 (&v)[P::E], float2* b0, float2* b1, int t,
+                                               const float2* tw, L lay, S sync) {
+    sync();
+    transform_impl<N, P::E, INV, L, S>(typename P::R{}, v, b0, b1, t, tw, lay, sync);
 }
 
 }  // namespace fft

@@ -242,13 +242,15 @@ __device__ __forceinline__ auto row_sync_of(int row) {
     else return fft::WarpSync{};
 }
 
-template <int NX>
+// P is the transform plan: Plan<NX> (for 512 points: 8 values per thread, two
+// warps per row) or WarpPlan<NX> (16 values per thread, one warp per row).
+template <int NX, class P>
 __global__ void __launch_bounds__(kRowThreads)
 row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, const float2* __restrict__ twx,
                        const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int n_groups,
                        int* __restrict__ err, uint32_t polls) {
     using namespace fft;
-    constexpr int E = Plan<NX>::E;
+    constexpr int E = P::E;
     constexpr int TPT = NX / E;
     constexpr int ROWS = kRowThreads / TPT;
     constexpr int PSI_BYTES = ROWS * NX * (int)sizeof(float2);
@@ -311,14 +313,14 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
         for (int m = 0; m < E; ++m)
             v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * NX + t + TPT * m] : make_float2(0.f, 0.f);
         const auto row_sync = row_sync_of<TPT>(row);   // a row's transforms touch only its own row
-        transform<NX, true>(v, buf, buf, t, tw, lay, row_sync);
+        transform_plan<P, NX, true>(v, buf, buf, t, tw, lay, row_sync);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             float sn, cs;
             phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
             v[m] = cmul(v[m], make_float2(cs, sn));
         }
-        transform<NX, false>(v, buf, buf, t, tw, lay, row_sync);
+        transform_plan<P, NX, false>(v, buf, buf, t, tw, lay, row_sync);
         const int snap = g / groups_per_snap, y = (g % groups_per_snap) * ROWS + row;
         float2* rowp = psi + ((size_t)snap * ny + y) * NX;
 #pragma unroll
@@ -572,29 +574,52 @@ __global__ void snapshot_sum_kernel(const float2* __restrict__ psi, double2* __r
     sum[q] = acc;
 }
 
+// The staged row pass (slices after the first) with plan P.
+template <int NX, class P>
+cudaError_t launch_row_staged(float2* psi, const float* V, const float2* twx, const int* kymax, int ny, int n_t,
+                              int n_slices, int s, float sigma, WaitCtl wc, cudaStream_t st, bool* launched) {
+    constexpr int TPT = NX / P::E;
+    constexpr int ROWS = kRowThreads / TPT;
+    *launched = false;
+    const size_t smem = 2 * (size_t)ROWS * NX * (sizeof(float2) + sizeof(float)) +
+                        fft::TwSize<NX>::value * sizeof(float2) + 2 * sizeof(uint64_t);
+    cudaError_t e = ensure_smem((const void*)row_pass_staged_kernel<NX, P>, (int)smem);
+    if (e != cudaSuccess) return e;
+    int resident = 0;
+    e = resident_blocks((const void*)row_pass_staged_kernel<NX, P>, kRowThreads, (int)smem, &resident);
+    if (e != cudaSuccess) return e;
+    const long long groups = (long long)(ny / ROWS) * n_t;
+    if (groups > 0x7fffffffLL || ny % ROWS != 0) return cudaSuccess;
+    const int n_groups = (int)groups;
+    const int blocks = resident < n_groups ? resident : n_groups;
+    row_pass_staged_kernel<NX, P><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
+                                                                    n_groups, wc.flag, wc.polls);
+    *launched = true;
+    return cudaGetLastError();
+}
+
+// Row pass of slice s.  warp_rows: for 512-point rows, the staged pass with
+// one warp per row (WarpPlan) instead of two.
 template <int NX>
 cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const float2* twx,
                        const int* kymax, int ny, int n_t, int n_slices, int s, float sigma, int mode,
-                       WaitCtl wc, cudaStream_t st) {
+                       WaitCtl wc, bool warp_rows, cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
     if (mode == 0 && fft::Plan<NX>::E == 8 && reinterpret_cast<uintptr_t>(psi) % 16 == 0 &&
         reinterpret_cast<uintptr_t>(V) % 16 == 0) {
-        const size_t smem = 2 * (size_t)ROWS * NX * (sizeof(float2) + sizeof(float)) +
-                            fft::TwSize<NX>::value * sizeof(float2) + 2 * sizeof(uint64_t);
-        cudaError_t e = ensure_smem((const void*)row_pass_staged_kernel<NX>, (int)smem);
-        if (e != cudaSuccess) return e;
-        int resident = 0;
-        e = resident_blocks((const void*)row_pass_staged_kernel<NX>, kRowThreads, (int)smem, &resident);
-        if (e != cudaSuccess) return e;
-        const long long groups = (long long)(ny / ROWS) * n_t;
-        if (groups <= 0x7fffffffLL) {
-            const int n_groups = (int)groups;
-            const int blocks = resident < n_groups ? resident : n_groups;
-            row_pass_staged_kernel<NX><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
-                                                                         n_groups, wc.flag, wc.polls);
-            return cudaGetLastError();
+        bool launched = false;
+        cudaError_t e;
+        if constexpr (NX == 512) {
+            if (warp_rows) e = launch_row_staged<NX, fft::WarpPlan<NX>>(psi, V, twx, kymax, ny, n_t, n_slices, s,
+                                                                      sigma, wc, st, &launched);
+            else e = launch_row_staged<NX, fft::Plan<NX>>(psi, V, twx, kymax, ny, n_t, n_slices, s, sigma, wc, st,
+                                                         &launched);
+        } else {
+            e = launch_row_staged<NX, fft::Plan<NX>>(psi, V, twx, kymax, ny, n_t, n_slices, s, sigma, wc, st,
+                                                    &launched);
         }
+        if (e != cudaSuccess || launched) return e;
     }
     const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_pass_kernel<NX>, (int)smem);
@@ -660,9 +685,9 @@ cudaError_t launch_row_back(float2* g, const float2* state, const float* V, floa
 
 cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_in, const float2* twx,
                          const int* kymax, int ny, int n_t, int n_slices, int s, float sigma, int mode,
-                         WaitCtl wc, cudaStream_t st) {
+                         WaitCtl wc, cudaStream_t st, bool warp_rows = false) {
     TACAW_SIZE_SWITCH(nx, return launch_row<N_>(psi, V, psi_in, twx, kymax, ny, n_t, n_slices, s, sigma, mode, wc,
-                                                st));
+                                                warp_rows, st));
     return cudaErrorInvalidValue;
 }
 
@@ -753,7 +778,8 @@ size_t multislice_ws_bytes(const tacaw_grid& g) {
 constexpr uint32_t kRowWaitPolls = 1u << 24;
 
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
-                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st) {
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st, int flags) {
+    const bool warp_rows = (flags & TACAW_MS_WARP_ROWS) != 0;
     Carver cv(ws);
     MsTables tb = carve_ms(cv, g);
     WaitCtl wc{nullptr, wait_polls(kRowWaitPolls)};
@@ -771,7 +797,7 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
     for (int s = 0; s < g.n_slices; ++s) {
         const int mode = s > 0 ? 0 : (psi_in ? 2 : 1);
         TACAW_CUDA_CHECK(dispatch_row(g.nx, psi_q, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s,
-                                      sigma, mode, wc, st));
+                                      sigma, mode, wc, st, warp_rows));
         TACAW_CUDA_CHECK(dispatch_col(g.ny, psi_q, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t,
                                       s + 1 == g.n_slices, st));
     }

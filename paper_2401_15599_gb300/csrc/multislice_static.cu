@@ -18,7 +18,7 @@ namespace tacaw {
 
 size_t multislice_ws_bytes(const tacaw_grid& g);
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
-                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st);
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st, int flags);
 bool multislice_size_supported(int n);
 
 namespace {
@@ -70,7 +70,7 @@ extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, cons
                   "%s: this grid needs %zu bytes of scratch, more than the fixed %zu", fn, need,
                   kStaticScratchBytes);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
-    TACAW_REQUIRE(flags == 0, TACAW_EINVAL, "%s: flags must be 0", fn);
+    TACAW_REQUIRE((flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
     int rc = inject_launch_fault(fn);
@@ -81,5 +81,5 @@ extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, cons
     // The tables are rewritten in full at the start of every call, so no part
     // of the shared array has to start at zero.
     return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
-                          scratch, (cudaStream_t)stream);
+                          scratch, (cudaStream_t)stream, flags);
 }

@@ -26,6 +26,7 @@
 // The adjoint (potential_backward_kernel) keeps one block per band of 8 rows.
 
 #include <math.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -816,6 +817,289 @@ potential_slab_kernel(const int* __restrict__ bin_off, const float4* __restrict_
     store_tile_row(p, V, t, p.n_slices - 1, r0, c0, nrows, ncols, vec_out, acc_m);
 }
 
+// ------------------------------------------------------------------ forward, band walk
+// One block per (band of kBR rows, snapshot) walks the slices in order.  When
+// 6 s <= dz an atom of slab k reaches only slices k-1, k and k+1, so the block
+// builds, once per slab, the list of the slab's atoms whose window reaches the
+// band -- per atom its row factors amp-free gy over the band's rows, its slice
+// weights amp w_{k-1}, amp w_k, amp w_{k+1}, and its column and offset in the
+// pixel -- and keeps the lists of slabs s-1, s, s+1 in a ring of shared-memory
+// slots while it works on slice s.  Each list is sorted by the atom's pixel
+// column (periodic images of atoms near the left and right edges included as
+// entries of their own), so a thread that owns two adjacent columns of the band
+// runs over exactly the atoms whose window can reach them:
+//   v_s(x, y) = sum over slabs k = s-1, s, s+1 (in this order), over list
+//               entries in list order, of gy(y) * (amp w_s exp(-dx^2 / 2 s^2)).
+// List order is (column, position of the atom in the slab's bins), and the
+// bins hold atoms in input order, so the order -- and so the FP32 sum -- is
+// fixed by the configuration.  A slab whose list would not fit a slot is
+// processed per slice in chunks of sources through a fourth slot instead.
+constexpr int kBR = kBandRows;           // rows per band (the Bands bin layout)
+constexpr int kBCap = 160;               // list entries per slot
+constexpr int kBSlots = 4;               // slabs s-1, s, s+1 (ring of 3) + one slot for chunks
+constexpr int kBGroups = 129;            // 8-column groups for nx <= 1024, plus one
+constexpr int kBChunkSrc = kBCap / 3;    // sources per chunk (each gives at most 3 entries)
+constexpr int kBMaxBins = 32;            // bands within reach of a band (one warp scans them)
+constexpr int kBMaxNx = 1024;
+
+struct BandSmem {
+    float4 hd[kBSlots][kBCap];           // (column key as int bits, fx, log2(e) / (2 s^2), 6 s)
+    float4 g[kBSlots][kBCap][2];         // gy over the band's rows (0 outside |dy| <= 6 s)
+    float4 w[kBSlots][kBCap];            // amp w_{k-1}, amp w_k, amp w_{k+1}, 0
+    unsigned short first[kBSlots][kBGroups];
+    int n[kBSlots];                      // entries of the slot, or -1: slab processed in chunks
+    int tkey[kBCap];                     // keys in build order, for ranking
+    int bin_start[kBMaxBins], bin_cum[kBMaxBins + 1];
+    int warp_tot[kPotThreads / 32];
+};
+
+// Exclusive prefix sum of v over the block; *total receives the sum.  Ends
+// with a barrier.
+__device__ __forceinline__ int block_excl_scan(int v, int* warp_tot, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int c = warp_tot[w];
+        if (w < warp) before += c;
+        all += c;
+    }
+    *total = all;
+    __syncthreads();
+    return before + incl - v;
+}
+
+// Sources of slab k near band `band`: warp 0 loads the starts and counts of
+// the rb.count bins (k, band') with band' within reach and scans them into
+// bin_start / bin_cum.  Returns the slab's number of sources (after a barrier).
+__device__ int band_bins(BandSmem& sm, const PotParams& p, const int* __restrict__ off, int k, AxisRange rb) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int cnt = 0, start = 0;
+        if (lane < rb.count) {
+            const int bin = k * p.n_bands + (rb.first + lane) % p.n_bands;   // one column tile
+            start = __ldg(off + bin);
+            cnt = __ldg(off + bin + 1) - start;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane < rb.count) {
+            sm.bin_start[lane] = start;
+            sm.bin_cum[lane] = incl - cnt;
+        }
+        if (lane == 31) sm.bin_cum[rb.count] = incl;
+    }
+    __syncthreads();
+    return sm.bin_cum[rb.count];
+}
+
+// List of slab k's sources [src0, src1) (src1 - src0 <= blockDim.x; bin_start /
+// bin_cum loaded by band_bins) that reach the band's rows, into `slot`, sorted
+// by (column key, build position).  Returns the number of entries, or -1 when
+// they exceed kBCap (the slot is then unusable).  Ends with a barrier.
+__device__ int band_build(BandSmem& sm, int slot, const PotParams& p, const float4* __restrict__ atoms,
+                          const int2* __restrict__ atoms_px, int k, int src0, int src1, int nbins, int r0,
+                          int nrows, int kofs, int ngroups) {
+    const int src = src0 + (int)threadIdx.x;
+    int nkeys = 0, key[3] = {0, 0, 0};
+    float fx = 0.f, c2 = 0.f, rc = 0.f, g[kBR], w[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) g[r] = 0.f;
+    if (src < src1) {
+        int lo = 0, hi = nbins - 1;                      // the last bin starting at or before src
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.bin_cum[mid] <= src) lo = mid; else hi = mid - 1;
+        }
+        const int ai = sm.bin_start[lo] + (src - sm.bin_cum[lo]);
+        const float4 at = atoms[ai];                     // (fx, fy, z, species)
+        const int2 px = atoms_px[ai];                    // (ic, jc), wrapped
+        const int sp = __float_as_int(at.w);
+        bool ok = sp >= 0 && sp < p.n_species;
+        if (ok) {
+            rc = p.rc[sp];
+            c2 = p.c2[sp];
+            ok = range_gap(px.y, at.y, r0, nrows, p.ny, p.dy) <= rc;
+        }
+        if (ok) {
+            const float sg = p.sigma[sp], amp = p.amp[sp];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int s = k - 1 + j;
+                const float lo_z = slice_boundary(p, s), hi_z = slice_boundary(p, s + 1);
+                if (s >= 0 && s < p.n_slices && hi_z > at.z - rc && lo_z < at.z + rc)
+                    w[j] = amp * slice_weight(at.z, sg, lo_z, hi_z, s == 0, s == p.n_slices - 1, nullptr);
+            }
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) {
+                const int ky = nearest_image(r0 + r - px.y, p.ny);
+                const float d = small_int_to_float(ky) * p.dy - at.y;
+                g[r] = (r < nrows && fabsf(d) <= rc) ? exp2f(-(d * d) * c2) : 0.f;
+            }
+            fx = at.x;
+            key[nkeys++] = px.x + kofs;
+            if (px.x <= p.reach_x + 1) key[nkeys++] = px.x + p.nx + kofs;          // image to the right
+            if (px.x >= p.nx - p.reach_x - 2) key[nkeys++] = px.x - p.nx + kofs;   // image to the left
+        }
+    }
+    int total = 0;
+    const int base = block_excl_scan(nkeys, sm.warp_tot, &total);
+    if (total > kBCap) return -1;                        // uniform: every thread has the same total
+    for (int j = 0; j < nkeys; ++j) sm.tkey[base + j] = key[j];
+    __syncthreads();
+    for (int j = 0; j < nkeys; ++j) {
+        const int e = base + j, kj = key[j];
+        int rank = 0;
+        for (int m = 0; m < total; ++m) {
+            const int km = sm.tkey[m];
+            rank += (km < kj || (km == kj && m < e)) ? 1 : 0;
+        }
+        sm.hd[slot][rank] = make_float4(__int_as_float(kj), fx, c2, rc);
+        sm.g[slot][rank][0] = make_float4(g[0], g[1], g[2], g[3]);
+        sm.g[slot][rank][1] = make_float4(g[4], g[5], g[6], g[7]);
+        sm.w[slot][rank] = make_float4(w[0], w[1], w[2], 0.f);
+    }
+    __syncthreads();
+    // first[c]: the first entry whose key is >= the lowest key that can reach column group c
+    for (int c = threadIdx.x; c < ngroups; c += blockDim.x) {
+        const int want = 8 * c - p.reach_x - 1 + kofs;
+        int lo = 0, hi = total;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__float_as_int(sm.hd[slot][mid].x) < want) lo = mid + 1; else hi = mid;
+        }
+        sm.first[slot][c] = (unsigned short)lo;
+    }
+    if (threadIdx.x == 0) sm.n[slot] = total;
+    __syncthreads();
+    return total;
+}
+
+// Adds the list in `slot` to columns x0, x0 + 1 of the band for slice offset
+// widx (0: the slab below the slice, 1: its own, 2: the slab above).
+__device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, int widx, int x0, int reach, int kofs,
+                                                float d, float (&a0)[kBR], float (&a1)[kBR]) {
+    const int lo = x0 - reach - 1 + kofs, hi = x0 + reach + 2 + kofs;
+    const int n = sm.n[slot];
+    const float* wcol = reinterpret_cast<const float*>(&sm.w[slot][0]) + widx;
+    for (int i = sm.first[slot][x0 >> 3]; i < n; ++i) {
+        const float4 h = sm.hd[slot][i];
+        const int key = __float_as_int(h.x);
+        if (key > hi) break;
+        if (key < lo) continue;
+        const float wv = wcol[4 * i];
+        const int k0 = x0 + kofs - key;                  // column x0 minus the atom's column (this image)
+        const float dx0 = small_int_to_float(k0) * d - h.y;
+        const float dx1 = small_int_to_float(k0 + 1) * d - h.y;
+        const float g0 = fabsf(dx0) <= h.w ? wv * exp2f(-(dx0 * dx0) * h.z) : 0.f;
+        const float g1 = fabsf(dx1) <= h.w ? wv * exp2f(-(dx1 * dx1) * h.z) : 0.f;
+        const float4 ga = sm.g[slot][i][0], gb = sm.g[slot][i][1];
+        a0[0] = fmaf(ga.x, g0, a0[0]);
+        a0[1] = fmaf(ga.y, g0, a0[1]);
+        a0[2] = fmaf(ga.z, g0, a0[2]);
+        a0[3] = fmaf(ga.w, g0, a0[3]);
+        a0[4] = fmaf(gb.x, g0, a0[4]);
+        a0[5] = fmaf(gb.y, g0, a0[5]);
+        a0[6] = fmaf(gb.z, g0, a0[6]);
+        a0[7] = fmaf(gb.w, g0, a0[7]);
+        a1[0] = fmaf(ga.x, g1, a1[0]);
+        a1[1] = fmaf(ga.y, g1, a1[1]);
+        a1[2] = fmaf(ga.z, g1, a1[2]);
+        a1[3] = fmaf(ga.w, g1, a1[3]);
+        a1[4] = fmaf(gb.x, g1, a1[4]);
+        a1[5] = fmaf(gb.y, g1, a1[5]);
+        a1[6] = fmaf(gb.z, g1, a1[6]);
+        a1[7] = fmaf(gb.w, g1, a1[7]);
+    }
+}
+
+__global__ void __launch_bounds__(kPotThreads, 3)
+potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                      const int2* __restrict__ binned_px, PotParams p, int vec2, float* __restrict__ V) {
+    extern __shared__ __align__(16) unsigned char band_smem_raw[];
+    BandSmem& sm = *reinterpret_cast<BandSmem*>(band_smem_raw);
+    const int band = blockIdx.x;
+    const size_t t = blockIdx.y;
+    const int r0 = band * kBR, nrows = min(kBR, p.ny - r0);
+    const float4* atoms = binned + t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
+    const int* off = bin_off + t * (size_t)(p.n_bins + 1);
+    const AxisRange rb = axis_range(band, kBR, p.ny, p.n_bands, p.reach_y + 1);
+    const int kofs = p.reach_x + 2;                      // keys are columns + kofs >= 0
+    const int ngroups = (p.nx + 7) / 8;
+    const int passes = (p.nx + 2 * (int)blockDim.x - 1) / (2 * (int)blockDim.x);
+
+    // slab k's list into ring slot k % 3, or the slot marked for chunks
+    auto build_slab = [&](int k) {
+        const int nsrc = band_bins(sm, p, off, k, rb);
+        int n = -1;
+        if (nsrc <= (int)blockDim.x)
+            n = band_build(sm, k % 3, p, atoms, atoms_px, k, 0, nsrc, rb.count, r0, nrows, kofs, ngroups);
+        if (n < 0) {
+            if (threadIdx.x == 0) sm.n[k % 3] = -1;
+            __syncthreads();
+        }
+    };
+
+    for (int s = 0; s < p.n_slices; ++s) {
+        if (s == 0) {
+            build_slab(0);
+            if (p.n_slices > 1) build_slab(1);
+        } else if (s + 1 < p.n_slices) {
+            build_slab(s + 1);                           // replaces slab s - 2, last read in slice s - 1
+        }
+        for (int j = 0; j < passes; ++j) {
+            const int x0 = 2 * ((int)threadIdx.x + j * (int)blockDim.x);
+            const bool active = x0 < p.nx;
+            float a0[kBR], a1[kBR];
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) a0[r] = a1[r] = 0.f;
+            for (int k = max(0, s - 1); k <= min(p.n_slices - 1, s + 1); ++k) {
+                const int widx = s - k + 1;
+                if (sm.n[k % 3] >= 0) {
+                    if (active) band_accumulate(sm, k % 3, widx, x0, p.reach_x, kofs, p.dx, a0, a1);
+                    continue;
+                }
+                const int nsrc = band_bins(sm, p, off, k, rb);
+                for (int c0 = 0; c0 < nsrc; c0 += kBChunkSrc) {
+                    band_build(sm, 3, p, atoms, atoms_px, k, c0, min(nsrc, c0 + kBChunkSrc), rb.count, r0, nrows,
+                               kofs, ngroups);
+                    if (active) band_accumulate(sm, 3, widx, x0, p.reach_x, kofs, p.dx, a0, a1);
+                    __syncthreads();                     // slot 3 is rebuilt next
+                }
+            }
+            if (active) {
+                float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + r0) * p.nx + x0;
+                const bool two = x0 + 1 < p.nx;
+#pragma unroll
+                for (int r = 0; r < kBR; ++r) {
+                    if (r < nrows) {
+                        float* o = out + (size_t)r * p.nx;
+                        if (vec2) {
+                            *reinterpret_cast<float2*>(o) = make_float2(a0[r], a1[r]);
+                        } else {
+                            o[0] = a0[r];
+                            if (two) o[1] = a1[r];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();                                 // slice s + 1 rebuilds the slot of slab s - 1
+    }
+}
+
 // ------------------------------------------------------------------ adjoint
 // Candidate atoms of one block of the adjoint kernel, gathered per chunk of
 // source atoms.
@@ -1169,9 +1453,23 @@ int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n
 
 int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes) {
     Carver cv(nullptr);
-    carve_pot(cv, n_t, n_atoms, (int)clamp_bins(bin_shape(g, BinLayout::Tiles).n_bins));
+    const long long bins = std::max(clamp_bins(bin_shape(g, BinLayout::Tiles).n_bins),
+                                    clamp_bins(bin_shape(g, BinLayout::Bands).n_bins));
+    carve_pot(cv, n_t, n_atoms, (int)bins);
     *bytes = cv.bytes();
     return TACAW_OK;
+}
+
+// Parameters of the band-walking kernel, if it applies: every species has
+// 6 s <= dz (atoms reach only the neighbouring slices), the bands within
+// reach of a band fit one warp's scan, and nx <= kBMaxNx.
+static bool band_params(const tacaw_grid& g, int n_atoms, int n_species, const float* amp_sigma, PotParams* p) {
+    if (g.nx > kBMaxNx) return false;
+    if (make_params(g, n_atoms, n_species, amp_sigma, BinLayout::Bands, p) != TACAW_OK) {
+        clear_error();
+        return false;
+    }
+    return p->slab_reach <= 1 && p->n_ctiles == 1 && p->band_h == kBR && p->nb_max <= kBMaxBins;
 }
 
 static int run_binning(const PotParams& p, int n_t, const float* pos, const int* species, PotWs& w,
@@ -1195,6 +1493,21 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
     int rc = make_params(g, n_atoms, n_species, amp_sigma, BinLayout::Tiles, &p);
     if (rc == TACAW_OK) rc = check_launch_dims(g, n_t);
     if (rc != TACAW_OK) return rc;
+    PotParams pb;
+    if (band_params(g, n_atoms, n_species, amp_sigma, &pb)) {
+        // atoms reach at most the neighbouring slices: walk the slices once per band of rows
+        Carver cv(ws);
+        PotWs w = carve_pot(cv, n_t, n_atoms, pb.n_bins);
+        rc = run_binning(pb, n_t, pos, species, w, st);
+        if (rc != TACAW_OK) return rc;
+        const int vec2 = (g.nx % 2 == 0) && (reinterpret_cast<uintptr_t>(V) % 8 == 0);
+        const int bsm = (int)sizeof(BandSmem);
+        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel, bsm));
+        potential_band_kernel<<<dim3(pb.n_bands, n_t), kPotThreads, bsm, st>>>(w.bin_off, w.binned, w.binned_px,
+                                                                             pb, vec2, V);
+        TACAW_LAUNCH_CHECK();
+        return TACAW_OK;
+    }
     Carver cv(ws);
     PotWs w = carve_pot(cv, n_t, n_atoms, p.n_bins);
     rc = run_binning(p, n_t, pos, species, w, st);

@@ -1,5 +1,5 @@
-// Autotuning of the snapshot batch of the multislice: how many snapshots one
-// tacaw_multislice call advances together.  The slice step is two passes over
+// Autotuning of the multislice: how many snapshots one tacaw_multislice call
+// advances together (and, through `flags`, which row-pass variant it uses).  The slice step is two passes over
 // the batch's waves, so the batch sets how much of the wave stays in L2 between
 // the row and the column pass (32 snapshots of 512^2 are 64 MB) and how many
 // blocks each launch has.  The tuner times the real entry point on the
@@ -11,10 +11,10 @@ namespace tacaw {
 
 size_t multislice_ws_bytes(const tacaw_grid& g);
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
-                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st);
+                   float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st, int flags);
 
 int tune_multislice_run(const tacaw_grid& g, const float* V, float2* psi_q, const int* cand, int n_cand,
-                        int reps, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st) {
+                        int reps, int flags, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     TACAW_CUDA_CHECK(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -25,11 +25,11 @@ int tune_multislice_run(const tacaw_grid& g, const float* V, float2* psi_q, cons
     int rc = TACAW_OK;
     float best_ms = 0.f;
     for (int i = 0; i < n_cand && rc == TACAW_OK; ++i) {
-        rc = multislice_run(g, cand[i], V, nullptr, psi_q, nullptr, ws, st);     // warm-up
+        rc = multislice_run(g, cand[i], V, nullptr, psi_q, nullptr, ws, st, flags);     // warm-up
         if (rc) break;
         ce = cudaEventRecord(e0, st);
         for (int r = 0; r < reps && rc == TACAW_OK && ce == cudaSuccess; ++r)
-            rc = multislice_run(g, cand[i], V, nullptr, psi_q, nullptr, ws, st);
+            rc = multislice_run(g, cand[i], V, nullptr, psi_q, nullptr, ws, st, flags);
         if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
         if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -1,15 +1,19 @@
-"""Snapshot-batch autotuning with a JSON cache.
+"""Multislice autotuning with a JSON cache.
 
-``best_multislice_batch(grid)`` returns how many snapshots one multislice call
-should advance together on this GPU for this grid (candidates whose potentials
-would exceed MAX_TUNING_BYTES are skipped).  On a cache miss it times
-the candidates with the library's ``tacaw_tune_multislice`` (random slice
-potentials: the transform cost does not depend on the values) and stores the
-result under the key "<device name>|<nx>x<ny>x<n_slices>".
+``best_multislice_config(grid)`` returns how many snapshots one multislice
+call should advance together on this GPU for this grid, and which row-pass
+variant to use (for 512-point rows: two warps per row, or one warp per row,
+``warp_rows``); candidates whose potentials would exceed MAX_TUNING_BYTES are
+skipped.  On a cache miss it times every (batch, variant) pair with the
+library's ``tacaw_tune_multislice`` (random slice potentials: the transform
+cost does not depend on the values) and stores the result under the key
+"<device name>|<nx>x<ny>x<n_slices>".  ``best_multislice_batch`` returns the
+batch alone.
 
 The cache file is ``$TACAW_TUNE_CACHE`` when set, else
-``~/.cache/tacaw/tune.json``.  Entries hold the batch and the measured
-milliseconds per snapshot of every candidate.
+``~/.cache/tacaw/tune.json``.  Entries hold the batch, the variant and the
+measured milliseconds per snapshot of every candidate; entries written before
+the variant was tuned are tuned again.
 """
 
 from __future__ import annotations
@@ -57,8 +61,17 @@ def cache_key(grid, device_name: str) -> str:
     return f"{device_name}|{int(grid.nx)}x{int(grid.ny)}x{int(grid.n_slices)}"
 
 
-def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, device="cuda"):
-    """Time every candidate batch on this device: {batch: ms per snapshot}."""
+CACHE_VERSION = 2
+
+
+def row_variants(grid):
+    """tacaw_multislice flags worth comparing for this grid."""
+    return (0, L.TACAW_MS_WARP_ROWS) if int(grid.nx) == 512 else (0,)
+
+
+def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, device="cuda", flags=0):
+    """Time every candidate batch on this device with the given tacaw_multislice
+    flags: ({batch: ms per snapshot}, best batch)."""
     lib = L.load()
     dev = torch.device(device)
     per_snapshot = 4 * int(grid.n_slices) * int(grid.ny) * int(grid.nx)
@@ -76,8 +89,8 @@ def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, devi
 
     def call(ws, nbytes):
         return lib.tacaw_tune_multislice(ctypes.byref(g), top, ctypes.c_void_p(V.data_ptr()),
-                                         ctypes.c_void_p(psi.data_ptr()), c_arr, len(cand), int(reps), ms,
-                                         ctypes.byref(best), ws, nbytes, stream)
+                                         ctypes.c_void_p(psi.data_ptr()), c_arr, len(cand), int(reps), int(flags),
+                                         ms, ctypes.byref(best), ws, nbytes, stream)
 
     nbytes = ctypes.c_size_t(0)
     L.check("tacaw_tune_multislice", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
@@ -87,15 +100,30 @@ def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, devi
     return {c: float(m) for c, m in zip(cand, ms)}, int(best.value)
 
 
-def best_multislice_batch(grid, candidates=DEFAULT_CANDIDATES, device="cuda", path=None, measure=None):
-    """Cached best snapshot batch for this grid on this device (tuned on a miss).
-    ``measure`` replaces the timing function (tests)."""
+def best_multislice_config(grid, candidates=DEFAULT_CANDIDATES, device="cuda", path=None, measure=None):
+    """Cached best (batch, warp_rows) for this grid on this device (tuned on a
+    miss).  ``measure(grid, candidates, device=..., flags=...)`` replaces the
+    timing function (tests)."""
     dev = torch.device(device)
     name = torch.cuda.get_device_name(dev) if measure is None else "test-device"
     key = cache_key(grid, name)
     entry = load_cache(path).get(key)
-    if entry and int(entry.get("batch", 0)) >= 1:
-        return int(entry["batch"])
-    timings, best = (measure or measure_multislice_batches)(grid, candidates, device=device)
-    store_cache({key: {"batch": int(best), "ms_per_snapshot": {str(k): v for k, v in timings.items()}}}, path)
-    return int(best)
+    if entry and int(entry.get("version", 0)) == CACHE_VERSION and int(entry.get("batch", 0)) >= 1:
+        return int(entry["batch"]), bool(entry.get("warp_rows", False))
+    best = None
+    timings = {}
+    for flags in row_variants(grid):
+        t, b = (measure or measure_multislice_batches)(grid, candidates, device=device, flags=flags)
+        timings[str(flags)] = {str(k): v for k, v in t.items()}
+        if best is None or t[b] < best[0]:
+            best = (t[b], b, flags)
+    _, batch, flags = best
+    warp_rows = bool(flags & L.TACAW_MS_WARP_ROWS)
+    store_cache({key: {"version": CACHE_VERSION, "batch": int(batch), "warp_rows": warp_rows,
+                       "ms_per_snapshot": timings}}, path)
+    return int(batch), warp_rows
+
+
+def best_multislice_batch(grid, candidates=DEFAULT_CANDIDATES, device="cuda", path=None, measure=None):
+    """Cached best snapshot batch for this grid on this device (tuned on a miss)."""
+    return best_multislice_config(grid, candidates, device=device, path=path, measure=measure)[0]

@@ -70,8 +70,8 @@ def _entry_points(lib):
         ("tacaw_relative_difference", lambda: lib.tacaw_relative_difference(16, FAKE, FAKE, FAKE, NULL)),
         ("tacaw_probe", lambda: lib.tacaw_probe(64, 64, 32.0, 32.0, 200.0, 1.0, 0.0, 0.0, 0.0, FAKE, FAKE, _big(),
                                                 NULL)),
-        ("tacaw_tune_multislice", lambda: lib.tacaw_tune_multislice(ctypes.byref(g), 2, FAKE, FAKE, cands, 2, 1, ms,
-                                                                    ctypes.byref(best), FAKE, _big(), NULL)),
+        ("tacaw_tune_multislice", lambda: lib.tacaw_tune_multislice(ctypes.byref(g), 2, FAKE, FAKE, cands, 2, 1, 0,
+                                                                    ms, ctypes.byref(best), FAKE, _big(), NULL)),
     ]
 
 
@@ -108,7 +108,7 @@ def test_workspace_queries_and_argument_errors_come_first(lib, monkeypatch):
     assert n.value > 0
     assert lib.tacaw_multislice(ctypes.byref(g), -1, FAKE, NULL, FAKE, NULL, 0, FAKE, _big(),
                                 NULL) == L.TACAW_EINVAL
-    assert lib.tacaw_multislice_static(ctypes.byref(g), 2, FAKE, NULL, FAKE, NULL, 1, NULL) == L.TACAW_EINVAL
+    assert lib.tacaw_multislice_static(ctypes.byref(g), 2, FAKE, NULL, FAKE, NULL, 2, NULL) == L.TACAW_EINVAL
     assert lib.tacaw_multislice_static(ctypes.byref(g), 0, FAKE, NULL, FAKE, NULL, 0, NULL) == L.TACAW_OK
 
 

@@ -1,9 +1,11 @@
-"""GPU parity of the slab-walking slice-potential builder (used when every
-atom's z cut-off 6 s stays within one slice thickness, so an atom of slab k
-reaches only slices k-1, k and k+1) against the FP64 oracle: ragged grids, one
-and two slices, atoms beyond both ends of the stack and across the periodic
-edges, several species, and crowded slabs with more candidates than one
-tabulation chunk and more sources than one staged pass.  Bound as for the
+"""GPU parity of the slice-potential builder when every atom's z cut-off 6 s
+stays within one slice thickness, so an atom of slab k reaches only slices
+k-1, k and k+1 (the band-walking kernel: one block per band of 8 rows walks the
+slices with per-slab candidate lists sorted by column), against the FP64
+oracle: ragged grids (odd widths, a short last band, widths that take two
+column passes), one and two slices, atoms beyond both ends of the stack and
+across the periodic edges, several species, and crowded slabs whose candidate
+lists exceed a list slot (processed per slice in chunks).  Bound as for the
 other potential tests: 2e-6 of the peak; identical configurations give
 bit-identical potentials."""
 
@@ -41,7 +43,8 @@ def _check(api, g, pos, species, amp_sigma):
 # (nx, ny, lx, ly, n_slices, dz): every case has 6 s_max <= dz
 @pytest.mark.parametrize("shape", [(64, 64, 32.0, 32.0, 5, 2.0), (96, 40, 24.0, 10.0, 3, 2.5),
                                    (512, 512, 81.0, 81.0, 7, 2.0), (200, 136, 40.0, 27.0, 1, 2.0),
-                                   (128, 128, 40.5, 40.5, 2, 2.0)])
+                                   (128, 128, 40.5, 40.5, 2, 2.0), (97, 61, 24.25, 15.25, 3, 2.0),
+                                   (768, 100, 121.5, 15.8, 3, 2.0), (1024, 64, 162.0, 10.125, 2, 2.0)])
 def test_slab_walk_matches_oracle(api, shape):
     nx, ny, lx, ly, ns, dz = shape
     g = O.Grid(nx, ny, lx, ly, ns, dz, 0.5, 200.0, 2.0 / 3.0)

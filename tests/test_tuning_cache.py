@@ -1,6 +1,7 @@
-"""The snapshot-batch tuner's JSON cache (host logic, CPU): a miss measures
-and stores, a hit does not measure again, entries of other grids survive, a
-corrupt file counts as empty."""
+"""The multislice tuner's JSON cache (host logic, CPU): a miss measures every
+row-pass variant and stores the best (batch, variant), a hit does not measure
+again, entries of other grids survive, a corrupt file or an entry written
+before the variant was tuned counts as a miss."""
 
 import json
 
@@ -16,27 +17,44 @@ def test_miss_measures_and_hit_reuses(tmp_path):
     path = str(tmp_path / "tune.json")
     calls = []
 
-    def fake(grid, candidates, device="cuda"):
-        calls.append((grid.nx, tuple(candidates)))
-        t = {c: 1.0 / c + (0.5 if c == 32 else 0.0) for c in candidates}
+    def fake(grid, candidates, device="cuda", flags=0):
+        calls.append((grid.nx, tuple(candidates), flags))
+        t = {c: 1.0 / c + (0.5 if c == 32 else 0.0) - (0.001 if flags else 0.0) for c in candidates}
         return t, min(t, key=t.get)
 
     b1 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
-    assert b1 == 64 and len(calls) == 1
+    assert b1 == 64 and len(calls) == 1                     # 256-point rows: one variant
     b2 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
     assert b2 == 64 and len(calls) == 1                     # from the cache
-    tuning.best_multislice_batch(_grid(512, 101), candidates=(8, 16), path=path, measure=fake)
+    cfg = tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake)
+    assert cfg == (16, True) and len(calls) == 3            # 512-point rows: both variants timed
+    assert tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake) == (16, True)
     data = json.load(open(path))
-    assert len(calls) == 2 and len(data) == 2
+    assert len(calls) == 3 and len(data) == 2
     entry = data["test-device|256x256x10"]
-    assert entry["batch"] == 64 and set(entry["ms_per_snapshot"]) == {"8", "16", "32", "64"}
+    assert entry["batch"] == 64 and entry["warp_rows"] is False
+    assert set(entry["ms_per_snapshot"]["0"]) == {"8", "16", "32", "64"}
+
+
+def test_old_entries_are_tuned_again(tmp_path):
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({"test-device|512x512x101": {"batch": 8, "ms_per_snapshot": {"8": 1.0}}}))
+    calls = []
+
+    def fake(grid, candidates, device="cuda", flags=0):
+        calls.append(flags)
+        return {4: 2.0, 8: 1.0 + flags}, 8
+
+    assert tuning.best_multislice_config(_grid(512, 101), candidates=(4, 8), path=str(path),
+                                         measure=fake) == (8, False)
+    assert calls == [0, 1]
 
 
 def test_corrupt_cache_is_ignored(tmp_path):
     path = tmp_path / "tune.json"
     path.write_text("{not json")
     b = tuning.best_multislice_batch(_grid(), candidates=(4, 8), path=str(path),
-                                     measure=lambda g, c, device="cuda": ({4: 2.0, 8: 1.0}, 8))
+                                     measure=lambda g, c, device="cuda", flags=0: ({4: 2.0, 8: 1.0}, 8))
     assert b == 8 and json.load(open(path))["test-device|256x256x10"]["batch"] == 8
 
 
