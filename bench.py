@@ -9,9 +9,12 @@ metric is grid-point x slice x snapshot per second of that step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-With N > 1 (torchrun) every rank runs an independent replica of the
-workload (the path is not sharded across GPUs); value = all ranks' units /
-the slowest rank's time.
+With N > 1 (torchrun) the trajectory is sharded: each rank takes a
+contiguous block of snapshots (potentials and multislice), the FP64 sums of
+the exit waves are all-reduced, each rank accumulates its part of Phi(q, E)
+on the natural energies with the split-BF16 tensor-core transform, and Phi is
+reduce-scattered over q (NCCL); value = the whole trajectory's units / the
+slowest rank's time ("scaling": "strong").  --shard runs that path at N = 1.
 """
 
 from __future__ import annotations
@@ -60,6 +63,8 @@ def parse_args():
     p.add_argument("--spectrum-only", default="",
                    help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
                         "(a kernel micro-benchmark; not the benchmark line)")
+    p.add_argument("--shard", action="store_true",
+                   help="run the sharded multi-GPU path even on one GPU (the default for N > 1)")
     p.add_argument("--seg", default="512,256",
                    help="snapshots per set and offset for the set-averaged spectrum timing ('' = skip)")
     return p.parse_args()
@@ -715,12 +720,129 @@ def run_spectrum_only(args):
     return 0
 
 
+def natural_energies_meV(n_t, dt_fs):
+    """E_k = h (k - T/2) / (T dt), k = 0 .. T-1 (the natural grid, ascending)."""
+    import numpy as np
+    h = 6.62607015e-34 / 1.602176634e-19 * 1e3 * 1e15          # meV fs
+    return (np.arange(n_t) - n_t // 2) * (h / (n_t * dt_fs))
+
+
+def run_sharded(args):
+    """One trajectory over N GPUs (snapshot shards, all-reduce of the FP64 sums,
+    reduce-scatter of Phi over q); strong scaling."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2401_15599_gb300 import _lib, api
+    from paper_2401_15599_gb300.sharded import ShardedTimeToSpectrum, shard_bounds
+    from paper_2401_15599_gb300.tuning import best_multislice_config
+    import workloads as W
+
+    _lib.load()
+    w = workload(args)
+    g = w.grid
+    inp = W.build_inputs(w)
+    n_t = w.n_t
+    t_lo, t_hi = shard_bounds(n_t, world, rank)
+    batch, warp_rows = best_multislice_config(g, device=dev) if args.batch == "auto" else (int(args.batch), False)
+    batch = max(1, min(batch, t_hi - t_lo))
+    omega = natural_energies_meV(n_t, w.dt_fs)
+    sh = ShardedTimeToSpectrum(g, n_t, inp.crystal.n_atoms, inp.amp_sigma, w.dt_fs, omega, batch=batch,
+                               precision="bf16x6", device=dev, warp_rows=warp_rows)
+    pos_host = torch.from_numpy(inp.positions(list(range(t_lo, t_hi)))).pin_memory()
+    pos = pos_host.to(dev, non_blocking=True)
+    species = torch.from_numpy(inp.species).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        sh.run(pos, species)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        inten, iel = sh.run(pos, species)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    units = g.nx * g.ny * g.n_slices * n_t
+    value = units / (ms_step * 1e-3)
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty(tuple(inten.shape), dtype=torch.float32).pin_memory()
+        el_host = torch.empty(tuple(iel.shape), dtype=torch.float64).pin_memory()
+        s2 = torch.cuda.Event(enable_timing=True)
+        t2 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        s2.record(stream)
+        for _ in range(args.steps):
+            pos.copy_(pos_host, non_blocking=True)
+            a, b = sh.run(pos, species)
+            out_host.copy_(a, non_blocking=True)
+            el_host.copy_(b, non_blocking=True)
+        t2.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(s2.elapsed_time(t2) / args.steps, dev)
+        e2e = {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(pos_host.numel() * 4),
+               "d2h_bytes_per_step": int(out_host.numel() * 4 + el_host.numel() * 8), "ms_per_step": e2e_ms,
+               "call": "ShardedTimeToSpectrum.run with host copies of this rank's positions and I rows"}
+    # dominant kernel: one multislice call of `batch` snapshots of this rank
+    V = torch.empty((batch, g.n_slices, g.ny, g.nx), dtype=torch.float32, device=dev)
+    api.potential(g, pos[:batch], species, inp.amp_sigma, out=V)
+    out = torch.empty((batch, g.ny, g.nx), dtype=torch.complex64, device=dev)
+    api.multislice(g, V, out=out, warp_rows=warp_rows)
+    call_ms = _events_ms(lambda: api.multislice(g, V, out=out, warp_rows=warp_rows), 3, stream)
+    peak, _, peak_kind = load_peaks()
+    bytes_pt = slice_step_bytes(g)
+    achieved = bytes_pt * g.nx * g.ny * g.n_slices * batch / (call_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32+bf16x6", "data": "synthetic",
+            "config": workload_config(w, {"batch": batch, "warp_rows": warp_rows, "spectrum_precision": "bf16x6",
+                                          "spectrum": "natural energies as an explicit grid (n_omega = T)",
+                                          "parallelism": f"{world} snapshot shards; all-reduce of the FP64 sums; "
+                                                         f"reduce-scatter of Phi over q"}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"multislice slice step, one {batch}-snapshot call on rank 0",
+                         "bytes_per_unit": round(bytes_pt, 3), "peak_kind": f"{peak_kind} hbm_gbs"},
+            "cpu_baseline": None, "e2e": e2e,
+            # per rank and step: binning + potential and set-up + 2 passes per slice + sum per batch;
+            # mean; split A, split B, tensor-core transform; constant transform + finish
+            "gpu_launches": args.steps * world * (-(-(t_hi - t_lo) // batch) * (4 + 2 * g.n_slices) + 1 + 3 + 2),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.spectrum_only:
         return run_spectrum_only(args)
+    if args.shard or dist_env()[1] > 1:
+        return run_sharded(args)
     return run_ours(args)
 
 

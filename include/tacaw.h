@@ -243,6 +243,47 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
                    double temperature_K, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * Time-chunked spectra: Eq. (9) for a trajectory whose exit waves are never
+ * all resident at once (long trajectories, many jobs), or whose snapshots are
+ * spread over several GPUs.  With A = psi - m the inelastic transform is
+ * linear in the snapshots, so it can be summed chunk by chunk; the mean m is
+ * only known at the end, so every chunk is centred on a reference mean m_ref
+ * (any fixed estimate, e.g. the mean of the first chunk, or the exact mean
+ * when it is known) and the finishing call removes the rest in FP64:
+ *
+ *   Phi_ref(q, E_k) = sum_n (psi(q, t_n) - m_ref_q) exp(-i E_k t_n / hbar)
+ *   Phi(q, E_k)     = Phi_ref(q, E_k) - (m_q - m_ref_q) S(E_k),
+ *   S(E)            = sum_{n < T} exp(-i E t_n / hbar),   m_q = psi_sum_q / T
+ *
+ * Centring on a close reference keeps the summed terms small (the inelastic
+ * signal is a small difference of large terms, as for tacaw_spectrum).
+ *
+ * tacaw_time_mean: mean [nq] double2 = psi_sum [nq] double2 / n (FP64).
+ *
+ * tacaw_spectrum_accumulate: phi [nq][n_omega] float2 (in/out) +=
+ *   sum_{j < n_chunk} (psi[j][q] - m_ref[q]) exp(-i E_k (t0 + j) dt / hbar),
+ *   for the chunk psi [n_chunk][nq] float2 of snapshots t0 .. t0 + n_chunk - 1;
+ *   omega_meV DEVICE [n_omega] (required; pass the natural energies for the
+ *   natural grid of the whole trajectory); precision TACAW_FP32, TACAW_BF16X6
+ *   or TACAW_BF16X3 (as for tacaw_spectrum).  Workspace: query with ws == NULL.
+ *
+ * tacaw_spectrum_finish: I [nq][n_omega] float = |Phi|^2 / T^2 (times the Kubo
+ *   factor with TACAW_KUBO), I_el [nq] double = |m|^2 (or NULL), from the
+ *   accumulated phi, the m_ref used for every chunk and psi_sum = sum over all
+ *   T snapshots (FP64); TACAW_NORMALIZE as in tacaw_spectrum (over these nq).
+ *   S(E) and the correction are FP64.  Workspace: query with ws == NULL.
+ * Errors: TACAW_EINVAL for sizes, NULL arrays, missing energies, unknown
+ * precision or flags; TACAW_EUNSUPPORTED above 32640 energies on tensor cores.
+ */
+int tacaw_time_mean(int32_t nq, int32_t n, const void* psi_sum, void* mean, void* stream);
+int tacaw_spectrum_accumulate(int32_t nq, int32_t t0, int32_t n_chunk, double dt_fs, int32_t n_omega,
+                              const double* omega_meV, const void* psi, const void* m_ref, void* phi,
+                              int32_t precision, void* ws, size_t* ws_bytes, void* stream);
+int tacaw_spectrum_finish(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const double* omega_meV,
+                          const void* phi, const void* m_ref, const void* psi_sum, float* I, double* I_el,
+                          int32_t flags, double temperature_K, void* ws, size_t* ws_bytes, void* stream);
+
+/*
  * Spectrum averaged over sets of consecutive snapshots (the averaging over
  * segments of one trajectory described after Eq. (9); the paper averages,
  * e.g., 79 sets of 100 snapshots offset by 50).  Set g = 0 .. n_sets-1 holds

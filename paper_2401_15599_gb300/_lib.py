@@ -83,6 +83,11 @@ SIGNATURES = {
                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _P, _SZ, _P]),
     "tacaw_qep_intensity": (ctypes.c_int, [ctypes.c_int32] * 5 + [_P, _P, _P]),
+    "tacaw_time_mean": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "tacaw_spectrum_accumulate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                 ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, _SZ, _P]),
+    "tacaw_spectrum_finish": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P,
+                                             _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double, _P, _SZ, _P]),
     "tacaw_energy_integral": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
     "tacaw_line_profile": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                           _P, _P, _P, _P]),

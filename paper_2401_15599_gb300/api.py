@@ -390,3 +390,69 @@ def multislice_batch(jobs, workspace=None):
     def call(ws, nbytes):
         return lib.tacaw_multislice_batch(arr, len(jobs), ws, nbytes, _stream(dev))
     _call_with_workspace("tacaw_multislice_batch", call, dev, workspace)
+
+
+def time_mean(psi_sum, n, out=None):
+    """mean [nq] (complex128) = psi_sum [nq] (complex128) / n, on the device."""
+    lib = L.load()
+    _need_cuda("psi_sum", psi_sum, torch.complex128)
+    nq = psi_sum.numel()
+    if out is None:
+        out = torch.empty(nq, dtype=torch.complex128, device=psi_sum.device)
+    _need_cuda("out", out, torch.complex128)
+    L.check("tacaw_time_mean", lib.tacaw_time_mean(nq, int(n), _ptr(psi_sum), _ptr(out), _stream(psi_sum.device)))
+    return out
+
+
+def spectrum_accumulate(psi_chunk, t0, dt_fs, omega_meV, m_ref, phi, precision="bf16x6", workspace=None):
+    """phi [nq, n_omega] (complex64, in/out) += the transform of the chunk
+    psi_chunk [n_chunk, nq] (snapshots t0 ..) centred on m_ref [nq] (complex128)."""
+    lib = L.load()
+    if psi_chunk.dim() > 2:
+        psi_chunk = psi_chunk.reshape(psi_chunk.shape[0], -1)
+    _need_cuda("psi_chunk", psi_chunk, torch.complex64, 2)
+    _need_cuda("m_ref", m_ref, torch.complex128)
+    _need_cuda("phi", phi, torch.complex64, 2)
+    n_chunk, nq = psi_chunk.shape
+    dev = psi_chunk.device
+    omega = torch.as_tensor(omega_meV, dtype=torch.float64).to(dev).contiguous()
+    n_w = omega.numel()
+    if tuple(phi.shape) != (nq, n_w) or m_ref.numel() != nq:
+        raise ValueError("phi must be [nq, n_omega] and m_ref [nq]")
+    prec = _PRECISION[precision]
+
+    def call(ws, nbytes):
+        return lib.tacaw_spectrum_accumulate(nq, int(t0), n_chunk, float(dt_fs), n_w, _ptr(omega), _ptr(psi_chunk),
+                                             _ptr(m_ref), _ptr(phi), prec, ws, nbytes, _stream(dev))
+
+    _call_with_workspace("tacaw_spectrum_accumulate", call, dev, workspace)
+    return phi
+
+
+def spectrum_finish(phi, n_t, dt_fs, omega_meV, m_ref, psi_sum, kubo=False, temperature_K=300.0,
+                    normalize=False, out=None, i_el=None, workspace=None):
+    """I [nq, n_omega] (float32) and I_el [nq] (float64) from the accumulated phi."""
+    lib = L.load()
+    _need_cuda("phi", phi, torch.complex64, 2)
+    _need_cuda("m_ref", m_ref, torch.complex128)
+    _need_cuda("psi_sum", psi_sum, torch.complex128)
+    nq, n_w = phi.shape
+    dev = phi.device
+    omega = torch.as_tensor(omega_meV, dtype=torch.float64).to(dev).contiguous()
+    if omega.numel() != n_w:
+        raise ValueError("omega_meV must have n_omega entries")
+    if out is None:
+        out = torch.empty((nq, n_w), dtype=torch.float32, device=dev)
+    if i_el is None:
+        i_el = torch.empty(nq, dtype=torch.float64, device=dev)
+    _need_cuda("out", out, torch.float32, 2)
+    _need_cuda("i_el", i_el, torch.float64, 1)
+    flags = (L.TACAW_KUBO if kubo else 0) | (L.TACAW_NORMALIZE if normalize else 0)
+
+    def call(ws, nbytes):
+        return lib.tacaw_spectrum_finish(nq, int(n_t), float(dt_fs), n_w, _ptr(omega), _ptr(phi), _ptr(m_ref),
+                                         _ptr(psi_sum), _ptr(out), _ptr(i_el), flags, float(temperature_K), ws,
+                                         nbytes, _stream(dev))
+
+    _call_with_workspace("tacaw_spectrum_finish", call, dev, workspace)
+    return out, i_el

@@ -80,6 +80,16 @@ int probe_run(int nx, int ny, double lx, double ly, double lam, double alpha, do
 
 bool time_fft_size_supported(int n);
 
+size_t spectrum_accumulate_ws_bytes(int nq, int n_chunk, int n_w, int precision);
+int spectrum_accumulate_run(int nq, int t0, int n_chunk, double dt_fs, int n_w, const double* omega,
+                            const float2* psi, size_t ld, const double2* m_ref, float2* phi, int precision,
+                            void* ws, cudaStream_t st);
+int time_mean_run(int nq, int n, const double2* sum, double2* mean, cudaStream_t st);
+size_t spectrum_finish_ws_bytes(int nq, int n_w);
+int spectrum_finish_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* phi,
+                        const double2* m_ref, const double2* psi_sum, float* out, double* i_el, int flags,
+                        double temperature_K, void* ws, cudaStream_t st);
+
 int tune_multislice_run(const tacaw_grid& g, const float* V, float2* psi_q, const int* cand, int n_cand,
                         int reps, int flags, float* ms_per_snapshot, int* best, void* ws, cudaStream_t st);
 
@@ -244,6 +254,60 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
     return spectrum_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
                         (const double2*)psi_sum, I, I_el, precision, flags, temperature_K, ws,
                         (cudaStream_t)stream);
+}
+
+int tacaw_time_mean(int32_t nq, int32_t n, const void* psi_sum, void* mean, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_time_mean";
+    TACAW_REQUIRE(nq > 0 && n > 0, TACAW_EINVAL, "%s: nq and n must be positive", fn);
+    TACAW_REQUIRE(psi_sum && mean, TACAW_EINVAL, "%s: NULL array", fn);
+    const int frc = inject_launch_fault(fn);
+    if (frc) return frc;
+    return time_mean_run(nq, n, (const double2*)psi_sum, (double2*)mean, (cudaStream_t)stream);
+}
+
+int tacaw_spectrum_accumulate(int32_t nq, int32_t t0, int32_t n_chunk, double dt_fs, int32_t n_omega,
+                              const double* omega_meV, const void* psi, const void* m_ref, void* phi,
+                              int32_t precision, void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_spectrum_accumulate";
+    TACAW_REQUIRE(nq > 0 && n_chunk > 0 && n_chunk <= 65535 && n_omega > 0 && t0 >= 0, TACAW_EINVAL,
+                  "%s: need nq, n_omega > 0, t0 >= 0 and n_chunk in [1, 65535]", fn);
+    TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
+    TACAW_REQUIRE(omega_meV != nullptr, TACAW_EINVAL, "%s: the energies are required", fn);
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_BF16X6, TACAW_EINVAL,
+                  "%s: precision must be TACAW_FP32, TACAW_BF16X3 or TACAW_BF16X6", fn);
+    TACAW_REQUIRE(precision == TACAW_FP32 || n_omega <= 32640, TACAW_EUNSUPPORTED,
+                  "%s: the tensor-core path takes at most 32640 energies", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, spectrum_accumulate_ws_bytes(nq, n_chunk, n_omega, precision), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(psi && m_ref && phi, TACAW_EINVAL, "%s: NULL array", fn);
+    const int frc = inject_launch_fault(fn);
+    if (frc) return frc;
+    return spectrum_accumulate_run(nq, t0, n_chunk, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
+                                   (const double2*)m_ref, (float2*)phi, precision, ws, (cudaStream_t)stream);
+}
+
+int tacaw_spectrum_finish(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const double* omega_meV,
+                          const void* phi, const void* m_ref, const void* psi_sum, float* I, double* I_el,
+                          int32_t flags, double temperature_K, void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_spectrum_finish";
+    TACAW_REQUIRE(nq > 0 && n_t > 0 && n_omega > 0, TACAW_EINVAL, "%s: nq, n_t, n_omega must be positive", fn);
+    TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
+    TACAW_REQUIRE(omega_meV != nullptr, TACAW_EINVAL, "%s: the energies are required", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)), TACAW_EINVAL,
+                  "%s: the Kubo factor needs a positive temperature", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, spectrum_finish_ws_bytes(nq, n_omega), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(phi && m_ref && psi_sum && I, TACAW_EINVAL, "%s: NULL array", fn);
+    const int frc = inject_launch_fault(fn);
+    if (frc) return frc;
+    return spectrum_finish_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)phi, (const double2*)m_ref,
+                               (const double2*)psi_sum, I, I_el, flags, temperature_K, ws, (cudaStream_t)stream);
 }
 
 int tacaw_spectrum_segments(int32_t nq, int32_t n_t, double dt_fs, int32_t seg_len, int32_t hop,

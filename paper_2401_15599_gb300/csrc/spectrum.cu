@@ -52,7 +52,7 @@ __global__ void centre_kernel(const float2* __restrict__ psi, size_t ld, const d
 // kubo[k] = beta E_k / (1 - exp(-beta E_k)) (1 at E = 0) when requested.
 __global__ void dft_table_kernel(float2* __restrict__ e, float* __restrict__ kubo,
                                  const double* __restrict__ omega, int n_t, int n_w, double dt,
-                                 double beta) {
+                                 double beta, int t0 = 0) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (k >= n_w) return;
@@ -65,7 +65,7 @@ __global__ void dft_table_kernel(float2* __restrict__ e, float* __restrict__ kub
         ek = (double)kk * kPlanckMeVfs / ((double)n_t * dt);
     } else {
         ek = omega[k];
-        const double cyc = ek * ((double)n * dt) / kPlanckMeVfs;
+        const double cyc = ek * ((double)(t0 + n) * dt) / kPlanckMeVfs;
         const double frac = cyc - rint(cyc);
         sincospi(-2.0 * frac, &s, &c);
     }
@@ -76,12 +76,14 @@ __global__ void dft_table_kernel(float2* __restrict__ e, float* __restrict__ kub
     }
 }
 
-// I[q][k] = |sum_n A[n][q] E[n][k]|^2 * scale (* kubo[k]), FP32 SIMT.
+// I[q][k] = |sum_n A[n][q] E[n][k]|^2 * scale (* kubo[k]), FP32 SIMT; with
+// phi_acc given, Phi itself is added to phi_acc[q][k] instead (time-chunked
+// accumulation, tacaw_spectrum_accumulate).
 constexpr int BM = 64, BN = 64, BK = 16;
 __global__ void __launch_bounds__(256)
 cgemm_power_kernel(const float2* __restrict__ a, const float2* __restrict__ e,
                    const float* __restrict__ kubo, float* __restrict__ out, int nq, int n_t,
-                   int n_w, float scale) {
+                   int n_w, float scale, float2* __restrict__ phi_acc = nullptr) {
     __shared__ float2 as[BK][BM];
     __shared__ float2 es[BK][BN];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -129,6 +131,12 @@ cgemm_power_kernel(const float2* __restrict__ a, const float2* __restrict__ e,
         for (int j = 0; j < 4; ++j) {
             const int k = w0 + tx + 16 * j;
             if (k >= n_w) continue;
+            if (phi_acc) {
+                float2* pp = phi_acc + (size_t)q * n_w + k;
+                const float2 old = *pp;
+                *pp = make_float2(old.x + acc[i][j].x, old.y + acc[i][j].y);
+                continue;
+            }
             float v = (acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y) * scale;
             if (kubo) v *= __ldg(kubo + k);
             out[(size_t)q * n_w + k] = v;
@@ -314,6 +322,79 @@ __global__ void kubo_kernel(float* __restrict__ kubo, const double* __restrict__
     kubo[k] = (be == 0.0) ? 1.0f : (float)(be / (-expm1(-be)));
 }
 
+// A = psi - m_ref in FP64, rounded to float (a chunk of snapshots).
+__global__ void centre_ref_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restrict__ m_ref,
+                                  float2* __restrict__ a, int nq) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (q >= nq) return;
+    const double2 m = m_ref[q];
+    const float2 v = __ldg(psi + (size_t)t * ld + q);
+    a[(size_t)t * nq + q] = make_float2((float)((double)v.x - m.x), (float)((double)v.y - m.y));
+}
+
+// mean[q] = sum[q] / n (FP64).
+__global__ void mean_kernel(const double2* __restrict__ sum, double2* __restrict__ mean, int n, int nq) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double2 s = sum[q];
+    mean[q] = make_double2(s.x / (double)n, s.y / (double)n);
+}
+
+// S[k] = sum_{n < T} exp(-i E_k n dt / hbar) in FP64, a fixed-order block sum
+// per energy (the transform of a constant: what the reference mean leaves
+// behind when it differs from the true mean).
+__global__ void __launch_bounds__(256)
+const_transform_kernel(const double* __restrict__ omega, int n_t, double dt, double2* __restrict__ s_out) {
+    __shared__ double sr[256], si[256];
+    const int k = blockIdx.x;
+    const double ek = omega[k];
+    double re = 0.0, im = 0.0;
+    for (int n = threadIdx.x; n < n_t; n += blockDim.x) {
+        const double cyc = ek * ((double)n * dt) / kPlanckMeVfs;
+        double sn, cs;
+        sincospi(-2.0 * (cyc - rint(cyc)), &sn, &cs);
+        re += cs;
+        im += sn;
+    }
+    sr[threadIdx.x] = re;
+    si[threadIdx.x] = im;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sr[threadIdx.x] += sr[threadIdx.x + h];
+            si[threadIdx.x] += si[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_out[k] = make_double2(sr[0], si[0]);
+}
+
+// Phi'(q, k) = Phi(q, k) - (m_q - m_ref_q) S[k] (FP64), I = |Phi'|^2 / T^2 (* kubo),
+// I_el = |m_q|^2 with m_q = sum_q / T.
+__global__ void finish_kernel(const float2* __restrict__ phi, const double2* __restrict__ m_ref,
+                              const double2* __restrict__ sum, const double2* __restrict__ s_k,
+                              const float* __restrict__ kubo, float* __restrict__ out, double* __restrict__ i_el,
+                              int nq, int n_t, int n_w, double scale) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nq * n_w) return;
+    const int q = (int)(i / n_w), k = (int)(i % n_w);
+    const double2 sm = sum[q], mr = m_ref[q];
+    const double inv_t = 1.0 / (double)n_t;
+    const double dr = sm.x * inv_t - mr.x, di = sm.y * inv_t - mr.y;
+    const double2 sk = s_k[k];
+    const float2 p = phi[(size_t)q * n_w + k];
+    const double pr = (double)p.x - (dr * sk.x - di * sk.y);
+    const double pi = (double)p.y - (dr * sk.y + di * sk.x);
+    double v = (pr * pr + pi * pi) * scale;
+    if (kubo) v *= (double)__ldg(kubo + k);
+    out[(size_t)q * n_w + k] = (float)v;
+    if (k == 0 && i_el) {
+        const double mx = sm.x * inv_t, my = sm.y * inv_t;
+        i_el[q] = mx * mx + my * my;
+    }
+}
+
 struct SpecWs {
     double2* sum;
     float2* a;
@@ -484,6 +565,86 @@ int spectrum_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, co
         TACAW_LAUNCH_CHECK();
         scale_kernel<<<1024, 256, 0, st>>>(out, n, i_el, nq, w.total);
         TACAW_LAUNCH_CHECK();
+    }
+    return TACAW_OK;
+}
+
+// ------------------------------------------------------------------ time-chunked spectra
+size_t spectrum_tc_accumulate_ws_bytes(int nq, int n_t, int n_w, int terms);
+int spectrum_tc_accumulate_run(int nq, int t0, int n_chunk, double dt_fs, int n_w, const double* omega,
+                               const float2* psi, size_t ld, const double2* m_ref, float2* phi, int terms,
+                               void* ws, cudaStream_t st);
+
+size_t spectrum_accumulate_ws_bytes(int nq, int n_chunk, int n_w, int precision) {
+    if (precision == TACAW_BF16X3) return spectrum_tc_accumulate_ws_bytes(nq, n_chunk, n_w, 2);
+    if (precision == TACAW_BF16X6) return spectrum_tc_accumulate_ws_bytes(nq, n_chunk, n_w, 3);
+    Carver cv(nullptr);
+    cv.take<float2>((size_t)n_chunk * nq);
+    cv.take<float2>((size_t)n_chunk * n_w);
+    return cv.bytes();
+}
+
+// phi[q][k] += sum_{j < n_chunk} (psi[j][q] - m_ref[q]) exp(-i E_k (t0 + j) dt / hbar)
+int spectrum_accumulate_run(int nq, int t0, int n_chunk, double dt_fs, int n_w, const double* omega,
+                            const float2* psi, size_t ld, const double2* m_ref, float2* phi, int precision,
+                            void* ws, cudaStream_t st) {
+    if (precision == TACAW_BF16X3 || precision == TACAW_BF16X6)
+        return spectrum_tc_accumulate_run(nq, t0, n_chunk, dt_fs, n_w, omega, psi, ld, m_ref, phi,
+                                          precision == TACAW_BF16X3 ? 2 : 3, ws, st);
+    Carver cv(ws);
+    float2* a = cv.take<float2>((size_t)n_chunk * nq);
+    float2* e = cv.take<float2>((size_t)n_chunk * n_w);
+    centre_ref_kernel<<<dim3((nq + 255) / 256, n_chunk), 256, 0, st>>>(psi, ld, m_ref, a, nq);
+    TACAW_LAUNCH_CHECK();
+    dft_table_kernel<<<dim3((n_w + 127) / 128, n_chunk), 128, 0, st>>>(e, nullptr, omega, n_chunk, n_w, dt_fs, 0.0,
+                                                                      t0);
+    TACAW_LAUNCH_CHECK();
+    cgemm_power_kernel<<<dim3((n_w + BN - 1) / BN, (nq + BM - 1) / BM), 256, 0, st>>>(a, e, nullptr, nullptr, nq,
+                                                                                    n_chunk, n_w, 0.f, phi);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+int time_mean_run(int nq, int n, const double2* sum, double2* mean, cudaStream_t st) {
+    mean_kernel<<<(nq + 255) / 256, 256, 0, st>>>(sum, mean, n, nq);
+    TACAW_LAUNCH_CHECK();
+    return TACAW_OK;
+}
+
+size_t spectrum_finish_ws_bytes(int nq, int n_w) {
+    Carver cv(nullptr);
+    cv.take<double2>(n_w);
+    cv.take<float>(n_w);
+    cv.take<double>(kRedBlocks + 1);
+    cv.take<double>(nq);
+    return cv.bytes();
+}
+
+int spectrum_finish_run(int nq, int n_t, double dt_fs, int n_w, const double* omega, const float2* phi,
+                        const double2* m_ref, const double2* psi_sum, float* out, double* i_el, int flags,
+                        double temperature_K, void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    double2* s_k = cv.take<double2>(n_w);
+    float* kubo = cv.take<float>(n_w);
+    double* red = cv.take<double>(kRedBlocks + 1);
+    double* iel_ws = cv.take<double>(nq);
+    double* iel = i_el ? i_el : iel_ws;
+    const_transform_kernel<<<n_w, 256, 0, st>>>(omega, n_t, dt_fs, s_k);
+    TACAW_LAUNCH_CHECK();
+    const bool use_kubo = (flags & TACAW_KUBO) != 0;
+    if (use_kubo) {
+        const double beta = 1.0 / (kBoltzmannMeVK * temperature_K);
+        kubo_kernel<<<(n_w + 255) / 256, 256, 0, st>>>(kubo, omega, n_t, n_w, dt_fs, beta);
+        TACAW_LAUNCH_CHECK();
+    }
+    const size_t n_el = (size_t)nq * n_w;
+    finish_kernel<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(phi, m_ref, psi_sum, s_k,
+                                                                  use_kubo ? kubo : nullptr, out, iel, nq, n_t, n_w,
+                                                                  1.0 / ((double)n_t * (double)n_t));
+    TACAW_LAUNCH_CHECK();
+    if (flags & TACAW_NORMALIZE) {
+        int rc = launch_normalize(out, (size_t)nq * n_w, i_el, iel, nq, red, red + kRedBlocks, st);
+        if (rc) return rc;
     }
     return TACAW_OK;
 }

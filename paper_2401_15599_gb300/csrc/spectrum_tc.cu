@@ -80,7 +80,7 @@ __device__ __forceinline__ void split_bf16(float x, int nt, __nv_bfloat16* t) {
 __global__ void __launch_bounds__(256)
 split_a_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restrict__ sum, int n_t,
                int nq, int t_pad, __nv_bfloat16* __restrict__ a0, __nv_bfloat16* __restrict__ a1,
-               __nv_bfloat16* __restrict__ a2, double* __restrict__ i_el) {
+               __nv_bfloat16* __restrict__ a2, double* __restrict__ i_el, const double2* __restrict__ mean = nullptr) {
     __shared__ float2 tile[32][33];
     const int q0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
@@ -88,7 +88,10 @@ split_a_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restr
     {
         const int q = q0 + tx;
         double mr = 0.0, mi = 0.0;
-        if (q < nq) {
+        if (q < nq && mean) {                        // a given reference mean (time-chunked spectra)
+            mr = mean[q].x;
+            mi = mean[q].y;
+        } else if (q < nq) {
             const double2 s = sum[q];
             mr = s.x * inv_t;
             mi = s.y * inv_t;
@@ -127,7 +130,8 @@ split_a_kernel(const float2* __restrict__ psi, size_t ld, const double2* __restr
 // computed in FP64 (exact integer phase on the natural grid), zero beyond n_w / T.
 __global__ void __launch_bounds__(128)
 split_b_kernel(const double* __restrict__ omega, int n_t, int n_w, int t_pad, double dt, int tn,
-               __nv_bfloat16* __restrict__ b0, __nv_bfloat16* __restrict__ b1, __nv_bfloat16* __restrict__ b2) {
+               __nv_bfloat16* __restrict__ b0, __nv_bfloat16* __restrict__ b1, __nv_bfloat16* __restrict__ b2,
+               int t0 = 0) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;   // time index
     const int j = blockIdx.y;                              // B' row
     if (n >= t_pad) return;
@@ -143,7 +147,7 @@ split_b_kernel(const double* __restrict__ omega, int n_t, int n_w, int t_pad, do
             if (r < 0) r += n_t;
             sincospi(-2.0 * (double)r / (double)n_t, &s, &co);
         } else {
-            const double cyc = omega[k] * ((double)n * dt) / kPlanckMeVfs;
+            const double cyc = omega[k] * ((double)(t0 + n) * dt) / kPlanckMeVfs;
             sincospi(-2.0 * (cyc - rint(cyc)), &s, &co);
         }
         er = (float)co;
@@ -174,7 +178,7 @@ template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_power_kernel(const __grid_constant__ TcMaps maps, const float* __restrict__ kubo, float* __restrict__ out,
                 int nq, int n_w, int n_kblocks, int n_mtiles, int n_ntiles, float scale, int* __restrict__ err,
-                int* __restrict__ status) {
+                int* __restrict__ status, float2* __restrict__ phi_acc) {
     using Cfg = TcCfg<NT>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr int B_BYTES = Cfg::B_BYTES;
@@ -302,7 +306,20 @@ tc_power_kernel(const __grid_constant__ TcMaps maps, const float* __restrict__ k
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
-        if (ok && !*(volatile int*)err) {
+        if (ok && !*(volatile int*)err && phi_acc) {   // time-chunked: add Phi itself
+            const int row = mt * TM + warp * 32 + lane;
+            if (row < nq) {
+                float2* prow = phi_acc + (size_t)row * n_w;
+#pragma unroll
+                for (int i = 0; i < TN / 2; ++i) {
+                    const int k = nt * (TN / 2) + i;
+                    if (k < n_w) {
+                        const float2 old = prow[k];
+                        prow[k] = make_float2(old.x + acc[i], old.y + acc[TN / 2 + i]);
+                    }
+                }
+            }
+        } else if (ok && !*(volatile int*)err) {
             const int row = mt * TM + warp * 32 + lane;
             if (row < nq) {
                 float* orow = out + (size_t)row * n_w;
@@ -469,18 +486,67 @@ int spectrum_tc_run(int nq, int n_t, double dt_fs, int n_w, const double* omega,
         TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<2>, (int)TcCfg<2>::SMEM));
         tc_power_kernel<2><<<blocks, TC_THREADS, TcCfg<2>::SMEM, st>>>(maps, kubo ? w.kubo : nullptr, out, nq, n_w,
                                                                       g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
-                                                                      w.err, status);
+                                                                      w.err, status, nullptr);
     } else {
         TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<3>, (int)TcCfg<3>::SMEM));
         tc_power_kernel<3><<<blocks, TC_THREADS, TcCfg<3>::SMEM, st>>>(maps, kubo ? w.kubo : nullptr, out, nq, n_w,
                                                                       g.n_kblocks, g.n_mtiles, g.n_ntiles, scale,
-                                                                      w.err, status);
+                                                                      w.err, status, nullptr);
     }
     TACAW_LAUNCH_CHECK();
     if (flags & TACAW_NORMALIZE) {
         rc = launch_normalize(out, (size_t)nq * n_w, i_el, iel, nq, w.red, w.red + normalize_ws_doubles() - 1, st);
         if (rc) return rc;
     }
+    return TACAW_OK;
+}
+
+// ------------------------------------------------------------------ time-chunked spectra
+// phi[q][k] += sum_{j < n_chunk} (psi[j][q] - m_ref[q]) exp(-i E_k (t0 + j) dt / hbar),
+// the same split-BF16 GEMM with the FP32 drains, Phi added in the epilogue.
+size_t spectrum_tc_accumulate_ws_bytes(int nq, int n_t, int n_w, int terms) {
+    Carver cv(nullptr);
+    carve_tc(cv, nq, n_t, n_w, false, false, terms);
+    return cv.bytes();
+}
+
+int spectrum_tc_accumulate_run(int nq, int t0, int n_chunk, double dt_fs, int n_w, const double* omega,
+                               const float2* psi, size_t ld, const double2* m_ref, float2* phi, int terms,
+                               void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    TcWs w = carve_tc(cv, nq, n_chunk, n_w, false, false, terms);
+    const TcGeom g = geom(nq, n_chunk, n_w, terms);
+    TACAW_REQUIRE((size_t)g.n_mtiles * g.n_ntiles <= 0x7fffffffu, TACAW_EUNSUPPORTED,
+                  "tacaw_spectrum_accumulate: too many output tiles");
+    TACAW_CUDA_CHECK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    split_a_kernel<<<dim3(g.nq_pad / 32, g.t_pad / 32), 256, 0, st>>>(psi, ld, nullptr, n_chunk, nq, g.t_pad, w.a[0],
+                                                                      w.a[1], w.a[2], nullptr, m_ref);
+    TACAW_LAUNCH_CHECK();
+    split_b_kernel<<<dim3((g.t_pad + 127) / 128, g.n_ntiles * g.tn), 128, 0, st>>>(omega, n_chunk, n_w, g.t_pad, dt_fs,
+                                                                                 g.tn, w.b[0], w.b[1], w.b[2], t0);
+    TACAW_LAUNCH_CHECK();
+    TcMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    int rc = TACAW_OK;
+    for (int i = 0; i < terms && !rc; ++i) {
+        rc = make_map(&maps.a[i], w.a[i], g.nq_pad, g.k2, TM);
+        if (!rc) rc = make_map(&maps.b[i], w.b[i], (size_t)g.n_ntiles * g.tn, g.k2, g.tn);
+    }
+    if (rc) return rc;
+    int* status = nullptr;
+    rc = timeout_flag(&status, "tacaw_spectrum_accumulate");
+    if (rc) return rc;
+    const unsigned blocks = (unsigned)(g.n_mtiles * g.n_ntiles);
+    if (terms == 2) {
+        TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<2>, (int)TcCfg<2>::SMEM));
+        tc_power_kernel<2><<<blocks, TC_THREADS, TcCfg<2>::SMEM, st>>>(maps, nullptr, nullptr, nq, n_w, g.n_kblocks,
+                                                                      g.n_mtiles, g.n_ntiles, 1.f, w.err, status, phi);
+    } else {
+        TACAW_CUDA_CHECK(ensure_smem((const void*)tc_power_kernel<3>, (int)TcCfg<3>::SMEM));
+        tc_power_kernel<3><<<blocks, TC_THREADS, TcCfg<3>::SMEM, st>>>(maps, nullptr, nullptr, nq, n_w, g.n_kblocks,
+                                                                      g.n_mtiles, g.n_ntiles, 1.f, w.err, status, phi);
+    }
+    TACAW_LAUNCH_CHECK();
     return TACAW_OK;
 }
 

@@ -70,6 +70,11 @@ def _entry_points(lib):
         ("tacaw_relative_difference", lambda: lib.tacaw_relative_difference(16, FAKE, FAKE, FAKE, NULL)),
         ("tacaw_probe", lambda: lib.tacaw_probe(64, 64, 32.0, 32.0, 200.0, 1.0, 0.0, 0.0, 0.0, FAKE, FAKE, _big(),
                                                 NULL)),
+        ("tacaw_time_mean", lambda: lib.tacaw_time_mean(64, 8, FAKE, FAKE, NULL)),
+        ("tacaw_spectrum_accumulate", lambda: lib.tacaw_spectrum_accumulate(64, 0, 8, 5.0, 16, FAKE, FAKE, FAKE, FAKE,
+                                                                            L.TACAW_FP32, FAKE, _big(), NULL)),
+        ("tacaw_spectrum_finish", lambda: lib.tacaw_spectrum_finish(64, 8, 5.0, 16, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                                                    0, 300.0, FAKE, _big(), NULL)),
         ("tacaw_tune_multislice", lambda: lib.tacaw_tune_multislice(ctypes.byref(g), 2, FAKE, FAKE, cands, 2, 1, 0,
                                                                     ms, ctypes.byref(best), FAKE, _big(), NULL)),
     ]

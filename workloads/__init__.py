@@ -14,6 +14,7 @@ from .trajectory import (  # noqa: F401
     draw_modes,
     classical_amplitudes,
     positions,
+    TrajectorySynth,
     static_positions,
 )
 from .configs import (  # noqa: F401

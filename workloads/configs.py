@@ -161,6 +161,12 @@ class Inputs:
         """(T, Na, 3) positions for the given snapshot indices (default: all)."""
         return positions(self.crystal, self.modes, self.times(snapshots), dtype=dtype)
 
+    def synth(self, device):
+        """A TrajectorySynth of this workload's trajectory on `device`:
+        synth(t0, t1, out) gives the positions of snapshots t0 .. t1-1."""
+        from .trajectory import TrajectorySynth
+        return TrajectorySynth(self.crystal, self.modes, self.workload.dt_fs, device=device)
+
 
 def build_inputs(w: Workload) -> Inputs:
     """Build the crystal and modes of a workload.

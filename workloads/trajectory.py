@@ -173,3 +173,40 @@ def static_positions(crystal: Crystal, n_t: int, dtype=np.float32) -> np.ndarray
     """T identical snapshots of the equilibrium structure."""
     p = crystal.positions.astype(dtype)
     return np.broadcast_to(p[None], (n_t,) + p.shape).copy()
+
+
+class TrajectorySynth:
+    """Positions R_a + u_a(t_n) of a crystal and its harmonic modes synthesised
+    with torch on a device, window by window, for trajectories too large to
+    hold for every snapshot at once.  The per-atom mode coefficients are staged
+    on the device once; a window needs only device work (so it can be recorded
+    in a CUDA graph).  Same expansion of cos(theta - Omega t) as ``positions``:
+    phases and cos/sin in FP64, the mode sum in FP32, the result float32
+    (within two float32 ulps of ``positions``)."""
+
+    def __init__(self, crystal: Crystal, modes: HarmonicModes, dt_fs: float, device="cpu"):
+        import torch
+        self.device = torch.device(device)
+        self.dt = float(dt_fs)
+        r = crystal.positions.astype(np.float64)
+        theta = r @ modes.k.T + modes.phase[None, :]                       # (Na, M)
+        ae = modes.amp[:, None] * modes.e                                  # (M, 3)
+        coef = np.concatenate([np.cos(theta)[:, :, None] * ae[None], np.sin(theta)[:, :, None] * ae[None]],
+                              axis=1)                                      # (Na, 2M, 3)
+        self.coef = torch.as_tensor(coef.transpose(1, 0, 2).reshape(coef.shape[1], -1).astype(np.float32),
+                                    device=self.device)                    # (2M, Na * 3)
+        self.r = torch.as_tensor(r.reshape(-1), device=self.device)        # (Na * 3,) FP64
+        self.w = torch.as_tensor(modes.omega.astype(np.float64), device=self.device)
+        self.n_atoms = r.shape[0]
+
+    def __call__(self, t0: int, t1: int, out=None):
+        import torch
+        t = torch.arange(t0, t1, dtype=torch.float64, device=self.device) * self.dt
+        wt = torch.outer(t, self.w)
+        z = torch.cat([torch.cos(wt), torch.sin(wt)], dim=1).to(torch.float32)   # (T, 2M)
+        u = z @ self.coef                                                          # (T, Na * 3)
+        res = (self.r[None, :] + u.to(torch.float64)).to(torch.float32).reshape(t1 - t0, self.n_atoms, 3)
+        if out is not None:
+            out.copy_(res)
+            return out
+        return res
