@@ -63,6 +63,10 @@ def parse_args():
     p.add_argument("--spectrum-only", default="",
                    help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
                         "(a kernel micro-benchmark; not the benchmark line)")
+    p.add_argument("--no-c3", action="store_true",
+                   help="skip the full batched configuration (64 uneven jobs, 512-4096 snapshots each)")
+    p.add_argument("--c3-only", action="store_true",
+                   help="time only the full batched configuration (one eager run, then a CUDA-graph replay)")
     p.add_argument("--shard", action="store_true",
                    help="run the sharded multi-GPU path even on one GPU (the default for N > 1)")
     p.add_argument("--seg", default="512,256",
@@ -392,16 +396,22 @@ def run_ours(args):
     units_step = g.nx * g.ny * g.n_slices * n_t
     value = aggregate_rate(units_step, world, ms_step)
 
-    # end to end through the public host-input call: pinned host positions in (copied batch by
-    # batch on a copy stream, overlapping the work on the previous batch), host I(q, E) out;
-    # measured right after the device-timed steps, one untimed warm-up call first
+    # end to end through one library call with host buffers (tacaw_time_to_spectrum_host): pinned
+    # host positions in (copied batch by batch on the library's copy stream, overlapping the work
+    # on the previous batch), host I(q, E) and I_el out; one untimed warm-up call first
     e2e = None
     if not args.no_e2e:
         i_host = torch.empty(tts.I.shape, dtype=torch.float32).pin_memory()
         el_host = torch.empty(tts.I_el.shape, dtype=torch.float64).pin_memory()
-        tts.precision = args.precision
-        tts.run_host(pos_host, species, out=i_host, out_el=el_host)
-        tts.wait_host()
+        host_ws = None
+
+        def host_call():
+            return api.time_to_spectrum_host(g, pos_host, species, inp.amp_sigma, w.dt_fs, tts.batch,
+                                             warp_rows=tts.warp_rows, precision=args.precision, out=i_host,
+                                             out_el=el_host, workspace=host_ws)
+
+        host_ws = api.time_to_spectrum_host_workspace(g, n_t, n_atoms, tts.batch, args.precision, device=dev)
+        host_call()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -411,8 +421,7 @@ def run_ours(args):
         e2 = torch.cuda.Event(enable_timing=True)
         s2.record(stream)
         for _ in range(args.steps):
-            tts.run_host(pos_host, species, out=i_host, out_el=el_host)
-        tts.wait_host()                       # the last step's outputs are in host memory
+            host_call()
         e2.record(stream)
         torch.cuda.synchronize()
         clk_e2e = clocks_e2e.stop()
@@ -420,7 +429,10 @@ def run_ours(args):
         e2e = {"value": aggregate_rate(units_step, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(pos_host.numel() * 4),
                "d2h_bytes_per_step": int(i_host.numel() * 4 + el_host.numel() * 8),
-               "ms_per_step": e2e_ms, "call": "TimeToSpectrum.run_host", "clocks": clk_e2e}
+               "ms_per_step": e2e_ms, "call": "tacaw_time_to_spectrum_host (one C-ABI call, host buffers)",
+               "clocks": clk_e2e}
+        del host_ws
+        torch.cuda.empty_cache()
 
     def stage_ms(name):
         return [a.elapsed_time(b) for a, b in events[name]]
@@ -515,6 +527,19 @@ def run_ours(args):
             "adjoint": adjoint_sample(args.steps, stream),
         }
         torch.cuda.synchronize()
+        if not args.no_c3:
+            # the full batched configuration needs most of the device: free this run's buffers first
+            tts.psi = tts.V = tts.I = tts.I_el = None
+            tts._ws.clear()
+            tts._pos_stage = None
+            del pos
+            torch.cuda.empty_cache()
+            try:
+                further["batched_jobs_full"] = full_batched_jobs(stream)
+            except torch.OutOfMemoryError as exc:         # report, do not lose the benchmark line
+                further["batched_jobs_full"] = {"error": f"out of device memory: {exc}"[:300]}
+                torch.cuda.empty_cache()
+            torch.cuda.synchronize()
 
     n_batches = (n_t + tts.batch - 1) // tts.batch
     # twiddles, FFT | split A, split B, GEMM | centre, table, GEMM
@@ -658,6 +683,57 @@ def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=64):
     return {"jobs": n_jobs, "snapshots_per_job": snapshots, "window": 8, "units": units,
             "eager_ms": eager_ms, "graph_ms": graph_ms,
             "value_graph": units / (graph_ms * 1e-3), "unit": UNIT}
+
+
+def full_batched_jobs(stream, window=8, graph=False, max_jobs=64, max_snapshots=None):
+    """The batched configuration as stated: the 64 seeded uneven jobs (seeds
+    1000-1063; grids 128-768, 10-150 slices, 512-4096 snapshots, 1-3 species)
+    through the time-chunked batched driver: per window of snapshots, the
+    positions are synthesised on the device (the inputs of all jobs together
+    would take 94 GB), then slice potentials, one batched multislice call for
+    all jobs, and each job's Phi(q, E) accumulated on 1024 bins over
+    [-200, 200) meV in split BF16 (three terms); each job's I(q, E) is finished
+    at the end.  One eager run, timed with CUDA events (the synthesis of the
+    positions is inside the timed region and is timed separately too)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2401_15599_gb300.batch import BatchTimeToSpectrum, Job
+    omega = np.arange(1024) * (400.0 / 1024) - 200.0
+    jobs, units, synth_only = [], 0, []
+    for wj in W.batching_jobs(n_jobs=max_jobs):
+        if max_snapshots:
+            wj = wj.with_(n_t=min(wj.n_t, max_snapshots))
+        inp = W.build_inputs(wj)
+        synth = inp.synth("cuda")
+        jobs.append(Job(wj.grid, None, torch.from_numpy(inp.species).cuda(), inp.amp_sigma, wj.dt_fs,
+                        omega_meV=omega, n_t=wj.n_t, positions=synth))
+        synth_only.append((synth, wj.n_t, inp.crystal.n_atoms))
+        units += wj.grid.nx * wj.grid.ny * wj.grid.n_slices * wj.n_t
+    run = BatchTimeToSpectrum(jobs, window=window, precision="bf16x6", chunked=True)
+    run.prepare()
+    run.run()                                            # warm-up (fills the per-kernel attributes)
+    torch.cuda.synchronize()
+    ms = _events_ms(run.run, 1, stream)
+
+    def synth_all():
+        for synth, n_t, na in synth_only:
+            buf = torch.empty((window, na, 3), dtype=torch.float32, device="cuda")
+            for t0 in range(0, n_t, window):
+                synth(t0, min(n_t, t0 + window), out=buf[: min(n_t, t0 + window) - t0])
+
+    synth_ms = _events_ms(synth_all, 1, stream)
+    out = {"jobs": len(jobs), "snapshots": int(sum(j.n_t for j in jobs)), "window": window, "units": units,
+           "ms": ms, "value": units / (ms * 1e-3), "unit": UNIT, "position_synthesis_ms": synth_ms,
+           "value_without_synthesis": units / ((ms - synth_ms) * 1e-3),
+           "spectrum": "1024 bins over [-200, 200) meV, BF16X6, time-chunked"}
+    if graph:
+        run.capture()
+        out["graph_ms"] = _events_ms(run.replay, 1, stream)
+        out["value_graph"] = units / (out["graph_ms"] * 1e-3)
+    del run
+    torch.cuda.empty_cache()
+    return out
 
 
 def adjoint_sample(reps, stream, snapshots=64):
@@ -841,6 +917,13 @@ def main():
         return run_reference(args)
     if args.spectrum_only:
         return run_spectrum_only(args)
+    if args.c3_only:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2401_15599_gb300 import _lib
+        _lib.load()
+        print(json.dumps({"batched_jobs_full": full_batched_jobs(torch.cuda.current_stream(), graph=True)}))
+        return 0
     if args.shard or dist_env()[1] > 1:
         return run_sharded(args)
     return run_ours(args)

@@ -243,6 +243,33 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega,
                    double temperature_K, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * The whole path in one call, from host positions to host I(q, E): the
+ * procedure after Eq. (9) for a trajectory of T snapshots -- per batch of
+ * `batch` snapshots, the positions are copied to the device on a copy stream
+ * of the library's own (two staging buffers: the copy of the next batch
+ * overlaps the work on this one), then tacaw_potential and tacaw_multislice
+ * (ms_flags) with the FP64 running sum; then tacaw_spectrum on the natural
+ * energy grid (precision, flags, temperature_K as there); then I and I_el are
+ * copied back on `stream`.  Outputs are valid once `stream` reaches the end of
+ * the call.
+ *
+ * pos_host   HOST [T][n_atoms][3] float (page-locked memory lets the copies
+ *            overlap the compute; pageable memory works but serialises them)
+ * species    DEVICE [n_atoms] int32; amp_sigma HOST [n_species][2] as for
+ *            tacaw_potential
+ * I_host     HOST out [nx*ny][T] float;  I_el_host HOST out [nx*ny] double or NULL
+ * Workspace (device): the staging buffers, one batch of potentials, all exit
+ * waves, the device I and the workspaces of the three calls; query with
+ * ws == NULL.  Creates and destroys one stream and five events per call (not
+ * for stream capture).  Errors as for the three calls it chains.
+ */
+int tacaw_time_to_spectrum_host(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms, const float* pos_host,
+                                const int32_t* species, int32_t n_species, const float* amp_sigma, double dt_fs,
+                                int32_t batch, int32_t ms_flags, int32_t precision, int32_t flags,
+                                double temperature_K, float* I_host, double* I_el_host, void* ws, size_t* ws_bytes,
+                                void* stream);
+
+/*
  * Time-chunked spectra: Eq. (9) for a trajectory whose exit waves are never
  * all resident at once (long trajectories, many jobs), or whose snapshots are
  * spread over several GPUs.  With A = psi - m the inelastic transform is

@@ -84,6 +84,10 @@ SIGNATURES = {
                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _P, _SZ, _P]),
     "tacaw_qep_intensity": (ctypes.c_int, [ctypes.c_int32] * 5 + [_P, _P, _P]),
     "tacaw_time_mean": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "tacaw_time_to_spectrum_host": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.c_double,
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_double, _P, _P, _P, _SZ, _P]),
     "tacaw_spectrum_accumulate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                  ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, _SZ, _P]),
     "tacaw_spectrum_finish": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P,

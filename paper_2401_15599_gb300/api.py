@@ -456,3 +456,54 @@ def spectrum_finish(phi, n_t, dt_fs, omega_meV, m_ref, psi_sum, kubo=False, temp
 
     _call_with_workspace("tacaw_spectrum_finish", call, dev, workspace)
     return out, i_el
+
+
+def time_to_spectrum_host(grid, pos_host, species, amp_sigma, dt_fs, batch, warp_rows=False, precision="fft32",
+                          kubo=False, temperature_K=300.0, normalize=False, out=None, out_el=None, workspace=None):
+    """The whole path in one library call: positions pos_host [T, Na, 3]
+    (float32, CPU; page-locked for overlapped copies) -> I [nq, T] and I_el
+    [nq] in host memory (natural energy grid).  Outputs are valid once the
+    current stream has reached the end of the call."""
+    lib = L.load()
+    if pos_host.device.type != "cpu" or pos_host.dtype != torch.float32 or not pos_host.is_contiguous():
+        raise ValueError("pos_host must be a contiguous float32 CPU tensor")
+    _need_cuda("species", species, torch.int32, 1)
+    n_t, n_atoms = int(pos_host.shape[0]), int(pos_host.shape[1])
+    nq = int(grid.nx) * int(grid.ny)
+    if out is None:
+        out = torch.empty((nq, n_t), dtype=torch.float32).pin_memory()
+    if out_el is None:
+        out_el = torch.empty(nq, dtype=torch.float64).pin_memory()
+    if out.device.type != "cpu" or tuple(out.shape) != (nq, n_t) or out.dtype != torch.float32:
+        raise ValueError("out must be a float32 CPU tensor [nq, T]")
+    if out_el.device.type != "cpu" or out_el.numel() != nq or out_el.dtype != torch.float64:
+        raise ValueError("out_el must be a float64 CPU tensor [nq]")
+    amp = torch.as_tensor(amp_sigma, dtype=torch.float32).reshape(-1, 2).contiguous().cpu()
+    amp_c = (ctypes.c_float * amp.numel())(*amp.flatten().tolist())
+    g = L.make_grid(grid)
+    flags = (L.TACAW_KUBO if kubo else 0) | (L.TACAW_NORMALIZE if normalize else 0)
+    dev = species.device
+
+    def call(ws, nbytes):
+        return lib.tacaw_time_to_spectrum_host(ctypes.byref(g), n_t, n_atoms, ctypes.c_void_p(pos_host.data_ptr()),
+                                               _ptr(species), amp.shape[0], amp_c, float(dt_fs), int(batch),
+                                               L.TACAW_MS_WARP_ROWS if warp_rows else 0, _PRECISION[precision],
+                                               flags, float(temperature_K), ctypes.c_void_p(out.data_ptr()),
+                                               ctypes.c_void_p(out_el.data_ptr()), ws, nbytes, _stream(dev))
+
+    _call_with_workspace("tacaw_time_to_spectrum_host", call, dev, workspace)
+    return out, out_el
+
+
+def time_to_spectrum_host_workspace(grid, n_t, n_atoms, batch, precision="fft32", device="cuda"):
+    """A device workspace large enough for time_to_spectrum_host with these sizes."""
+    lib = L.load()
+    g = L.make_grid(grid)
+    amp = (ctypes.c_float * 2)(1.0, 1.0)
+    nbytes = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    L.check("tacaw_time_to_spectrum_host",
+            lib.tacaw_time_to_spectrum_host(ctypes.byref(g), int(n_t), int(n_atoms), null, null, 1, amp, 1.0,
+                                            int(batch), 0, _PRECISION[precision], 0, 300.0, null, null, null,
+                                            ctypes.byref(nbytes), null))
+    return torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=device)

@@ -80,6 +80,11 @@ int probe_run(int nx, int ny, double lx, double ly, double lam, double alpha, do
 
 bool time_fft_size_supported(int n);
 
+size_t host_path_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int batch, int precision);
+int host_path_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos_host, const int* species,
+                  int n_species, const float* amp_sigma, double dt_fs, int batch, int ms_flags, int precision,
+                  int flags, double temperature_K, float* I_host, double* I_el_host, void* ws, cudaStream_t st);
+
 size_t spectrum_accumulate_ws_bytes(int nq, int n_chunk, int n_w, int precision);
 int spectrum_accumulate_run(int nq, int t0, int n_chunk, double dt_fs, int n_w, const double* omega,
                             const float2* psi, size_t ld, const double2* m_ref, float2* phi, int precision,
@@ -254,6 +259,43 @@ int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const
     return spectrum_run(nq, n_t, dt_fs, n_omega, omega_meV, (const float2*)psi, (size_t)nq,
                         (const double2*)psi_sum, I, I_el, precision, flags, temperature_K, ws,
                         (cudaStream_t)stream);
+}
+
+int tacaw_time_to_spectrum_host(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms, const float* pos_host,
+                                const int32_t* species, int32_t n_species, const float* amp_sigma, double dt_fs,
+                                int32_t batch, int32_t ms_flags, int32_t precision, int32_t flags,
+                                double temperature_K, float* I_host, double* I_el_host, void* ws, size_t* ws_bytes,
+                                void* stream) {
+    clear_error();
+    const char* fn = "tacaw_time_to_spectrum_host";
+    int rc = check_grid(grid, fn);
+    if (rc) return rc;
+    TACAW_REQUIRE(multislice_size_supported(grid->nx) && multislice_size_supported(grid->ny), TACAW_EUNSUPPORTED,
+                  "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn, grid->nx, grid->ny);
+    TACAW_REQUIRE(n_t >= 1 && n_t <= 65535 && n_atoms >= 0 && batch >= 1, TACAW_EINVAL,
+                  "%s: need n_t in [1, 65535], n_atoms >= 0 and batch >= 1", fn);
+    TACAW_REQUIRE(n_species >= 1 && n_species <= TACAW_MAX_SPECIES && amp_sigma, TACAW_EINVAL,
+                  "%s: need 1..%d species with amp_sigma", fn, TACAW_MAX_SPECIES);
+    TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
+    TACAW_REQUIRE((ms_flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown multislice flags", fn);
+    TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_BF16X6 ||
+                      precision == TACAW_FFT32, TACAW_EINVAL, "%s: unknown precision %d", fn, precision);
+    TACAW_REQUIRE(precision != TACAW_FFT32 || time_fft_size_supported(n_t), TACAW_EUNSUPPORTED,
+                  "%s: TACAW_FFT32 has no plan for T = %d", fn, n_t);
+    TACAW_REQUIRE((precision != TACAW_BF16X3 && precision != TACAW_BF16X6) || n_t <= 32640, TACAW_EUNSUPPORTED,
+                  "%s: the tensor-core path takes at most 32640 energies", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_KUBO | TACAW_NORMALIZE)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE(!(flags & TACAW_KUBO) || (temperature_K > 0 && isfinite(temperature_K)), TACAW_EINVAL,
+                  "%s: the Kubo factor needs a positive temperature", fn);
+    const int b = batch < n_t ? batch : n_t;
+    bool query = false;
+    rc = check_ws(ws, ws_bytes, host_path_ws_bytes(*grid, n_t, n_atoms, b, precision), fn, &query);
+    if (rc || query) return rc;
+    TACAW_REQUIRE(pos_host && I_host && (n_atoms == 0 || species), TACAW_EINVAL, "%s: NULL array", fn);
+    const int frc = inject_launch_fault(fn);
+    if (frc) return frc;
+    return host_path_run(*grid, n_t, n_atoms, pos_host, species, n_species, amp_sigma, dt_fs, b, ms_flags, precision,
+                         flags, temperature_K, I_host, I_el_host, ws, (cudaStream_t)stream);
 }
 
 int tacaw_time_mean(int32_t nq, int32_t n, const void* psi_sum, void* mean, void* stream) {

@@ -71,6 +71,9 @@ def _entry_points(lib):
         ("tacaw_probe", lambda: lib.tacaw_probe(64, 64, 32.0, 32.0, 200.0, 1.0, 0.0, 0.0, 0.0, FAKE, FAKE, _big(),
                                                 NULL)),
         ("tacaw_time_mean", lambda: lib.tacaw_time_mean(64, 8, FAKE, FAKE, NULL)),
+        ("tacaw_time_to_spectrum_host", lambda: lib.tacaw_time_to_spectrum_host(
+            ctypes.byref(g), 64, 4, FAKE, FAKE, 1, amp, 5.0, 16, 0, L.TACAW_FFT32, 0, 300.0, FAKE, FAKE, FAKE, _big(),
+            NULL)),
         ("tacaw_spectrum_accumulate", lambda: lib.tacaw_spectrum_accumulate(64, 0, 8, 5.0, 16, FAKE, FAKE, FAKE, FAKE,
                                                                             L.TACAW_FP32, FAKE, _big(), NULL)),
         ("tacaw_spectrum_finish", lambda: lib.tacaw_spectrum_finish(64, 8, 5.0, 16, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
