@@ -63,6 +63,8 @@ def parse_args():
     p.add_argument("--spectrum-only", default="",
                    help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
                         "(a kernel micro-benchmark; not the benchmark line)")
+    p.add_argument("--warp-rows", choices=["auto", "0", "1"], default="auto",
+                   help="row-pass variant for 512-point rows: tuned (auto), two warps per row (0), one (1)")
     p.add_argument("--no-c3", action="store_true",
                    help="skip the full batched configuration (64 uneven jobs, 512-4096 snapshots each)")
     p.add_argument("--c3-only", action="store_true",
@@ -341,6 +343,12 @@ def run_ours(args):
         args.precision = "bf16x3"                 # no time-FFT plan for this T: the GEMM path
     tts = TimeToSpectrum(g, n_t, n_atoms, inp.amp_sigma, w.dt_fs, batch=args.batch, device=dev,
                          precision=args.precision)
+    if args.warp_rows != "auto":
+        tts.warp_rows = args.warp_rows == "1"
+    tuning = None
+    if args.batch == "auto":
+        from paper_2401_15599_gb300 import tuning as T
+        tuning = T.load_cache().get(T.cache_key(g, torch.cuda.get_device_name(dev)))
     tts.prepare(None, None)
     torch.cuda.synchronize()
 
@@ -551,6 +559,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+bf16x3" if args.precision == "bf16x3" else "f32",
             "data": "synthetic",
+            "tuning": tuning,
             "config": workload_config(w, {"batch": tts.batch, "warp_rows": tts.warp_rows,
                                           "spectrum_precision": args.precision,
                                           "parallelism": "replicas" if world > 1 else "single GPU"}),

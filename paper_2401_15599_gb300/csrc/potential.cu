@@ -821,37 +821,72 @@ potential_slab_kernel(const int* __restrict__ bin_off, const float4* __restrict_
 // One block per (band of kBR rows, snapshot) walks the slices in order.  When
 // 6 s <= dz an atom of slab k reaches only slices k-1, k and k+1, so the block
 // builds, once per slab, the list of the slab's atoms whose window reaches the
-// band -- per atom its row factors amp-free gy over the band's rows, its slice
-// weights amp w_{k-1}, amp w_k, amp w_{k+1}, and its column and offset in the
-// pixel -- and keeps the lists of slabs s-1, s, s+1 in a ring of shared-memory
-// slots while it works on slice s.  Each list is sorted by the atom's pixel
-// column (periodic images of atoms near the left and right edges included as
-// entries of their own), so a thread that owns two adjacent columns of the band
-// runs over exactly the atoms whose window can reach them:
+// band -- per atom its row factors gy over the band's rows, its weights
+// amp w_{k-1}, amp w_k, amp w_{k+1} (computed once per atom and snapshot by
+// atom_weights_kernel), and its column and offset in the pixel -- and keeps the
+// lists of slabs s-1 .. s+kB2Group in a ring of shared-memory slots.  Each list
+// is sorted by the atom's pixel column (periodic images of atoms near the left
+// and right edges included as entries of their own), so a thread that owns
+// kB2Cols adjacent columns of the band runs over exactly the atoms whose window
+// can reach them:
 //   v_s(x, y) = sum over slabs k = s-1, s, s+1 (in this order), over list
 //               entries in list order, of gy(y) * (amp w_s exp(-dx^2 / 2 s^2)).
 // List order is (column, position of the atom in the slab's bins), and the
 // bins hold atoms in input order, so the order -- and so the FP32 sum -- is
-// fixed by the configuration.  A slab whose list would not fit a slot is
-// processed per slice in chunks of sources through a fourth slot instead.
+// fixed by the configuration.  The lists of kB2Group slabs are built in one
+// round by all threads; a slab whose list would not fit a slot is processed
+// per slice in chunks of sources through one more slot.
 constexpr int kBR = kBandRows;           // rows per band (the Bands bin layout)
-constexpr int kBCap = 160;               // list entries per slot
-constexpr int kBSlots = 4;               // slabs s-1, s, s+1 (ring of 3) + one slot for chunks
+constexpr int kB2Threads = 128;
+constexpr int kB2Cols = 4;               // adjacent columns per thread
+constexpr int kB2Cap = 96;               // list entries per slot
+constexpr int kB2Group = 2;              // slabs built per round
+constexpr int kB2Ring = kB2Group + 2;    // slots for slabs s-1 .. s+kB2Group
+constexpr int kB2Chunk = kB2Ring;        // the slot for chunks of an over-full slab
+constexpr int kB2Slots = kB2Ring + 1;
+constexpr int kB2ChunkSrc = kB2Cap / 3;  // sources per chunk (each gives at most 3 entries)
 constexpr int kBGroups = 129;            // 8-column groups for nx <= 1024, plus one
-constexpr int kBChunkSrc = kBCap / 3;    // sources per chunk (each gives at most 3 entries)
 constexpr int kBMaxBins = 32;            // bands within reach of a band (one warp scans them)
 constexpr int kBMaxNx = 1024;
+static_assert(kB2Cap <= 255, "first[] holds list positions in a byte");
 
 struct BandSmem {
-    float4 hd[kBSlots][kBCap];           // (column key as int bits, fx, log2(e) / (2 s^2), 6 s)
-    float4 g[kBSlots][kBCap][2];         // gy over the band's rows (0 outside |dy| <= 6 s)
-    float4 w[kBSlots][kBCap];            // amp w_{k-1}, amp w_k, amp w_{k+1}, 0
-    unsigned short first[kBSlots][kBGroups];
-    int n[kBSlots];                      // entries of the slot, or -1: slab processed in chunks
-    int tkey[kBCap];                     // keys in build order, for ranking
-    int bin_start[kBMaxBins], bin_cum[kBMaxBins + 1];
-    int warp_tot[kPotThreads / 32];
+    float4 hd[kB2Slots][kB2Cap];         // (column key as int bits, fx, log2(e) / (2 s^2), 6 s)
+    float4 g[kB2Slots][kB2Cap][2];       // gy over the band's rows (0 outside |dy| <= 6 s)
+    float4 w[kB2Slots][kB2Cap];          // amp w_{k-1}, amp w_k, amp w_{k+1}, 0
+    unsigned char first[kB2Slots][kBGroups];
+    int n[kB2Slots];                     // entries of the slot, or -1: slab processed in chunks
+    int tkey[kB2Threads * 3];            // keys in build order, for ranking
+    int bin_start[kB2Group][kBMaxBins], bin_cum[kB2Group][kBMaxBins + 1];
+    int nsrc[kB2Group];                  // sources of each slab of the round
+    int lstart[kB2Group + 1];            // build positions where each slab's entries start
+    int warp_tot[kB2Threads / 32];
 };
+
+// Slice weights amp w_{k-1}, amp w_k, amp w_{k+1} of every binned atom, k its
+// slab (the same rounded expression as the binning), 0 for slices outside the
+// stack or the 6 s window and for skipped atoms.
+__global__ void atom_weights_kernel(const float4* __restrict__ binned, float4* __restrict__ wts, PotParams p,
+                                    size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 at = binned[i];
+    const int sp = __float_as_int(at.w);
+    float w[3] = {0.f, 0.f, 0.f};
+    if (sp >= 0 && sp < p.n_species) {
+        int k = (int)floorf(__fmul_rn(__fsub_rn(at.z, p.z0), p.inv_dz));
+        k = min(max(k, 0), p.n_slices - 1);
+        const float sg = p.sigma[sp], rc = p.rc[sp], amp = p.amp[sp];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int s = k - 1 + j;
+            const float lo = slice_boundary(p, s), hi = slice_boundary(p, s + 1);
+            if (s >= 0 && s < p.n_slices && hi > at.z - rc && lo < at.z + rc)
+                w[j] = amp * slice_weight(at.z, sg, lo, hi, s == 0, s == p.n_slices - 1, nullptr);
+        }
+    }
+    wts[i] = make_float4(w[0], w[1], w[2], 0.f);
+}
 
 // Exclusive prefix sum of v over the block; *total receives the sum.  Ends
 // with a barrier.
@@ -876,15 +911,16 @@ __device__ __forceinline__ int block_excl_scan(int v, int* warp_tot, int* total)
     return before + incl - v;
 }
 
-// Sources of slab k near band `band`: warp 0 loads the starts and counts of
-// the rb.count bins (k, band') with band' within reach and scans them into
-// bin_start / bin_cum.  Returns the slab's number of sources (after a barrier).
-__device__ int band_bins(BandSmem& sm, const PotParams& p, const int* __restrict__ off, int k, AxisRange rb) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+// Sources of slabs k0 .. k0 + nk - 1 near band `band`: warp j loads the starts
+// and counts of the rb.count bins (k0 + j, band') with band' within reach and
+// scans them into bin_start[j] / bin_cum[j], nsrc[j].  Ends with a barrier.
+__device__ void band_bins(BandSmem& sm, const PotParams& p, const int* __restrict__ off, int k0, int nk,
+                          AxisRange rb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < nk; j += kB2Threads / 32) {
         int cnt = 0, start = 0;
         if (lane < rb.count) {
-            const int bin = k * p.n_bands + (rb.first + lane) % p.n_bands;   // one column tile
+            const int bin = (k0 + j) * p.n_bands + (rb.first + lane) % p.n_bands;   // one column tile
             start = __ldg(off + bin);
             cnt = __ldg(off + bin + 1) - start;
         }
@@ -895,34 +931,45 @@ __device__ int band_bins(BandSmem& sm, const PotParams& p, const int* __restrict
             if (lane >= o) incl += u;
         }
         if (lane < rb.count) {
-            sm.bin_start[lane] = start;
-            sm.bin_cum[lane] = incl - cnt;
+            sm.bin_start[j][lane] = start;
+            sm.bin_cum[j][lane] = incl - cnt;
         }
-        if (lane == 31) sm.bin_cum[rb.count] = incl;
+        if (lane == 31) sm.nsrc[j] = incl;
     }
     __syncthreads();
-    return sm.bin_cum[rb.count];
 }
 
-// List of slab k's sources [src0, src1) (src1 - src0 <= blockDim.x; bin_start /
-// bin_cum loaded by band_bins) that reach the band's rows, into `slot`, sorted
-// by (column key, build position).  Returns the number of entries, or -1 when
-// they exceed kBCap (the slot is then unusable).  Ends with a barrier.
-__device__ int band_build(BandSmem& sm, int slot, const PotParams& p, const float4* __restrict__ atoms,
-                          const int2* __restrict__ atoms_px, int k, int src0, int src1, int nbins, int r0,
-                          int nrows, int kofs, int ngroups) {
-    const int src = src0 + (int)threadIdx.x;
+// Lists of nk consecutive slabs k0 .. in one round: slab j's sources
+// [src0_j, src1_j) (bin tables loaded by band_bins; the sources of all slabs
+// together at most blockDim.x) into slot slot_j, each sorted by (column key,
+// build position).  slot_j < 0 skips a slab.  Every slab's entry count goes to
+// sm.n[slot_j], or -1 when it exceeds kB2Cap.  Ends with a barrier.
+__device__ void band_build(BandSmem& sm, const PotParams& p, const float4* __restrict__ atoms,
+                           const int2* __restrict__ atoms_px, const float4* __restrict__ wts, int nk,
+                           const int* src0, const int* src1, const int* slot, int nbins, int r0, int nrows,
+                           int kofs, int ngroups) {
+    // this thread's source: slab j, source index src
+    int j = -1, src = 0, before = 0;
+    for (int q = 0; q < nk; ++q) {
+        const int cnt = slot[q] >= 0 ? src1[q] - src0[q] : 0;
+        if (j < 0 && (int)threadIdx.x < before + cnt) {
+            j = q;
+            src = src0[q] + ((int)threadIdx.x - before);
+        }
+        before += cnt;
+    }
     int nkeys = 0, key[3] = {0, 0, 0};
-    float fx = 0.f, c2 = 0.f, rc = 0.f, g[kBR], w[3] = {0.f, 0.f, 0.f};
+    float fx = 0.f, c2 = 0.f, rc = 0.f, g[kBR];
+    float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kBR; ++r) g[r] = 0.f;
-    if (src < src1) {
+    if (j >= 0) {
         int lo = 0, hi = nbins - 1;                      // the last bin starting at or before src
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (sm.bin_cum[mid] <= src) lo = mid; else hi = mid - 1;
+            if (sm.bin_cum[j][mid] <= src) lo = mid; else hi = mid - 1;
         }
-        const int ai = sm.bin_start[lo] + (src - sm.bin_cum[lo]);
+        const int ai = sm.bin_start[j][lo] + (src - sm.bin_cum[j][lo]);
         const float4 at = atoms[ai];                     // (fx, fy, z, species)
         const int2 px = atoms_px[ai];                    // (ic, jc), wrapped
         const int sp = __float_as_int(at.w);
@@ -933,14 +980,7 @@ __device__ int band_build(BandSmem& sm, int slot, const PotParams& p, const floa
             ok = range_gap(px.y, at.y, r0, nrows, p.ny, p.dy) <= rc;
         }
         if (ok) {
-            const float sg = p.sigma[sp], amp = p.amp[sp];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const int s = k - 1 + j;
-                const float lo_z = slice_boundary(p, s), hi_z = slice_boundary(p, s + 1);
-                if (s >= 0 && s < p.n_slices && hi_z > at.z - rc && lo_z < at.z + rc)
-                    w[j] = amp * slice_weight(at.z, sg, lo_z, hi_z, s == 0, s == p.n_slices - 1, nullptr);
-            }
+            wv = wts[ai];
 #pragma unroll
             for (int r = 0; r < kBR; ++r) {
                 const int ky = nearest_image(r0 + r - px.y, p.ny);
@@ -955,42 +995,70 @@ __device__ int band_build(BandSmem& sm, int slot, const PotParams& p, const floa
     }
     int total = 0;
     const int base = block_excl_scan(nkeys, sm.warp_tot, &total);
-    if (total > kBCap) return -1;                        // uniform: every thread has the same total
-    for (int j = 0; j < nkeys; ++j) sm.tkey[base + j] = key[j];
+    // sources are ordered by slab, so each slab's entries are contiguous in build order
+    if (j >= 0 && src == src0[j]) sm.lstart[j] = base;
+    for (int q = threadIdx.x; q < nk; q += blockDim.x)
+        if (slot[q] < 0 || src1[q] == src0[q]) sm.lstart[q] = -1;
+    for (int m = 0; m < nkeys; ++m) sm.tkey[base + m] = key[m];
     __syncthreads();
-    for (int j = 0; j < nkeys; ++j) {
-        const int e = base + j, kj = key[j];
-        int rank = 0;
-        for (int m = 0; m < total; ++m) {
-            const int km = sm.tkey[m];
-            rank += (km < kj || (km == kj && m < e)) ? 1 : 0;
+    if (threadIdx.x == 0) {                              // empty or skipped slabs start where the next one does
+        int next = total;
+        for (int q = nk - 1; q >= 0; --q) {
+            if (sm.lstart[q] < 0) sm.lstart[q] = next;
+            next = sm.lstart[q];
         }
-        sm.hd[slot][rank] = make_float4(__int_as_float(kj), fx, c2, rc);
-        sm.g[slot][rank][0] = make_float4(g[0], g[1], g[2], g[3]);
-        sm.g[slot][rank][1] = make_float4(g[4], g[5], g[6], g[7]);
-        sm.w[slot][rank] = make_float4(w[0], w[1], w[2], 0.f);
+        sm.lstart[nk] = total;
+    }
+    __syncthreads();
+    if (j >= 0) {
+        const int l0 = sm.lstart[j], l1 = sm.lstart[j + 1];
+        if (l1 - l0 <= kB2Cap) {
+            float4* hd = sm.hd[slot[j]];
+            float4 (*gs)[2] = sm.g[slot[j]];
+            float4* ws = sm.w[slot[j]];
+            for (int m = 0; m < nkeys; ++m) {
+                const int e = base + m, kj = key[m];
+                int rank = 0;
+                for (int q = l0; q < l1; ++q) {
+                    const int kq = sm.tkey[q];
+                    rank += (kq < kj || (kq == kj && q < e)) ? 1 : 0;
+                }
+                hd[rank] = make_float4(__int_as_float(kj), fx, c2, rc);
+                gs[rank][0] = make_float4(g[0], g[1], g[2], g[3]);
+                gs[rank][1] = make_float4(g[4], g[5], g[6], g[7]);
+                ws[rank] = wv;
+            }
+        }
     }
     __syncthreads();
     // first[c]: the first entry whose key is >= the lowest key that can reach column group c
-    for (int c = threadIdx.x; c < ngroups; c += blockDim.x) {
+    for (int t = threadIdx.x; t < nk * ngroups; t += blockDim.x) {
+        const int q = t / ngroups, c = t - q * ngroups;
+        if (slot[q] < 0) continue;
+        const int n = sm.lstart[q + 1] - sm.lstart[q];
+        if (n > kB2Cap) continue;
         const int want = 8 * c - p.reach_x - 1 + kofs;
-        int lo = 0, hi = total;
+        const float4* hd = sm.hd[slot[q]];
+        int lo = 0, hi = n;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (__float_as_int(sm.hd[slot][mid].x) < want) lo = mid + 1; else hi = mid;
+            if (__float_as_int(hd[mid].x) < want) lo = mid + 1; else hi = mid;
         }
-        sm.first[slot][c] = (unsigned short)lo;
+        sm.first[slot[q]][c] = (unsigned char)lo;
     }
-    if (threadIdx.x == 0) sm.n[slot] = total;
+    for (int q = threadIdx.x; q < nk; q += blockDim.x)
+        if (slot[q] >= 0) {
+            const int n = sm.lstart[q + 1] - sm.lstart[q];
+            sm.n[slot[q]] = n <= kB2Cap ? n : -1;
+        }
     __syncthreads();
-    return total;
 }
 
-// Adds the list in `slot` to columns x0, x0 + 1 of the band for slice offset
-// widx (0: the slab below the slice, 1: its own, 2: the slab above).
+// Adds the list in `slot` to columns x0 .. x0 + kB2Cols - 1 of the band for
+// slice offset widx (0: the slab below the slice, 1: its own, 2: the slab above).
 __device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, int widx, int x0, int reach, int kofs,
-                                                float d, float (&a0)[kBR], float (&a1)[kBR]) {
-    const int lo = x0 - reach - 1 + kofs, hi = x0 + reach + 2 + kofs;
+                                                float d, float (&acc)[kBR][kB2Cols]) {
+    const int lo = x0 - reach - 1 + kofs, hi = x0 + kB2Cols - 1 + reach + 2 + kofs;
     const int n = sm.n[slot];
     const float* wcol = reinterpret_cast<const float*>(&sm.w[slot][0]) + widx;
     for (int i = sm.first[slot][x0 >> 3]; i < n; ++i) {
@@ -1000,33 +1068,25 @@ __device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, in
         if (key < lo) continue;
         const float wv = wcol[4 * i];
         const int k0 = x0 + kofs - key;                  // column x0 minus the atom's column (this image)
-        const float dx0 = small_int_to_float(k0) * d - h.y;
-        const float dx1 = small_int_to_float(k0 + 1) * d - h.y;
-        const float g0 = fabsf(dx0) <= h.w ? wv * exp2f(-(dx0 * dx0) * h.z) : 0.f;
-        const float g1 = fabsf(dx1) <= h.w ? wv * exp2f(-(dx1 * dx1) * h.z) : 0.f;
+        float gx[kB2Cols];
+#pragma unroll
+        for (int m = 0; m < kB2Cols; ++m) {
+            const float dx = small_int_to_float(k0 + m) * d - h.y;
+            gx[m] = fabsf(dx) <= h.w ? wv * exp2f(-(dx * dx) * h.z) : 0.f;
+        }
         const float4 ga = sm.g[slot][i][0], gb = sm.g[slot][i][1];
-        a0[0] = fmaf(ga.x, g0, a0[0]);
-        a0[1] = fmaf(ga.y, g0, a0[1]);
-        a0[2] = fmaf(ga.z, g0, a0[2]);
-        a0[3] = fmaf(ga.w, g0, a0[3]);
-        a0[4] = fmaf(gb.x, g0, a0[4]);
-        a0[5] = fmaf(gb.y, g0, a0[5]);
-        a0[6] = fmaf(gb.z, g0, a0[6]);
-        a0[7] = fmaf(gb.w, g0, a0[7]);
-        a1[0] = fmaf(ga.x, g1, a1[0]);
-        a1[1] = fmaf(ga.y, g1, a1[1]);
-        a1[2] = fmaf(ga.z, g1, a1[2]);
-        a1[3] = fmaf(ga.w, g1, a1[3]);
-        a1[4] = fmaf(gb.x, g1, a1[4]);
-        a1[5] = fmaf(gb.y, g1, a1[5]);
-        a1[6] = fmaf(gb.z, g1, a1[6]);
-        a1[7] = fmaf(gb.w, g1, a1[7]);
+        const float gy[kBR] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+#pragma unroll
+        for (int r = 0; r < kBR; ++r)
+#pragma unroll
+            for (int m = 0; m < kB2Cols; ++m) acc[r][m] = fmaf(gy[r], gx[m], acc[r][m]);
     }
 }
 
-__global__ void __launch_bounds__(kPotThreads, 3)
+__global__ void __launch_bounds__(kB2Threads, 6)
 potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
-                      const int2* __restrict__ binned_px, PotParams p, int vec2, float* __restrict__ V) {
+                      const int2* __restrict__ binned_px, const float4* __restrict__ binned_w, PotParams p,
+                      int vec4, float* __restrict__ V) {
     extern __shared__ __align__(16) unsigned char band_smem_raw[];
     BandSmem& sm = *reinterpret_cast<BandSmem*>(band_smem_raw);
     const int band = blockIdx.x;
@@ -1034,69 +1094,89 @@ potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict_
     const int r0 = band * kBR, nrows = min(kBR, p.ny - r0);
     const float4* atoms = binned + t * (size_t)p.n_atoms;
     const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
+    const float4* wts = binned_w + t * (size_t)p.n_atoms;
     const int* off = bin_off + t * (size_t)(p.n_bins + 1);
     const AxisRange rb = axis_range(band, kBR, p.ny, p.n_bands, p.reach_y + 1);
     const int kofs = p.reach_x + 2;                      // keys are columns + kofs >= 0
     const int ngroups = (p.nx + 7) / 8;
-    const int passes = (p.nx + 2 * (int)blockDim.x - 1) / (2 * (int)blockDim.x);
+    constexpr int span = kB2Cols * kB2Threads;
+    const int passes = (p.nx + span - 1) / span;
 
-    // slab k's list into ring slot k % 3, or the slot marked for chunks
-    auto build_slab = [&](int k) {
-        const int nsrc = band_bins(sm, p, off, k, rb);
-        int n = -1;
-        if (nsrc <= (int)blockDim.x)
-            n = band_build(sm, k % 3, p, atoms, atoms_px, k, 0, nsrc, rb.count, r0, nrows, kofs, ngroups);
-        if (n < 0) {
-            if (threadIdx.x == 0) sm.n[k % 3] = -1;
-            __syncthreads();
+    // lists of slabs k0 .. k1 - 1 into their ring slots, in rounds of at most kB2Group slabs whose
+    // sources fit one per thread; a slab with more sources than threads is marked for chunks
+    auto build = [&](int k0, int k1) {
+        while (k0 < k1) {
+            const int nk = min(kB2Group, k1 - k0);
+            band_bins(sm, p, off, k0, nk, rb);       // ends with a barrier: nsrc[] is uniform
+            int s0[kB2Group], s1[kB2Group], sl[kB2Group], take = 0, sum = 0;
+            for (int q = 0; q < nk; ++q) {
+                const int c = sm.nsrc[q];
+                if (sum + c > (int)blockDim.x) break;
+                s0[q] = 0;
+                s1[q] = c;
+                sl[q] = (k0 + q) % kB2Ring;
+                sum += c;
+                take = q + 1;
+            }
+            if (take == 0) {                         // slab k0 alone exceeds the threads: chunks per slice
+                if (threadIdx.x == 0) sm.n[k0 % kB2Ring] = -1;
+                __syncthreads();
+                k0 += 1;
+                continue;
+            }
+            band_build(sm, p, atoms, atoms_px, wts, take, s0, s1, sl, rb.count, r0, nrows, kofs, ngroups);
+            k0 += take;
         }
     };
 
-    for (int s = 0; s < p.n_slices; ++s) {
-        if (s == 0) {
-            build_slab(0);
-            if (p.n_slices > 1) build_slab(1);
-        } else if (s + 1 < p.n_slices) {
-            build_slab(s + 1);                           // replaces slab s - 2, last read in slice s - 1
-        }
-        for (int j = 0; j < passes; ++j) {
-            const int x0 = 2 * ((int)threadIdx.x + j * (int)blockDim.x);
-            const bool active = x0 < p.nx;
-            float a0[kBR], a1[kBR];
+    for (int s = 0; s < p.n_slices; s += kB2Group) {
+        const int s_end = min(p.n_slices, s + kB2Group);
+        // slabs s-1 .. s_end are needed; s-1 and s are in the ring from the previous round
+        build(s == 0 ? 0 : s + 1, min(p.n_slices, s_end + 1));
+        for (int si = s; si < s_end; ++si) {
+            for (int pass = 0; pass < passes; ++pass) {
+                const int x0 = kB2Cols * ((int)threadIdx.x + pass * kB2Threads);
+                const bool active = x0 < p.nx;
+                float acc[kBR][kB2Cols];
 #pragma unroll
-            for (int r = 0; r < kBR; ++r) a0[r] = a1[r] = 0.f;
-            for (int k = max(0, s - 1); k <= min(p.n_slices - 1, s + 1); ++k) {
-                const int widx = s - k + 1;
-                if (sm.n[k % 3] >= 0) {
-                    if (active) band_accumulate(sm, k % 3, widx, x0, p.reach_x, kofs, p.dx, a0, a1);
-                    continue;
-                }
-                const int nsrc = band_bins(sm, p, off, k, rb);
-                for (int c0 = 0; c0 < nsrc; c0 += kBChunkSrc) {
-                    band_build(sm, 3, p, atoms, atoms_px, k, c0, min(nsrc, c0 + kBChunkSrc), rb.count, r0, nrows,
-                               kofs, ngroups);
-                    if (active) band_accumulate(sm, 3, widx, x0, p.reach_x, kofs, p.dx, a0, a1);
-                    __syncthreads();                     // slot 3 is rebuilt next
-                }
-            }
-            if (active) {
-                float* out = V + ((t * p.n_slices + s) * (size_t)p.ny + r0) * p.nx + x0;
-                const bool two = x0 + 1 < p.nx;
+                for (int r = 0; r < kBR; ++r)
 #pragma unroll
-                for (int r = 0; r < kBR; ++r) {
-                    if (r < nrows) {
-                        float* o = out + (size_t)r * p.nx;
-                        if (vec2) {
-                            *reinterpret_cast<float2*>(o) = make_float2(a0[r], a1[r]);
-                        } else {
-                            o[0] = a0[r];
-                            if (two) o[1] = a1[r];
+                    for (int m = 0; m < kB2Cols; ++m) acc[r][m] = 0.f;
+                for (int k = max(0, si - 1); k <= min(p.n_slices - 1, si + 1); ++k) {
+                    const int widx = si - k + 1;
+                    if (sm.n[k % kB2Ring] >= 0) {
+                        if (active) band_accumulate(sm, k % kB2Ring, widx, x0, p.reach_x, kofs, p.dx, acc);
+                        continue;
+                    }
+                    band_bins(sm, p, off, k, 1, rb);
+                    const int nsrc = sm.nsrc[0];
+                    for (int c0 = 0; c0 < nsrc; c0 += kB2ChunkSrc) {
+                        const int a0 = c0, a1 = min(nsrc, c0 + kB2ChunkSrc), sl = kB2Chunk;
+                        band_build(sm, p, atoms, atoms_px, wts, 1, &a0, &a1, &sl, rb.count, r0, nrows, kofs,
+                                   ngroups);
+                        if (active) band_accumulate(sm, kB2Chunk, widx, x0, p.reach_x, kofs, p.dx, acc);
+                        __syncthreads();                 // the chunk slot is rebuilt next
+                    }
+                }
+                if (active) {
+                    float* out = V + ((t * p.n_slices + si) * (size_t)p.ny + r0) * p.nx + x0;
+#pragma unroll
+                    for (int r = 0; r < kBR; ++r) {
+                        if (r < nrows) {
+                            float* o = out + (size_t)r * p.nx;
+                            if (vec4) {
+                                *reinterpret_cast<float4*>(o) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+                            } else {
+#pragma unroll
+                                for (int m = 0; m < kB2Cols; ++m)
+                                    if (x0 + m < p.nx) o[m] = acc[r][m];
+                            }
                         }
                     }
                 }
             }
         }
-        __syncthreads();                                 // slice s + 1 rebuilds the slot of slab s - 1
+        __syncthreads();                                 // the next round rebuilds the slots of older slabs
     }
 }
 
@@ -1456,6 +1536,7 @@ int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes)
     const long long bins = std::max(clamp_bins(bin_shape(g, BinLayout::Tiles).n_bins),
                                     clamp_bins(bin_shape(g, BinLayout::Bands).n_bins));
     carve_pot(cv, n_t, n_atoms, (int)bins);
+    cv.take<float4>((size_t)n_t * n_atoms);              // per-atom slice weights (band-walking kernel)
     *bytes = cv.bytes();
     return TACAW_OK;
 }
@@ -1498,13 +1579,19 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
         // atoms reach at most the neighbouring slices: walk the slices once per band of rows
         Carver cv(ws);
         PotWs w = carve_pot(cv, n_t, n_atoms, pb.n_bins);
+        float4* wts = cv.take<float4>((size_t)n_t * n_atoms);
         rc = run_binning(pb, n_t, pos, species, w, st);
         if (rc != TACAW_OK) return rc;
-        const int vec2 = (g.nx % 2 == 0) && (reinterpret_cast<uintptr_t>(V) % 8 == 0);
+        const size_t n_rec = (size_t)n_t * n_atoms;
+        if (n_rec > 0) {
+            atom_weights_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, st>>>(w.binned, wts, pb, n_rec);
+            TACAW_LAUNCH_CHECK();
+        }
+        const int vec4 = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
         const int bsm = (int)sizeof(BandSmem);
         TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel, bsm));
-        potential_band_kernel<<<dim3(pb.n_bands, n_t), kPotThreads, bsm, st>>>(w.bin_off, w.binned, w.binned_px,
-                                                                             pb, vec2, V);
+        potential_band_kernel<<<dim3(pb.n_bands, n_t), kB2Threads, bsm, st>>>(w.bin_off, w.binned, w.binned_px, wts,
+                                                                            pb, vec4, V);
         TACAW_LAUNCH_CHECK();
         return TACAW_OK;
     }
