@@ -849,14 +849,17 @@ constexpr int kBGroups = 129;            // 8-column groups for nx <= 1024, plus
 constexpr int kBMaxBins = 32;            // bands within reach of a band (one warp scans them)
 constexpr int kBMaxNx = 1024;
 static_assert(kB2Cap <= 255, "first[] holds list positions in a byte");
+static_assert(kB2Threads * 3 <= 512, "positions in a slab's build order fit the low 9 bits of a sort key");
 
 struct BandSmem {
     float4 hd[kB2Slots][kB2Cap];         // (column key as int bits, fx, log2(e) / (2 s^2), 6 s)
     float4 g[kB2Slots][kB2Cap][2];       // gy over the band's rows (0 outside |dy| <= 6 s)
-    float4 w[kB2Slots][kB2Cap];          // amp w_{k-1}, amp w_k, amp w_{k+1}, 0
+    float4 w[kB2Slots][kB2Cap];          // amp w_{k-1}, amp w_k, amp w_{k+1}, q = exp2(-2 d^2 c2)
     unsigned char first[kB2Slots][kBGroups];
     int n[kB2Slots];                     // entries of the slot, or -1: slab processed in chunks
-    int tkey[kB2Threads * 3];            // keys in build order, for ranking
+    // per slab of a round: unique sort keys (column key * 512 + position in the slab's build
+    // order), padded with INT_MAX to a multiple of 4 so the ranking reads four at a time
+    __align__(16) int ckey[kB2Group][kB2Threads * 3 + 4];
     int bin_start[kB2Group][kBMaxBins], bin_cum[kB2Group][kBMaxBins + 1];
     int nsrc[kB2Group];                  // sources of each slab of the round
     int lstart[kB2Group + 1];            // build positions where each slab's entries start
@@ -981,6 +984,7 @@ __device__ void band_build(BandSmem& sm, const PotParams& p, const float4* __res
         }
         if (ok) {
             wv = wts[ai];
+            wv.w = exp2f(-2.f * (p.dx * p.dx) * c2);    // ratio of ratios of consecutive column factors
 #pragma unroll
             for (int r = 0; r < kBR; ++r) {
                 const int ky = nearest_image(r0 + r - px.y, p.ny);
@@ -999,7 +1003,6 @@ __device__ void band_build(BandSmem& sm, const PotParams& p, const float4* __res
     if (j >= 0 && src == src0[j]) sm.lstart[j] = base;
     for (int q = threadIdx.x; q < nk; q += blockDim.x)
         if (slot[q] < 0 || src1[q] == src0[q]) sm.lstart[q] = -1;
-    for (int m = 0; m < nkeys; ++m) sm.tkey[base + m] = key[m];
     __syncthreads();
     if (threadIdx.x == 0) {                              // empty or skipped slabs start where the next one does
         int next = total;
@@ -1010,24 +1013,36 @@ __device__ void band_build(BandSmem& sm, const PotParams& p, const float4* __res
         sm.lstart[nk] = total;
     }
     __syncthreads();
+    int l0 = 0, l1 = 0;
     if (j >= 0) {
-        const int l0 = sm.lstart[j], l1 = sm.lstart[j + 1];
-        if (l1 - l0 <= kB2Cap) {
-            float4* hd = sm.hd[slot[j]];
-            float4 (*gs)[2] = sm.g[slot[j]];
-            float4* ws = sm.w[slot[j]];
-            for (int m = 0; m < nkeys; ++m) {
-                const int e = base + m, kj = key[m];
-                int rank = 0;
-                for (int q = l0; q < l1; ++q) {
-                    const int kq = sm.tkey[q];
-                    rank += (kq < kj || (kq == kj && q < e)) ? 1 : 0;
-                }
-                hd[rank] = make_float4(__int_as_float(kj), fx, c2, rc);
-                gs[rank][0] = make_float4(g[0], g[1], g[2], g[3]);
-                gs[rank][1] = make_float4(g[4], g[5], g[6], g[7]);
-                ws[rank] = wv;
+        l0 = sm.lstart[j];
+        l1 = sm.lstart[j + 1];
+        for (int m = 0; m < nkeys; ++m) sm.ckey[j][base + m - l0] = key[m] * 512 + (base + m - l0);
+    }
+    for (int t = threadIdx.x; t < 4 * nk; t += blockDim.x) {   // INT_MAX padding to a multiple of 4
+        const int q = t >> 2, n = sm.lstart[q + 1] - sm.lstart[q];
+        const int pos = n + (t & 3);
+        if (pos < ((n + 3) & ~3)) sm.ckey[q][pos] = 0x7fffffff;
+    }
+    __syncthreads();
+    if (j >= 0 && l1 - l0 <= kB2Cap) {
+        float4* hd = sm.hd[slot[j]];
+        float4 (*gs)[2] = sm.g[slot[j]];
+        float4* ws = sm.w[slot[j]];
+        const int4* ck4 = reinterpret_cast<const int4*>(sm.ckey[j]);
+        const int n4 = (l1 - l0 + 3) >> 2;
+        for (int m = 0; m < nkeys; ++m) {
+            const int ck = key[m] * 512 + (base + m - l0);
+            int rank = 0;
+#pragma unroll 4
+            for (int q = 0; q < n4; ++q) {
+                const int4 v = ck4[q];
+                rank += (v.x < ck) + (v.y < ck) + (v.z < ck) + (v.w < ck);
             }
+            hd[rank] = make_float4(__int_as_float(key[m]), fx, c2, rc);
+            gs[rank][0] = make_float4(g[0], g[1], g[2], g[3]);
+            gs[rank][1] = make_float4(g[4], g[5], g[6], g[7]);
+            ws[rank] = wv;
         }
     }
     __syncthreads();
@@ -1056,6 +1071,13 @@ __device__ void band_build(BandSmem& sm, const PotParams& p, const float4* __res
 
 // Adds the list in `slot` to columns x0 .. x0 + kB2Cols - 1 of the band for
 // slice offset widx (0: the slab below the slice, 1: its own, 2: the slab above).
+// RECUR: the column factors g_m = exp2(-dx_m^2 c2), dx_m = dx_0 + m d, by the
+// exact recurrence g_{m+1} = g_m r_m, r_{m+1} = r_m q with
+// r_0 = exp2(-(2 dx_0 d + d^2) c2) and q = exp2(-2 d^2 c2) (two exponentials
+// per entry instead of kB2Cols; a few ulp of rounding), used when no factor
+// within reach underflows (pixels fine enough next to the width: the host
+// checks).  Otherwise each factor is its own exponential.
+template <bool RECUR>
 __device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, int widx, int x0, int reach, int kofs,
                                                 float d, float (&acc)[kBR][kB2Cols]) {
     const int lo = x0 - reach - 1 + kofs, hi = x0 + kB2Cols - 1 + reach + 2 + kofs;
@@ -1069,10 +1091,24 @@ __device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, in
         const float wv = wcol[4 * i];
         const int k0 = x0 + kofs - key;                  // column x0 minus the atom's column (this image)
         float gx[kB2Cols];
+        if constexpr (RECUR) {
+            const float q = wcol[4 * i + 3 - widx];
+            const float dx0 = small_int_to_float(k0) * d - h.y;
+            float g = wv * exp2f(-(dx0 * dx0) * h.z);
+            float r = exp2f(-fmaf(2.f * dx0, d, d * d) * h.z);
 #pragma unroll
-        for (int m = 0; m < kB2Cols; ++m) {
-            const float dx = small_int_to_float(k0 + m) * d - h.y;
-            gx[m] = fabsf(dx) <= h.w ? wv * exp2f(-(dx * dx) * h.z) : 0.f;
+            for (int m = 0; m < kB2Cols; ++m) {
+                const float dx = fmaf((float)m, d, dx0);
+                gx[m] = fabsf(dx) <= h.w ? g : 0.f;
+                g *= r;
+                r *= q;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kB2Cols; ++m) {
+                const float dx = small_int_to_float(k0 + m) * d - h.y;
+                gx[m] = fabsf(dx) <= h.w ? wv * exp2f(-(dx * dx) * h.z) : 0.f;
+            }
         }
         const float4 ga = sm.g[slot][i][0], gb = sm.g[slot][i][1];
         const float gy[kBR] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
@@ -1083,6 +1119,7 @@ __device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, in
     }
 }
 
+template <bool RECUR>
 __global__ void __launch_bounds__(kB2Threads, 6)
 potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
                       const int2* __restrict__ binned_px, const float4* __restrict__ binned_w, PotParams p,
@@ -1145,7 +1182,7 @@ potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict_
                 for (int k = max(0, si - 1); k <= min(p.n_slices - 1, si + 1); ++k) {
                     const int widx = si - k + 1;
                     if (sm.n[k % kB2Ring] >= 0) {
-                        if (active) band_accumulate(sm, k % kB2Ring, widx, x0, p.reach_x, kofs, p.dx, acc);
+                        if (active) band_accumulate<RECUR>(sm, k % kB2Ring, widx, x0, p.reach_x, kofs, p.dx, acc);
                         continue;
                     }
                     band_bins(sm, p, off, k, 1, rb);
@@ -1154,7 +1191,7 @@ potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict_
                         const int a0 = c0, a1 = min(nsrc, c0 + kB2ChunkSrc), sl = kB2Chunk;
                         band_build(sm, p, atoms, atoms_px, wts, 1, &a0, &a1, &sl, rb.count, r0, nrows, kofs,
                                    ngroups);
-                        if (active) band_accumulate(sm, kB2Chunk, widx, x0, p.reach_x, kofs, p.dx, acc);
+                        if (active) band_accumulate<RECUR>(sm, kB2Chunk, widx, x0, p.reach_x, kofs, p.dx, acc);
                         __syncthreads();                 // the chunk slot is rebuilt next
                     }
                 }
@@ -1589,9 +1626,22 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
         }
         const int vec4 = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
         const int bsm = (int)sizeof(BandSmem);
-        TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel, bsm));
-        potential_band_kernel<<<dim3(pb.n_bands, n_t), kB2Threads, bsm, st>>>(w.bin_off, w.binned, w.binned_px, wts,
-                                                                            pb, vec4, V);
+        // the column-factor recurrence needs every factor within reach of a thread's columns to stay a
+        // normal float: exponent (6 s + kB2Cols d)^2 log2(e) / (2 s^2) below 120 for every species
+        bool recur = true;
+        for (int i = 0; i < n_species; ++i) {
+            const double sg = amp_sigma[2 * i + 1], reach = 6.0 * sg + kB2Cols * (g.lx / g.nx);
+            recur = recur && reach * reach * 1.4426950408889634 / (2.0 * sg * sg) < 120.0;
+        }
+        if (recur) {
+            TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel<true>, bsm));
+            potential_band_kernel<true><<<dim3(pb.n_bands, n_t), kB2Threads, bsm, st>>>(
+                w.bin_off, w.binned, w.binned_px, wts, pb, vec4, V);
+        } else {
+            TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel<false>, bsm));
+            potential_band_kernel<false><<<dim3(pb.n_bands, n_t), kB2Threads, bsm, st>>>(
+                w.bin_off, w.binned, w.binned_px, wts, pb, vec4, V);
+        }
         TACAW_LAUNCH_CHECK();
         return TACAW_OK;
     }
