@@ -63,8 +63,9 @@ def parse_args():
     p.add_argument("--spectrum-only", default="",
                    help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
                         "(a kernel micro-benchmark; not the benchmark line)")
-    p.add_argument("--warp-rows", choices=["auto", "0", "1"], default="auto",
-                   help="row-pass variant for 512-point rows: tuned (auto), two warps per row (0), one (1)")
+    p.add_argument("--ms-flags", choices=["auto", "0", "1", "2", "3"], default="auto",
+                   help="variants of the multislice passes (tacaw_multislice flags): tuned (auto), or 0-3 "
+                        "(1: one warp per 512-point row, 2: one block per column block)")
     p.add_argument("--no-c3", action="store_true",
                    help="skip the full batched configuration (64 uneven jobs, 512-4096 snapshots each)")
     p.add_argument("--c3-only", action="store_true",
@@ -343,8 +344,8 @@ def run_ours(args):
         args.precision = "bf16x3"                 # no time-FFT plan for this T: the GEMM path
     tts = TimeToSpectrum(g, n_t, n_atoms, inp.amp_sigma, w.dt_fs, batch=args.batch, device=dev,
                          precision=args.precision)
-    if args.warp_rows != "auto":
-        tts.warp_rows = args.warp_rows == "1"
+    if args.ms_flags != "auto":
+        tts.ms_flags = int(args.ms_flags)
     tuning = None
     if args.batch == "auto":
         from paper_2401_15599_gb300 import tuning as T
@@ -376,7 +377,7 @@ def run_ours(args):
                 g, pos[t0:t1], species, inp.amp_sigma, out=v, workspace=tts._ws.get("pot")))
             timed("multislice", record, lambda: api.multislice(
                 g, v, out=tts.psi[t0:t1], psi_sum=tts.psi_sum, workspace=tts._ws.get("ms"),
-                warp_rows=tts.warp_rows))
+                ms_flags=tts.ms_flags))
         tts.precision = precision
         return timed("spectrum", record, tts.spectrum)
 
@@ -415,7 +416,7 @@ def run_ours(args):
 
         def host_call():
             return api.time_to_spectrum_host(g, pos_host, species, inp.amp_sigma, w.dt_fs, tts.batch,
-                                             warp_rows=tts.warp_rows, precision=args.precision, out=i_host,
+                                             ms_flags=tts.ms_flags, precision=args.precision, out=i_host,
                                              out_el=el_host, workspace=host_ws)
 
         host_ws = api.time_to_spectrum_host_workspace(g, n_t, n_atoms, tts.batch, args.precision, device=dev)
@@ -560,7 +561,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+bf16x3" if args.precision == "bf16x3" else "f32",
             "data": "synthetic",
             "tuning": tuning,
-            "config": workload_config(w, {"batch": tts.batch, "warp_rows": tts.warp_rows,
+            "config": workload_config(w, {"batch": tts.batch, "ms_flags": tts.ms_flags,
                                           "spectrum_precision": args.precision,
                                           "parallelism": "replicas" if world > 1 else "single GPU"}),
             "time_to_spectrum_ms": ms_step,
@@ -663,10 +664,10 @@ def plain_cufft_slice_step(tts, g, reps, stream):
     ref = run()
     ours = torch.empty_like(ref)
     from paper_2401_15599_gb300 import api
-    api.multislice(g, V, out=ours, warp_rows=tts.warp_rows)
+    api.multislice(g, V, out=ours, ms_flags=tts.ms_flags)
     diff = float(torch.linalg.norm(ours - ref) / torch.linalg.norm(ref))
     ms = _events_ms(run, reps, stream)
-    ours_ms = _events_ms(lambda: api.multislice(g, V, out=ours, warp_rows=tts.warp_rows), reps, stream)
+    ours_ms = _events_ms(lambda: api.multislice(g, V, out=ours, ms_flags=tts.ms_flags), reps, stream)
     return {"snapshots": int(V.shape[0]), "plain_cufft_ms": ms, "ours_ms": ours_ms,
             "speedup": ms / ours_ms, "rel_l2_difference": diff}
 
@@ -835,11 +836,13 @@ def run_sharded(args):
     inp = W.build_inputs(w)
     n_t = w.n_t
     t_lo, t_hi = shard_bounds(n_t, world, rank)
-    batch, warp_rows = best_multislice_config(g, device=dev) if args.batch == "auto" else (int(args.batch), False)
+    batch, ms_flags = best_multislice_config(g, device=dev) if args.batch == "auto" else (int(args.batch), 0)
+    if args.ms_flags != "auto":
+        ms_flags = int(args.ms_flags)
     batch = max(1, min(batch, t_hi - t_lo))
     omega = natural_energies_meV(n_t, w.dt_fs)
     sh = ShardedTimeToSpectrum(g, n_t, inp.crystal.n_atoms, inp.amp_sigma, w.dt_fs, omega, batch=batch,
-                               precision="bf16x6", device=dev, warp_rows=warp_rows)
+                               precision="bf16x6", device=dev, ms_flags=ms_flags)
     pos_host = torch.from_numpy(inp.positions(list(range(t_lo, t_hi)))).pin_memory()
     pos = pos_host.to(dev, non_blocking=True)
     species = torch.from_numpy(inp.species).to(dev)
@@ -890,8 +893,8 @@ def run_sharded(args):
     V = torch.empty((batch, g.n_slices, g.ny, g.nx), dtype=torch.float32, device=dev)
     api.potential(g, pos[:batch], species, inp.amp_sigma, out=V)
     out = torch.empty((batch, g.ny, g.nx), dtype=torch.complex64, device=dev)
-    api.multislice(g, V, out=out, warp_rows=warp_rows)
-    call_ms = _events_ms(lambda: api.multislice(g, V, out=out, warp_rows=warp_rows), 3, stream)
+    api.multislice(g, V, out=out, ms_flags=ms_flags)
+    call_ms = _events_ms(lambda: api.multislice(g, V, out=out, ms_flags=ms_flags), 3, stream)
     peak, _, peak_kind = load_peaks()
     bytes_pt = slice_step_bytes(g)
     achieved = bytes_pt * g.nx * g.ny * g.n_slices * batch / (call_ms * 1e-3) / 1e9
@@ -900,7 +903,7 @@ def run_sharded(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32+bf16x6", "data": "synthetic",
-            "config": workload_config(w, {"batch": batch, "warp_rows": warp_rows, "spectrum_precision": "bf16x6",
+            "config": workload_config(w, {"batch": batch, "ms_flags": ms_flags, "spectrum_precision": "bf16x6",
                                           "spectrum": "natural energies as an explicit grid (n_omega = T)",
                                           "parallelism": f"{world} snapshot shards; all-reduce of the FP64 sums; "
                                                          f"reduce-scatter of Phi over q"}),

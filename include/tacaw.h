@@ -64,6 +64,9 @@ extern "C" {
 #define TACAW_MS_WARP_ROWS 1    /* 512-point rows: row pass with one warp per row (16 values per
                                    thread) instead of two; same results to rounding, chosen by
                                    the autotuner where faster; ignored for other sizes */
+#define TACAW_MS_BLOCK_COLS 2   /* 512-point columns: one block per column block instead of the
+                                   persistent column pass with TMA-staged tiles; identical
+                                   results; ignored for other sizes */
 
 /* flags of tacaw_spectrum */
 #define TACAW_KUBO 1            /* multiply by beta E / (1 - exp(-beta E)), Eq. (8) */
@@ -181,7 +184,8 @@ int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
  *          used as the working buffer (no other scratch for the waves)
  * psi_sum  in/out [ny][nx] double2 running sum over snapshots, or NULL; when
  *          given, sum_t psi_q(t) is ADDED to it in FP64 (snapshot order)
- * flags    0 or TACAW_MS_WARP_ROWS (a variant of the row pass's thread layout)
+ * flags    0, TACAW_MS_WARP_ROWS and / or TACAW_MS_BLOCK_COLS (variants of the
+ *          passes' thread layout and staging, for the autotuner)
  * Supported sizes: nx, ny in {64, 128, 256, 384, 512, 768, 1024}.
  */
 int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,

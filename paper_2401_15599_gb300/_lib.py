@@ -29,6 +29,7 @@ TACAW_NORMALIZE = 2
 TACAW_MAX_SPECIES = 8
 TACAW_MAX_BATCH = 64
 TACAW_MS_WARP_ROWS = 1
+TACAW_MS_BLOCK_COLS = 2
 
 ERRORS = {
     TACAW_EINVAL: "EINVAL", TACAW_ECUDA: "ECUDA", TACAW_ENOMEM: "ENOMEM",

@@ -90,9 +90,10 @@ def potential(grid, pos, species, amp_sigma, out=None, workspace=None):
     return out
 
 
-def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None, warp_rows=False):
+def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None, ms_flags=0):
     """Exit waves psi_q [T, ny, nx] (complex64, q-space, FFT order) for potentials V.
-    warp_rows: the row-pass variant with one warp per 512-point row (TACAW_MS_WARP_ROWS)."""
+    ms_flags: tacaw_multislice flags choosing variants of the passes (TACAW_MS_WARP_ROWS,
+    TACAW_MS_BLOCK_COLS; the tuner picks them per grid and GPU)."""
     lib = L.load()
     _need_cuda("V", V, torch.float32, 4)
     n_t = V.shape[0]
@@ -109,7 +110,7 @@ def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None, war
 
     def call(ws, nbytes):
         return lib.tacaw_multislice(ctypes.byref(g), n_t, _ptr(V), _ptr(psi_in), _ptr(out), _ptr(psi_sum),
-                                    L.TACAW_MS_WARP_ROWS if warp_rows else 0, ws, nbytes, _stream(V.device))
+                                    int(ms_flags), ws, nbytes, _stream(V.device))
 
     nbytes = ctypes.c_size_t(0)
     L.check("tacaw_multislice", call(ctypes.c_void_p(0), ctypes.byref(nbytes)))
@@ -458,7 +459,7 @@ def spectrum_finish(phi, n_t, dt_fs, omega_meV, m_ref, psi_sum, kubo=False, temp
     return out, i_el
 
 
-def time_to_spectrum_host(grid, pos_host, species, amp_sigma, dt_fs, batch, warp_rows=False, precision="fft32",
+def time_to_spectrum_host(grid, pos_host, species, amp_sigma, dt_fs, batch, ms_flags=0, precision="fft32",
                           kubo=False, temperature_K=300.0, normalize=False, out=None, out_el=None, workspace=None):
     """The whole path in one library call: positions pos_host [T, Na, 3]
     (float32, CPU; page-locked for overlapped copies) -> I [nq, T] and I_el
@@ -487,7 +488,7 @@ def time_to_spectrum_host(grid, pos_host, species, amp_sigma, dt_fs, batch, warp
     def call(ws, nbytes):
         return lib.tacaw_time_to_spectrum_host(ctypes.byref(g), n_t, n_atoms, ctypes.c_void_p(pos_host.data_ptr()),
                                                _ptr(species), amp.shape[0], amp_c, float(dt_fs), int(batch),
-                                               L.TACAW_MS_WARP_ROWS if warp_rows else 0, _PRECISION[precision],
+                                               int(ms_flags), _PRECISION[precision],
                                                flags, float(temperature_K), ctypes.c_void_p(out.data_ptr()),
                                                ctypes.c_void_p(out_el.data_ptr()), ws, nbytes, _stream(dev))
 

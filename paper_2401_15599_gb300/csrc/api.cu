@@ -182,7 +182,7 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
                   TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
-    TACAW_REQUIRE((flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     bool query = false;
     rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
     if (rc || query) return rc;
@@ -277,7 +277,7 @@ int tacaw_time_to_spectrum_host(const tacaw_grid* grid, int32_t n_t, int32_t n_a
     TACAW_REQUIRE(n_species >= 1 && n_species <= TACAW_MAX_SPECIES && amp_sigma, TACAW_EINVAL,
                   "%s: need 1..%d species with amp_sigma", fn, TACAW_MAX_SPECIES);
     TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
-    TACAW_REQUIRE((ms_flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown multislice flags", fn);
+    TACAW_REQUIRE((ms_flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown multislice flags", fn);
     TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_BF16X6 ||
                       precision == TACAW_FFT32, TACAW_EINVAL, "%s: unknown precision %d", fn, precision);
     TACAW_REQUIRE(precision != TACAW_FFT32 || time_fft_size_supported(n_t), TACAW_EUNSUPPORTED,
@@ -586,7 +586,7 @@ int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float
                   "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn, grid->nx, grid->ny);
     TACAW_REQUIRE(max_batch >= 1 && max_batch <= 65535 && n_candidates >= 1 && reps >= 1 && reps <= 1000,
                   TACAW_EINVAL, "%s: need 1 <= max_batch <= 65535, n_candidates >= 1, 1 <= reps <= 1000", fn);
-    TACAW_REQUIRE((flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     bool query = false;
     rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
     if (rc || query) return rc;

@@ -16,6 +16,7 @@
 // move 4 + 16 f_col + 16 f_blk = 25.4 bytes per point and slice (f_col: kept
 // columns, f_blk: column-pass blocks holding a kept column).
 
+#include <cuda.h>
 #include <stdint.h>
 
 #include <map>
@@ -462,6 +463,124 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
                                smem + W * NY, tw, t, c);
 }
 
+// Staged column pass of the forward slice step (Fy -> x P BL / (nx ny) -> Fy^-1,
+// or no Fy^-1 after the last slice): a persistent grid in which each block
+// walks the column blocks that hold a kept column (W columns of one snapshot;
+// the band-limited blocks are never read), and while it transforms one, TMA
+// brings the next block's NY x W tile into the other half of a two-stage
+// shared-memory ring (two boxes of NY/2 rows; the tile arrives dense, row by
+// row, which is the order in which a warp's 8 rows x W columns read it).  The
+// stage being transformed doubles as the exchange buffer.  Same arithmetic as
+// col_body, so the results are identical.  The waits give up after `polls`
+// polls like the staged row pass's (status flag, then a drain of both stages).
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), ColCfg<NY>::kMinBlocks)
+col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restrict__ psi,
+                       const float2* __restrict__ twy, const float2* __restrict__ px, const float2* __restrict__ py,
+                       const int* __restrict__ kymax, int nx, int n_t, int last, int* __restrict__ err,
+                       uint32_t polls) {
+    using namespace fft;
+    constexpr int E = Plan<NY>::E;
+    constexpr int TPT = NY / E;
+    constexpr int W = ColCfg<NY>::W;
+    constexpr int STAGE = NY * W;                       // float2 per stage
+    constexpr uint32_t STAGE_BYTES = STAGE * sizeof(float2);
+    extern __shared__ __align__(128) float2 cstage[];
+    float2* tw = cstage + 2 * STAGE;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + TwSize<NY>::value);
+    const int c = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    // kept column blocks: [0, n_lo) and [nb - n_hi, nb) of the nb = nx / W blocks
+    const int K = __ldg(kymax + nx);
+    const int nb = nx / W;
+    const int n_lo = K / W + 1;
+    int hi0 = (nx - K - W + 1 + W - 1) / W;              // first block with a column >= nx - K
+    if (hi0 < n_lo) hi0 = n_lo;
+    const int n_kept = n_lo + (nb - hi0);
+    const long long n_items = (long long)n_t * n_kept;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::fence_mbar_init();
+    }
+    stage_twiddles<NY>(tw, twy);
+    __syncthreads();
+    auto item_block = [&](long long i, int* snap) {
+        *snap = (int)(i / n_kept);
+        const int j = (int)(i % n_kept);
+        return j < n_lo ? j : hi0 + (j - n_lo);
+    };
+    auto issue = [&](long long i, int st) {               // thread 0
+        int snap;
+        const int kb = item_block(i, &snap);
+        float2* dst = cstage + st * STAGE;
+        fence_proxy_async_smem();                        // the stage was exchange scratch two items ago
+        tc::mbar_arrive_expect_tx(&bar[st], STAGE_BYTES);
+        tc::tma_load_2d(dst, &map, &bar[st], kb * W, snap * NY);
+        tc::tma_load_2d(dst + (NY / 2) * W, &map, &bar[st], kb * W, snap * NY + NY / 2);
+    };
+    if (threadIdx.x == 0 && (long long)blockIdx.x < n_items) issue(blockIdx.x, 0);
+    int it = 0;
+    bool timed_out = false, next_issued = false;
+    for (long long i = blockIdx.x; i < n_items; i += gridDim.x, ++it) {
+        const int st = it & 1;
+        const long long inext = i + gridDim.x;
+        if (threadIdx.x == 0 && inext < n_items) issue(inext, st ^ 1);
+        const bool ok = tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, polls);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            next_issued = inext < n_items;
+            break;
+        }
+        int snap;
+        const int kb = item_block(i, &snap);
+        const int kx = kb * W + c;
+        float2* buf = cstage + st * STAGE;
+        const ColLayout<W> lay{c};
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = buf[(t + TPT * m) * W + c];
+        transform<NY, false>(v, buf, buf, t, tw, lay);
+        const float2 pxv = __ldg(px + kx);
+        const int kmax = __ldg(kymax + kx);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int ky = t + TPT * m;
+            const int aky = ky < NY / 2 ? ky : NY - ky;
+            v[m] = (aky <= kmax) ? cmul(v[m], cmul(pxv, __ldg(py + ky))) : make_float2(0.f, 0.f);
+        }
+        if (!last) transform<NY, true>(v, buf, buf, t, tw, lay);
+        float2* col = psi + (size_t)snap * NY * nx + kx;
+#pragma unroll
+        for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
+        __syncthreads();                                 // this stage is refilled two items later
+    }
+    if (timed_out && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        const int st = it & 1;
+        for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 20); ++k) {
+        }
+        if (next_issued)
+            for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st ^ 1], ((it + 1) >> 1) & 1, 1u << 20); ++k) {
+            }
+    }
+}
+
+// After the last slice: zeros into the exit wave's band-limited column blocks
+// (the staged column pass never touches them).
+template <int NY>
+__global__ void zero_dropped_kernel(float2* __restrict__ psi, const int* __restrict__ kymax, int nx) {
+    constexpr int W = ColCfg<NY>::W;
+    const int K = __ldg(kymax + nx);
+    const int n_lo = K / W + 1;
+    int hi0 = (nx - K - W + 1 + W - 1) / W;
+    if (hi0 < n_lo) hi0 = n_lo;
+    const int x = n_lo * W + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= hi0 * W) return;
+    float2* p = psi + (size_t)blockIdx.y * NY * nx + x;
+    for (int y = 0; y < NY; ++y) p[(size_t)y * nx] = make_float2(0.f, 0.f);
+}
+
 struct ColJobs {
     int n;
     int start[kMaxBatch + 1];
@@ -635,6 +754,65 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
     return cudaGetLastError();
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map of the waves [rows][nx] of 8-byte complex values with a box of
+// box_x columns x box_y rows (no swizzle); false if the driver cannot encode it.
+bool encode_wave_map(CUtensorMap* map, const void* ptr, int nx, long long rows, int box_x, int box_y) {
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        looked = true;
+    }
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The staged column pass of the forward step (512-point columns); *launched is
+// false when it does not apply (then the per-block pass runs).
+template <int NY>
+cudaError_t launch_col_staged(float2* psi, const float2* twy, const float2* px, const float2* py, const int* kymax,
+                              int nx, int n_t, int last, WaitCtl wc, cudaStream_t st, bool* launched) {
+    constexpr int TPT = NY / fft::Plan<NY>::E;
+    constexpr int W = ColCfg<NY>::W;
+    *launched = false;
+    if (wc.flag == nullptr || reinterpret_cast<uintptr_t>(psi) % 16 != 0 || nx % W != 0) return cudaSuccess;
+    CUtensorMap map;
+    if (!encode_wave_map(&map, psi, nx, (long long)n_t * NY, W, NY / 2)) return cudaSuccess;
+    const size_t smem = (2 * (size_t)W * NY + fft::TwSize<NY>::value) * sizeof(float2) + 2 * sizeof(uint64_t);
+    cudaError_t e = ensure_smem((const void*)col_pass_staged_kernel<NY>, (int)smem);
+    if (e != cudaSuccess) return e;
+    int resident = 0;
+    e = resident_blocks((const void*)col_pass_staged_kernel<NY>, W * TPT, (int)smem, &resident);
+    if (e != cudaSuccess) return e;
+    const long long items = (long long)n_t * (nx / W);   // at most: the kernel walks the kept blocks only
+    const int blocks = (long long)resident < items ? resident : (int)items;
+    col_pass_staged_kernel<NY><<<blocks, W * TPT, smem, st>>>(map, psi, twy, px, py, kymax, nx, n_t, last, wc.flag,
+                                                              wc.polls);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (last) {
+        zero_dropped_kernel<NY><<<dim3((nx + 127) / 128, n_t), 128, 0, st>>>(psi, kymax, nx);
+        e = cudaGetLastError();
+    }
+    *launched = true;
+    return e;
+}
+
 template <int NY, bool CONJ, bool FFT_IN>
 cudaError_t launch_col_t(float2* psi, const float2* twy, const float2* px, const float2* py,
                          const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
@@ -651,7 +829,15 @@ cudaError_t launch_col_t(float2* psi, const float2* twy, const float2* px, const
 // dir 0: forward; 1: adjoint with a leading Fy; 2: adjoint of q-space input (no leading Fy)
 template <int NY>
 cudaError_t launch_col(float2* psi, const float2* twy, const float2* px, const float2* py,
-                       const int* kymax, int nx, int n_t, int last, cudaStream_t st, int dir = 0) {
+                       const int* kymax, int nx, int n_t, int last, cudaStream_t st, int dir = 0,
+                       WaitCtl wc = WaitCtl{nullptr, 0}) {
+    if constexpr (NY == 512) {
+        if (dir == 0) {
+            bool launched = false;
+            cudaError_t e = launch_col_staged<NY>(psi, twy, px, py, kymax, nx, n_t, last, wc, st, &launched);
+            if (e != cudaSuccess || launched) return e;
+        }
+    }
     if (dir == 0) return launch_col_t<NY, false, true>(psi, twy, px, py, kymax, nx, n_t, last, st);
     if (dir == 1) return launch_col_t<NY, true, true>(psi, twy, px, py, kymax, nx, n_t, last, st);
     return launch_col_t<NY, true, false>(psi, twy, px, py, kymax, nx, n_t, last, st);
@@ -692,12 +878,13 @@ cudaError_t dispatch_row(int nx, float2* psi, const float* V, const float2* psi_
 }
 
 cudaError_t dispatch_col(int ny, float2* psi, const float2* twy, const float2* px, const float2* py,
-                         const int* kymax, int nx, int n_t, int last, cudaStream_t st, int dir = 0) {
+                         const int* kymax, int nx, int n_t, int last, cudaStream_t st, int dir = 0,
+                         WaitCtl wc = WaitCtl{nullptr, 0}) {
     switch (ny) {
         case 64: return launch_col<64>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
         case 128: return launch_col<128>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
         case 256: return launch_col<256>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
-        case 512: return launch_col<512>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
+        case 512: return launch_col<512>(psi, twy, px, py, kymax, nx, n_t, last, st, dir, wc);
         case 1024: return launch_col<1024>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
         case 384: return launch_col<384>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
         case 768: return launch_col<768>(psi, twy, px, py, kymax, nx, n_t, last, st, dir);
@@ -780,6 +967,7 @@ constexpr uint32_t kRowWaitPolls = 1u << 24;
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
                    float2* psi_q, double2* psi_sum, void* ws, cudaStream_t st, int flags) {
     const bool warp_rows = (flags & TACAW_MS_WARP_ROWS) != 0;
+    const bool block_cols = (flags & TACAW_MS_BLOCK_COLS) != 0;
     Carver cv(ws);
     MsTables tb = carve_ms(cv, g);
     WaitCtl wc{nullptr, wait_polls(kRowWaitPolls)};
@@ -799,7 +987,7 @@ int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* p
         TACAW_CUDA_CHECK(dispatch_row(g.nx, psi_q, V, psi_in, tb.twx, tb.kymax, g.ny, n_t, g.n_slices, s,
                                       sigma, mode, wc, st, warp_rows));
         TACAW_CUDA_CHECK(dispatch_col(g.ny, psi_q, tb.twy, tb.px, tb.py, tb.kymax, g.nx, n_t,
-                                      s + 1 == g.n_slices, st));
+                                      s + 1 == g.n_slices, st, 0, block_cols ? WaitCtl{nullptr, 0} : wc));
     }
     if (psi_sum) {
         const size_t nq = (size_t)g.nx * g.ny;

@@ -70,7 +70,7 @@ extern "C" int tacaw_multislice_static(const tacaw_grid* grid, int32_t n_t, cons
                   "%s: this grid needs %zu bytes of scratch, more than the fixed %zu", fn, need,
                   kStaticScratchBytes);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
-    TACAW_REQUIRE((flags & ~TACAW_MS_WARP_ROWS) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
     int rc = inject_launch_fault(fn);

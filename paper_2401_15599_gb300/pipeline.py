@@ -17,16 +17,16 @@ from . import api
 class TimeToSpectrum:
     def __init__(self, grid, n_t, n_atoms, amp_sigma, dt_fs, batch=32, omega_meV=None,
                  precision="fp32", kubo=False, temperature_K=300.0, normalize=False,
-                 device="cuda", warp_rows=False):
+                 device="cuda", ms_flags=0):
         self.grid = grid
         self.n_t = int(n_t)
         self.n_atoms = int(n_atoms)
         self.amp_sigma = amp_sigma
         self.dt_fs = float(dt_fs)
-        self.warp_rows = bool(warp_rows)        # row-pass variant (TACAW_MS_WARP_ROWS)
+        self.ms_flags = int(ms_flags)           # variants of the passes (tacaw_multislice flags)
         if batch == "auto":                     # batch and row-pass variant tuned per grid and GPU, cached
             from .tuning import best_multislice_config
-            batch, self.warp_rows = best_multislice_config(grid, device=device)
+            batch, self.ms_flags = best_multislice_config(grid, device=device)
         self.batch = max(1, min(int(batch), self.n_t))
         self.precision = precision
         self.kubo = kubo
@@ -67,7 +67,7 @@ class TimeToSpectrum:
             api.potential(self.grid, pos[t0:t1], species, self.amp_sigma, out=v,
                           workspace=self._ws.get("pot"))
             api.multislice(self.grid, v, out=self.psi[t0:t1], psi_sum=self.psi_sum,
-                           workspace=self._ws.get("ms"), warp_rows=self.warp_rows)
+                           workspace=self._ws.get("ms"), ms_flags=self.ms_flags)
         return self.psi
 
     def spectrum(self):
@@ -181,7 +181,7 @@ class TimeToSpectrum:
                           workspace=self._ws.get("pot"))
             free[slot].record(comp)
             api.multislice(self.grid, v, out=self.psi[t0:t1], psi_sum=self.psi_sum,
-                           workspace=self._ws.get("ms"), warp_rows=self.warp_rows)
+                           workspace=self._ws.get("ms"), ms_flags=self.ms_flags)
         if self._d2h_done is not None:
             comp.wait_event(self._d2h_done)     # the previous call's outputs have left I, I_el
         self.spectrum()

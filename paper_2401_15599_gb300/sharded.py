@@ -46,14 +46,14 @@ class CudaOps:
 
     phi_dtype = torch.complex64
 
-    def __init__(self, grid, n_atoms, amp_sigma, batch, precision, device, warp_rows=False):
+    def __init__(self, grid, n_atoms, amp_sigma, batch, precision, device, ms_flags=0):
         from .pipeline import TimeToSpectrum
         self.grid = grid
         self.amp_sigma = amp_sigma
         self.batch = batch
         self.precision = precision
         self.device = torch.device(device)
-        self.warp_rows = warp_rows
+        self.ms_flags = ms_flags
         self.n_atoms = n_atoms
         self._tts = None
         self._TTS = TimeToSpectrum
@@ -63,7 +63,7 @@ class CudaOps:
         n = int(pos.shape[0])
         if self._tts is None or self._tts.n_t != n:
             self._tts = self._TTS(self.grid, n, self.n_atoms, self.amp_sigma, 1.0, batch=self.batch,
-                                  device=self.device, warp_rows=self.warp_rows)
+                                  device=self.device, ms_flags=self.ms_flags)
             self._tts.prepare(None, None)
         psi = self._tts.exit_waves(pos, species)
         return psi.reshape(n, -1), self._tts.psi_sum.reshape(-1)
@@ -89,7 +89,7 @@ class ShardedTimeToSpectrum:
 
     def __init__(self, grid, n_t, n_atoms, amp_sigma, dt_fs, omega_meV, group=None, batch=32,
                  precision="bf16x6", kubo=False, temperature_K=300.0, device="cuda", ops=None,
-                 warp_rows=False):
+                 ms_flags=0):
         self.grid = grid
         self.n_t = int(n_t)
         self.dt_fs = float(dt_fs)
@@ -105,7 +105,7 @@ class ShardedTimeToSpectrum:
         self.q_lo = min(self.nq, self.rank * self.rows)
         self.q_hi = min(self.nq, self.q_lo + self.rows)
         self.ops = ops if ops is not None else CudaOps(grid, n_atoms, amp_sigma, batch, precision, device,
-                                                       warp_rows=warp_rows)
+                                                       ms_flags=ms_flags)
 
     def _all_reduce_sum(self, x):
         if self.world == 1:

@@ -1,10 +1,11 @@
 """Multislice autotuning with a JSON cache.
 
 ``best_multislice_config(grid)`` returns how many snapshots one multislice
-call should advance together on this GPU for this grid, and which row-pass
-variant to use (for 512-point rows: two warps per row, or one warp per row,
-``warp_rows``); candidates whose potentials would exceed MAX_TUNING_BYTES are
-skipped.  On a cache miss it times every (batch, variant) pair with the
+call should advance together on this GPU for this grid, and which variants of
+the passes to use (tacaw_multislice flags: for 512-point rows two warps per
+row or one, for 512-point columns the persistent TMA-staged pass or one block
+per column block); candidates whose potentials would exceed MAX_TUNING_BYTES
+are skipped.  On a cache miss it times every (batch, flags) pair with the
 library's ``tacaw_tune_multislice`` (random slice potentials: the transform
 cost does not depend on the values) and stores the result under the key
 "<device name>|<nx>x<ny>x<n_slices>".  ``best_multislice_batch`` returns the
@@ -61,12 +62,14 @@ def cache_key(grid, device_name: str) -> str:
     return f"{device_name}|{int(grid.nx)}x{int(grid.ny)}x{int(grid.n_slices)}"
 
 
-CACHE_VERSION = 2
+CACHE_VERSION = 3
 
 
-def row_variants(grid):
+def multislice_variants(grid):
     """tacaw_multislice flags worth comparing for this grid."""
-    return (0, L.TACAW_MS_WARP_ROWS) if int(grid.nx) == 512 else (0,)
+    rows = (0, L.TACAW_MS_WARP_ROWS) if int(grid.nx) == 512 else (0,)
+    cols = (0, L.TACAW_MS_BLOCK_COLS) if int(grid.ny) == 512 else (0,)
+    return tuple(r | c for r in rows for c in cols)
 
 
 def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, device="cuda", flags=0):
@@ -101,7 +104,7 @@ def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, devi
 
 
 def best_multislice_config(grid, candidates=DEFAULT_CANDIDATES, device="cuda", path=None, measure=None):
-    """Cached best (batch, warp_rows) for this grid on this device (tuned on a
+    """Cached best (batch, tacaw_multislice flags) for this grid on this device (tuned on a
     miss).  ``measure(grid, candidates, device=..., flags=...)`` replaces the
     timing function (tests)."""
     dev = torch.device(device)
@@ -109,19 +112,18 @@ def best_multislice_config(grid, candidates=DEFAULT_CANDIDATES, device="cuda", p
     key = cache_key(grid, name)
     entry = load_cache(path).get(key)
     if entry and int(entry.get("version", 0)) == CACHE_VERSION and int(entry.get("batch", 0)) >= 1:
-        return int(entry["batch"]), bool(entry.get("warp_rows", False))
+        return int(entry["batch"]), int(entry.get("flags", 0))
     best = None
     timings = {}
-    for flags in row_variants(grid):
+    for flags in multislice_variants(grid):
         t, b = (measure or measure_multislice_batches)(grid, candidates, device=device, flags=flags)
         timings[str(flags)] = {str(k): v for k, v in t.items()}
         if best is None or t[b] < best[0]:
             best = (t[b], b, flags)
     _, batch, flags = best
-    warp_rows = bool(flags & L.TACAW_MS_WARP_ROWS)
-    store_cache({key: {"version": CACHE_VERSION, "batch": int(batch), "warp_rows": warp_rows,
+    store_cache({key: {"version": CACHE_VERSION, "batch": int(batch), "flags": int(flags),
                        "ms_per_snapshot": timings}}, path)
-    return int(batch), warp_rows
+    return int(batch), int(flags)
 
 
 def best_multislice_batch(grid, candidates=DEFAULT_CANDIDATES, device="cuda", path=None, measure=None):

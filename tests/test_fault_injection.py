@@ -116,7 +116,7 @@ def test_workspace_queries_and_argument_errors_come_first(lib, monkeypatch):
     assert n.value > 0
     assert lib.tacaw_multislice(ctypes.byref(g), -1, FAKE, NULL, FAKE, NULL, 0, FAKE, _big(),
                                 NULL) == L.TACAW_EINVAL
-    assert lib.tacaw_multislice_static(ctypes.byref(g), 2, FAKE, NULL, FAKE, NULL, 2, NULL) == L.TACAW_EINVAL
+    assert lib.tacaw_multislice_static(ctypes.byref(g), 2, FAKE, NULL, FAKE, NULL, 4, NULL) == L.TACAW_EINVAL
     assert lib.tacaw_multislice_static(ctypes.byref(g), 0, FAKE, NULL, FAKE, NULL, 0, NULL) == L.TACAW_OK
 
 

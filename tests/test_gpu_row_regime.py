@@ -9,7 +9,9 @@ row groups per resident block (2048 and 4096 groups, and a long call of
 the FP64 oracle (second step of the procedure after Eq. (9): the multislice
 of each snapshot), as well as the FP64 running sum over snapshots.  Both
 thread layouts of the 512-point row pass are covered (two warps per row, and
-one warp per row with 16 values per thread).
+one warp per row with 16 values per thread), and both forms of the
+512-point column pass (the persistent pass with TMA-staged tiles, and one
+block per column block).
 """
 
 import numpy as np
@@ -37,14 +39,16 @@ def _grid(n, n_slices, pixel=0.158203125):
     return O.Grid(n, n, n * pixel, n * pixel, n_slices, 2.0, 0.0, 200.0, 2.0 / 3.0)
 
 
-@pytest.mark.parametrize("n,n_slices,n_t,with_psi_in,warp_rows", [
-    (256, 4, 64, False, False),      # 32 groups of 8 rows per snapshot: 2048 groups
-    (512, 3, 32, True, False),       # 128 groups of 4 rows per snapshot: 4096 groups
-    (512, 2, 128, False, False),     # 16384 groups, about 27 per resident block
-    (512, 3, 32, True, True),        # one warp per row: 64 groups of 8 rows per snapshot
-    (512, 2, 128, False, True),
+@pytest.mark.parametrize("n,n_slices,n_t,with_psi_in,ms_flags", [
+    (256, 4, 64, False, 0),          # 32 groups of 8 rows per snapshot: 2048 groups
+    (512, 3, 32, True, 0),           # 128 groups of 4 rows per snapshot: 4096 groups; staged columns
+    (512, 2, 128, False, 0),         # 16384 groups, about 27 per resident block
+    (512, 3, 32, True, 1),           # one warp per row: 64 groups of 8 rows per snapshot
+    (512, 2, 128, False, 1),
+    (512, 3, 32, True, 2),           # one block per column block
+    (512, 2, 64, False, 3),
 ])
-def test_row_pass_many_groups_per_block(api, n, n_slices, n_t, with_psi_in, warp_rows):
+def test_row_pass_many_groups_per_block(api, n, n_slices, n_t, with_psi_in, ms_flags):
     g = _grid(n, n_slices)
     rng = np.random.default_rng(1000 + n + n_t)
     v = rng.uniform(0.0, 30.0, (n_t, n_slices, n, n)).astype(np.float32)
@@ -54,7 +58,7 @@ def test_row_pass_many_groups_per_block(api, n, n_slices, n_t, with_psi_in, warp
     V = torch.from_numpy(v).cuda()
     pin = None if psi_in is None else torch.from_numpy(psi_in).cuda()
     psum = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
-    out = api.multislice(g, V, psi_in=pin, psi_sum=psum, warp_rows=warp_rows)
+    out = api.multislice(g, V, psi_in=pin, psi_sum=psum, ms_flags=ms_flags)
     api.status()
     got = out.cpu().numpy()
     ref_sum = np.zeros((n, n), dtype=np.complex128)
@@ -66,7 +70,7 @@ def test_row_pass_many_groups_per_block(api, n, n_slices, n_t, with_psi_in, warp
         worst = max(worst, err)
         worst_abs = max(worst_abs, float(np.max(np.abs(got[t] - ref))))
         assert err < WAVE_TOL, (t, err)
-    print(f"\n{n}^2 x {n_slices} slices x {n_t} snapshots (warp_rows={warp_rows}): worst rel-L2 {worst:.2e}, max |diff| {worst_abs:.2e}")
+    print(f"\n{n}^2 x {n_slices} slices x {n_t} snapshots (flags {ms_flags}): worst rel-L2 {worst:.2e}, max |diff| {worst_abs:.2e}")
     # the FP64 running sum adds the FP32 exit waves: compare it with their own sum, and with the oracle's
     own = got.astype(np.complex128).sum(axis=0)
     assert np.allclose(psum.cpu().numpy(), own, rtol=1e-12, atol=1e-12)

@@ -19,7 +19,7 @@ def test_miss_measures_and_hit_reuses(tmp_path):
 
     def fake(grid, candidates, device="cuda", flags=0):
         calls.append((grid.nx, tuple(candidates), flags))
-        t = {c: 1.0 / c + (0.5 if c == 32 else 0.0) - (0.001 if flags else 0.0) for c in candidates}
+        t = {c: 1.0 / c + (0.5 if c == 32 else 0.0) - (0.001 if flags == 1 else 0.0) for c in candidates}
         return t, min(t, key=t.get)
 
     b1 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
@@ -27,12 +27,13 @@ def test_miss_measures_and_hit_reuses(tmp_path):
     b2 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
     assert b2 == 64 and len(calls) == 1                     # from the cache
     cfg = tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake)
-    assert cfg == (16, True) and len(calls) == 3            # 512-point rows: both variants timed
-    assert tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake) == (16, True)
+    assert cfg == (16, 1) and len(calls) == 5               # 512-point grids: four variants timed
+    assert {c[2] for c in calls[1:]} == {0, 1, 2, 3}
+    assert tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake) == (16, 1)
     data = json.load(open(path))
-    assert len(calls) == 3 and len(data) == 2
+    assert len(calls) == 5 and len(data) == 2
     entry = data["test-device|256x256x10"]
-    assert entry["batch"] == 64 and entry["warp_rows"] is False
+    assert entry["batch"] == 64 and entry["flags"] == 0
     assert set(entry["ms_per_snapshot"]["0"]) == {"8", "16", "32", "64"}
 
 
@@ -46,8 +47,8 @@ def test_old_entries_are_tuned_again(tmp_path):
         return {4: 2.0, 8: 1.0 + flags}, 8
 
     assert tuning.best_multislice_config(_grid(512, 101), candidates=(4, 8), path=str(path),
-                                         measure=fake) == (8, False)
-    assert calls == [0, 1]
+                                         measure=fake) == (8, 0)
+    assert sorted(calls) == [0, 1, 2, 3]
 
 
 def test_corrupt_cache_is_ignored(tmp_path):
