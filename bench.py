@@ -695,55 +695,57 @@ def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=64):
             "value_graph": units / (graph_ms * 1e-3), "unit": UNIT}
 
 
-def full_batched_jobs(stream, window=8, graph=False, max_jobs=64, max_snapshots=None):
+def full_batched_jobs(stream, graph=True, max_jobs=64, max_snapshots=None, v_budget=48e9, max_window=512):
     """The batched configuration as stated: the 64 seeded uneven jobs (seeds
     1000-1063; grids 128-768, 10-150 slices, 512-4096 snapshots, 1-3 species)
-    through the time-chunked batched driver: per window of snapshots, the
+    through the time-chunked batched driver, one group per grid size (so one
+    launch covers many snapshots of like jobs): per window of snapshots the
     positions are synthesised on the device (the inputs of all jobs together
-    would take 94 GB), then slice potentials, one batched multislice call for
-    all jobs, and each job's Phi(q, E) accumulated on 1024 bins over
+    would take 94 GB), then slice potentials, one batched multislice call for the
+    group's jobs, and each job's Phi(q, E) accumulated on 1024 bins over
     [-200, 200) meV in split BF16 (three terms); each job's I(q, E) is finished
-    at the end.  One eager run, timed with CUDA events (the synthesis of the
-    positions is inside the timed region and is timed separately too)."""
+    at the end.  A group's window holds `v_budget` bytes of potentials.  Each
+    group runs once eagerly (untimed), is captured in a CUDA graph and replayed
+    (timed, CUDA events); the groups run one after another and their times add
+    up.  The synthesis of the positions is inside the timed region."""
     import numpy as np
     import torch
     import workloads as W
     from paper_2401_15599_gb300.batch import BatchTimeToSpectrum, Job
     omega = np.arange(1024) * (400.0 / 1024) - 200.0
-    jobs, units, synth_only = [], 0, []
-    for wj in W.batching_jobs(n_jobs=max_jobs):
-        if max_snapshots:
-            wj = wj.with_(n_t=min(wj.n_t, max_snapshots))
-        inp = W.build_inputs(wj)
-        synth = inp.synth("cuda")
-        jobs.append(Job(wj.grid, None, torch.from_numpy(inp.species).cuda(), inp.amp_sigma, wj.dt_fs,
-                        omega_meV=omega, n_t=wj.n_t, positions=synth))
-        synth_only.append((synth, wj.n_t, inp.crystal.n_atoms))
-        units += wj.grid.nx * wj.grid.ny * wj.grid.n_slices * wj.n_t
-    run = BatchTimeToSpectrum(jobs, window=window, precision="bf16x6", chunked=True)
-    run.prepare()
-    run.run()                                            # warm-up (fills the per-kernel attributes)
-    torch.cuda.synchronize()
-    ms = _events_ms(run.run, 1, stream)
-
-    def synth_all():
-        for synth, n_t, na in synth_only:
-            buf = torch.empty((window, na, 3), dtype=torch.float32, device="cuda")
-            for t0 in range(0, n_t, window):
-                synth(t0, min(n_t, t0 + window), out=buf[: min(n_t, t0 + window) - t0])
-
-    synth_ms = _events_ms(synth_all, 1, stream)
-    out = {"jobs": len(jobs), "snapshots": int(sum(j.n_t for j in jobs)), "window": window, "units": units,
-           "ms": ms, "value": units / (ms * 1e-3), "unit": UNIT, "position_synthesis_ms": synth_ms,
-           "value_without_synthesis": units / ((ms - synth_ms) * 1e-3),
-           "spectrum": "1024 bins over [-200, 200) meV, BF16X6, time-chunked"}
-    if graph:
-        run.capture()
-        out["graph_ms"] = _events_ms(run.replay, 1, stream)
-        out["value_graph"] = units / (out["graph_ms"] * 1e-3)
-    del run
-    torch.cuda.empty_cache()
-    return out
+    specs = W.batching_jobs(n_jobs=max_jobs)
+    if max_snapshots:
+        specs = [wj.with_(n_t=min(wj.n_t, max_snapshots)) for wj in specs]
+    sizes = sorted({wj.grid.nx for wj in specs})
+    groups, total_ms, units_all = [], 0.0, 0
+    for n in sizes:
+        members = [wj for wj in specs if wj.grid.nx == n]
+        per_snapshot = sum(4.0 * wj.grid.n_slices * wj.grid.nx * wj.grid.ny for wj in members)
+        window = int(max(8, min(max_window, v_budget // per_snapshot)))
+        jobs, units = [], 0
+        for wj in members:
+            inp = W.build_inputs(wj)
+            jobs.append(Job(wj.grid, None, torch.from_numpy(inp.species).cuda(), inp.amp_sigma, wj.dt_fs,
+                            omega_meV=omega, n_t=wj.n_t, positions=inp.synth("cuda")))
+            units += wj.grid.nx * wj.grid.ny * wj.grid.n_slices * wj.n_t
+        run = BatchTimeToSpectrum(jobs, window=window, precision="bf16x6", chunked=True)
+        if graph:
+            run.capture()                                    # one eager run, then the recording
+            ms = _events_ms(run.replay, 1, stream)
+        else:
+            run.prepare()
+            run.run()
+            torch.cuda.synchronize()
+            ms = _events_ms(run.run, 1, stream)
+        groups.append({"grid": n, "jobs": len(jobs), "window": window, "units": units, "ms": ms,
+                       "value": units / (ms * 1e-3)})
+        total_ms += ms
+        units_all += units
+        del run, jobs
+        torch.cuda.empty_cache()
+    return {"jobs": len(specs), "snapshots": int(sum(wj.n_t for wj in specs)), "units": units_all,
+            "ms": total_ms, "value": units_all / (total_ms * 1e-3), "unit": UNIT, "graph": graph,
+            "groups": groups, "spectrum": "1024 bins over [-200, 200) meV, BF16X6, time-chunked"}
 
 
 def adjoint_sample(reps, stream, snapshots=64):
@@ -934,7 +936,7 @@ def main():
         torch.cuda.set_device(0)
         from paper_2401_15599_gb300 import _lib
         _lib.load()
-        print(json.dumps({"batched_jobs_full": full_batched_jobs(torch.cuda.current_stream(), graph=True)}))
+        print(json.dumps({"batched_jobs_full": full_batched_jobs(torch.cuda.current_stream())}))
         return 0
     if args.shard or dist_env()[1] > 1:
         return run_sharded(args)
