@@ -165,6 +165,39 @@ struct ColLayout {
     __device__ __forceinline__ int operator()(int p) const { return (p ^ ((p >> 3) & (kGroups - 1))) * W + c; }
 };
 
+// Padded layouts: position p is stored at p + p / 16 (one spare slot after
+// every sixteen), so a transform of N positions takes PaddedLen<N> slots.  In
+// every exchange of these plans a butterfly touches positions base + o whose
+// offsets o keep (base mod 16) + (o mod 16) below 16, so the padded address is
+// the butterfly's padded base plus a compile-time offset: one address
+// computation per butterfly instead of one per element.  For 8-byte elements
+// every exchange of the plans then takes the minimum number of shared-memory
+// wavefronts, for one row per transform (PadRowLayout) as for W interleaved
+// transforms (PadColLayout).
+template <int N>
+struct PaddedLen { static constexpr int value = N + N / 16; };
+
+__host__ __device__ constexpr int pad16(int p) { return p + (p >> 4); }
+
+struct PadRowLayout {
+    static constexpr bool kPadded = true;
+    int base;  // row * PaddedLen<N>
+    __device__ __forceinline__ int operator()(int p) const { return base + pad16(p); }
+    __device__ __forceinline__ int at(int pb, int o) const { return base + pb + pad16(o); }   // pb = pad16(b)
+};
+template <int W>
+struct PadColLayout {
+    static constexpr bool kPadded = true;
+    int c;
+    __device__ __forceinline__ int operator()(int p) const { return pad16(p) * W + c; }
+    __device__ __forceinline__ int at(int pb, int o) const { return (pb + pad16(o)) * W + c; }
+};
+
+template <class L, class = void>
+struct IsPadded { static constexpr bool value = false; };
+template <class L>
+struct IsPadded<L, decltype(void(L::kPadded))> { static constexpr bool value = L::kPadded; };
+
 // Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
 template <int N, int E, int R, int NS, int OFF, bool INV>
 __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw) {
@@ -193,8 +226,18 @@ __device__ __forceinline__ void write_out(const float2 (&v)[E], float2* buf, int
     for (int b = 0; b < E / R; ++b) {
         const int j = t + b * TPT;
         const int base = (j / NS) * NS * R + (j % NS);
+        if constexpr (IsPadded<L>::value) {
+            // base + r NS: NS a multiple of 16; NS = 8 with R even (base mod 16 below 8); or NS = 1
+            // with R dividing 16 (base a multiple of R)
+            static_assert(NS % 16 == 0 || (NS == 8 && R % 2 == 0) || (NS == 1 && 16 % R == 0),
+                          "padded exchange needs offsets that do not carry");
+            const int pb = pad16(base);
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[lay(base + r * NS)] = v[b * R + r];
+            for (int r = 0; r < R; ++r) buf[lay.at(pb, r * NS)] = v[b * R + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[lay(base + r * NS)] = v[b * R + r];
+        }
     }
 }
 
@@ -204,8 +247,16 @@ __device__ __forceinline__ void read_in(float2 (&v)[E], const float2* buf, int t
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const int j = t + b * TPT;
+        if constexpr (IsPadded<L>::value) {
+            // j + r N/R: N/R a multiple of 16, or 8 (then j < 8)
+            static_assert((N / R) % 16 == 0 || N / R == 8, "padded exchange needs offsets that do not carry");
+            const int pb = pad16(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay(j + r * (N / R))];
+            for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay.at(pb, r * (N / R))];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay(j + r * (N / R))];
+        }
     }
 }
 

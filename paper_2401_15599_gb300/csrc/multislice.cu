@@ -162,7 +162,7 @@ __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float*
     using namespace fft;
     constexpr int E = Plan<NX>::E;
     constexpr int TPT = NX / E;
-    const RowLayout lay{row * NX};
+    const PadRowLayout lay{row * PaddedLen<NX>::value};
     float2 v[E];
     if (mode == 0) {
 #pragma unroll
@@ -200,8 +200,9 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
                 int ahead) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
+    constexpr int PL = fft::PaddedLen<NX>::value;
     extern __shared__ float2 smem[];
-    float2* tw = smem + 2 * ROWS * NX;
+    float2* tw = smem + 2 * ROWS * PL;
     if (ahead > 0 && threadIdx.x == 0) {
         prefetch_l2_bulk(V + (((size_t)blockIdx.y * n_slices + s) * ny + (size_t)blockIdx.x * ROWS) * NX,
                          ROWS * NX * sizeof(float));
@@ -219,7 +220,7 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
     const size_t snap = blockIdx.y;
     row_body<NX>(psi + (snap * ny + y) * NX, V + ((snap * n_slices + s) * ny + y) * NX,
                  psi_in ? psi_in + (size_t)y * NX : nullptr, mode, sigma, __ldg(kymax + NX), smem,
-                 smem + ROWS * NX, tw, t, row);
+                 smem + ROWS * PL, tw, t, row);
 }
 
 
@@ -254,7 +255,8 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     constexpr int E = P::E;
     constexpr int TPT = NX / E;
     constexpr int ROWS = kRowThreads / TPT;
-    constexpr int PSI_BYTES = ROWS * NX * (int)sizeof(float2);
+    constexpr int PL = PaddedLen<NX>::value;            // a row's slot: the padded exchange layout
+    constexpr int PSI_BYTES = ROWS * PL * (int)sizeof(float2);
     constexpr int V_BYTES = ROWS * NX * (int)sizeof(float);
     constexpr int STAGE = PSI_BYTES + V_BYTES;
     extern __shared__ __align__(128) unsigned char stage_raw[];
@@ -284,9 +286,9 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
         tc::mbar_arrive_expect_tx(&bar[st], tx_bytes);
         const float2* src = psi + ((size_t)snap * ny + y0) * NX;
         for (int r = 0; r < ROWS; ++r) {
-            bulk_copy_g2s(dst + (size_t)r * NX * sizeof(float2), src + (size_t)r * NX, a * sizeof(float2), &bar[st]);
+            bulk_copy_g2s(dst + (size_t)r * PL * sizeof(float2), src + (size_t)r * NX, a * sizeof(float2), &bar[st]);
             if (b < NX)
-                bulk_copy_g2s(dst + ((size_t)r * NX + b) * sizeof(float2), src + (size_t)r * NX + b,
+                bulk_copy_g2s(dst + ((size_t)r * PL + b) * sizeof(float2), src + (size_t)r * NX + b,
                               (NX - b) * sizeof(float2), &bar[st]);
         }
         bulk_copy_g2s(dst + PSI_BYTES, V + (((size_t)snap * n_slices + s) * ny + y0) * NX, V_BYTES, &bar[st]);
@@ -308,11 +310,11 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
         }
         float2* buf = reinterpret_cast<float2*>(stage_raw + st * STAGE);
         const float* vrow = reinterpret_cast<const float*>(stage_raw + st * STAGE + PSI_BYTES) + row * NX;
-        const RowLayout lay{row * NX};
+        const PadRowLayout lay{row * PL};
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m)
-            v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * NX + t + TPT * m] : make_float2(0.f, 0.f);
+            v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * PL + t + TPT * m] : make_float2(0.f, 0.f);
         const auto row_sync = row_sync_of<TPT>(row);   // a row's transforms touch only its own row
         transform_plan<P, NX, true>(v, buf, buf, t, tw, lay, row_sync);
 #pragma unroll
@@ -368,8 +370,9 @@ __global__ void __launch_bounds__(kRowThreads)
 row_batch_kernel(const __grid_constant__ RowJobs jobs, const float2* __restrict__ twx, int ny, int s) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
+    constexpr int PL = fft::PaddedLen<NX>::value;
     extern __shared__ float2 smem[];
-    float2* tw = smem + 2 * ROWS * NX;
+    float2* tw = smem + 2 * ROWS * PL;
     stage_twiddles<NX>(tw, twx);
     const int t = threadIdx.x % TPT;
     const int row = threadIdx.x / TPT;
@@ -379,7 +382,7 @@ row_batch_kernel(const __grid_constant__ RowJobs jobs, const float2* __restrict_
     const float2* pin = jobs.psi_in[j];
     row_body<NX>(jobs.psi[j] + (snap * ny + y) * NX, jobs.V[j] + ((snap * jobs.n_slices[j] + s) * ny + y) * NX,
                  pin ? pin + (size_t)y * NX : nullptr, jobs.mode[j], jobs.sigma[j], __ldg(jobs.kymax[j] + NX),
-                 smem, smem + ROWS * NX, tw, t, row);
+                 smem, smem + ROWS * PL, tw, t, row);
 }
 
 // W columns per column-pass block and the blocks per SM the register budget
@@ -407,7 +410,7 @@ __device__ __forceinline__ void col_body(float2* __restrict__ col, int nx, int k
     constexpr int E = Plan<NY>::E;
     constexpr int TPT = NY / E;
     constexpr int W = ColCfg<NY>::W;
-    const ColLayout<W> lay{c};
+    const PadColLayout<W> lay{c};
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = col[(size_t)(t + TPT * m) * nx];
@@ -449,8 +452,9 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
                 const float2* __restrict__ px, const float2* __restrict__ py,
                 const int* __restrict__ kymax, int nx, int last) {
     constexpr int W = ColCfg<NY>::W;
+    constexpr int PL = fft::PaddedLen<NY>::value;
     extern __shared__ float2 smem[];
-    float2* tw = smem + 2 * W * NY;
+    float2* tw = smem + 2 * W * PL;
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int kx = blockIdx.x * W + c;
@@ -460,7 +464,7 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
         return;
     stage_twiddles<NY>(tw, twy);
     col_body<NY, CONJ, FFT_IN>(psi + snap * NY * (size_t)nx + kx, nx, kx, px, py, kymax, last, smem,
-                               smem + W * NY, tw, t, c);
+                               smem + W * PL, tw, t, c);
 }
 
 // Staged column pass of the forward slice step (Fy -> x P BL / (nx ny) -> Fy^-1,
@@ -483,8 +487,8 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
     constexpr int E = Plan<NY>::E;
     constexpr int TPT = NY / E;
     constexpr int W = ColCfg<NY>::W;
-    constexpr int STAGE = NY * W;                       // float2 per stage
-    constexpr uint32_t STAGE_BYTES = STAGE * sizeof(float2);
+    constexpr int STAGE = PaddedLen<NY>::value * W;     // float2 per stage: the padded exchange layout
+    constexpr uint32_t STAGE_BYTES = NY * W * sizeof(float2);   // what TMA brings (dense)
     extern __shared__ __align__(128) float2 cstage[];
     float2* tw = cstage + 2 * STAGE;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + TwSize<NY>::value);
@@ -536,7 +540,7 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
         const int kb = item_block(i, &snap);
         const int kx = kb * W + c;
         float2* buf = cstage + st * STAGE;
-        const ColLayout<W> lay{c};
+        const PadColLayout<W> lay{c};
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = buf[(t + TPT * m) * W + c];
@@ -595,8 +599,9 @@ template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), ColCfg<NY>::kMinBlocks)
 col_batch_kernel(const __grid_constant__ ColJobs jobs, const float2* __restrict__ twy, int nx) {
     constexpr int W = ColCfg<NY>::W;
+    constexpr int PL = fft::PaddedLen<NY>::value;
     extern __shared__ float2 smem[];
-    float2* tw = smem + 2 * W * NY;
+    float2* tw = smem + 2 * W * PL;
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int kx = blockIdx.x * W + c;
@@ -607,7 +612,7 @@ col_batch_kernel(const __grid_constant__ ColJobs jobs, const float2* __restrict_
         return;
     stage_twiddles<NY>(tw, twy);
     col_body<NY, false, true>(jobs.psi[j] + snap * NY * (size_t)nx + kx, nx, kx, jobs.px[j], jobs.py[j],
-                              jobs.kymax[j], jobs.last[j], smem, smem + W * NY, tw, t, c);
+                              jobs.kymax[j], jobs.last[j], smem, smem + W * PL, tw, t, c);
 }
 
 // Adjoint row pass of slice s.  g holds the gradient (k_x, y) rows after the
@@ -626,10 +631,11 @@ row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const 
     constexpr int E = Plan<NX>::E;
     constexpr int TPT = NX / E;
     constexpr int ROWS = kRowThreads / TPT;
+    constexpr int PL = PaddedLen<NX>::value;
     extern __shared__ float2 smem[];
     float2* b0 = smem;
-    float2* b1 = smem + ROWS * NX;
-    float2* tw = smem + 2 * ROWS * NX;
+    float2* b1 = smem + ROWS * PL;
+    float2* tw = smem + 2 * ROWS * PL;
     stage_twiddles<NX>(tw, twx);
 
     const int t = threadIdx.x % TPT;
@@ -638,7 +644,7 @@ row_back_kernel(float2* __restrict__ g, const float2* __restrict__ state, const 
     const size_t snap = blockIdx.y;
     float2* grow = g + (snap * ny + y) * NX;
     const size_t vrow_off = ((snap * n_slices + s) * ny + y) * NX;
-    const RowLayout lay{row * NX};
+    const PadRowLayout lay{row * PL};
 
     // g and the hybrid state hold data only in the kept columns
     const int K = __ldg(kymax + NX);
@@ -700,7 +706,7 @@ cudaError_t launch_row_staged(float2* psi, const float* V, const float2* twx, co
     constexpr int TPT = NX / P::E;
     constexpr int ROWS = kRowThreads / TPT;
     *launched = false;
-    const size_t smem = 2 * (size_t)ROWS * NX * (sizeof(float2) + sizeof(float)) +
+    const size_t smem = 2 * (size_t)ROWS * (fft::PaddedLen<NX>::value * sizeof(float2) + NX * sizeof(float)) +
                         fft::TwSize<NX>::value * sizeof(float2) + 2 * sizeof(uint64_t);
     cudaError_t e = ensure_smem((const void*)row_pass_staged_kernel<NX, P>, (int)smem);
     if (e != cudaSuccess) return e;
@@ -740,7 +746,7 @@ cudaError_t launch_row(float2* psi, const float* V, const float2* psi_in, const 
         }
         if (e != cudaSuccess || launched) return e;
     }
-    const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
+    const size_t smem = (2 * ROWS * fft::PaddedLen<NX>::value + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_pass_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     int ahead = 0;
@@ -793,7 +799,8 @@ cudaError_t launch_col_staged(float2* psi, const float2* twy, const float2* px, 
     if (wc.flag == nullptr || reinterpret_cast<uintptr_t>(psi) % 16 != 0 || nx % W != 0) return cudaSuccess;
     CUtensorMap map;
     if (!encode_wave_map(&map, psi, nx, (long long)n_t * NY, W, NY / 2)) return cudaSuccess;
-    const size_t smem = (2 * (size_t)W * NY + fft::TwSize<NY>::value) * sizeof(float2) + 2 * sizeof(uint64_t);
+    const size_t smem = (2 * (size_t)W * fft::PaddedLen<NY>::value + fft::TwSize<NY>::value) * sizeof(float2) +
+                        2 * sizeof(uint64_t);
     cudaError_t e = ensure_smem((const void*)col_pass_staged_kernel<NY>, (int)smem);
     if (e != cudaSuccess) return e;
     int resident = 0;
@@ -818,7 +825,7 @@ cudaError_t launch_col_t(float2* psi, const float2* twy, const float2* px, const
                          const int* kymax, int nx, int n_t, int last, cudaStream_t st) {
     constexpr int TPT = NY / fft::Plan<NY>::E;
     constexpr int W = ColCfg<NY>::W;
-    const size_t smem = (2 * W * NY + fft::TwSize<NY>::value) * sizeof(float2);
+    const size_t smem = (2 * W * fft::PaddedLen<NY>::value + fft::TwSize<NY>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)col_pass_kernel<NY, CONJ, FFT_IN>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(nx / W, n_t);
@@ -849,7 +856,7 @@ cudaError_t launch_row_back(float2* g, const float2* state, const float* V, floa
                             int n_slices, int s, float sigma, int mode, int fft_out, cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
-    const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
+    const size_t smem = (2 * ROWS * fft::PaddedLen<NX>::value + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_back_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / ROWS, n_t);
@@ -896,7 +903,7 @@ template <int NX>
 cudaError_t launch_row_batch(const RowJobs& jobs, const float2* twx, int ny, int total, int s, cudaStream_t st) {
     constexpr int TPT = NX / fft::Plan<NX>::E;
     constexpr int ROWS = kRowThreads / TPT;
-    const size_t smem = (2 * ROWS * NX + fft::TwSize<NX>::value) * sizeof(float2);
+    const size_t smem = (2 * ROWS * fft::PaddedLen<NX>::value + fft::TwSize<NX>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)row_batch_kernel<NX>, (int)smem);
     if (e != cudaSuccess) return e;
     row_batch_kernel<NX><<<dim3(ny / ROWS, total), kRowThreads, smem, st>>>(jobs, twx, ny, s);
@@ -907,7 +914,7 @@ template <int NY>
 cudaError_t launch_col_batch(const ColJobs& jobs, const float2* twy, int nx, int total, cudaStream_t st) {
     constexpr int TPT = NY / fft::Plan<NY>::E;
     constexpr int W = ColCfg<NY>::W;
-    const size_t smem = (2 * W * NY + fft::TwSize<NY>::value) * sizeof(float2);
+    const size_t smem = (2 * W * fft::PaddedLen<NY>::value + fft::TwSize<NY>::value) * sizeof(float2);
     cudaError_t e = ensure_smem((const void*)col_batch_kernel<NY>, (int)smem);
     if (e != cudaSuccess) return e;
     col_batch_kernel<NY><<<dim3(nx / W, total), W * TPT, smem, st>>>(jobs, twy, nx);
