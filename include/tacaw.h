@@ -67,6 +67,10 @@ extern "C" {
 #define TACAW_MS_BLOCK_COLS 2   /* 512-point columns: one block per column block instead of the
                                    persistent column pass with TMA-staged tiles; identical
                                    results; ignored for other sizes */
+#define TACAW_MS_QUEUE 4        /* square grids: all slices in one persistent launch over a device
+                                   work queue (tacaw_multislice_queue with one job and the default
+                                   wave); identical results; alone, not with the flags above; the
+                                   workspace then also holds the queue's counters */
 
 /* flags of tacaw_spectrum */
 #define TACAW_KUBO 1            /* multiply by beta E / (1 - exp(-beta E)), Eq. (8) */
@@ -185,7 +189,8 @@ int tacaw_potential(const tacaw_grid* grid, int32_t n_t, int32_t n_atoms,
  * psi_sum  in/out [ny][nx] double2 running sum over snapshots, or NULL; when
  *          given, sum_t psi_q(t) is ADDED to it in FP64 (snapshot order)
  * flags    0, TACAW_MS_WARP_ROWS and / or TACAW_MS_BLOCK_COLS (variants of the
- *          passes' thread layout and staging, for the autotuner)
+ *          passes' thread layout and staging, for the autotuner), or
+ *          TACAW_MS_QUEUE alone (square grids)
  * Supported sizes: nx, ny in {64, 128, 256, 384, 512, 768, 1024}.
  */
 int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V,
@@ -467,6 +472,40 @@ typedef struct tacaw_job {
 
 int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size_t* ws_bytes,
                            void* stream);
+
+/*
+ * The jobs of tacaw_multislice_batch (square grids only) through one
+ * persistent launch per grid size that takes its work from a device queue
+ * instead of two launches per slice.  Every snapshot is an independent
+ * multislice run (second step of the procedure after Eq. (9)); a queue item
+ * is one pass (row: x transforms and transmission; column: y transforms and
+ * propagator with band limit) of one slice over item_span rows or columns
+ * of one snapshot.  Items run job by job and, within a job, in waves of
+ * `wave_snapshots` snapshots: slice 0 row items of the whole wave, its column
+ * items, slice 1, and so on, so a wave's exit-wave buffers stay in L2 between
+ * the passes.  An item starts when the items it depends on (the previous
+ * pass of the same snapshot) have finished: device-side counters, waits
+ * bounded by the limit of tacaw_set_wait_limit (default a few seconds each);
+ * a wait that gives up stops the launch and makes tacaw_status report
+ * TACAW_ETIMEOUT.  Results are bit-identical to tacaw_multislice_batch and
+ * to tacaw_multislice for each job.
+ * jobs            HOST array as for tacaw_multislice_batch (n_t up to 2^24 per
+ *                 job, 2^28 in all); grids with nx == ny in the supported sizes;
+ *                 V and psi_q 16-byte aligned
+ * wave_snapshots  snapshots per wave, or 0: as many as fit about 64 MiB of
+ *                 exit waves (32 at 512^2)
+ * item_span       rows or columns per item: a multiple of the rows one block
+ *                 transforms at once (256 / (N / values per thread): 4 at
+ *                 512^2) that divides N; 0 or any other value: 16 (the
+ *                 block's rows where those exceed 16)
+ * Workspace: the per-job tables of tacaw_multislice plus 8 bytes per snapshot
+ * and 16 bytes of queue state.  Errors: TACAW_EUNSUPPORTED for a grid that is
+ * not square or not a supported size, TACAW_EINVAL for bad counts or NULL
+ * arrays.  Enqueues only (memsets and kernels): suited to CUDA graph capture
+ * after one call outside capture.
+ */
+int tacaw_multislice_queue(const tacaw_job* jobs, int32_t n_jobs, int32_t wave_snapshots, int32_t item_span,
+                           void* ws, size_t* ws_bytes, void* stream);
 
 /*
  * Adjoint of tacaw_multislice for gradient-based fitting (PyTorch convention

@@ -30,6 +30,7 @@ TACAW_MAX_SPECIES = 8
 TACAW_MAX_BATCH = 64
 TACAW_MS_WARP_ROWS = 1
 TACAW_MS_BLOCK_COLS = 2
+TACAW_MS_QUEUE = 4
 
 ERRORS = {
     TACAW_EINVAL: "EINVAL", TACAW_ECUDA: "ECUDA", TACAW_ENOMEM: "ENOMEM",
@@ -77,6 +78,8 @@ SIGNATURES = {
     "tacaw_multislice_static": (ctypes.c_int, [ctypes.POINTER(TacawGrid), ctypes.c_int32, _P, _P, _P, _P,
                                                ctypes.c_int32, _P]),
     "tacaw_multislice_batch": (ctypes.c_int, [ctypes.POINTER(TacawJob), ctypes.c_int32, _P, _SZ, _P]),
+    "tacaw_multislice_queue": (ctypes.c_int, [ctypes.POINTER(TacawJob), ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, _P, _SZ, _P]),
     "tacaw_spectrum": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P,
                                       _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                       _P, _SZ, _P]),

@@ -93,7 +93,7 @@ def potential(grid, pos, species, amp_sigma, out=None, workspace=None):
 def multislice(grid, V, psi_in=None, out=None, psi_sum=None, workspace=None, ms_flags=0):
     """Exit waves psi_q [T, ny, nx] (complex64, q-space, FFT order) for potentials V.
     ms_flags: tacaw_multislice flags choosing variants of the passes (TACAW_MS_WARP_ROWS,
-    TACAW_MS_BLOCK_COLS; the tuner picks them per grid and GPU)."""
+    TACAW_MS_BLOCK_COLS, or TACAW_MS_QUEUE alone; the tuner picks them per grid and GPU)."""
     lib = L.load()
     _need_cuda("V", V, torch.float32, 4)
     n_t = V.shape[0]
@@ -359,12 +359,16 @@ def potential_backward(grid, pos, species, amp_sigma, dl_dv, out=None, workspace
     return out
 
 
-def multislice_batch(jobs, workspace=None):
+def multislice_batch(jobs, workspace=None, queue=False, wave=0, span=0):
     """Run several multislice jobs of uneven size in one call.
 
     jobs: sequence of dicts with keys grid, V [T, n_s, ny, nx] float32, out
     [T, ny, nx] complex64 and optionally psi_in [ny, nx] complex64 and
     psi_sum [ny, nx] complex128.  All tensors on the same CUDA device.
+    queue: use tacaw_multislice_queue (square grids; one persistent launch per
+    grid size over a device work queue, waves of `wave` snapshots and items of
+    `span` rows or columns, 0 = defaults) instead of tacaw_multislice_batch (two
+    launches per slice).
     """
     lib = L.load()
     arr = (L.TacawJob * max(1, len(jobs)))()
@@ -386,6 +390,12 @@ def multislice_batch(jobs, workspace=None):
                             psi_sum.data_ptr() if psi_sum is not None else None)
         dev = V.device
     if dev is None:
+        return
+
+    if queue:
+        def call(ws, nbytes):
+            return lib.tacaw_multislice_queue(arr, len(jobs), int(wave), int(span), ws, nbytes, _stream(dev))
+        _call_with_workspace("tacaw_multislice_queue", call, dev, workspace)
         return
 
     def call(ws, nbytes):

@@ -50,6 +50,8 @@ int spectrum_backward_run(int nq, int n_t, double dt_fs, int n_w, const double* 
 size_t multislice_backward_ws_bytes(const tacaw_grid& g, int n_t, int every);
 size_t multislice_batch_ws_bytes(const tacaw_job* jobs, int n_jobs);
 int multislice_batch_run(const tacaw_job* jobs, int n_jobs, void* ws, cudaStream_t st);
+size_t multislice_queue_ws_bytes(const tacaw_job* jobs, int n_jobs);
+int multislice_queue_run(const tacaw_job* jobs, int n_jobs, int wave, int span, void* ws, cudaStream_t st);
 int multislice_backward_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in,
                             const float2* g_exit, float* dV, int every, void* ws, cudaStream_t st);
 int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n_species, size_t* bytes);
@@ -182,16 +184,33 @@ int tacaw_multislice(const tacaw_grid* grid, int32_t n_t, const float* V, const 
                   TACAW_EUNSUPPORTED, "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn,
                   grid->nx, grid->ny);
     TACAW_REQUIRE(n_t >= 0 && n_t <= 65535, TACAW_EINVAL, "%s: n_t must be in [0, 65535]", fn);
-    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS | TACAW_MS_QUEUE)) == 0, TACAW_EINVAL,
+                  "%s: unknown flags", fn);
+    const bool queue = (flags & TACAW_MS_QUEUE) != 0;
+    TACAW_REQUIRE(!queue || flags == TACAW_MS_QUEUE, TACAW_EINVAL,
+                  "%s: TACAW_MS_QUEUE takes no other flag", fn);
+    TACAW_REQUIRE(!queue || grid->nx == grid->ny, TACAW_EUNSUPPORTED,
+                  "%s: the work-queue pass needs a square grid (nx = %d, ny = %d)", fn, grid->nx, grid->ny);
+    tacaw_job job;
+    job.grid = *grid;
+    job.n_t = n_t;
+    job.V = V;
+    job.psi_in = psi_in;
+    job.psi_q = psi_q;
+    job.psi_sum = psi_sum;
     bool query = false;
-    rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
+    rc = check_ws(ws, ws_bytes, queue ? multislice_queue_ws_bytes(&job, 1) : multislice_ws_bytes(*grid), fn,
+                  &query);
     if (rc || query) return rc;
     if (n_t == 0) return TACAW_OK;
     TACAW_REQUIRE(V && psi_q, TACAW_EINVAL, "%s: NULL array", fn);
+    TACAW_REQUIRE(!queue || (reinterpret_cast<uintptr_t>(V) % 16 == 0 && reinterpret_cast<uintptr_t>(psi_q) % 16 == 0),
+                  TACAW_EINVAL, "%s: TACAW_MS_QUEUE needs 16-byte aligned V and psi_q", fn);
     {
         const int frc = inject_launch_fault(fn);
         if (frc) return frc;
     }
+    if (queue) return multislice_queue_run(&job, 1, 0, 0, ws, (cudaStream_t)stream);
     return multislice_run(*grid, n_t, V, (const float2*)psi_in, (float2*)psi_q, (double2*)psi_sum,
                           ws, (cudaStream_t)stream, flags);
 }
@@ -220,6 +239,40 @@ int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size
         if (frc) return frc;
     }
     return multislice_batch_run(jobs, n_jobs, ws, (cudaStream_t)stream);
+}
+
+int tacaw_multislice_queue(const tacaw_job* jobs, int32_t n_jobs, int32_t wave_snapshots, int32_t item_span,
+                           void* ws, size_t* ws_bytes, void* stream) {
+    clear_error();
+    const char* fn = "tacaw_multislice_queue";
+    TACAW_REQUIRE(jobs != nullptr && n_jobs >= 0, TACAW_EINVAL, "%s: bad job list", fn);
+    TACAW_REQUIRE(wave_snapshots >= 0, TACAW_EINVAL, "%s: wave_snapshots must be >= 0", fn);
+    TACAW_REQUIRE(item_span >= 0, TACAW_EINVAL, "%s: item_span must be >= 0", fn);
+    long long total = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        int rc = check_grid(&jobs[j].grid, fn);
+        if (rc) return rc;
+        TACAW_REQUIRE(multislice_size_supported(jobs[j].grid.nx) && jobs[j].grid.nx == jobs[j].grid.ny,
+                      TACAW_EUNSUPPORTED, "%s: job %d: nx = %d, ny = %d: needs a square grid of a supported size",
+                      fn, j, jobs[j].grid.nx, jobs[j].grid.ny);
+        TACAW_REQUIRE(jobs[j].n_t >= 0 && jobs[j].n_t <= (1 << 24), TACAW_EINVAL,
+                      "%s: job %d: n_t must be in [0, 2^24]", fn, j);
+        TACAW_REQUIRE(jobs[j].n_t == 0 || (jobs[j].V && jobs[j].psi_q), TACAW_EINVAL,
+                      "%s: job %d: NULL array", fn, j);
+        TACAW_REQUIRE(reinterpret_cast<uintptr_t>(jobs[j].V) % 16 == 0 &&
+                          reinterpret_cast<uintptr_t>(jobs[j].psi_q) % 16 == 0,
+                      TACAW_EINVAL, "%s: job %d: V and psi_q must be 16-byte aligned", fn, j);
+        total += jobs[j].n_t;
+    }
+    TACAW_REQUIRE(total <= (1 << 28), TACAW_EINVAL, "%s: at most 2^28 snapshots in one call", fn);
+    bool query = false;
+    int rc = check_ws(ws, ws_bytes, multislice_queue_ws_bytes(jobs, n_jobs), fn, &query);
+    if (rc || query) return rc;
+    {
+        const int frc = inject_launch_fault(fn);
+        if (frc) return frc;
+    }
+    return multislice_queue_run(jobs, n_jobs, wave_snapshots, item_span, ws, (cudaStream_t)stream);
 }
 
 int tacaw_spectrum(int32_t nq, int32_t n_t, double dt_fs, int32_t n_omega, const double* omega_meV,

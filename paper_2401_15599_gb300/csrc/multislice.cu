@@ -941,6 +941,383 @@ cudaError_t dispatch_row_back(int nx, float2* g, const float2* state, const floa
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------ work queue
+// Persistent multislice over a device work queue, for jobs whose grids are
+// square (nx = ny = N).  An item is one pass of one slice over kQSpan rows
+// (row item) or kQSpan columns (column item) of one snapshot; a resident
+// grid of 256-thread blocks takes items from a global counter in a fixed
+// order.  The order runs the snapshots of a job in waves of `wave` snapshots:
+// within a wave, slice 0 row items of every snapshot, then slice 0 column
+// items, then slice 1 row items, and so on, so between the passes of a
+// snapshot the blocks touch only the wave's other snapshots and the wave's
+// waves stay in L2.  A row item of slice s needs the column items of slice
+// s - 1 of its snapshot, a column item the row items of slice s: per-snapshot
+// counters of finished items (release after the item's stores, acquire before
+// its loads).  Every item an item waits on comes earlier in the order and is
+// held by a running block, so the waits end; each is bounded all the same
+// (then the status flag and the call's abort word are set and every block
+// leaves).  Results equal the per-slice launches' bit for bit: same plans,
+// twiddles, layouts and per-point arithmetic.
+constexpr int kQThreads = 256;
+constexpr int kQMaxJobs = 64;
+constexpr int kQSpan = 16;               // default rows (row item) or columns (column item) per item
+
+template <int N>
+struct QCfg {
+    static constexpr int E = fft::Plan<N>::E;
+    static constexpr int TPT = N / E;                 // threads per transform
+    static constexpr int ROWS = kQThreads / TPT;      // rows per row tile = columns per column tile
+    static constexpr int SPAN = ROWS > kQSpan ? ROWS : kQSpan;   // default span
+    static constexpr int PL = fft::PaddedLen<N>::value;
+    static constexpr int MIN_BLOCKS = E > 8 ? 2 : 4;    // resident blocks per SM the registers allow
+    static_assert(ROWS * TPT == kQThreads && N % SPAN == 0, "queue tiles");
+    // a span (rows or columns per item) is a multiple of ROWS that divides N
+    static constexpr bool valid_span(int span) { return span >= ROWS && span % ROWS == 0 && N % span == 0; }
+};
+
+struct QJobs {
+    int n;                                // jobs in this launch
+    int wave;                             // snapshots per wave
+    int span;                             // rows (row item) or columns (column item) per item
+    int items;                            // items per snapshot and pass: N / span
+    long long item0[kQMaxJobs + 1];       // first queue position of each job; item0[n] = total
+    int snap0[kQMaxJobs + 1];             // first counter slot of each job
+    float2* psi[kQMaxJobs];
+    const float* V[kQMaxJobs];
+    const float2* psi_in[kQMaxJobs];
+    const float2* px[kQMaxJobs];
+    const float2* py[kQMaxJobs];
+    const int* kymax[kQMaxJobs];
+    int n_t[kQMaxJobs], n_slices[kQMaxJobs];
+    float sigma[kQMaxJobs];
+};
+
+struct QItem {
+    int job, t, s, pass, tile;
+};
+
+__device__ __forceinline__ QItem q_decode(const QJobs& jobs, long long it) {
+    const int IT = jobs.items;
+    QItem q;
+    int j = 0;
+    while (j + 1 < jobs.n && jobs.item0[j + 1] <= it) ++j;
+    const long long r = it - jobs.item0[j];
+    const int S = jobs.n_slices[j], T = jobs.n_t[j], Tw = jobs.wave;
+    const long long per_wave = (long long)S * 2 * IT * Tw;
+    const int w = (int)(r / per_wave);
+    const int first = w * Tw;
+    const int nw = min(Tw, T - first);
+    const long long in_wave = r - (long long)w * per_wave;
+    const int s = (int)(in_wave / (2LL * nw * IT));
+    int rem = (int)(in_wave - (long long)s * 2 * nw * IT);
+    const int pass = rem >= nw * IT ? 1 : 0;
+    if (pass) rem -= nw * IT;
+    q.job = j;
+    q.t = first + rem / IT;
+    q.s = s;
+    q.pass = pass;
+    q.tile = rem % IT;
+    return q;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0: waits until *ctr >= need, at most `polls` polls, leaving early when
+// the call's abort word is set.  On giving up it sets the status flag and the
+// abort word.  Returns whether the count was reached.
+__device__ bool q_wait(const int* ctr, int need, int* abort_word, int* err, uint32_t polls) {
+    for (uint32_t i = 0; i < polls; ++i) {
+        if (ld_acquire_gpu(ctr) >= need) return true;
+        if (*reinterpret_cast<volatile int*>(abort_word)) return false;
+        __nanosleep(32);
+    }
+    atomicExch(err, 1);
+    atomicExch(abort_word, 1);
+    return false;
+}
+
+__device__ __forceinline__ void cp_async_cg16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// A tile's stage: ROWS slots of PL float2 (row tile: the rows of psi at their
+// natural positions, then the padded exchanges in place; column tile: the
+// ROWS x N columns densely as [row][column], then the padded exchanges in
+// place), followed by the tile's ROWS rows of v_s (row tiles).
+template <int N>
+struct QStage {
+    static constexpr int PSI = QCfg<N>::ROWS * QCfg<N>::PL;             // float2
+    static constexpr int F2 = PSI + QCfg<N>::ROWS * N / 2;              // float2 per stage
+    static constexpr int NST = (2 * F2 + fft::TwSize<N>::value) * (int)sizeof(float2) <= 100 * 1024 ? 2 : 1;
+};
+
+// Starts the copies of tile ti of item q into a stage (cp.async through L2
+// only, so no block sees an old copy of another block's results): a row tile
+// takes its rows of psi (the kept columns, from the second slice on) and of
+// v_s, a column tile its ROWS columns (nothing for a tile the band limit
+// drops).  All threads; 16-byte aligned arrays.
+template <int N>
+__device__ __forceinline__ void q_issue(const QJobs& jobs, const QItem& q, int ti, float2* stage) {
+    using C = QCfg<N>;
+    const float2* snap = jobs.psi[q.job] + (size_t)q.t * N * N;
+    const int K = __ldg(jobs.kymax[q.job] + N);
+    if (q.pass == 0) {
+        const int y0 = q.tile * jobs.span + ti * C::ROWS;
+        if (q.s > 0) {
+            int a = K + 1;                               // kept columns [0, a) and [b, N), both ends even
+            a += a & 1;
+            if (a > N) a = N;
+            int b = N - K;
+            b -= b & 1;
+            if (b < a) b = a;
+            for (int i = threadIdx.x; i < C::ROWS * (N / 2); i += kQThreads) {
+                const int r = i / (N / 2), c2 = (i % (N / 2)) * 2;
+                if (c2 < a || c2 >= b) cp_async_cg16(stage + r * C::PL + c2, snap + (size_t)(y0 + r) * N + c2);
+            }
+        }
+        const float* Vs = jobs.V[q.job] + (((size_t)q.t * jobs.n_slices[q.job] + q.s) * N + y0) * N;
+        float* vst = reinterpret_cast<float*>(stage + QStage<N>::PSI);
+        for (int i = threadIdx.x; i < C::ROWS * N / 4; i += kQThreads) cp_async_cg16(vst + 4 * i, Vs + 4 * i);
+    } else {
+        const int kx0 = q.tile * jobs.span + ti * C::ROWS;
+        if (kx0 > K && kx0 + C::ROWS - 1 < N - K) return;
+        constexpr int CH = C::ROWS / 2;                  // 16-byte chunks per row of the tile
+        for (int i = threadIdx.x; i < N * CH; i += kQThreads) {
+            const int r = i / CH, h = i % CH;
+            cp_async_cg16(stage + r * C::ROWS + 2 * h, snap + (size_t)r * N + kx0 + 2 * h);
+        }
+    }
+}
+
+// Row tile from its stage: ROWS rows of one snapshot (mode 0: the hybrid wave;
+// 1: unit plane wave; 2: psi_in) transmitted by slice s and transformed back
+// along x, kept columns written to the wave.
+template <int N>
+__device__ __forceinline__ void q_row_tile(float2* stage, float2* __restrict__ rowp, const float2* __restrict__ inrow,
+                                           int mode, float sigma, int K, const float2* tw, int t, int row) {
+    using namespace fft;
+    using C = QCfg<N>;
+    constexpr int E = C::E, TPT = C::TPT;
+    const PadRowLayout lay{row * C::PL};
+    const auto sync = row_sync_of<TPT>(row);
+    const float* vrow = reinterpret_cast<const float*>(stage + QStage<N>::PSI) + row * N;
+    float2 v[E];
+    if (mode == 0) {
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            v[m] = kept_column(t + TPT * m, N, K) ? stage[row * C::PL + t + TPT * m] : make_float2(0.f, 0.f);
+        transform_plan<Plan<N>, N, true>(v, stage, stage, t, tw, lay, sync);
+    } else if (mode == 1) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = make_float2(1.f, 0.f);
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = __ldg(inrow + t + TPT * m);
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float sn, cs;
+        phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
+        v[m] = cmul(v[m], make_float2(cs, sn));
+    }
+    transform_plan<Plan<N>, N, false>(v, stage, stage, t, tw, lay, sync);
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        if (kept_column(t + TPT * m, N, K)) rowp[t + TPT * m] = v[m];
+}
+
+// Column tile from its stage: ROWS adjacent columns (Fy, times P BL / (nx ny),
+// Fy^-1 unless `last`); a tile the band limit drops entirely only writes its
+// zeros after the last slice.
+template <int N>
+__device__ __forceinline__ void q_col_tile(float2* stage, float2* __restrict__ snap, int kx0,
+                                           const float2* __restrict__ px, const float2* __restrict__ py,
+                                           const int* __restrict__ kymax, int K, int last, const float2* tw, int t,
+                                           int c) {
+    using namespace fft;
+    using C = QCfg<N>;
+    constexpr int E = C::E, TPT = C::TPT, W = C::ROWS;
+    float2* col = snap + kx0 + c;
+    if (kx0 > K && kx0 + W - 1 < N - K) {
+        if (last) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * N] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
+    const int kx = kx0 + c;
+    const PadColLayout<W> lay{c};
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = stage[(t + TPT * m) * W + c];
+    transform_plan<Plan<N>, N, false>(v, stage, stage, t, tw, lay, BlockSync{});
+    const float2 pxv = __ldg(px + kx);
+    const int kmax = __ldg(kymax + kx);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int ky = t + TPT * m;
+        const int aky = ky < N / 2 ? ky : N - ky;
+        v[m] = (aky <= kmax) ? cmul(v[m], cmul(pxv, __ldg(py + ky))) : make_float2(0.f, 0.f);
+    }
+    if (!last) transform_plan<Plan<N>, N, true>(v, stage, stage, t, tw, lay, BlockSync{});
+#pragma unroll
+    for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * N] = v[m];
+}
+
+__device__ __forceinline__ bool q_ready(const QJobs& jobs, const QItem& q, const int* row_done, const int* col_done) {
+    const int u = jobs.snap0[q.job] + q.t;
+    if (q.pass == 0) return q.s == 0 || ld_acquire_gpu(col_done + u) >= q.s * jobs.items;
+    return ld_acquire_gpu(row_done + u) >= (q.s + 1) * jobs.items;
+}
+
+__device__ __forceinline__ bool q_wait_ready(const QJobs& jobs, const QItem& q, int* row_done, int* col_done,
+                                             int* abort_word, int* err, uint32_t polls) {
+    const int u = jobs.snap0[q.job] + q.t;
+    if (q.pass == 0) return q.s == 0 || q_wait(col_done + u, q.s * jobs.items, abort_word, err, polls);
+    return q_wait(row_done + u, (q.s + 1) * jobs.items, abort_word, err, polls);
+}
+
+// ctl (8-byte aligned): [0, 1] 64-bit queue head, [2] abort word, [3] unused;
+// then row_done[U], col_done[U].  All zero before the launch.
+// Each block walks its tiles through a ring of QStage<N>::NST stages: while
+// tile k is transformed, the copies of tile k + 1 (the next tile of the same
+// item, or the first of the block's next item once that item's inputs are
+// final) are in flight.  Three barriers per tile: the plan of the next tile,
+// the arrival of this tile's copies, the end of its use of the stage.
+template <int N>
+__global__ void __launch_bounds__(kQThreads, QCfg<N>::MIN_BLOCKS)
+ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ tw_g, int* __restrict__ ctl,
+                int* __restrict__ err, uint32_t polls) {
+    using C = QCfg<N>;
+    constexpr int NST = QStage<N>::NST;
+    extern __shared__ __align__(16) float2 qsm[];
+    float2* tw = qsm + NST * QStage<N>::F2;
+    // written by thread 0, each read by all threads between two barriers: the first item, the plan of
+    // the next tile (item, tile in item, 0 ready / 1 not yet / 2 none), the verdict of a blocking wait
+    __shared__ long long s_first, s_it;
+    __shared__ int s_first_ok, s_ti, s_flag, s_ok;
+    unsigned long long* head = reinterpret_cast<unsigned long long*>(ctl);
+    int* abort_word = ctl + 2;
+    const int U = jobs.snap0[jobs.n];
+    int* row_done = ctl + 4;
+    int* col_done = ctl + 4 + U;
+    const long long total = jobs.item0[jobs.n];
+    const int tiles = jobs.span / C::ROWS;
+    stage_twiddles<N>(tw, tw_g);
+    const int tr = threadIdx.x % C::TPT, row = threadIdx.x / C::TPT;     // row tiles
+    const int cc = threadIdx.x % C::ROWS, tc = threadIdx.x / C::ROWS;     // column tiles
+    // thread 0: the block's next item, taken one tile before it is planned (during the second-to-last
+    // tile of the current item, or with the current item when items are one tile), so that few items
+    // are taken but not started
+    unsigned long long nxt = 0;
+    bool have_nxt = false;
+    if (threadIdx.x == 0) {
+        const unsigned long long cur = atomicAdd(head, 1ull);
+        if (tiles == 1) {
+            nxt = atomicAdd(head, 1ull);
+            have_nxt = true;
+        }
+        s_first = (long long)cur;
+        s_first_ok = (long long)cur < total &&
+                     q_wait_ready(jobs, q_decode(jobs, (long long)cur), row_done, col_done, abort_word, err, polls);
+    }
+    __syncthreads();
+    if (!s_first_ok) return;
+    long long item = s_first;
+    QItem q = q_decode(jobs, item);
+    int ti = 0, st = 0;
+    q_issue<N>(jobs, q, 0, qsm);
+    cp_async_commit_group();
+    for (;;) {
+        if (threadIdx.x == 0) {                     // plan the next tile
+            if (ti + 1 < tiles) {
+                s_it = item;
+                s_ti = ti + 1;
+                s_flag = 0;
+                if (ti + 2 == tiles && !have_nxt) {
+                    nxt = atomicAdd(head, 1ull);
+                    have_nxt = true;
+                }
+            } else {
+                if (!have_nxt) nxt = atomicAdd(head, 1ull);
+                have_nxt = false;
+                if ((long long)nxt >= total || *reinterpret_cast<volatile int*>(abort_word)) {
+                    s_flag = 2;
+                } else {
+                    s_it = (long long)nxt;
+                    s_ti = 0;
+                    s_flag = q_ready(jobs, q_decode(jobs, (long long)nxt), row_done, col_done) ? 0 : 1;
+                    if (tiles == 1) {
+                        nxt = atomicAdd(head, 1ull);
+                        have_nxt = true;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int flag = s_flag;
+        const long long nit = s_it;
+        const int nti = s_ti;
+        QItem qn = q;
+        if (flag != 2 && nti == 0) qn = q_decode(jobs, nit);
+        float2* cur_stage = qsm + st * QStage<N>::F2;
+        float2* nxt_stage = qsm + (st ^ (NST - 1)) * QStage<N>::F2;
+        const bool early = NST == 2 && flag == 0;
+        if (early) {
+            q_issue<N>(jobs, qn, nti, nxt_stage);
+            cp_async_commit_group();
+            cp_async_wait_pending<1>();
+        } else {
+            cp_async_wait_pending<0>();
+        }
+        __syncthreads();                            // this tile's copies have landed
+        const int S = jobs.n_slices[q.job];
+        float2* snap = jobs.psi[q.job] + (size_t)q.t * N * N;
+        const int K = __ldg(jobs.kymax[q.job] + N);
+        if (q.pass == 0) {
+            const int mode = q.s > 0 ? 0 : (jobs.psi_in[q.job] ? 2 : 1);
+            const int y = q.tile * jobs.span + ti * C::ROWS + row;
+            q_row_tile<N>(cur_stage, snap + (size_t)y * N,
+                          mode == 2 ? jobs.psi_in[q.job] + (size_t)y * N : nullptr, mode, jobs.sigma[q.job], K,
+                          tw, tr, row);
+        } else {
+            q_col_tile<N>(cur_stage, snap, q.tile * jobs.span + ti * C::ROWS, jobs.px[q.job], jobs.py[q.job],
+                          jobs.kymax[q.job], K, q.s + 1 == S, tw, tc, cc);
+        }
+        __syncthreads();                            // the stage is free; the tile's stores are issued
+        if (ti + 1 == tiles && threadIdx.x == 0) {  // the item is done: release it
+            __threadfence();
+            atomicAdd((q.pass == 0 ? row_done : col_done) + jobs.snap0[q.job] + q.t, 1);
+        }
+        if (flag == 2) break;
+        if (!early) {                               // inputs not final yet, or one stage: wait, then copy
+            if (threadIdx.x == 0)
+                s_ok = flag == 0 || q_wait_ready(jobs, qn, row_done, col_done, abort_word, err, polls);
+            __syncthreads();
+            if (!s_ok) break;
+            q_issue<N>(jobs, qn, nti, nxt_stage);
+            cp_async_commit_group();
+        }
+        item = nit;
+        ti = nti;
+        q = qn;
+        st ^= NST - 1;
+    }
+    cp_async_wait_pending<0>();
+}
+
 }  // namespace
 
 bool multislice_size_supported(int n) {
@@ -1080,6 +1457,143 @@ int multislice_batch_run(const tacaw_job* jobs, int n_jobs, void* ws, cudaStream
                 TACAW_CUDA_CHECK(dispatch_row_batch(a.grid.nx, rj, tb[first].twx, a.grid.ny, total, s, st));
                 TACAW_CUDA_CHECK(dispatch_col_batch(a.grid.ny, cj, tb[first].twy, a.grid.nx, total, st));
             }
+        }
+    }
+    for (int j = 0; j < n_jobs; ++j) {
+        if (!jobs[j].psi_sum || jobs[j].n_t <= 0) continue;
+        const size_t nq = (size_t)jobs[j].grid.nx * jobs[j].grid.ny;
+        snapshot_sum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>((const float2*)jobs[j].psi_q,
+                                                                         (double2*)jobs[j].psi_sum,
+                                                                         jobs[j].n_t, nq);
+        TACAW_LAUNCH_CHECK();
+    }
+    return TACAW_OK;
+}
+
+// ------------------------------------------------------------------ work queue (host)
+namespace {
+
+constexpr uint32_t kQueueWaitPolls = 1u << 22;   // a few seconds per dependency wait
+constexpr double kQueueWaveBytes = 64.0 * 1024 * 1024;   // default: waves of about 64 MiB of waves in L2
+
+// The span for grid size n: the requested one where valid, else the default.
+int queue_span(int n, int want) {
+    switch (n) {
+        case 64: return QCfg<64>::valid_span(want) ? want : QCfg<64>::SPAN;
+        case 128: return QCfg<128>::valid_span(want) ? want : QCfg<128>::SPAN;
+        case 256: return QCfg<256>::valid_span(want) ? want : QCfg<256>::SPAN;
+        case 384: return QCfg<384>::valid_span(want) ? want : QCfg<384>::SPAN;
+        case 512: return QCfg<512>::valid_span(want) ? want : QCfg<512>::SPAN;
+        case 768: return QCfg<768>::valid_span(want) ? want : QCfg<768>::SPAN;
+        case 1024: return QCfg<1024>::valid_span(want) ? want : QCfg<1024>::SPAN;
+    }
+    return 0;
+}
+
+template <int N>
+cudaError_t launch_queue(const QJobs& jobs, const float2* tw, int* ctl, int* err, uint32_t polls, cudaStream_t st) {
+    const size_t smem = (QStage<N>::NST * QStage<N>::F2 + fft::TwSize<N>::value) * sizeof(float2);
+    cudaError_t e = ensure_smem((const void*)ms_queue_kernel<N>, (int)smem);
+    if (e != cudaSuccess) return e;
+    int resident = 0;
+    e = resident_blocks((const void*)ms_queue_kernel<N>, kQThreads, (int)smem, &resident);
+    if (e != cudaSuccess) return e;
+    const long long total = jobs.item0[jobs.n];
+    const int blocks = (long long)resident < total ? resident : (int)total;
+    if (blocks <= 0) return cudaSuccess;
+    ms_queue_kernel<N><<<blocks, kQThreads, smem, st>>>(jobs, tw, ctl, err, polls);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_queue(int n, const QJobs& jobs, const float2* tw, int* ctl, int* err, uint32_t polls,
+                           cudaStream_t st) {
+    TACAW_SIZE_SWITCH(n, return launch_queue<N_>(jobs, tw, ctl, err, polls, st));
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t multislice_queue_ws_bytes(const tacaw_job* jobs, int n_jobs) {
+    Carver cv(nullptr);
+    long long U = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        carve_ms(cv, jobs[j].grid);
+        if (jobs[j].n_t > 0) U += jobs[j].n_t;
+    }
+    cv.take<int>((size_t)(4 + 2 * U));
+    return cv.bytes();
+}
+
+// Jobs grouped by grid size (in order of first appearance, at most kQMaxJobs
+// per launch): per group one persistent launch over the group's queue, after
+// a reset of its counters; then the FP64 snapshot sums.
+int multislice_queue_run(const tacaw_job* jobs, int n_jobs, int wave, int span, void* ws, cudaStream_t st) {
+    Carver cv(ws);
+    std::vector<MsTables> tb(n_jobs);
+    std::vector<float> sigma(n_jobs);
+    long long U = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const tacaw_grid& g = jobs[j].grid;
+        tb[j] = carve_ms(cv, g);
+        double lam = 0.0, sig = 0.0;
+        beam_constants(g.kev, &lam, &sig);
+        sigma[j] = (float)sig;
+        const double qmax = g.bandlimit * fmin((double)g.nx / (2.0 * g.lx), (double)g.ny / (2.0 * g.ly));
+        ms_setup_kernel<<<(g.nx + 127) / 128, 128, 0, st>>>(tb[j].twx, tb[j].twy, tb[j].px, tb[j].py,
+                                                            tb[j].kymax, g.nx, g.ny, g.lx, g.ly, lam * g.dz,
+                                                            qmax * qmax);
+        TACAW_LAUNCH_CHECK();
+        if (jobs[j].n_t > 0) U += jobs[j].n_t;
+    }
+    int* ctl_all = cv.take<int>((size_t)(4 + 2 * U));
+    WaitCtl wc{nullptr, wait_polls(kQueueWaitPolls)};
+    int rc = timeout_flag(&wc.flag, "tacaw_multislice_queue");
+    if (rc) return rc;
+    std::vector<char> used(n_jobs, 0);
+    for (int j0 = 0; j0 < n_jobs; ++j0) {
+        if (used[j0] || jobs[j0].n_t <= 0 || jobs[j0].grid.n_slices <= 0) continue;
+        const int n = jobs[j0].grid.nx;
+        const int sp = queue_span(n, span);
+        const int items = n / sp;
+        int wv = wave;
+        if (wv <= 0) {
+            const double per = 8.0 * n * n;
+            wv = (int)(kQueueWaveBytes / per);
+            wv = wv < 1 ? 1 : wv;
+        }
+        int j = j0;
+        while (j < n_jobs) {
+            QJobs q;
+            q.n = 0;
+            q.wave = wv;
+            q.span = sp;
+            q.items = items;
+            long long item = 0;
+            int snaps = 0;
+            for (; j < n_jobs && q.n < kQMaxJobs; ++j) {
+                const tacaw_job& b = jobs[j];
+                if (used[j] || b.n_t <= 0 || b.grid.n_slices <= 0 || b.grid.nx != n) continue;
+                used[j] = 1;
+                const int k = q.n++;
+                q.item0[k] = item;
+                q.snap0[k] = snaps;
+                q.psi[k] = (float2*)b.psi_q;
+                q.V[k] = b.V;
+                q.psi_in[k] = (const float2*)b.psi_in;
+                q.px[k] = tb[j].px;
+                q.py[k] = tb[j].py;
+                q.kymax[k] = tb[j].kymax;
+                q.n_t[k] = b.n_t;
+                q.n_slices[k] = b.grid.n_slices;
+                q.sigma[k] = sigma[j];
+                item += (long long)b.grid.n_slices * 2 * items * b.n_t;
+                snaps += b.n_t;
+            }
+            if (q.n == 0) break;
+            q.item0[q.n] = item;
+            q.snap0[q.n] = snaps;
+            TACAW_CUDA_CHECK(cudaMemsetAsync(ctl_all, 0, (size_t)(4 + 2 * snaps) * sizeof(int), st));
+            TACAW_CUDA_CHECK(dispatch_queue(n, q, tb[j0].twx, ctl_all, wc.flag, wc.polls, st));
         }
     }
     for (int j = 0; j < n_jobs; ++j) {

@@ -123,3 +123,44 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "libtacaw.so"))
     with pytest.raises(RuntimeError, match="not built"):
         L.load()
+
+
+def test_queue_arguments_and_workspace(lib):
+    """tacaw_multislice_queue and the TACAW_MS_QUEUE flag: square grids only,
+    the flag alone, and a workspace that grows by 8 bytes per snapshot."""
+    fake = ctypes.c_void_p(1 << 20)
+    null = ctypes.c_void_p(0)
+
+    def grid(nx, ny):
+        return L.make_grid(O.Grid(nx, ny, nx * 0.15, ny * 0.15, 3, 2.0, 0.0, 200.0, 2.0 / 3.0))
+
+    def queue_bytes(jobs):
+        arr = (L.TacawJob * len(jobs))(*jobs)
+        n = ctypes.c_size_t(0)
+        assert lib.tacaw_multislice_queue(arr, len(jobs), 0, 0, null, ctypes.byref(n), null) == L.TACAW_OK
+        return n.value
+
+    g = grid(256, 256)
+    one = queue_bytes([L.TacawJob(g, 10, fake, None, fake, None)])
+    two = queue_bytes([L.TacawJob(g, 10, fake, None, fake, None), L.TacawJob(g, 30, fake, None, fake, None)])
+    tables = ctypes.c_size_t(0)
+    assert lib.tacaw_multislice(ctypes.byref(g), 10, null, null, null, null, 0, null, ctypes.byref(tables),
+                                null) == L.TACAW_OK
+    assert one >= tables.value + 8 * 10 + 16
+    assert two >= 2 * tables.value + 8 * 40 + 16
+    flag = ctypes.c_size_t(0)
+    assert lib.tacaw_multislice(ctypes.byref(g), 10, null, null, null, null, L.TACAW_MS_QUEUE, null,
+                                ctypes.byref(flag), null) == L.TACAW_OK
+    assert flag.value == one
+    big = ctypes.byref(ctypes.c_size_t(1 << 40))
+    rect = grid(256, 128)
+    arr = (L.TacawJob * 1)(L.TacawJob(rect, 4, fake, None, fake, None))
+    assert lib.tacaw_multislice_queue(arr, 1, 0, 0, fake, big, null) == L.TACAW_EUNSUPPORTED
+    assert lib.tacaw_multislice(ctypes.byref(rect), 4, fake, null, fake, null, L.TACAW_MS_QUEUE, fake, big,
+                                null) == L.TACAW_EUNSUPPORTED
+    assert lib.tacaw_multislice(ctypes.byref(g), 4, fake, null, fake, null, L.TACAW_MS_QUEUE | L.TACAW_MS_WARP_ROWS,
+                                fake, big, null) == L.TACAW_EINVAL
+    arr = (L.TacawJob * 1)(L.TacawJob(g, 4, fake, None, fake, None))
+    assert lib.tacaw_multislice_queue(arr, 1, -1, 0, fake, big, null) == L.TACAW_EINVAL
+    arr = (L.TacawJob * 1)(L.TacawJob(g, 4, None, None, fake, None))
+    assert lib.tacaw_multislice_queue(arr, 1, 0, 0, fake, big, null) == L.TACAW_EINVAL

@@ -51,6 +51,7 @@ def _entry_points(lib):
         ("tacaw_multislice_static", lambda: lib.tacaw_multislice_static(ctypes.byref(g), 2, FAKE, NULL, FAKE,
                                                                         NULL, 0, NULL)),
         ("tacaw_multislice_batch", lambda: lib.tacaw_multislice_batch(jobs, 1, FAKE, _big(), NULL)),
+        ("tacaw_multislice_queue", lambda: lib.tacaw_multislice_queue(jobs, 1, 0, 0, FAKE, _big(), NULL)),
         ("tacaw_spectrum", lambda: lib.tacaw_spectrum(64, 8, 5.0, 8, NULL, FAKE, NULL, FAKE, FAKE, L.TACAW_FP32, 0,
                                                       300.0, FAKE, _big(), NULL)),
         ("tacaw_spectrum_segments", lambda: lib.tacaw_spectrum_segments(64, 16, 5.0, 8, 4, 0, 8, NULL, FAKE, FAKE,
