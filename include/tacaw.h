@@ -423,11 +423,13 @@ int tacaw_probe(int32_t nx, int32_t ny, double lx, double ly, double kev, double
  * snapshot batches candidates[i] (HOST, each in [1, max_batch]): one warm-up
  * call, then `reps` timed calls per candidate (CUDA events on `stream`), every
  * call with the tacaw_multislice `flags` given (so the caller can compare the
- * row-pass variants as well).
+ * variants of the passes as well; TACAW_MS_QUEUE times the work-queue
+ * multislice with its default wave and span).
  * ms_per_snapshot [n_candidates] (HOST out) receives the device time per
  * snapshot of each; *best_batch (HOST out) the fastest candidate.  Blocks the
  * calling thread until the timings are read (not for stream capture).
- * Workspace as tacaw_multislice (query with ws == NULL).  TACAW_EINVAL for bad
+ * Workspace as tacaw_multislice with n_t = max_batch and these flags (query
+ * with ws == NULL).  TACAW_EINVAL for bad
  * sizes, TACAW_EUNSUPPORTED for grid sizes tacaw_multislice does not take.
  */
 int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float* V, void* psi_q,

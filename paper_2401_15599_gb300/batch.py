@@ -2,8 +2,10 @@
 
 Each job has its own grid, slice count, snapshot count and atoms.  Snapshots
 are processed in windows: for every window the slice potentials of each job
-are built, then one ``tacaw_multislice_batch`` call advances all jobs
-together (jobs of the same grid size share launches).
+are built, then one multislice call advances all jobs together: with square
+grids ``tacaw_multislice_queue`` (one persistent launch per grid size over a
+device work queue, the default), else ``tacaw_multislice_batch`` (two
+launches per slice, shared by the jobs of one grid size).
 
 Two forms of the spectrum (Eq. (9) with the elastic part removed):
 
@@ -51,8 +53,12 @@ class Job:
 
 
 class BatchTimeToSpectrum:
-    def __init__(self, jobs, window=8, precision="bf16x6", device="cuda", chunked=False):
+    def __init__(self, jobs, window=8, precision="bf16x6", device="cuda", chunked=False, queue="auto", wave=0,
+                 span=0):
         self.jobs = list(jobs)
+        if queue == "auto":
+            queue = all(j.grid.nx == j.grid.ny for j in self.jobs)
+        self.queue, self.wave, self.span = bool(queue), int(wave), int(span)
         if window == "auto":                    # tuned for the largest grid of the jobs (tuning.py)
             from .tuning import best_multislice_batch
             big = max(self.jobs, key=lambda j: j.grid.nx * j.grid.ny * j.grid.n_slices)
@@ -114,7 +120,8 @@ class BatchTimeToSpectrum:
                 out = st["psi"][: t1 - t0] if self.chunked else st["psi"][t0:t1]
                 batch.append({"grid": j.grid, "V": v, "out": out, "psi_sum": st["psi_sum"]})
                 live.append((j, st, t1))
-            api.multislice_batch(batch, workspace=getattr(self, "ws_batch", None))
+            api.multislice_batch(batch, workspace=getattr(self, "ws_batch", None), queue=self.queue,
+                                 wave=self.wave, span=self.span)
             if self.chunked:
                 for j, st, t1 in live:
                     if t0 == 0:                 # reference mean: the job's first window
@@ -172,8 +179,12 @@ class BatchTimeToSpectrum:
         for i, j in enumerate(self.jobs):
             arr[i] = L.TacawJob(L.make_grid(j.grid), min(self.window, j.snapshots()), 1, None, 1, None)
         n = ctypes.c_size_t(0)
-        L.check("tacaw_multislice_batch", lib.tacaw_multislice_batch(arr, len(self.jobs), null, ctypes.byref(n),
-                                                                     null))
+        if self.queue:
+            L.check("tacaw_multislice_queue", lib.tacaw_multislice_queue(arr, len(self.jobs), self.wave, self.span,
+                                                                         null, ctypes.byref(n), null))
+        else:
+            L.check("tacaw_multislice_batch", lib.tacaw_multislice_batch(arr, len(self.jobs), null, ctypes.byref(n),
+                                                                         null))
         self.ws_batch = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
 
     def capture(self):

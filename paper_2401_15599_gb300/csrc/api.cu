@@ -639,11 +639,24 @@ int tacaw_tune_multislice(const tacaw_grid* grid, int32_t max_batch, const float
                   "%s: nx = %d, ny = %d not in {64, 128, 256, 384, 512, 768, 1024}", fn, grid->nx, grid->ny);
     TACAW_REQUIRE(max_batch >= 1 && max_batch <= 65535 && n_candidates >= 1 && reps >= 1 && reps <= 1000,
                   TACAW_EINVAL, "%s: need 1 <= max_batch <= 65535, n_candidates >= 1, 1 <= reps <= 1000", fn);
-    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown flags", fn);
+    TACAW_REQUIRE((flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS | TACAW_MS_QUEUE)) == 0, TACAW_EINVAL,
+                  "%s: unknown flags", fn);
+    const bool queue = (flags & TACAW_MS_QUEUE) != 0;
+    TACAW_REQUIRE(!queue || (flags == TACAW_MS_QUEUE && grid->nx == grid->ny), TACAW_EINVAL,
+                  "%s: TACAW_MS_QUEUE alone, on a square grid", fn);
+    tacaw_job job;                                       // workspace of the largest queue call
+    job.grid = *grid;
+    job.n_t = max_batch;
+    job.V = V;
+    job.psi_in = nullptr;
+    job.psi_q = psi_q;
+    job.psi_sum = nullptr;
     bool query = false;
-    rc = check_ws(ws, ws_bytes, multislice_ws_bytes(*grid), fn, &query);
+    rc = check_ws(ws, ws_bytes, queue ? multislice_queue_ws_bytes(&job, 1) : multislice_ws_bytes(*grid), fn, &query);
     if (rc || query) return rc;
     TACAW_REQUIRE(V && psi_q && candidates && ms_per_snapshot && best_batch, TACAW_EINVAL, "%s: NULL array", fn);
+    TACAW_REQUIRE(!queue || (reinterpret_cast<uintptr_t>(V) % 16 == 0 && reinterpret_cast<uintptr_t>(psi_q) % 16 == 0),
+                  TACAW_EINVAL, "%s: TACAW_MS_QUEUE needs 16-byte aligned V and psi_q", fn);
     for (int i = 0; i < n_candidates; ++i)
         TACAW_REQUIRE(candidates[i] >= 1 && candidates[i] <= max_batch, TACAW_EINVAL,
                       "%s: candidate %d = %d outside [1, max_batch = %d]", fn, i, candidates[i], max_batch);

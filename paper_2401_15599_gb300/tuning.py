@@ -4,7 +4,8 @@
 call should advance together on this GPU for this grid, and which variants of
 the passes to use (tacaw_multislice flags: for 512-point rows two warps per
 row or one, for 512-point columns the persistent TMA-staged pass or one block
-per column block); candidates whose potentials would exceed MAX_TUNING_BYTES
+per column block; on square grids also the work-queue multislice, all slices
+in one persistent launch); candidates whose potentials would exceed MAX_TUNING_BYTES
 are skipped.  On a cache miss it times every (batch, flags) pair with the
 library's ``tacaw_tune_multislice`` (random slice potentials: the transform
 cost does not depend on the values) and stores the result under the key
@@ -62,14 +63,16 @@ def cache_key(grid, device_name: str) -> str:
     return f"{device_name}|{int(grid.nx)}x{int(grid.ny)}x{int(grid.n_slices)}"
 
 
-CACHE_VERSION = 3
+CACHE_VERSION = 4
 
 
 def multislice_variants(grid):
-    """tacaw_multislice flags worth comparing for this grid."""
+    """tacaw_multislice flags worth comparing for this grid: the variants of the
+    per-slice passes, and on square grids the work-queue multislice."""
     rows = (0, L.TACAW_MS_WARP_ROWS) if int(grid.nx) == 512 else (0,)
     cols = (0, L.TACAW_MS_BLOCK_COLS) if int(grid.ny) == 512 else (0,)
-    return tuple(r | c for r in rows for c in cols)
+    queue = (L.TACAW_MS_QUEUE,) if int(grid.nx) == int(grid.ny) else ()
+    return tuple(r | c for r in rows for c in cols) + queue
 
 
 def measure_multislice_batches(grid, candidates=DEFAULT_CANDIDATES, reps=3, device="cuda", flags=0):

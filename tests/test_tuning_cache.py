@@ -23,15 +23,16 @@ def test_miss_measures_and_hit_reuses(tmp_path):
         return t, min(t, key=t.get)
 
     b1 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
-    assert b1 == 64 and len(calls) == 1                     # 256-point rows: one variant
+    assert b1 == 64 and len(calls) == 2                     # 256^2: per-slice passes and the work queue
+    assert {c[2] for c in calls} == {0, 4}
     b2 = tuning.best_multislice_batch(_grid(), candidates=(8, 16, 32, 64), path=path, measure=fake)
-    assert b2 == 64 and len(calls) == 1                     # from the cache
+    assert b2 == 64 and len(calls) == 2                     # from the cache
     cfg = tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake)
-    assert cfg == (16, 1) and len(calls) == 5               # 512-point grids: four variants timed
-    assert {c[2] for c in calls[1:]} == {0, 1, 2, 3}
+    assert cfg == (16, 1) and len(calls) == 7               # 512^2: four pass variants and the queue timed
+    assert {c[2] for c in calls[2:]} == {0, 1, 2, 3, 4}
     assert tuning.best_multislice_config(_grid(512, 101), candidates=(8, 16), path=path, measure=fake) == (16, 1)
     data = json.load(open(path))
-    assert len(calls) == 5 and len(data) == 2
+    assert len(calls) == 7 and len(data) == 2
     entry = data["test-device|256x256x10"]
     assert entry["batch"] == 64 and entry["flags"] == 0
     assert set(entry["ms_per_snapshot"]["0"]) == {"8", "16", "32", "64"}
@@ -48,7 +49,7 @@ def test_old_entries_are_tuned_again(tmp_path):
 
     assert tuning.best_multislice_config(_grid(512, 101), candidates=(4, 8), path=str(path),
                                          measure=fake) == (8, 0)
-    assert sorted(calls) == [0, 1, 2, 3]
+    assert sorted(calls) == [0, 1, 2, 3, 4]
 
 
 def test_corrupt_cache_is_ignored(tmp_path):
