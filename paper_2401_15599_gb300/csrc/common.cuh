@@ -79,6 +79,8 @@ struct Carver {
 
 // Raise a kernel's dynamic shared-memory limit once per device (multislice.cu).
 cudaError_t ensure_smem(const void* kernel, int bytes);
+// Blocks of `kernel` resident on the whole device at once (occupancy times SM count).
+cudaError_t resident_blocks(const void* kernel, int threads, int smem, int* out);
 
 // Beam constants (textbook relativistic values, CODATA 2018).
 void beam_constants(double kev, double* lambda_A, double* sigma_e);

@@ -846,6 +846,7 @@ constexpr int kB2Chunk = kB2Ring;        // the slot for chunks of an over-full 
 constexpr int kB2Slots = kB2Ring + 1;
 constexpr int kB2ChunkSrc = kB2Cap / 3;  // sources per chunk (each gives at most 3 entries)
 constexpr int kBGroups = 129;            // 8-column groups for nx <= 1024, plus one
+constexpr int kBFirst = 144;             // bytes of a first[] table (kBGroups rounded up to 16)
 constexpr int kBMaxBins = 32;            // bands within reach of a band (one warp scans them)
 constexpr int kBMaxNx = 1024;
 static_assert(kB2Cap <= 255, "first[] holds list positions in a byte");
@@ -855,7 +856,7 @@ struct BandSmem {
     float4 hd[kB2Slots][kB2Cap];         // (column key as int bits, fx, log2(e) / (2 s^2), 6 s)
     float4 g[kB2Slots][kB2Cap][2];       // gy over the band's rows (0 outside |dy| <= 6 s)
     float4 w[kB2Slots][kB2Cap];          // amp w_{k-1}, amp w_k, amp w_{k+1}, q = exp2(-2 d^2 c2)
-    unsigned char first[kB2Slots][kBGroups];
+    __align__(16) unsigned char first[kB2Slots][kBFirst];
     int n[kB2Slots];                     // entries of the slot, or -1: slab processed in chunks
     // per slab of a round: unique sort keys (column key * 512 + position in the slab's build
     // order), padded with INT_MAX to a multiple of 4 so the ranking reads four at a time
@@ -1217,6 +1218,371 @@ potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict_
     }
 }
 
+// ------------------------------------------------------------ slab lists
+// The band kernel above builds each slab's list inside the block that uses it,
+// one round of slabs at a time behind block barriers, with few threads busy.
+// The pair below splits that work: potential_lists_kernel builds every list of
+// a chunk of snapshots at once, one warp per (snapshot, slab, band), into
+// global memory, and potential_accum_kernel only accumulates, streaming each
+// slab's list into its shared-memory ring two slabs ahead.  A list is the one
+// band_build makes (same entries, same order, same first[] table), so the
+// potentials are bit-identical to the band kernel's.
+constexpr int kLWarps = 4;                     // lists per block of the list kernel
+constexpr int kLFirst = 144;                   // bytes of a list's first[] table (kBGroups, padded)
+static_assert(kBFirst == kLFirst && kBGroups <= kLFirst && kLFirst % 16 == 0, "first[] table size");
+// one list in global memory: first[] table, then hd[], g[][2], w[] of kB2Cap entries
+constexpr int kLHd = kLFirst;
+constexpr int kLG = kLHd + 16 * kB2Cap;
+constexpr int kLW = kLG + 32 * kB2Cap;
+constexpr int kLBytes = kLW + 16 * kB2Cap;
+static_assert(kLBytes % 16 == 0, "lists are 16-byte aligned");
+
+__device__ __forceinline__ void cp_async_cg16_pot(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait_pot() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// Source `src` of a list: the atom index, or -1.  excl/start: per-lane
+// exclusive source counts and first atoms of the list's bins (lane j: bin j).
+__device__ __forceinline__ int list_source_atom(int src, int nsrc, int count, int excl, int start) {
+    int j = 0;
+    for (int q = 1; q < count; ++q) {
+        const int e = __shfl_sync(0xffffffffu, excl, q);
+        if (e <= src) j = q;
+    }
+    const int s0 = __shfl_sync(0xffffffffu, start, j);
+    const int e0 = __shfl_sync(0xffffffffu, excl, j);
+    return src < nsrc ? s0 + (src - e0) : -1;
+}
+
+// The keys of source atom ai for band rows [r0, r0 + nrows): none when the
+// atom is skipped or reaches none of the rows; else its column (+ kofs) and
+// the images within reach of the other edge.
+__device__ __forceinline__ int list_keys(const PotParams& p, const float4& at, const int2& px, int r0, int nrows,
+                                         int kofs, int (&key)[3]) {
+    const int sp = __float_as_int(at.w);
+    if (sp < 0 || sp >= p.n_species) return 0;
+    if (range_gap(px.y, at.y, r0, nrows, p.ny, p.dy) > p.rc[sp]) return 0;
+    int n = 0;
+    key[n++] = px.x + kofs;
+    if (px.x <= p.reach_x + 1) key[n++] = px.x + p.nx + kofs;
+    if (px.x >= p.nx - p.reach_x - 2) key[n++] = px.x - p.nx + kofs;
+    return n;
+}
+
+// One warp per (snapshot t0 + blockIdx.z, slab blockIdx.y, band): the sources
+// of the bins within reach, in bin order, each with its keys (build order);
+// entries ranked by (key, build position) and written at their rank, then
+// the first[] table and the entry count (n_list; -1 for a list over kB2Cap
+// entries, which the accumulating kernel builds in chunks itself).
+__global__ void __launch_bounds__(32 * kLWarps)
+potential_lists_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                       const int2* __restrict__ binned_px, const float4* __restrict__ binned_w, PotParams p, int t0,
+                       unsigned char* __restrict__ lists, int* __restrict__ n_list) {
+    __shared__ __align__(16) int ckey[kLWarps][kB2Cap + 4];
+    __shared__ int skey[kLWarps][kB2Cap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int band = blockIdx.x * kLWarps + warp;
+    if (band >= p.n_bands) return;                    // whole warps only: no block barrier below
+    const int k = blockIdx.y;
+    const size_t tl = blockIdx.z, t = t0 + tl;
+    const float4* atoms = binned + t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
+    const float4* wts = binned_w + t * (size_t)p.n_atoms;
+    const int* off = bin_off + t * (size_t)(p.n_bins + 1);
+    const AxisRange rb = axis_range(band, kBR, p.ny, p.n_bands, p.reach_y + 1);
+    const int r0 = band * kBR, nrows = min(kBR, p.ny - r0);
+    const int kofs = p.reach_x + 2;
+    unsigned char* L = lists + ((tl * p.n_slices + k) * (size_t)p.n_bands + band) * kLBytes;
+    int* nl = n_list + (tl * p.n_bands + band) * (size_t)p.n_slices + k;
+    int start = 0, cnt = 0;
+    if (lane < rb.count) {
+        const int bin = k * p.n_bands + (rb.first + lane) % p.n_bands;
+        start = __ldg(off + bin);
+        cnt = __ldg(off + bin + 1) - start;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    const int excl = incl - cnt;
+    const int nsrc = __shfl_sync(0xffffffffu, incl, 31);
+    // pass 1: composite keys (key * 512 + build position) of every entry
+    int total = 0;
+    for (int c0 = 0; c0 < nsrc; c0 += 32) {
+        const int ai = list_source_atom(c0 + lane, nsrc, rb.count, excl, start);
+        int key[3], nk = 0;
+        if (ai >= 0) nk = list_keys(p, __ldg(atoms + ai), __ldg(atoms_px + ai), r0, nrows, kofs, key);
+        int base = nk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, base, o);
+            if (lane >= o) base += u;
+        }
+        const int chunk = __shfl_sync(0xffffffffu, base, 31);
+        base += total - nk;
+        if (total + chunk <= kB2Cap)
+            for (int m = 0; m < nk; ++m) ckey[warp][base + m] = key[m] * 512 + (base + m);
+        total += chunk;
+    }
+    if (total > kB2Cap) {
+        if (lane == 0) *nl = -1;
+        return;
+    }
+    if (lane < 4 && total + lane < ((total + 3) & ~3)) ckey[warp][total + lane] = 0x7fffffff;
+    __syncwarp();
+    // pass 2: each entry at its rank
+    float4* hd = reinterpret_cast<float4*>(L + kLHd);
+    float4* gs = reinterpret_cast<float4*>(L + kLG);
+    float4* ws = reinterpret_cast<float4*>(L + kLW);
+    const int4* ck4 = reinterpret_cast<const int4*>(ckey[warp]);
+    const int n4 = (total + 3) >> 2;
+    int done = 0;
+    for (int c0 = 0; c0 < nsrc; c0 += 32) {
+        const int ai = list_source_atom(c0 + lane, nsrc, rb.count, excl, start);
+        int key[3], nk = 0;
+        float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
+        int2 px = make_int2(0, 0);
+        if (ai >= 0) {
+            at = __ldg(atoms + ai);
+            px = __ldg(atoms_px + ai);
+            nk = list_keys(p, at, px, r0, nrows, kofs, key);
+        }
+        int base = nk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, base, o);
+            if (lane >= o) base += u;
+        }
+        const int chunk = __shfl_sync(0xffffffffu, base, 31);
+        base += done - nk;
+        done += chunk;
+        if (nk == 0) continue;
+        const int sp = __float_as_int(at.w);
+        const float c2 = p.c2[sp], rc = p.rc[sp];
+        float4 wv = __ldg(wts + ai);
+        wv.w = exp2f(-2.f * (p.dx * p.dx) * c2);
+        float g[kBR];
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) {
+            const int ky = nearest_image(r0 + r - px.y, p.ny);
+            const float d = small_int_to_float(ky) * p.dy - at.y;
+            g[r] = (r < nrows && fabsf(d) <= rc) ? exp2f(-(d * d) * c2) : 0.f;
+        }
+        for (int m = 0; m < nk; ++m) {
+            const int ck = key[m] * 512 + (base + m);
+            int rank = 0;
+#pragma unroll 4
+            for (int q = 0; q < n4; ++q) {
+                const int4 v = ck4[q];
+                rank += (v.x < ck) + (v.y < ck) + (v.z < ck) + (v.w < ck);
+            }
+            hd[rank] = make_float4(__int_as_float(key[m]), at.x, c2, rc);
+            gs[2 * rank] = make_float4(g[0], g[1], g[2], g[3]);
+            gs[2 * rank + 1] = make_float4(g[4], g[5], g[6], g[7]);
+            ws[rank] = wv;
+            skey[warp][rank] = key[m];
+        }
+    }
+    __syncwarp();
+    // first[c]: the first entry whose key is >= the lowest key that can reach column group c,
+    // four groups per 32-bit word
+    const int ngroups = (p.nx + 7) / 8;
+    uint32_t* fw = reinterpret_cast<uint32_t*>(L);
+    for (int w4 = lane; 4 * w4 < ngroups; w4 += 32) {
+        uint32_t word = 0;
+        for (int b = 0; b < 4; ++b) {
+            const int c = 4 * w4 + b;
+            const int want = 8 * c - p.reach_x - 1 + kofs;
+            int lo = 0, hi = total;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (skey[warp][mid] < want) lo = mid + 1; else hi = mid;
+            }
+            word |= (uint32_t)lo << (8 * b);
+        }
+        fw[w4] = word;
+    }
+    if (lane == 0) *nl = total;
+}
+
+// Adds slab list `slot` to the three slices it reaches, for columns x0 ..
+// x0 + kB2Cols - 1 of the band: acc_m (slice k - 1, weight w_{k-1}), acc_0
+// (slice k), acc_p (slice k + 1).  Each entry's column factors
+// g_m = exp2(-dx_m^2 c2) are formed once for the three slices (RECUR: by the
+// recurrence of band_accumulate, without the weight folded in) and scaled by
+// each slice's weight; per slice the entries add in list order, as in
+// band_accumulate.
+template <bool RECUR>
+__device__ __forceinline__ void slab_accumulate(const BandSmem& sm, int slot, int x0, int reach, int kofs, float d,
+                                                float (&acc_m)[kBR][kB2Cols], float (&acc_0)[kBR][kB2Cols],
+                                                float (&acc_p)[kBR][kB2Cols]) {
+    const int lo = x0 - reach - 1 + kofs, hi = x0 + kB2Cols - 1 + reach + 2 + kofs;
+    const int n = sm.n[slot];
+    for (int i = sm.first[slot][x0 >> 3]; i < n; ++i) {
+        const float4 h = sm.hd[slot][i];
+        const int key = __float_as_int(h.x);
+        if (key > hi) break;
+        if (key < lo) continue;
+        const float4 w = sm.w[slot][i];
+        const int k0 = x0 + kofs - key;
+        float gx[kB2Cols];
+        if constexpr (RECUR) {
+            const float dx0 = small_int_to_float(k0) * d - h.y;
+            float g = exp2f(-(dx0 * dx0) * h.z);
+            float r = exp2f(-fmaf(2.f * dx0, d, d * d) * h.z);
+#pragma unroll
+            for (int m = 0; m < kB2Cols; ++m) {
+                const float dx = fmaf((float)m, d, dx0);
+                gx[m] = fabsf(dx) <= h.w ? g : 0.f;
+                g *= r;
+                r *= w.w;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kB2Cols; ++m) {
+                const float dx = small_int_to_float(k0 + m) * d - h.y;
+                gx[m] = fabsf(dx) <= h.w ? exp2f(-(dx * dx) * h.z) : 0.f;
+            }
+        }
+        const float4 ga = sm.g[slot][i][0], gb = sm.g[slot][i][1];
+        const float gy[kBR] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+#pragma unroll
+        for (int m = 0; m < kB2Cols; ++m) {
+            const float a = gx[m] * w.x, b = gx[m] * w.y, c = gx[m] * w.z;
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) {
+                acc_m[r][m] = fmaf(gy[r], a, acc_m[r][m]);
+                acc_0[r][m] = fmaf(gy[r], b, acc_0[r][m]);
+                acc_p[r][m] = fmaf(gy[r], c, acc_p[r][m]);
+            }
+        }
+    }
+}
+
+// Accumulates the band's potential slab by slab from the lists of
+// potential_lists_kernel (snapshot t0 + blockIdx.y; its lists are those of
+// the chunk's snapshot blockIdx.y): each thread holds its columns of three
+// slices (k - 1, k, k + 1), every list entry is read once, and after slab k
+// slice k - 1 is complete and stored.  Ring of kB2Ring slots, the list of slab
+// k + 2 copied (cp.async, 16-byte pieces) while slab k accumulates; an
+// over-full list is built in chunks here, as the band kernel does.  Dynamic
+// shared memory: BandSmem, then the entry counts of the band's lists.
+template <bool RECUR>
+__global__ void __launch_bounds__(kB2Threads, 4)
+potential_accum_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
+                       const int2* __restrict__ binned_px, const float4* __restrict__ binned_w, PotParams p,
+                       int vec4, float* __restrict__ V, const unsigned char* __restrict__ lists,
+                       const int* __restrict__ n_list, int t0) {
+    extern __shared__ __align__(16) unsigned char band_smem_raw[];
+    BandSmem& sm = *reinterpret_cast<BandSmem*>(band_smem_raw);
+    int* n_all = reinterpret_cast<int*>(band_smem_raw + sizeof(BandSmem));
+    const int band = blockIdx.x;
+    const size_t tl = blockIdx.y, t = t0 + tl;
+    const int r0 = band * kBR, nrows = min(kBR, p.ny - r0);
+    const float4* atoms = binned + t * (size_t)p.n_atoms;
+    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
+    const float4* wts = binned_w + t * (size_t)p.n_atoms;
+    const int* off = bin_off + t * (size_t)(p.n_bins + 1);
+    const AxisRange rb = axis_range(band, kBR, p.ny, p.n_bands, p.reach_y + 1);
+    const int kofs = p.reach_x + 2;
+    const int ngroups = (p.nx + 7) / 8;
+    constexpr int span = kB2Cols * kB2Threads;
+    const int passes = (p.nx + span - 1) / span;
+    const int S = p.n_slices;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) n_all[k] = __ldg(n_list + (tl * p.n_bands + band) * S + k);
+    __syncthreads();
+    // copies of slab k's list into ring slot k % kB2Ring (one commit group per call, possibly empty)
+    auto fetch = [&](int k) {
+        const int slot = k % kB2Ring;
+        if (k < S) {
+            const int n = n_all[k];
+            if (threadIdx.x == 0) sm.n[slot] = n;
+            if (n >= 0) {
+                const unsigned char* L = lists + ((tl * S + k) * (size_t)p.n_bands + band) * kLBytes;
+                const int pieces = kLFirst / 16 + 4 * n;     // first[], then hd, g (two each), w per entry
+                for (int i = threadIdx.x; i < pieces; i += blockDim.x) {
+                    if (i < kLFirst / 16) {
+                        cp_async_cg16_pot(&sm.first[slot][16 * i], L + 16 * i);
+                    } else {
+                        const int e = i - kLFirst / 16;
+                        if (e < n) cp_async_cg16_pot(&sm.hd[slot][e], L + kLHd + 16 * e);
+                        else if (e < 3 * n) cp_async_cg16_pot(reinterpret_cast<float4*>(sm.g[slot]) + (e - n),
+                                                               L + kLG + 16 * (e - n));
+                        else cp_async_cg16_pot(&sm.w[slot][e - 3 * n], L + kLW + 16 * (e - 3 * n));
+                    }
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto store = [&](int si, int x0, const float (&acc)[kBR][kB2Cols]) {
+        float* out = V + ((t * S + si) * (size_t)p.ny + r0) * p.nx + x0;
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) {
+            if (r < nrows) {
+                float* o = out + (size_t)r * p.nx;
+                if (vec4) {
+                    *reinterpret_cast<float4*>(o) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < kB2Cols; ++m)
+                        if (x0 + m < p.nx) o[m] = acc[r][m];
+                }
+            }
+        }
+    };
+    for (int pass = 0; pass < passes; ++pass) {
+        const int x0 = kB2Cols * ((int)threadIdx.x + pass * kB2Threads);
+        const bool active = x0 < p.nx;
+        float acc_m[kBR][kB2Cols], acc_0[kBR][kB2Cols], acc_p[kBR][kB2Cols];
+#pragma unroll
+        for (int r = 0; r < kBR; ++r)
+#pragma unroll
+            for (int m = 0; m < kB2Cols; ++m) acc_m[r][m] = acc_0[r][m] = acc_p[r][m] = 0.f;
+        fetch(0);
+        fetch(1);
+        for (int k = 0; k < S; ++k) {
+            fetch(k + 2);
+            cp_async_wait_pot<2>();                      // slab k has landed
+            __syncthreads();
+            const int slot = k % kB2Ring;
+            if (sm.n[slot] >= 0) {
+                if (active) slab_accumulate<RECUR>(sm, slot, x0, p.reach_x, kofs, p.dx, acc_m, acc_0, acc_p);
+            } else {
+                band_bins(sm, p, off, k, 1, rb);
+                const int nsrc = sm.nsrc[0];
+                for (int c0 = 0; c0 < nsrc; c0 += kB2ChunkSrc) {
+                    const int a0 = c0, a1 = min(nsrc, c0 + kB2ChunkSrc), sl = kB2Chunk;
+                    band_build(sm, p, atoms, atoms_px, wts, 1, &a0, &a1, &sl, rb.count, r0, nrows, kofs, ngroups);
+                    if (active)
+                        slab_accumulate<RECUR>(sm, kB2Chunk, x0, p.reach_x, kofs, p.dx, acc_m, acc_0, acc_p);
+                    __syncthreads();                     // the chunk slot is rebuilt next
+                }
+            }
+            if (active && k > 0) store(k - 1, x0, acc_m);     // slice k - 1 has all its slabs
+#pragma unroll
+            for (int r = 0; r < kBR; ++r)
+#pragma unroll
+                for (int m = 0; m < kB2Cols; ++m) {
+                    acc_m[r][m] = acc_0[r][m];
+                    acc_0[r][m] = acc_p[r][m];
+                    acc_p[r][m] = 0.f;
+                }
+        }
+        if (active) store(S - 1, x0, acc_m);
+        cp_async_wait_pot<0>();
+        __syncthreads();                                 // the ring is refilled by the next pass
+    }
+}
+
 // ------------------------------------------------------------------ adjoint
 // Candidate atoms of one block of the adjoint kernel, gathered per chunk of
 // source atoms.
@@ -1568,12 +1934,25 @@ int potential_backward_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, int n
     return TACAW_OK;
 }
 
+// Snapshots whose slab lists are built at once: lists of about kListChunkBytes.
+constexpr double kListChunkBytes = 2.5e9;
+
+static int list_chunk(const tacaw_grid& g, int n_t) {
+    const double per = (double)g.n_slices * ((g.ny + kBR - 1) / kBR) * (kLBytes + sizeof(int));
+    const double c = floor(kListChunkBytes / per);
+    const int chunk = c < 1.0 ? 1 : (c > n_t ? n_t : (int)c);
+    return chunk < 1 ? 1 : chunk;
+}
+
 int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes) {
     Carver cv(nullptr);
     const long long bins = std::max(clamp_bins(bin_shape(g, BinLayout::Tiles).n_bins),
                                     clamp_bins(bin_shape(g, BinLayout::Bands).n_bins));
     carve_pot(cv, n_t, n_atoms, (int)bins);
-    cv.take<float4>((size_t)n_t * n_atoms);              // per-atom slice weights (band-walking kernel)
+    cv.take<float4>((size_t)n_t * n_atoms);              // per-atom slice weights (band-walking kernels)
+    const size_t lists = (size_t)list_chunk(g, n_t) * g.n_slices * ((g.ny + kBR - 1) / kBR);
+    cv.take<unsigned char>(lists * kLBytes);             // slab lists of one chunk of snapshots
+    cv.take<int>(lists);                                 // their entry counts
     *bytes = cv.bytes();
     return TACAW_OK;
 }
@@ -1625,7 +2004,6 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
             TACAW_LAUNCH_CHECK();
         }
         const int vec4 = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
-        const int bsm = (int)sizeof(BandSmem);
         // the column-factor recurrence needs every factor within reach of a thread's columns to stay a
         // normal float: exponent (6 s + kB2Cols d)^2 log2(e) / (2 s^2) below 120 for every species
         bool recur = true;
@@ -1633,16 +2011,34 @@ int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, c
             const double sg = amp_sigma[2 * i + 1], reach = 6.0 * sg + kB2Cols * (g.lx / g.nx);
             recur = recur && reach * reach * 1.4426950408889634 / (2.0 * sg * sg) < 120.0;
         }
-        if (recur) {
-            TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel<true>, bsm));
-            potential_band_kernel<true><<<dim3(pb.n_bands, n_t), kB2Threads, bsm, st>>>(
-                w.bin_off, w.binned, w.binned_px, wts, pb, vec4, V);
-        } else {
-            TACAW_CUDA_CHECK(ensure_smem((const void*)potential_band_kernel<false>, bsm));
-            potential_band_kernel<false><<<dim3(pb.n_bands, n_t), kB2Threads, bsm, st>>>(
-                w.bin_off, w.binned, w.binned_px, wts, pb, vec4, V);
+        const int asm_bytes = (int)(sizeof(BandSmem) + (size_t)g.n_slices * sizeof(int));
+        const void* accum = recur ? (const void*)potential_accum_kernel<true> : (const void*)potential_accum_kernel<false>;
+        TACAW_CUDA_CHECK(ensure_smem(accum, asm_bytes));
+        // snapshots per chunk: as many as the list budget allows, rounded down to whole waves of
+        // resident accumulating blocks (one block per band and snapshot) where that leaves any
+        int chunk = list_chunk(g, n_t);
+        int resident = 0;
+        TACAW_CUDA_CHECK(resident_blocks(accum, kB2Threads, asm_bytes, &resident));
+        if (resident > 0 && chunk < n_t) {
+            const long long waves = (long long)chunk * pb.n_bands / resident;
+            if (waves >= 1) chunk = (int)(waves * resident / pb.n_bands);
         }
-        TACAW_LAUNCH_CHECK();
+        const size_t n_lists = (size_t)chunk * g.n_slices * pb.n_bands;
+        unsigned char* lists = cv.take<unsigned char>(n_lists * kLBytes);
+        int* n_list = cv.take<int>(n_lists);
+        for (int t0 = 0; t0 < n_t; t0 += chunk) {
+            const int nc = n_t - t0 < chunk ? n_t - t0 : chunk;
+            potential_lists_kernel<<<dim3((pb.n_bands + kLWarps - 1) / kLWarps, g.n_slices, nc), 32 * kLWarps, 0,
+                                     st>>>(w.bin_off, w.binned, w.binned_px, wts, pb, t0, lists, n_list);
+            TACAW_LAUNCH_CHECK();
+            if (recur)
+                potential_accum_kernel<true><<<dim3(pb.n_bands, nc), kB2Threads, asm_bytes, st>>>(
+                    w.bin_off, w.binned, w.binned_px, wts, pb, vec4, V, lists, n_list, t0);
+            else
+                potential_accum_kernel<false><<<dim3(pb.n_bands, nc), kB2Threads, asm_bytes, st>>>(
+                    w.bin_off, w.binned, w.binned_px, wts, pb, vec4, V, lists, n_list, t0);
+            TACAW_LAUNCH_CHECK();
+        }
         return TACAW_OK;
     }
     Carver cv(ws);
