@@ -996,20 +996,22 @@ struct QItem {
     int job, t, s, pass, tile;
 };
 
+// (The host keeps every job's item count below 2^31, so positions within a job
+// are 32-bit.)
 __device__ __forceinline__ QItem q_decode(const QJobs& jobs, long long it) {
     const int IT = jobs.items;
     QItem q;
     int j = 0;
     while (j + 1 < jobs.n && jobs.item0[j + 1] <= it) ++j;
-    const long long r = it - jobs.item0[j];
+    const int r = (int)(it - jobs.item0[j]);
     const int S = jobs.n_slices[j], T = jobs.n_t[j], Tw = jobs.wave;
-    const long long per_wave = (long long)S * 2 * IT * Tw;
-    const int w = (int)(r / per_wave);
+    const int per_wave = S * 2 * IT * Tw;
+    const int w = r / per_wave;
     const int first = w * Tw;
     const int nw = min(Tw, T - first);
-    const long long in_wave = r - (long long)w * per_wave;
-    const int s = (int)(in_wave / (2LL * nw * IT));
-    int rem = (int)(in_wave - (long long)s * 2 * nw * IT);
+    const int in_wave = r - w * per_wave;
+    const int s = in_wave / (2 * nw * IT);
+    int rem = in_wave - s * 2 * nw * IT;
     const int pass = rem >= nw * IT ? 1 : 0;
     if (pass) rem -= nw * IT;
     q.job = j;
@@ -1082,21 +1084,35 @@ __device__ __forceinline__ void q_issue(const QJobs& jobs, const QItem& q, int t
             int b = N - K;
             b -= b & 1;
             if (b < a) b = a;
-            for (int i = threadIdx.x; i < C::ROWS * (N / 2); i += kQThreads) {
+            const float2* rows = snap + (size_t)y0 * N;
+            constexpr int CH = C::ROWS * (N / 2), REP = (CH + kQThreads - 1) / kQThreads;
+#pragma unroll
+            for (int j = 0; j < REP; ++j) {
+                const int i = threadIdx.x + j * kQThreads;
                 const int r = i / (N / 2), c2 = (i % (N / 2)) * 2;
-                if (c2 < a || c2 >= b) cp_async_cg16(stage + r * C::PL + c2, snap + (size_t)(y0 + r) * N + c2);
+                if ((CH % kQThreads == 0 || i < CH) && (c2 < a || c2 >= b))
+                    cp_async_cg16(stage + r * C::PL + c2, rows + r * N + c2);
             }
         }
         const float* Vs = jobs.V[q.job] + (((size_t)q.t * jobs.n_slices[q.job] + q.s) * N + y0) * N;
         float* vst = reinterpret_cast<float*>(stage + QStage<N>::PSI);
-        for (int i = threadIdx.x; i < C::ROWS * N / 4; i += kQThreads) cp_async_cg16(vst + 4 * i, Vs + 4 * i);
+        constexpr int VCH = C::ROWS * N / 4, VREP = (VCH + kQThreads - 1) / kQThreads;
+#pragma unroll
+        for (int j = 0; j < VREP; ++j) {
+            const int i = threadIdx.x + j * kQThreads;
+            if (VCH % kQThreads == 0 || i < VCH) cp_async_cg16(vst + 4 * i, Vs + 4 * i);
+        }
     } else {
         const int kx0 = q.tile * jobs.span + ti * C::ROWS;
         if (kx0 > K && kx0 + C::ROWS - 1 < N - K) return;
         constexpr int CH = C::ROWS / 2;                  // 16-byte chunks per row of the tile
-        for (int i = threadIdx.x; i < N * CH; i += kQThreads) {
+        constexpr int ALL = N * CH, REP = (ALL + kQThreads - 1) / kQThreads;
+        const float2* cols = snap + kx0;
+#pragma unroll
+        for (int j = 0; j < REP; ++j) {
+            const int i = threadIdx.x + j * kQThreads;
             const int r = i / CH, h = i % CH;
-            cp_async_cg16(stage + r * C::ROWS + 2 * h, snap + (size_t)r * N + kx0 + 2 * h);
+            if (ALL % kQThreads == 0 || i < ALL) cp_async_cg16(stage + r * C::ROWS + 2 * h, cols + r * N + 2 * h);
         }
     }
 }
@@ -1194,8 +1210,10 @@ __device__ __forceinline__ bool q_wait_ready(const QJobs& jobs, const QItem& q, 
 // Each block walks its tiles through a ring of QStage<N>::NST stages: while
 // tile k is transformed, the copies of tile k + 1 (the next tile of the same
 // item, or the first of the block's next item once that item's inputs are
-// final) are in flight.  Three barriers per tile: the plan of the next tile,
-// the arrival of this tile's copies, the end of its use of the stage.
+// final) are in flight.  Thread 0 takes items from the queue, decodes them and
+// plans the tile after next while the block transforms; two barriers per
+// tile: the arrival of the tile's copies, and the end of its use of the stage
+// (which also publishes the plan).
 template <int N>
 __global__ void __launch_bounds__(kQThreads, QCfg<N>::MIN_BLOCKS)
 ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ tw_g, int* __restrict__ ctl,
@@ -1204,10 +1222,11 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
     constexpr int NST = QStage<N>::NST;
     extern __shared__ __align__(16) float2 qsm[];
     float2* tw = qsm + NST * QStage<N>::F2;
-    // written by thread 0, each read by all threads between two barriers: the first item, the plan of
-    // the next tile (item, tile in item, 0 ready / 1 not yet / 2 none), the verdict of a blocking wait
-    __shared__ long long s_first, s_it;
-    __shared__ int s_first_ok, s_ti, s_flag, s_ok;
+    // written by thread 0, read by all threads between two barriers: the first item; the plan of
+    // the next tile (item, tile in item, 0 ready / 1 inputs not final yet / 2 none); the verdict of
+    // a blocking wait
+    __shared__ QItem s_first, s_next;
+    __shared__ int s_first_ok, s_next_ti, s_next_flag, s_ok;
     unsigned long long* head = reinterpret_cast<unsigned long long*>(ctl);
     int* abort_word = ctl + 2;
     const int U = jobs.snap0[jobs.n];
@@ -1218,60 +1237,57 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
     stage_twiddles<N>(tw, tw_g);
     const int tr = threadIdx.x % C::TPT, row = threadIdx.x / C::TPT;     // row tiles
     const int cc = threadIdx.x % C::ROWS, tc = threadIdx.x / C::ROWS;     // column tiles
-    // thread 0: the block's next item, taken one tile before it is planned (during the second-to-last
-    // tile of the current item, or with the current item when items are one tile), so that few items
-    // are taken but not started
+    // thread 0: the block's next item, taken when the tile before the last of the current item is
+    // planned (with the current item when items are one tile), so that few items are taken but
+    // not started and the queue's latency hides behind a tile
     unsigned long long nxt = 0;
     bool have_nxt = false;
-    if (threadIdx.x == 0) {
-        const unsigned long long cur = atomicAdd(head, 1ull);
+    auto plan = [&](const QItem& pq, int pti) {     // thread 0: the tile after (pq, pti)
+        if (pti + 1 < tiles) {
+            s_next = pq;
+            s_next_ti = pti + 1;
+            s_next_flag = 0;
+            if (pti + 2 == tiles && !have_nxt) {
+                nxt = atomicAdd(head, 1ull);
+                have_nxt = true;
+            }
+            return;
+        }
+        if (!have_nxt) nxt = atomicAdd(head, 1ull);
+        have_nxt = false;
+        if ((long long)nxt >= total || *reinterpret_cast<volatile int*>(abort_word)) {
+            s_next_flag = 2;
+            return;
+        }
+        const QItem qd = q_decode(jobs, (long long)nxt);
+        s_next = qd;
+        s_next_ti = 0;
+        s_next_flag = q_ready(jobs, qd, row_done, col_done) ? 0 : 1;
         if (tiles == 1) {
             nxt = atomicAdd(head, 1ull);
             have_nxt = true;
         }
-        s_first = (long long)cur;
-        s_first_ok = (long long)cur < total &&
-                     q_wait_ready(jobs, q_decode(jobs, (long long)cur), row_done, col_done, abort_word, err, polls);
+    };
+    if (threadIdx.x == 0) {
+        const unsigned long long cur = atomicAdd(head, 1ull);
+        s_first_ok = 0;
+        if ((long long)cur < total) {
+            s_first = q_decode(jobs, (long long)cur);
+            s_first_ok = q_wait_ready(jobs, s_first, row_done, col_done, abort_word, err, polls);
+        }
     }
     __syncthreads();
     if (!s_first_ok) return;
-    long long item = s_first;
-    QItem q = q_decode(jobs, item);
+    QItem q = s_first;
     int ti = 0, st = 0;
     q_issue<N>(jobs, q, 0, qsm);
     cp_async_commit_group();
+    if (threadIdx.x == 0) plan(q, 0);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) {                     // plan the next tile
-            if (ti + 1 < tiles) {
-                s_it = item;
-                s_ti = ti + 1;
-                s_flag = 0;
-                if (ti + 2 == tiles && !have_nxt) {
-                    nxt = atomicAdd(head, 1ull);
-                    have_nxt = true;
-                }
-            } else {
-                if (!have_nxt) nxt = atomicAdd(head, 1ull);
-                have_nxt = false;
-                if ((long long)nxt >= total || *reinterpret_cast<volatile int*>(abort_word)) {
-                    s_flag = 2;
-                } else {
-                    s_it = (long long)nxt;
-                    s_ti = 0;
-                    s_flag = q_ready(jobs, q_decode(jobs, (long long)nxt), row_done, col_done) ? 0 : 1;
-                    if (tiles == 1) {
-                        nxt = atomicAdd(head, 1ull);
-                        have_nxt = true;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        const int flag = s_flag;
-        const long long nit = s_it;
-        const int nti = s_ti;
-        QItem qn = q;
-        if (flag != 2 && nti == 0) qn = q_decode(jobs, nit);
+        const int flag = s_next_flag;
+        const int nti = s_next_ti;
+        const QItem qn = flag == 2 ? q : s_next;
         float2* cur_stage = qsm + st * QStage<N>::F2;
         float2* nxt_stage = qsm + (st ^ (NST - 1)) * QStage<N>::F2;
         const bool early = NST == 2 && flag == 0;
@@ -1282,7 +1298,7 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
         } else {
             cp_async_wait_pending<0>();
         }
-        __syncthreads();                            // this tile's copies have landed
+        __syncthreads();                            // this tile's copies have landed; the plan is read
         const int S = jobs.n_slices[q.job];
         float2* snap = jobs.psi[q.job] + (size_t)q.t * N * N;
         const int K = __ldg(jobs.kymax[q.job] + N);
@@ -1296,6 +1312,7 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
             q_col_tile<N>(cur_stage, snap, q.tile * jobs.span + ti * C::ROWS, jobs.px[q.job], jobs.py[q.job],
                           jobs.kymax[q.job], K, q.s + 1 == S, tw, tc, cc);
         }
+        if (threadIdx.x == 0 && flag != 2) plan(qn, nti);
         __syncthreads();                            // the stage is free; the tile's stores are issued
         if (ti + 1 == tiles && threadIdx.x == 0) {  // the item is done: release it
             __threadfence();
@@ -1310,9 +1327,8 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
             q_issue<N>(jobs, qn, nti, nxt_stage);
             cp_async_commit_group();
         }
-        item = nit;
-        ti = nti;
         q = qn;
+        ti = nti;
         st ^= NST - 1;
     }
     cp_async_wait_pending<0>();
@@ -1586,7 +1602,10 @@ int multislice_queue_run(const tacaw_job* jobs, int n_jobs, int wave, int span, 
                 q.n_t[k] = b.n_t;
                 q.n_slices[k] = b.grid.n_slices;
                 q.sigma[k] = sigma[j];
-                item += (long long)b.grid.n_slices * 2 * items * b.n_t;
+                const long long job_items = (long long)b.grid.n_slices * 2 * items * b.n_t;
+                TACAW_REQUIRE(job_items < (1LL << 31), TACAW_EINVAL,
+                              "tacaw_multislice_queue: job %d has %lld queue items (at most 2^31 - 1)", j, job_items);
+                item += job_items;
                 snaps += b.n_t;
             }
             if (q.n == 0) break;

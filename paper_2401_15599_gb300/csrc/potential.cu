@@ -818,24 +818,23 @@ potential_slab_kernel(const int* __restrict__ bin_off, const float4* __restrict_
 }
 
 // ------------------------------------------------------------------ forward, band walk
-// One block per (band of kBR rows, snapshot) walks the slices in order.  When
-// 6 s <= dz an atom of slab k reaches only slices k-1, k and k+1, so the block
-// builds, once per slab, the list of the slab's atoms whose window reaches the
-// band -- per atom its row factors gy over the band's rows, its weights
-// amp w_{k-1}, amp w_k, amp w_{k+1} (computed once per atom and snapshot by
-// atom_weights_kernel), and its column and offset in the pixel -- and keeps the
-// lists of slabs s-1 .. s+kB2Group in a ring of shared-memory slots.  Each list
-// is sorted by the atom's pixel column (periodic images of atoms near the left
-// and right edges included as entries of their own), so a thread that owns
-// kB2Cols adjacent columns of the band runs over exactly the atoms whose window
+// Band-walking potential (6 s <= dz: an atom of slab k reaches only slices
+// k-1, k and k+1).  For every (snapshot, slab, band of kBR rows) a list holds
+// the slab's atoms whose window reaches the band -- per atom its row factors
+// gy over the band's rows, its weights amp w_{k-1}, amp w_k, amp w_{k+1}
+// (computed once per atom and snapshot by atom_weights_kernel), and its column
+// and offset in the pixel -- sorted by the atom's pixel column (periodic
+// images of atoms near the left and right edges as entries of their own), with
+// a table of the first entry that can reach each group of 8 columns.  One block
+// per (band, snapshot) then walks the slabs in order, a thread owning kB2Cols
+// adjacent columns of the band running over exactly the entries whose window
 // can reach them:
 //   v_s(x, y) = sum over slabs k = s-1, s, s+1 (in this order), over list
-//               entries in list order, of gy(y) * (amp w_s exp(-dx^2 / 2 s^2)).
+//               entries in list order, of gy(y) * amp w_s * exp(-dx^2 / 2 s^2).
 // List order is (column, position of the atom in the slab's bins), and the
 // bins hold atoms in input order, so the order -- and so the FP32 sum -- is
-// fixed by the configuration.  The lists of kB2Group slabs are built in one
-// round by all threads; a slab whose list would not fit a slot is processed
-// per slice in chunks of sources through one more slot.
+// fixed by the configuration.  A slab whose list would not fit a slot is
+// built in chunks of sources by the accumulating block itself.
 constexpr int kBR = kBandRows;           // rows per band (the Bands bin layout)
 constexpr int kB2Threads = 128;
 constexpr int kB2Cols = 4;               // adjacent columns per thread
@@ -943,7 +942,8 @@ __device__ void band_bins(BandSmem& sm, const PotParams& p, const int* __restric
     __syncthreads();
 }
 
-// Lists of nk consecutive slabs k0 .. in one round: slab j's sources
+// Lists of nk consecutive slabs k0 .. in one round (the accumulating kernel's
+// chunks of an over-full slab): slab j's sources
 // [src0_j, src1_j) (bin tables loaded by band_bins; the sources of all slabs
 // together at most blockDim.x) into slot slot_j, each sorted by (column key,
 // build position).  slot_j < 0 skips a slab.  Every slab's entry count goes to
@@ -1070,163 +1070,13 @@ __device__ void band_build(BandSmem& sm, const PotParams& p, const float4* __res
     __syncthreads();
 }
 
-// Adds the list in `slot` to columns x0 .. x0 + kB2Cols - 1 of the band for
-// slice offset widx (0: the slab below the slice, 1: its own, 2: the slab above).
-// RECUR: the column factors g_m = exp2(-dx_m^2 c2), dx_m = dx_0 + m d, by the
-// exact recurrence g_{m+1} = g_m r_m, r_{m+1} = r_m q with
-// r_0 = exp2(-(2 dx_0 d + d^2) c2) and q = exp2(-2 d^2 c2) (two exponentials
-// per entry instead of kB2Cols; a few ulp of rounding), used when no factor
-// within reach underflows (pixels fine enough next to the width: the host
-// checks).  Otherwise each factor is its own exponential.
-template <bool RECUR>
-__device__ __forceinline__ void band_accumulate(const BandSmem& sm, int slot, int widx, int x0, int reach, int kofs,
-                                                float d, float (&acc)[kBR][kB2Cols]) {
-    const int lo = x0 - reach - 1 + kofs, hi = x0 + kB2Cols - 1 + reach + 2 + kofs;
-    const int n = sm.n[slot];
-    const float* wcol = reinterpret_cast<const float*>(&sm.w[slot][0]) + widx;
-    for (int i = sm.first[slot][x0 >> 3]; i < n; ++i) {
-        const float4 h = sm.hd[slot][i];
-        const int key = __float_as_int(h.x);
-        if (key > hi) break;
-        if (key < lo) continue;
-        const float wv = wcol[4 * i];
-        const int k0 = x0 + kofs - key;                  // column x0 minus the atom's column (this image)
-        float gx[kB2Cols];
-        if constexpr (RECUR) {
-            const float q = wcol[4 * i + 3 - widx];
-            const float dx0 = small_int_to_float(k0) * d - h.y;
-            float g = wv * exp2f(-(dx0 * dx0) * h.z);
-            float r = exp2f(-fmaf(2.f * dx0, d, d * d) * h.z);
-#pragma unroll
-            for (int m = 0; m < kB2Cols; ++m) {
-                const float dx = fmaf((float)m, d, dx0);
-                gx[m] = fabsf(dx) <= h.w ? g : 0.f;
-                g *= r;
-                r *= q;
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < kB2Cols; ++m) {
-                const float dx = small_int_to_float(k0 + m) * d - h.y;
-                gx[m] = fabsf(dx) <= h.w ? wv * exp2f(-(dx * dx) * h.z) : 0.f;
-            }
-        }
-        const float4 ga = sm.g[slot][i][0], gb = sm.g[slot][i][1];
-        const float gy[kBR] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
-#pragma unroll
-        for (int r = 0; r < kBR; ++r)
-#pragma unroll
-            for (int m = 0; m < kB2Cols; ++m) acc[r][m] = fmaf(gy[r], gx[m], acc[r][m]);
-    }
-}
-
-template <bool RECUR>
-__global__ void __launch_bounds__(kB2Threads, 6)
-potential_band_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
-                      const int2* __restrict__ binned_px, const float4* __restrict__ binned_w, PotParams p,
-                      int vec4, float* __restrict__ V) {
-    extern __shared__ __align__(16) unsigned char band_smem_raw[];
-    BandSmem& sm = *reinterpret_cast<BandSmem*>(band_smem_raw);
-    const int band = blockIdx.x;
-    const size_t t = blockIdx.y;
-    const int r0 = band * kBR, nrows = min(kBR, p.ny - r0);
-    const float4* atoms = binned + t * (size_t)p.n_atoms;
-    const int2* atoms_px = binned_px + t * (size_t)p.n_atoms;
-    const float4* wts = binned_w + t * (size_t)p.n_atoms;
-    const int* off = bin_off + t * (size_t)(p.n_bins + 1);
-    const AxisRange rb = axis_range(band, kBR, p.ny, p.n_bands, p.reach_y + 1);
-    const int kofs = p.reach_x + 2;                      // keys are columns + kofs >= 0
-    const int ngroups = (p.nx + 7) / 8;
-    constexpr int span = kB2Cols * kB2Threads;
-    const int passes = (p.nx + span - 1) / span;
-
-    // lists of slabs k0 .. k1 - 1 into their ring slots, in rounds of at most kB2Group slabs whose
-    // sources fit one per thread; a slab with more sources than threads is marked for chunks
-    auto build = [&](int k0, int k1) {
-        while (k0 < k1) {
-            const int nk = min(kB2Group, k1 - k0);
-            band_bins(sm, p, off, k0, nk, rb);       // ends with a barrier: nsrc[] is uniform
-            int s0[kB2Group], s1[kB2Group], sl[kB2Group], take = 0, sum = 0;
-            for (int q = 0; q < nk; ++q) {
-                const int c = sm.nsrc[q];
-                if (sum + c > (int)blockDim.x) break;
-                s0[q] = 0;
-                s1[q] = c;
-                sl[q] = (k0 + q) % kB2Ring;
-                sum += c;
-                take = q + 1;
-            }
-            if (take == 0) {                         // slab k0 alone exceeds the threads: chunks per slice
-                if (threadIdx.x == 0) sm.n[k0 % kB2Ring] = -1;
-                __syncthreads();
-                k0 += 1;
-                continue;
-            }
-            band_build(sm, p, atoms, atoms_px, wts, take, s0, s1, sl, rb.count, r0, nrows, kofs, ngroups);
-            k0 += take;
-        }
-    };
-
-    for (int s = 0; s < p.n_slices; s += kB2Group) {
-        const int s_end = min(p.n_slices, s + kB2Group);
-        // slabs s-1 .. s_end are needed; s-1 and s are in the ring from the previous round
-        build(s == 0 ? 0 : s + 1, min(p.n_slices, s_end + 1));
-        for (int si = s; si < s_end; ++si) {
-            for (int pass = 0; pass < passes; ++pass) {
-                const int x0 = kB2Cols * ((int)threadIdx.x + pass * kB2Threads);
-                const bool active = x0 < p.nx;
-                float acc[kBR][kB2Cols];
-#pragma unroll
-                for (int r = 0; r < kBR; ++r)
-#pragma unroll
-                    for (int m = 0; m < kB2Cols; ++m) acc[r][m] = 0.f;
-                for (int k = max(0, si - 1); k <= min(p.n_slices - 1, si + 1); ++k) {
-                    const int widx = si - k + 1;
-                    if (sm.n[k % kB2Ring] >= 0) {
-                        if (active) band_accumulate<RECUR>(sm, k % kB2Ring, widx, x0, p.reach_x, kofs, p.dx, acc);
-                        continue;
-                    }
-                    band_bins(sm, p, off, k, 1, rb);
-                    const int nsrc = sm.nsrc[0];
-                    for (int c0 = 0; c0 < nsrc; c0 += kB2ChunkSrc) {
-                        const int a0 = c0, a1 = min(nsrc, c0 + kB2ChunkSrc), sl = kB2Chunk;
-                        band_build(sm, p, atoms, atoms_px, wts, 1, &a0, &a1, &sl, rb.count, r0, nrows, kofs,
-                                   ngroups);
-                        if (active) band_accumulate<RECUR>(sm, kB2Chunk, widx, x0, p.reach_x, kofs, p.dx, acc);
-                        __syncthreads();                 // the chunk slot is rebuilt next
-                    }
-                }
-                if (active) {
-                    float* out = V + ((t * p.n_slices + si) * (size_t)p.ny + r0) * p.nx + x0;
-#pragma unroll
-                    for (int r = 0; r < kBR; ++r) {
-                        if (r < nrows) {
-                            float* o = out + (size_t)r * p.nx;
-                            if (vec4) {
-                                *reinterpret_cast<float4*>(o) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-                            } else {
-#pragma unroll
-                                for (int m = 0; m < kB2Cols; ++m)
-                                    if (x0 + m < p.nx) o[m] = acc[r][m];
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();                                 // the next round rebuilds the slots of older slabs
-    }
-}
-
 // ------------------------------------------------------------ slab lists
-// The band kernel above builds each slab's list inside the block that uses it,
-// one round of slabs at a time behind block barriers, with few threads busy.
-// The pair below splits that work: potential_lists_kernel builds every list of
-// a chunk of snapshots at once, one warp per (snapshot, slab, band), into
-// global memory, and potential_accum_kernel only accumulates, streaming each
-// slab's list into its shared-memory ring two slabs ahead.  A list is the one
-// band_build makes (same entries, same order, same first[] table), so the
-// potentials are bit-identical to the band kernel's.
+// Two kernels per chunk of snapshots: potential_lists_kernel builds every
+// list of the chunk at once, one warp per (snapshot, slab, band), into global
+// memory (no block barriers, every warp busy), and potential_accum_kernel only
+// accumulates, streaming each slab's list into its shared-memory ring two
+// slabs ahead.  A list is the one band_build makes from the same sources
+// (same entries, order and first[] table).
 constexpr int kLWarps = 4;                     // lists per block of the list kernel
 constexpr int kLFirst = 144;                   // bytes of a list's first[] table (kBGroups, padded)
 static_assert(kBFirst == kLFirst && kBGroups <= kLFirst && kLFirst % 16 == 0, "first[] table size");
@@ -1416,10 +1266,12 @@ potential_lists_kernel(const int* __restrict__ bin_off, const float4* __restrict
 // Adds slab list `slot` to the three slices it reaches, for columns x0 ..
 // x0 + kB2Cols - 1 of the band: acc_m (slice k - 1, weight w_{k-1}), acc_0
 // (slice k), acc_p (slice k + 1).  Each entry's column factors
-// g_m = exp2(-dx_m^2 c2) are formed once for the three slices (RECUR: by the
-// recurrence of band_accumulate, without the weight folded in) and scaled by
-// each slice's weight; per slice the entries add in list order, as in
-// band_accumulate.
+// g_m = exp2(-dx_m^2 c2) are formed once for the three slices and scaled by
+// each slice's weight.  RECUR: the factors by the exact recurrence
+// g_{m+1} = g_m r_m, r_{m+1} = r_m q with r_0 = exp2(-(2 dx_0 d + d^2) c2) and
+// q = exp2(-2 d^2 c2) (two exponentials per entry instead of kB2Cols, a few
+// ulp of rounding), used when no factor within reach underflows (the host
+// checks); otherwise one exponential per factor.
 template <bool RECUR>
 __device__ __forceinline__ void slab_accumulate(const BandSmem& sm, int slot, int x0, int reach, int kofs, float d,
                                                 float (&acc_m)[kBR][kB2Cols], float (&acc_0)[kBR][kB2Cols],
