@@ -63,9 +63,9 @@ def parse_args():
     p.add_argument("--spectrum-only", default="",
                    help="T,NQ: time only the temporal transform on seeded synthetic exit waves [T][NQ] "
                         "(a kernel micro-benchmark; not the benchmark line)")
-    p.add_argument("--ms-flags", choices=["auto", "0", "1", "2", "3"], default="auto",
-                   help="variants of the multislice passes (tacaw_multislice flags): tuned (auto), or 0-3 "
-                        "(1: one warp per 512-point row, 2: one block per column block)")
+    p.add_argument("--ms-flags", choices=["auto", "0", "1", "2", "3", "4"], default="auto",
+                   help="variants of the multislice passes (tacaw_multislice flags): tuned (auto), or 0-4 "
+                        "(1: one warp per 512-point row, 2: one block per column block, 4: work queue)")
     p.add_argument("--no-c3", action="store_true",
                    help="skip the full batched configuration (64 uneven jobs, 512-4096 snapshots each)")
     p.add_argument("--c3-only", action="store_true",
@@ -533,6 +533,7 @@ def run_ours(args):
             "explicit_grid_1024_bins": explicit_grid_comparison(tts, w, args.steps, stream),
             "plain_cufft_multislice_call": plain_cufft_slice_step(tts, g, args.steps, stream),
             "batched_jobs": batched_jobs_sample(args.steps, stream),
+            "batched_queue_vs_launches": batched_queue_vs_launches(args.steps, stream),
             "adjoint": adjoint_sample(args.steps, stream),
         }
         torch.cuda.synchronize()
@@ -670,6 +671,40 @@ def plain_cufft_slice_step(tts, g, reps, stream):
     ours_ms = _events_ms(lambda: api.multislice(g, V, out=ours, ms_flags=tts.ms_flags), reps, stream)
     return {"snapshots": int(V.shape[0]), "plain_cufft_ms": ms, "ours_ms": ours_ms,
             "speedup": ms / ours_ms, "rel_l2_difference": diff}
+
+
+def batched_queue_vs_launches(reps, stream, n_jobs=16, snapshots=24):
+    """The multislice of uneven jobs (the first `n_jobs` of the 64 seeded batched
+    jobs: grids 128-768, 10-150 slices; `snapshots` snapshots each, random slice
+    potentials) through tacaw_multislice_batch (two launches per slice and grid
+    size) and through tacaw_multislice_queue (one persistent launch per grid
+    size over the device work queue), on the same buffers; the exit waves must
+    agree bit for bit."""
+    import torch
+    import workloads as W
+    from paper_2401_15599_gb300 import api
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    jobs, units, sizes = [], 0, []
+    for wj in W.batching_jobs(n_jobs=n_jobs):
+        g = wj.grid
+        V = torch.rand((snapshots, g.n_slices, g.ny, g.nx), generator=gen, device="cuda") * 30.0
+        jobs.append({"grid": g, "V": V, "out": torch.empty((snapshots, g.ny, g.nx), dtype=torch.complex64,
+                                                           device="cuda")})
+        units += g.nx * g.ny * g.n_slices * snapshots
+        sizes.append(g.nx)
+    api.multislice_batch(jobs)                           # warm-up (workspace, kernel attributes)
+    launches_ms = _events_ms(lambda: api.multislice_batch(jobs), reps, stream)
+    ref = [j["out"].clone() for j in jobs]
+    api.multislice_batch(jobs, queue=True)
+    queue_ms = _events_ms(lambda: api.multislice_batch(jobs, queue=True), reps, stream)
+    api.status()
+    same = all(torch.equal(j["out"], r) for j, r in zip(jobs, ref))
+    del jobs, ref
+    torch.cuda.empty_cache()
+    return {"jobs": n_jobs, "snapshots_per_job": snapshots, "grids": sorted(set(sizes)), "units": units,
+            "per_slice_launches_ms": launches_ms, "queue_ms": queue_ms,
+            "value_per_slice_launches": units / (launches_ms * 1e-3), "value_queue": units / (queue_ms * 1e-3),
+            "unit": UNIT, "bit_identical": same}
 
 
 def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=64):

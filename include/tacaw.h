@@ -494,8 +494,8 @@ int tacaw_multislice_batch(const tacaw_job* jobs, int32_t n_jobs, void* ws, size
  * jobs            HOST array as for tacaw_multislice_batch (n_t up to 2^24 per
  *                 job, 2^28 in all); grids with nx == ny in the supported sizes;
  *                 V and psi_q 16-byte aligned
- * wave_snapshots  snapshots per wave, or 0: as many as fit about 64 MiB of
- *                 exit waves (32 at 512^2)
+ * wave_snapshots  snapshots per wave, or 0: as many as fit about 128 MiB of
+ *                 exit waves (64 at 512^2)
  * item_span       rows or columns per item: a multiple of the rows one block
  *                 transforms at once (256 / (N / values per thread): 4 at
  *                 512^2) that divides N; 0 or any other value: 16 (the

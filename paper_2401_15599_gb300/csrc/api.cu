@@ -259,15 +259,16 @@ int tacaw_multislice_queue(const tacaw_job* jobs, int32_t n_jobs, int32_t wave_s
                       "%s: job %d: n_t must be in [0, 2^24]", fn, j);
         TACAW_REQUIRE(jobs[j].n_t == 0 || (jobs[j].V && jobs[j].psi_q), TACAW_EINVAL,
                       "%s: job %d: NULL array", fn, j);
-        TACAW_REQUIRE(reinterpret_cast<uintptr_t>(jobs[j].V) % 16 == 0 &&
-                          reinterpret_cast<uintptr_t>(jobs[j].psi_q) % 16 == 0,
-                      TACAW_EINVAL, "%s: job %d: V and psi_q must be 16-byte aligned", fn, j);
         total += jobs[j].n_t;
     }
     TACAW_REQUIRE(total <= (1 << 28), TACAW_EINVAL, "%s: at most 2^28 snapshots in one call", fn);
     bool query = false;
     int rc = check_ws(ws, ws_bytes, multislice_queue_ws_bytes(jobs, n_jobs), fn, &query);
     if (rc || query) return rc;
+    for (int j = 0; j < n_jobs; ++j)
+        TACAW_REQUIRE(jobs[j].n_t == 0 || (reinterpret_cast<uintptr_t>(jobs[j].V) % 16 == 0 &&
+                                           reinterpret_cast<uintptr_t>(jobs[j].psi_q) % 16 == 0),
+                      TACAW_EINVAL, "%s: job %d: V and psi_q must be 16-byte aligned", fn, j);
     {
         const int frc = inject_launch_fault(fn);
         if (frc) return frc;
@@ -330,7 +331,10 @@ int tacaw_time_to_spectrum_host(const tacaw_grid* grid, int32_t n_t, int32_t n_a
     TACAW_REQUIRE(n_species >= 1 && n_species <= TACAW_MAX_SPECIES && amp_sigma, TACAW_EINVAL,
                   "%s: need 1..%d species with amp_sigma", fn, TACAW_MAX_SPECIES);
     TACAW_REQUIRE(dt_fs > 0 && isfinite(dt_fs), TACAW_EINVAL, "%s: dt must be positive", fn);
-    TACAW_REQUIRE((ms_flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS)) == 0, TACAW_EINVAL, "%s: unknown multislice flags", fn);
+    TACAW_REQUIRE((ms_flags & ~(TACAW_MS_WARP_ROWS | TACAW_MS_BLOCK_COLS | TACAW_MS_QUEUE)) == 0, TACAW_EINVAL,
+                  "%s: unknown multislice flags", fn);
+    TACAW_REQUIRE(!(ms_flags & TACAW_MS_QUEUE) || (ms_flags == TACAW_MS_QUEUE && grid->nx == grid->ny), TACAW_EINVAL,
+                  "%s: TACAW_MS_QUEUE alone, on a square grid", fn);
     TACAW_REQUIRE(precision == TACAW_FP32 || precision == TACAW_BF16X3 || precision == TACAW_BF16X6 ||
                       precision == TACAW_FFT32, TACAW_EINVAL, "%s: unknown precision %d", fn, precision);
     TACAW_REQUIRE(precision != TACAW_FFT32 || time_fft_size_supported(n_t), TACAW_EUNSUPPORTED,

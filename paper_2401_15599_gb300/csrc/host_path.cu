@@ -6,6 +6,8 @@
 // waves); then the temporal transform on the natural energy grid, and the
 // copies of I and I_el back to the host, all on the caller's stream.
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tacaw {
@@ -14,6 +16,8 @@ int potential_ws_bytes(const tacaw_grid& g, int n_t, int n_atoms, size_t* bytes)
 int potential_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos, const int* species,
                   int n_species, const float* amp_sigma, float* V, void* ws, cudaStream_t st);
 size_t multislice_ws_bytes(const tacaw_grid& g);
+size_t multislice_queue_ws_bytes(const tacaw_job* jobs, int n_jobs);
+int multislice_queue_run(const tacaw_job* jobs, int n_jobs, int wave, int span, void* ws, cudaStream_t st);
 int multislice_run(const tacaw_grid& g, int n_t, const float* V, const float2* psi_in, float2* psi_q,
                    double2* psi_sum, void* ws, cudaStream_t st, int flags);
 size_t spectrum_ws_bytes(int nq, int n_t, int n_w, bool have_sum, bool have_iel, int precision);
@@ -44,7 +48,14 @@ HostPathWs carve_host_path(Carver& cv, const tacaw_grid& g, int n_t, int n_atoms
     w.I = cv.take<float>(nq * (size_t)n_t);
     w.I_el = cv.take<double>(nq);
     potential_ws_bytes(g, batch, n_atoms, &w.b_pot);
-    w.b_ms = multislice_ws_bytes(g);
+    tacaw_job job;                                   // the work-queue multislice of one batch
+    job.grid = g;
+    job.n_t = batch;
+    job.V = nullptr;
+    job.psi_in = nullptr;
+    job.psi_q = nullptr;
+    job.psi_sum = nullptr;
+    w.b_ms = std::max(multislice_ws_bytes(g), multislice_queue_ws_bytes(&job, 1));
     w.b_spec = spectrum_ws_bytes((int)nq, n_t, n_t, true, true, precision);
     w.ws_pot = cv.take<unsigned char>(w.b_pot);
     w.ws_ms = cv.take<unsigned char>(w.b_ms);
@@ -96,7 +107,18 @@ int host_path_run(const tacaw_grid& g, int n_t, int n_atoms, const float* pos_ho
         if (rc) break;
         e = cudaEventRecord(freed[slot], st);
         if (e != cudaSuccess) break;
-        rc = multislice_run(g, nb, w.V, nullptr, w.psi + (size_t)t0 * nq, w.psi_sum, w.ws_ms, st, ms_flags);
+        if (ms_flags & TACAW_MS_QUEUE) {
+            tacaw_job job;
+            job.grid = g;
+            job.n_t = nb;
+            job.V = w.V;
+            job.psi_in = nullptr;
+            job.psi_q = w.psi + (size_t)t0 * nq;
+            job.psi_sum = w.psi_sum;
+            rc = multislice_queue_run(&job, 1, 0, 0, w.ws_ms, st);
+        } else {
+            rc = multislice_run(g, nb, w.V, nullptr, w.psi + (size_t)t0 * nq, w.psi_sum, w.ws_ms, st, ms_flags);
+        }
     }
     if (rc == TACAW_OK && e == cudaSuccess)
         rc = spectrum_run((int)nq, n_t, dt_fs, n_t, nullptr, w.psi, nq, w.psi_sum, w.I, w.I_el, precision, flags,

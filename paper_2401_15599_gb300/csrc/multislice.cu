@@ -1490,7 +1490,7 @@ int multislice_batch_run(const tacaw_job* jobs, int n_jobs, void* ws, cudaStream
 namespace {
 
 constexpr uint32_t kQueueWaitPolls = 1u << 22;   // a few seconds per dependency wait
-constexpr double kQueueWaveBytes = 64.0 * 1024 * 1024;   // default: waves of about 64 MiB of waves in L2
+constexpr double kQueueWaveBytes = 128.0 * 1024 * 1024;  // default wave: about 128 MiB of exit waves
 
 // The span for grid size n: the requested one where valid, else the default.
 int queue_span(int n, int want) {

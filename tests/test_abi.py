@@ -164,3 +164,15 @@ def test_queue_arguments_and_workspace(lib):
     assert lib.tacaw_multislice_queue(arr, 1, -1, 0, fake, big, null) == L.TACAW_EINVAL
     arr = (L.TacawJob * 1)(L.TacawJob(g, 4, None, None, fake, None))
     assert lib.tacaw_multislice_queue(arr, 1, 0, 0, fake, big, null) == L.TACAW_EINVAL
+
+
+def test_queue_workspace_query_takes_any_pointer(lib):
+    """The workspace query answers before the arrays are checked (callers
+    query with placeholder pointers); a real call checks their alignment."""
+    g = L.make_grid(O.Grid(256, 256, 38.4, 38.4, 3, 2.0, 0.0, 200.0, 2.0 / 3.0))
+    arr = (L.TacawJob * 1)(L.TacawJob(g, 8, 1, None, 1, None))
+    n = ctypes.c_size_t(0)
+    assert lib.tacaw_multislice_queue(arr, 1, 0, 0, None, ctypes.byref(n), None) == L.TACAW_OK and n.value > 0
+    big = ctypes.byref(ctypes.c_size_t(1 << 40))
+    assert lib.tacaw_multislice_queue(arr, 1, 0, 0, ctypes.c_void_p(1 << 20), big, None) == L.TACAW_EINVAL
+    assert b"16-byte aligned" in lib.tacaw_last_error()

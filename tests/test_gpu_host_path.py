@@ -51,3 +51,19 @@ def test_host_path_matches_device_pipeline_and_oracle(api, precision):
     ref, ref_e, _ = O.spectrum(psi, w.dt_fs)
     assert np.linalg.norm(out.numpy() - ref) / np.linalg.norm(ref) < 2e-5
     assert np.linalg.norm(out_el.numpy() - ref_e) / np.linalg.norm(ref_e) < 1e-6
+
+
+def test_host_path_with_the_work_queue(api):
+    """ms_flags = TACAW_MS_QUEUE: the one-call path runs each batch through the
+    work-queue multislice; the spectrum equals the per-slice path's bit for bit."""
+    from paper_2401_15599_gb300 import _lib as L
+    w = W.WORKLOADS["plain_small"].with_(n_t=64)
+    inp = W.build_inputs(w)
+    pos = torch.from_numpy(inp.positions())
+    sp = torch.from_numpy(inp.species).cuda()
+    a, a_el = api.time_to_spectrum_host(w.grid, pos, sp, inp.amp_sigma, w.dt_fs, 24, precision="fft32")
+    b, b_el = api.time_to_spectrum_host(w.grid, pos, sp, inp.amp_sigma, w.dt_fs, 24, ms_flags=L.TACAW_MS_QUEUE,
+                                        precision="fft32")
+    torch.cuda.synchronize()
+    api.status()
+    assert torch.equal(a, b) and torch.equal(a_el, b_el)

@@ -47,7 +47,7 @@ def _incident(rng, n):
 @pytest.mark.parametrize("n,n_slices,n_t,wave,span,with_psi_in", [
     (256, 4, 13, 4, 8, False),     # waves of 4, 4, 4 and 1 snapshots; items of one 8-row tile
     (512, 3, 20, 8, 0, True),      # 32 row and 32 column items per snapshot and slice
-    (512, 2, 40, 0, 64, False),    # default wave (32 at 512^2): a full and a partial wave; 8 items per pass
+    (512, 2, 80, 0, 64, False),    # default wave (64 at 512^2): a full and a partial wave; 8 items per pass
     (64, 5, 33, 7, 0, True),
     (1024, 2, 3, 2, 32, False),
 ])
