@@ -730,7 +730,7 @@ def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=64):
             "value_graph": units / (graph_ms * 1e-3), "unit": UNIT}
 
 
-def full_batched_jobs(stream, graph=True, max_jobs=64, max_snapshots=None, v_budget=48e9, max_window=512):
+def full_batched_jobs(stream, graph=True, max_jobs=64, max_snapshots=None, v_budget=120e9, max_window=512):
     """The batched configuration as stated: the 64 seeded uneven jobs (seeds
     1000-1063; grids 128-768, 10-150 slices, 512-4096 snapshots, 1-3 species)
     through the time-chunked batched driver, one group per grid size (so one
