@@ -1568,22 +1568,27 @@ __device__ __forceinline__ float col_dist2(const CandSmem& sm, const PotParams& 
 // Adjoint of the potential for the per-species Gaussian parameters: with
 // P = exp(-rho^2 / 2 s^2) inside the cut-off and g = dL/dv,
 //   dL/d amp += g P w,   dL/d s += g amp P (rho^2 / s^3 w + dw/ds).
-// Each lane sums its contributions per candidate, the warp reduces them and
-// adds to per-species FP64 block totals; every block writes its totals to
-// `partial` [block][n_species][2] for a fixed-order final reduction.
+// Each lane sums its contributions per candidate, the warp reduces them, and
+// lane 0 adds the candidate's two terms (FP32 products, amp applied at the
+// end) into its warp's per-species sums in shared memory, compensated
+// (Kahan) so that they carry FP32 rounding per term only, not per addition.
+// At the end the block adds its warps' sums in FP64 in warp order and writes
+// its totals to `partial` [block][n_species][2] for a fixed-order final
+// reduction.
 template <int CPL>
 __global__ void __launch_bounds__(kPotThreads)
 potential_backward_kernel(const int* __restrict__ bin_off, const float4* __restrict__ binned,
                           const int2* __restrict__ binned_px, PotParams p, const float* __restrict__ dV,
                           double* __restrict__ partial) {
     __shared__ CandSmem sm;
-    __shared__ double tot[TACAW_MAX_SPECIES][2];
+    __shared__ float wsum[kPotThreads / 32][TACAW_MAX_SPECIES][2][2];   // per warp: (sum, compensation)
     extern __shared__ float gtile[];                // [kBandRows][nx]: dL/dv of the band
     const Tile tl = make_tile(p);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* atoms = binned + tl.t * (size_t)p.n_atoms;
     const int2* atoms_px = binned_px + tl.t * (size_t)p.n_atoms;
-    if (threadIdx.x < 2 * TACAW_MAX_SPECIES) tot[threadIdx.x / 2][threadIdx.x % 2] = 0.0;
+    for (int i = threadIdx.x; i < (kPotThreads / 32) * TACAW_MAX_SPECIES * 4; i += blockDim.x)
+        (&wsum[0][0][0][0])[i] = 0.f;
     const float* grow = dV + ((tl.t * p.n_slices + tl.s) * (size_t)p.ny + tl.r0) * p.nx;
     for (int i = threadIdx.x; i < tl.nrows * p.nx; i += blockDim.x)
         gtile[i] = __ldg(grow + i);
@@ -1628,17 +1633,28 @@ potential_backward_kernel(const int* __restrict__ bin_off, const float4* __restr
                 gs += __shfl_xor_sync(0xffffffffu, gs, o);
             }
             if (lane == 0) {
-                atomicAdd(&tot[sp][0], (double)ga * (double)w);
-                atomicAdd(&tot[sp][1], (double)p.amp[sp] * ((double)gs * (double)w * (double)inv_s3 +
-                                                            (double)ga * (double)dw));
+                const float term[2] = {ga * w, fmaf(gs * w, inv_s3, ga * dw)};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {           // compensated running sums
+                    float* acc = wsum[warp][sp][q];
+                    const float y = term[q] - acc[1];
+                    const float tsum = acc[0] + y;
+                    acc[1] = (tsum - acc[0]) - y;
+                    acc[0] = tsum;
+                }
             }
         }
         __syncthreads();
     }
     __syncthreads();
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    if (threadIdx.x < 2 * p.n_species)
-        partial[blk * 2 * p.n_species + threadIdx.x] = tot[threadIdx.x / 2][threadIdx.x % 2];
+    if (threadIdx.x < 2 * p.n_species) {
+        const int sp = threadIdx.x / 2, q = threadIdx.x % 2;
+        double total = 0.0;
+        for (int wi = 0; wi < kPotThreads / 32; ++wi)
+            total += (double)wsum[wi][sp][q][0] - (double)wsum[wi][sp][q][1];
+        partial[blk * 2 * p.n_species + threadIdx.x] = q == 0 ? total : (double)p.amp[sp] * total;
+    }
 }
 
 // out[i] = sum over blocks of partial[block][i], fixed order (one block per i).
