@@ -55,7 +55,7 @@ constexpr int EPI_WARPS = 4;                   // warps 0-3: TMEM lanes 0-127, t
 constexpr int LOAD_WARP = 4, MMA_WARP = 5;
 constexpr int TC_THREADS = 6 * 32;
 constexpr int GROUP_N = 8;                     // N tiles sharing an L2 panel of B'
-constexpr int CHUNK = 2;                       // K blocks summed in TMEM before the FP32 drain
+constexpr int CHUNK = 8;                       // K blocks summed in TMEM before the FP32 drain
 constexpr uint32_t TMEM_COLS = 4 * TN;         // two buffers x (big, small) accumulators
 
 template <int NT>                              // BF16 terms per operand: 2 or 3
