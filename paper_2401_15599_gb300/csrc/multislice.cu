@@ -990,6 +990,9 @@ struct QJobs {
     const int* kymax[kQMaxJobs];
     int n_t[kQMaxJobs], n_slices[kQMaxJobs];
     float sigma[kQMaxJobs];
+    // per job: the exit waves as a 2-D array of 8-byte elements [n_t * N][N], boxes of
+    // (ROWS columns) x (qbox rows) for the column tiles
+    alignas(64) CUtensorMap cmap[kQMaxJobs];
 };
 
 struct QItem {
@@ -1042,18 +1045,6 @@ __device__ bool q_wait(const int* ctr, int need, int* abort_word, int* err, uint
     return false;
 }
 
-__device__ __forceinline__ void cp_async_cg16(void* smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                     static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait_pending() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
-}
-
 // A tile's stage: ROWS slots of PL float2 (row tile: the rows of psi at their
 // natural positions, then the padded exchanges in place; column tile: the
 // ROWS x N columns densely as [row][column], then the padded exchanges in
@@ -1065,55 +1056,62 @@ struct QStage {
     static constexpr int NST = (2 * F2 + fft::TwSize<N>::value) * (int)sizeof(float2) <= 100 * 1024 ? 2 : 1;
 };
 
-// Starts the copies of tile ti of item q into a stage (cp.async through L2
-// only, so no block sees an old copy of another block's results): a row tile
-// takes its rows of psi (the kept columns, from the second slice on) and of
-// v_s, a column tile its ROWS columns (nothing for a tile the band limit
-// drops).  All threads; 16-byte aligned arrays.
+// Rows of the column tiles' TMA boxes (at most 256 per box; N / qbox boxes per tile).
 template <int N>
-__device__ __forceinline__ void q_issue(const QJobs& jobs, const QItem& q, int ti, float2* stage) {
+struct QBox {
+    static constexpr int ROWS = N <= 256 ? N : (N % 256 == 0 ? 256 : N / 2);
+    static constexpr int COUNT = N / ROWS;
+    static_assert(ROWS <= 256 && N % ROWS == 0, "column-tile boxes");
+};
+
+// Thread 0: starts the asynchronous copies of tile ti of item q into a stage,
+// completing on the stage's mbarrier: a row tile takes its rows of psi (the
+// kept columns, from the second slice on; bulk copies of the two kept ranges of
+// each row) and of v_s (one bulk copy), a column tile its ROWS columns (TMA
+// boxes of the job's map); a tile the band limit drops arrives without bytes.
+// The inputs were written by other blocks with ordinary stores and acquired
+// through their counters, and the stage was last used by ordinary accesses:
+// proxy fences order both before the copies.  16-byte aligned arrays.
+template <int N>
+__device__ __forceinline__ void q_issue(const QJobs& jobs, const QItem& q, int ti, float2* stage, uint64_t* bar) {
     using C = QCfg<N>;
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    fence_proxy_async_smem();
     const float2* snap = jobs.psi[q.job] + (size_t)q.t * N * N;
     const int K = __ldg(jobs.kymax[q.job] + N);
     if (q.pass == 0) {
         const int y0 = q.tile * jobs.span + ti * C::ROWS;
+        int a = K + 1;                                   // kept columns [0, a) and [b, N), both ends even
+        a += a & 1;
+        if (a > N) a = N;
+        int b = N - K;
+        b -= b & 1;
+        if (b < a) b = a;
+        constexpr uint32_t V_BYTES = C::ROWS * N * (uint32_t)sizeof(float);
+        const uint32_t psi_bytes = q.s > 0 ? (uint32_t)(C::ROWS * (a + N - b) * (int)sizeof(float2)) : 0u;
+        tc::mbar_arrive_expect_tx(bar, psi_bytes + V_BYTES);
         if (q.s > 0) {
-            int a = K + 1;                               // kept columns [0, a) and [b, N), both ends even
-            a += a & 1;
-            if (a > N) a = N;
-            int b = N - K;
-            b -= b & 1;
-            if (b < a) b = a;
             const float2* rows = snap + (size_t)y0 * N;
-            constexpr int CH = C::ROWS * (N / 2), REP = (CH + kQThreads - 1) / kQThreads;
-#pragma unroll
-            for (int j = 0; j < REP; ++j) {
-                const int i = threadIdx.x + j * kQThreads;
-                const int r = i / (N / 2), c2 = (i % (N / 2)) * 2;
-                if ((CH % kQThreads == 0 || i < CH) && (c2 < a || c2 >= b))
-                    cp_async_cg16(stage + r * C::PL + c2, rows + r * N + c2);
+            for (int r = 0; r < C::ROWS; ++r) {
+                if (a > 0) bulk_copy_g2s(stage + r * C::PL, rows + (size_t)r * N, a * (uint32_t)sizeof(float2), bar);
+                if (b < N)
+                    bulk_copy_g2s(stage + r * C::PL + b, rows + (size_t)r * N + b, (N - b) * (uint32_t)sizeof(float2),
+                                  bar);
             }
         }
         const float* Vs = jobs.V[q.job] + (((size_t)q.t * jobs.n_slices[q.job] + q.s) * N + y0) * N;
-        float* vst = reinterpret_cast<float*>(stage + QStage<N>::PSI);
-        constexpr int VCH = C::ROWS * N / 4, VREP = (VCH + kQThreads - 1) / kQThreads;
-#pragma unroll
-        for (int j = 0; j < VREP; ++j) {
-            const int i = threadIdx.x + j * kQThreads;
-            if (VCH % kQThreads == 0 || i < VCH) cp_async_cg16(vst + 4 * i, Vs + 4 * i);
-        }
+        bulk_copy_g2s(stage + QStage<N>::PSI, Vs, V_BYTES, bar);
     } else {
         const int kx0 = q.tile * jobs.span + ti * C::ROWS;
-        if (kx0 > K && kx0 + C::ROWS - 1 < N - K) return;
-        constexpr int CH = C::ROWS / 2;                  // 16-byte chunks per row of the tile
-        constexpr int ALL = N * CH, REP = (ALL + kQThreads - 1) / kQThreads;
-        const float2* cols = snap + kx0;
-#pragma unroll
-        for (int j = 0; j < REP; ++j) {
-            const int i = threadIdx.x + j * kQThreads;
-            const int r = i / CH, h = i % CH;
-            if (ALL % kQThreads == 0 || i < ALL) cp_async_cg16(stage + r * C::ROWS + 2 * h, cols + r * N + 2 * h);
+        if (kx0 > K && kx0 + C::ROWS - 1 < N - K) {
+            tc::mbar_arrive(bar);
+            return;
         }
+        tc::mbar_arrive_expect_tx(bar, (uint32_t)(N * C::ROWS * (int)sizeof(float2)));
+#pragma unroll
+        for (int k = 0; k < QBox<N>::COUNT; ++k)
+            tc::tma_load_2d(stage + k * QBox<N>::ROWS * C::ROWS, &jobs.cmap[q.job], bar, kx0,
+                            q.t * N + k * QBox<N>::ROWS);
     }
 }
 
@@ -1207,21 +1205,26 @@ __device__ __forceinline__ bool q_wait_ready(const QJobs& jobs, const QItem& q, 
 
 // ctl (8-byte aligned): [0, 1] 64-bit queue head, [2] abort word, [3] unused;
 // then row_done[U], col_done[U].  All zero before the launch.
-// Each block walks its tiles through a ring of QStage<N>::NST stages: while
-// tile k is transformed, the copies of tile k + 1 (the next tile of the same
-// item, or the first of the block's next item once that item's inputs are
-// final) are in flight.  Thread 0 takes items from the queue, decodes them and
-// plans the tile after next while the block transforms; two barriers per
-// tile: the arrival of the tile's copies, and the end of its use of the stage
-// (which also publishes the plan).
+// Each block walks its tiles through a ring of QStage<N>::NST stages, each
+// with an mbarrier: while tile k is transformed, the copies of tile k + 1 (the
+// next tile of the same item, or the first of the block's next item once that
+// item's inputs are final) are in flight.  Thread 0 takes items from the
+// queue, decodes them, plans the tile after next and issues the copies; every
+// thread waits on the stage's mbarrier (bounded: a wait that gives up sets the
+// status flag and the abort word, and the block drains its copies and leaves).
+// Two barriers per tile: after the wait (a thread that gave up tells the
+// others), and at the end of the tile's use of the stage (which also
+// publishes the plan).  Lane 0 of warp 1 releases finished items, so that the
+// release's fence does not hold up the next copies.
 template <int N>
 __global__ void __launch_bounds__(kQThreads, QCfg<N>::MIN_BLOCKS)
 ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ tw_g, int* __restrict__ ctl,
                 int* __restrict__ err, uint32_t polls) {
     using C = QCfg<N>;
     constexpr int NST = QStage<N>::NST;
-    extern __shared__ __align__(16) float2 qsm[];
+    extern __shared__ __align__(128) float2 qsm[];
     float2* tw = qsm + NST * QStage<N>::F2;
+    __shared__ __align__(8) uint64_t bars[2];
     // written by thread 0, read by all threads between two barriers: the first item; the plan of
     // the next tile (item, tile in item, 0 ready / 1 inputs not final yet / 2 none); the verdict of
     // a blocking wait
@@ -1234,9 +1237,14 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
     int* col_done = ctl + 4 + U;
     const long long total = jobs.item0[jobs.n];
     const int tiles = jobs.span / C::ROWS;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::fence_mbar_init();
+    }
     stage_twiddles<N>(tw, tw_g);
     const int tr = threadIdx.x % C::TPT, row = threadIdx.x / C::TPT;     // row tiles
-    const int cc = threadIdx.x % C::ROWS, tc = threadIdx.x / C::ROWS;     // column tiles
+    const int cc = threadIdx.x % C::ROWS, tc_ = threadIdx.x / C::ROWS;    // column tiles
     // thread 0: the block's next item, taken when the tile before the last of the current item is
     // planned (with the current item when items are one tile), so that few items are taken but
     // not started and the queue's latency hides behind a tile
@@ -1280,25 +1288,37 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
     if (!s_first_ok) return;
     QItem q = s_first;
     int ti = 0, st = 0;
-    q_issue<N>(jobs, q, 0, qsm);
-    cp_async_commit_group();
-    if (threadIdx.x == 0) plan(q, 0);
+    uint32_t uses[2] = {0u, 0u};                    // completed phases of each stage's mbarrier
+    bool pending[2] = {true, false};                // a phase of the stage is in flight (thread 0 view)
+    if (threadIdx.x == 0) {
+        q_issue<N>(jobs, q, 0, qsm, &bars[0]);
+        plan(q, 0);
+    }
     __syncthreads();
+    bool failed = false;
     for (;;) {
         const int flag = s_next_flag;
         const int nti = s_next_ti;
         const QItem qn = flag == 2 ? q : s_next;
+        const int st_next = st ^ (NST - 1);
         float2* cur_stage = qsm + st * QStage<N>::F2;
-        float2* nxt_stage = qsm + (st ^ (NST - 1)) * QStage<N>::F2;
+        float2* nxt_stage = qsm + st_next * QStage<N>::F2;
         const bool early = NST == 2 && flag == 0;
-        if (early) {
-            q_issue<N>(jobs, qn, nti, nxt_stage);
-            cp_async_commit_group();
-            cp_async_wait_pending<1>();
-        } else {
-            cp_async_wait_pending<0>();
+        if (early && threadIdx.x == 0) {
+            q_issue<N>(jobs, qn, nti, nxt_stage, &bars[st_next]);
+            pending[st_next] = true;
         }
-        __syncthreads();                            // this tile's copies have landed; the plan is read
+        const bool ok = tc::mbar_wait_quiet(&bars[st], uses[st] & 1u, polls);
+        if (__syncthreads_or(!ok)) {                // this tile's copies never arrived
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                atomicExch(abort_word, 1);
+            }
+            failed = true;
+            break;
+        }
+        ++uses[st];
+        if (threadIdx.x == 0) pending[st] = false;
         const int S = jobs.n_slices[q.job];
         float2* snap = jobs.psi[q.job] + (size_t)q.t * N * N;
         const int K = __ldg(jobs.kymax[q.job] + N);
@@ -1310,28 +1330,37 @@ ms_queue_kernel(const __grid_constant__ QJobs jobs, const float2* __restrict__ t
                           tw, tr, row);
         } else {
             q_col_tile<N>(cur_stage, snap, q.tile * jobs.span + ti * C::ROWS, jobs.px[q.job], jobs.py[q.job],
-                          jobs.kymax[q.job], K, q.s + 1 == S, tw, tc, cc);
+                          jobs.kymax[q.job], K, q.s + 1 == S, tw, tc_, cc);
         }
         if (threadIdx.x == 0 && flag != 2) plan(qn, nti);
         __syncthreads();                            // the stage is free; the tile's stores are issued
-        if (ti + 1 == tiles && threadIdx.x == 0) {  // the item is done: release it
+        if (ti + 1 == tiles && threadIdx.x == 32) { // the item is done: warp 1 releases it while thread 0
+            asm volatile("fence.proxy.async.global;" ::: "memory");   // goes on to the next copies
             __threadfence();
             atomicAdd((q.pass == 0 ? row_done : col_done) + jobs.snap0[q.job] + q.t, 1);
         }
         if (flag == 2) break;
         if (!early) {                               // inputs not final yet, or one stage: wait, then copy
-            if (threadIdx.x == 0)
+            if (threadIdx.x == 0) {
                 s_ok = flag == 0 || q_wait_ready(jobs, qn, row_done, col_done, abort_word, err, polls);
+                if (s_ok) {
+                    q_issue<N>(jobs, qn, nti, nxt_stage, &bars[st_next]);
+                    pending[st_next] = true;
+                }
+            }
             __syncthreads();
             if (!s_ok) break;
-            q_issue<N>(jobs, qn, nti, nxt_stage);
-            cp_async_commit_group();
         }
         q = qn;
         ti = nti;
-        st ^= NST - 1;
+        st = st_next;
     }
-    cp_async_wait_pending<0>();
+    if (failed && threadIdx.x == 0) {               // copies still in flight land before the block leaves
+        for (int k = 0; k < 2; ++k)
+            if (pending[k])
+                for (int i = 0; i < 64 && !tc::mbar_wait_quiet(&bars[k], uses[k] & 1u, 1u << 20); ++i) {
+                }
+    }
 }
 
 }  // namespace
@@ -1492,6 +1521,20 @@ namespace {
 constexpr uint32_t kQueueWaitPolls = 1u << 22;   // a few seconds per dependency wait
 constexpr double kQueueWaveBytes = 128.0 * 1024 * 1024;  // default wave: about 128 MiB of exit waves
 
+// Columns of a column tile and rows of its TMA boxes, for grid size n.
+void queue_tile_dims(int n, int* cols, int* box_rows) {
+    switch (n) {
+        case 64: *cols = QCfg<64>::ROWS; *box_rows = QBox<64>::ROWS; return;
+        case 128: *cols = QCfg<128>::ROWS; *box_rows = QBox<128>::ROWS; return;
+        case 256: *cols = QCfg<256>::ROWS; *box_rows = QBox<256>::ROWS; return;
+        case 384: *cols = QCfg<384>::ROWS; *box_rows = QBox<384>::ROWS; return;
+        case 512: *cols = QCfg<512>::ROWS; *box_rows = QBox<512>::ROWS; return;
+        case 768: *cols = QCfg<768>::ROWS; *box_rows = QBox<768>::ROWS; return;
+        case 1024: *cols = QCfg<1024>::ROWS; *box_rows = QBox<1024>::ROWS; return;
+    }
+    *cols = *box_rows = 0;
+}
+
 // The span for grid size n: the requested one where valid, else the default.
 int queue_span(int n, int want) {
     switch (n) {
@@ -1570,6 +1613,8 @@ int multislice_queue_run(const tacaw_job* jobs, int n_jobs, int wave, int span, 
         if (used[j0] || jobs[j0].n_t <= 0 || jobs[j0].grid.n_slices <= 0) continue;
         const int n = jobs[j0].grid.nx;
         const int sp = queue_span(n, span);
+        int tile_cols = 0, box_rows = 0;
+        queue_tile_dims(n, &tile_cols, &box_rows);
         const int items = n / sp;
         int wv = wave;
         if (wv <= 0) {
@@ -1602,6 +1647,9 @@ int multislice_queue_run(const tacaw_job* jobs, int n_jobs, int wave, int span, 
                 q.n_t[k] = b.n_t;
                 q.n_slices[k] = b.grid.n_slices;
                 q.sigma[k] = sigma[j];
+                TACAW_REQUIRE(encode_wave_map(&q.cmap[k], b.psi_q, n, (long long)b.n_t * n, tile_cols, box_rows),
+                              TACAW_ECUDA, "tacaw_multislice_queue: job %d: tensor map of the exit waves not encoded",
+                              j);
                 const long long job_items = (long long)b.grid.n_slices * 2 * items * b.n_t;
                 TACAW_REQUIRE(job_items < (1LL << 31), TACAW_EINVAL,
                               "tacaw_multislice_queue: job %d has %lld queue items (at most 2^31 - 1)", j, job_items);
