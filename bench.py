@@ -678,8 +678,8 @@ def batched_queue_vs_launches(reps, stream, n_jobs=16, snapshots=24):
     jobs: grids 128-768, 10-150 slices; `snapshots` snapshots each, random slice
     potentials) through tacaw_multislice_batch (two launches per slice and grid
     size) and through tacaw_multislice_queue (one persistent launch per grid
-    size over the device work queue), on the same buffers; the exit waves must
-    agree bit for bit."""
+    size over the device work queue, items of 32 rows or columns as the batched
+    driver uses), on the same buffers; the exit waves must agree bit for bit."""
     import torch
     import workloads as W
     from paper_2401_15599_gb300 import api
@@ -695,8 +695,8 @@ def batched_queue_vs_launches(reps, stream, n_jobs=16, snapshots=24):
     api.multislice_batch(jobs)                           # warm-up (workspace, kernel attributes)
     launches_ms = _events_ms(lambda: api.multislice_batch(jobs), reps, stream)
     ref = [j["out"].clone() for j in jobs]
-    api.multislice_batch(jobs, queue=True)
-    queue_ms = _events_ms(lambda: api.multislice_batch(jobs, queue=True), reps, stream)
+    api.multislice_batch(jobs, queue=True, span=32)
+    queue_ms = _events_ms(lambda: api.multislice_batch(jobs, queue=True, span=32), reps, stream)
     api.status()
     same = all(torch.equal(j["out"], r) for j, r in zip(jobs, ref))
     del jobs, ref
