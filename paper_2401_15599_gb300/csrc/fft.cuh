@@ -22,6 +22,8 @@
 // inverse transform uses their conjugates and is unnormalised.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tacaw {
@@ -198,10 +200,20 @@ struct IsPadded { static constexpr bool value = false; };
 template <class L>
 struct IsPadded<L, decltype(void(L::kPadded))> { static constexpr bool value = L::kPadded; };
 
+// Twiddles of a plan's last stage held in registers by a thread that owns one
+// butterfly there (E == R): w[r - 1] = W_{NS R}^{jm r}, the table's entries
+// for its jm, loaded once (load_last) by a persistent kernel that runs many
+// transforms with the same thread layout.  NoRegTw: every stage reads the table.
+template <int R>
+struct RegTw { float2 w[R - 1]; };
+struct NoRegTw {};
+
 // Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
-template <int N, int E, int R, int NS, int OFF, bool INV>
-__device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw) {
+template <int N, int E, int R, int NS, int OFF, bool INV, class RT = NoRegTw>
+__device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw, const RT& rt = RT{}) {
     constexpr int TPT = N / E;
+    constexpr bool kReg = !std::is_same<RT, NoRegTw>::value;
+    static_assert(!kReg || (E == R && std::is_same<RT, RegTw<R>>::value), "register twiddles: one butterfly");
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         float2* x = v + b * R;
@@ -210,7 +222,9 @@ __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw) {
             const int jm = j % NS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[OFF + (r - 1) * NS + jm];
+                float2 w;
+                if constexpr (kReg) w = rt.w[r - 1];
+                else w = tw[OFF + (r - 1) * NS + jm];
                 if (INV) w.y = -w.y;
                 x[r] = cmul(x[r], w);
             }
@@ -300,29 +314,59 @@ struct WarpSync {
     __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
 
-template <int N, int E, bool INV, int NS, int OFF, class L, class S, int R, int... Rest>
+template <int N, int E, bool INV, int NS, int OFF, class L, class S, class RT, int R, int... Rest>
 __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
-                                           const float2* tw, L lay, S sync) {
-    stage<N, E, R, NS, OFF, INV>(v, t, tw);
+                                           const float2* tw, L lay, S sync, const RT& rt) {
     if constexpr (sizeof...(Rest) > 0) {
+        stage<N, E, R, NS, OFF, INV>(v, t, tw);
         constexpr int RN = First<Rest...>::value;
         constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
         if (b0 == b1) sync();            // one buffer: the previous exchange's reads come first
         write_out<N, E, R, NS>(v, b0, t, lay);
         sync();
         read_in<N, E, RN>(v, b0, t, lay);
-        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, Rest...>(v, b1, b0, t, tw, lay, sync);
+        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, RT, Rest...>(v, b1, b0, t, tw, lay, sync, rt);
     } else {
+        stage<N, E, R, NS, OFF, INV>(v, t, tw, rt);
         stage_to_canon<E, R>(v);
     }
 }
 
-template <int N, int E, bool INV, class L, class S, int R0, int... Rs>
+template <int N, int E, bool INV, class L, class S, class RT, int R0, int... Rs>
 __device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[E],
                                                float2* b0, float2* b1, int t, const float2* tw,
-                                               L lay, S sync) {
+                                               L lay, S sync, const RT& rt) {
     canon_to_stage<E, R0>(v);
-    run_stages<N, E, INV, 1, 0, L, S, R0, Rs...>(v, b0, b1, t, tw, lay, sync);
+    run_stages<N, E, INV, 1, 0, L, S, RT, R0, Rs...>(v, b0, b1, t, tw, lay, sync, rt);
+}
+
+// The last stage of radices Rs: its radix, NS and table offset.
+template <int NS, int OFF, int R, int... Rest>
+struct LastStageOf {
+    static constexpr int kNextOff = OFF + (NS > 1 ? (R - 1) * NS : 0);
+    using Next = LastStageOf<NS * R, kNextOff, Rest...>;
+    static constexpr int radix = Next::radix, ns = Next::ns, off = Next::off;
+};
+template <int NS, int OFF, int R>
+struct LastStageOf<NS, OFF, R> {
+    static constexpr int radix = R, ns = NS, off = OFF;
+};
+template <class Rs>
+struct LastStage;
+template <int... Rs>
+struct LastStage<Radices<Rs...>> : LastStageOf<1, 0, Rs...> {};
+
+// Load the last-stage twiddles of plan P for thread t (one butterfly, j = t)
+// from its table tw (shared memory).
+template <class P>
+__device__ __forceinline__ RegTw<LastStage<typename P::R>::radix> load_last(const float2* tw, int t) {
+    using LS = LastStage<typename P::R>;
+    static_assert(P::E == LS::radix && LS::ns > 1, "one last-stage butterfly per thread");
+    RegTw<LS::radix> rt;
+    const int jm = t % LS::ns;
+#pragma unroll
+    for (int r = 1; r < LS::radix; ++r) rt.w[r - 1] = tw[LS::off + (r - 1) * LS::ns + jm];
+    return rt;
 }
 
 // Size of the per-stage twiddle table of a plan.
@@ -365,23 +409,27 @@ __device__ void fill_twiddles(float2* tw, int tid, int nthr) {
 // number of times (it contains barriers: __syncthreads, or the named barrier
 // `sync` of the threads sharing the buffers).  tw: the plan's per-stage
 // twiddle table (TwSize<N> entries), normally staged in shared memory.
-// The leading barrier separates the last shared-memory reads of a previous
-// transform from the first writes of this one (plans with one exchange would
-// otherwise reuse a buffer without a barrier in between).
+// With two buffers a leading barrier separates the last shared-memory reads
+// of a previous transform from the first writes of this one (plans with one
+// exchange would otherwise reuse a buffer without a barrier in between).  With
+// one buffer (b0 == b1) every exchange already starts with a barrier before
+// its writes, and the first stage touches no shared memory but the twiddles
+// (read-only), so no leading barrier is needed.
 template <int N, bool INV, class L, class S = BlockSync>
 __device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, float2* b1, int t,
                                           const float2* tw, L lay, S sync = S{}) {
-    sync();
-    transform_impl<N, Plan<N>::E, INV, L, S>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync);
+    if (b0 != b1) sync();
+    transform_impl<N, Plan<N>::E, INV, L, S>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync, NoRegTw{});
 }
 
 // The same with an explicit plan P (P::E values per thread, radices P::R; its
 // twiddle table is that of Plan<N> when the radices agree).
-template <class P, int N, bool INV, class L, class S>
+// rt: NoRegTw, or the last stage's twiddles from load_last<P>.
+template <class P, int N, bool INV, class L, class S, class RT = NoRegTw>
 __device__ __forceinline__ void transform_plan(float2 (&v)[P::E], float2* b0, float2* b1, int t,
-                                               const float2* tw, L lay, S sync) {
-    sync();
-    transform_impl<N, P::E, INV, L, S>(typename P::R{}, v, b0, b1, t, tw, lay, sync);
+                                               const float2* tw, L lay, S sync, const RT& rt = RT{}) {
+    if (b0 != b1) sync();
+    transform_impl<N, P::E, INV, L, S, RT>(typename P::R{}, v, b0, b1, t, tw, lay, sync, rt);
 }
 
 }  // namespace fft

@@ -233,8 +233,11 @@ row_pass_kernel(float2* __restrict__ psi, const float* __restrict__ V,
 // exchange buffer (one-buffer mode).  Same arithmetic as row_body, so the
 // results are identical.  The waits for a group's data give up after
 // `polls` polls: the block then sets the status flag *err, stops, and waits
-// (with a fixed long bound) for the copies it has issued into both stages,
-// so no copy lands in shared memory after the block has exited.
+// (with a fixed long bound) for the copy it is waiting on, so no copy lands in
+// shared memory after the block has exited.  A group's copy is issued once
+// every thread has passed the wait of the group before (the barrier after that
+// wait), when the stage it refills is free, so at most one copy is in flight
+// at a wait and a group ends without a barrier of its own.
 // The barrier of one row's transform threads: a named barrier per row when a
 // row spans several warps, the warp itself when it spans one or part of one.
 template <int TPT>
@@ -246,8 +249,14 @@ __device__ __forceinline__ auto row_sync_of(int row) {
 
 // P is the transform plan: Plan<NX> (for 512 points: 8 values per thread, two
 // warps per row) or WarpPlan<NX> (16 values per thread, one warp per row).
+// Blocks per SM the staged row pass's register budget targets: four for the
+// 8-value plans (their shared memory allows four), two for the 16- and
+// 24-value plans (at most 128 registers a thread).
+template <class P>
+struct RowStagedMinBlocks { static constexpr int value = P::E == 8 ? 4 : 2; };
+
 template <int NX, class P>
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowThreads, RowStagedMinBlocks<P>::value)
 row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, const float2* __restrict__ twx,
                        const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int n_groups,
                        int* __restrict__ err, uint32_t polls) {
@@ -279,6 +288,13 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     }
     stage_twiddles<NX>(tw, twx);
     __syncthreads();
+    // a thread owns one butterfly of the last stage (8-value plans of 64 and
+    // 512 points): its twiddles stay in registers for every group
+    using LS = LastStage<typename P::R>;
+    constexpr bool kRegLast = P::E == LS::radix && LS::ns > 1;
+    using RT = typename std::conditional<kRegLast, RegTw<LS::radix>, NoRegTw>::type;
+    RT rt{};
+    if constexpr (kRegLast) rt = load_last<P>(tw, threadIdx.x % TPT);
     auto issue = [&](int g, int st) {              // thread 0
         const int snap = g / groups_per_snap, y0 = (g % groups_per_snap) * ROWS;
         unsigned char* dst = stage_raw + st * STAGE;
@@ -297,17 +313,17 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     const int row = threadIdx.x / TPT;
     if (threadIdx.x == 0 && (int)blockIdx.x < n_groups) issue(blockIdx.x, 0);
     int it = 0;
-    bool timed_out = false, next_issued = false;   // at a timeout: copies in flight into st and st ^ 1
+    bool timed_out = false;                        // at a timeout: a copy in flight into stage it & 1
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++it) {
         const int st = it & 1;
-        const int gn = g + gridDim.x;
-        if (threadIdx.x == 0 && gn < n_groups) issue(gn, st ^ 1);
         const bool ok = tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, polls);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
-            next_issued = gn < n_groups;
             break;
         }
+        // every thread has left the previous group, so its stage takes the next copy
+        const int gn = g + gridDim.x;
+        if (threadIdx.x == 0 && gn < n_groups) issue(gn, st ^ 1);
         float2* buf = reinterpret_cast<float2*>(stage_raw + st * STAGE);
         const float* vrow = reinterpret_cast<const float*>(stage_raw + st * STAGE + PSI_BYTES) + row * NX;
         const PadRowLayout lay{row * PL};
@@ -316,31 +332,27 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
         for (int m = 0; m < E; ++m)
             v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * PL + t + TPT * m] : make_float2(0.f, 0.f);
         const auto row_sync = row_sync_of<TPT>(row);   // a row's transforms touch only its own row
-        transform_plan<P, NX, true>(v, buf, buf, t, tw, lay, row_sync);
+        transform_plan<P, NX, true>(v, buf, buf, t, tw, lay, row_sync, rt);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             float sn, cs;
             phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
             v[m] = cmul(v[m], make_float2(cs, sn));
         }
-        transform_plan<P, NX, false>(v, buf, buf, t, tw, lay, row_sync);
+        transform_plan<P, NX, false>(v, buf, buf, t, tw, lay, row_sync, rt);
         const int snap = g / groups_per_snap, y = (g % groups_per_snap) * ROWS + row;
         float2* rowp = psi + ((size_t)snap * ny + y) * NX;
 #pragma unroll
         for (int m = 0; m < E; ++m)
             if (kept_column(t + TPT * m, NX, K)) rowp[t + TPT * m] = v[m];
-        __syncthreads();                           // this stage is refilled two groups later
     }
     if (timed_out && threadIdx.x == 0) {
         atomicExch(err, 1);
-        // drain: the copy into stage it & 1 (whose wait gave up) and, if issued,
-        // the one into the other stage; each completes once its bytes land
+        // drain: the copy into stage it & 1 (whose wait gave up; the next group's
+        // copy is issued only after that wait) completes once its bytes land
         const int st = it & 1;
         for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 20); ++k) {
         }
-        if (next_issued)
-            for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st ^ 1], ((it + 1) >> 1) & 1, 1u << 20); ++k) {
-            }
     }
 }
 
@@ -476,7 +488,8 @@ col_pass_kernel(float2* __restrict__ psi, const float2* __restrict__ twy,
 // row, which is the order in which a warp's 8 rows x W columns read it).  The
 // stage being transformed doubles as the exchange buffer.  Same arithmetic as
 // col_body, so the results are identical.  The waits give up after `polls`
-// polls like the staged row pass's (status flag, then a drain of both stages).
+// polls like the staged row pass's (status flag, then a drain of the stage
+// waited on; the next tile is issued after the barrier that follows a wait).
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::W * (NY / fft::Plan<NY>::E), ColCfg<NY>::kMinBlocks)
 col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restrict__ psi,
@@ -525,17 +538,17 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
     };
     if (threadIdx.x == 0 && (long long)blockIdx.x < n_items) issue(blockIdx.x, 0);
     int it = 0;
-    bool timed_out = false, next_issued = false;
+    bool timed_out = false;
     for (long long i = blockIdx.x; i < n_items; i += gridDim.x, ++it) {
         const int st = it & 1;
-        const long long inext = i + gridDim.x;
-        if (threadIdx.x == 0 && inext < n_items) issue(inext, st ^ 1);
         const bool ok = tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, polls);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
-            next_issued = inext < n_items;
             break;
         }
+        // every thread has left the previous item, so its stage takes the next tile
+        const long long inext = i + gridDim.x;
+        if (threadIdx.x == 0 && inext < n_items) issue(inext, st ^ 1);
         int snap;
         const int kb = item_block(i, &snap);
         const int kx = kb * W + c;
@@ -557,16 +570,12 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
         float2* col = psi + (size_t)snap * NY * nx + kx;
 #pragma unroll
         for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
-        __syncthreads();                                 // this stage is refilled two items later
     }
     if (timed_out && threadIdx.x == 0) {
         atomicExch(err, 1);
         const int st = it & 1;
         for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 20); ++k) {
         }
-        if (next_issued)
-            for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st ^ 1], ((it + 1) >> 1) & 1, 1u << 20); ++k) {
-            }
     }
 }
 
