@@ -522,6 +522,11 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
     }
     stage_twiddles<NY>(tw, twy);
     __syncthreads();
+    using LS = LastStage<typename Plan<NY>::R>;
+    constexpr bool kRegLast = Plan<NY>::E == LS::radix && LS::ns > 1;
+    using RT = typename std::conditional<kRegLast, RegTw<LS::radix>, NoRegTw>::type;
+    RT rt{};
+    if constexpr (kRegLast) rt = load_last<Plan<NY>>(tw, t);
     auto item_block = [&](long long i, int* snap) {
         *snap = (int)(i / n_kept);
         const int j = (int)(i % n_kept);
@@ -557,7 +562,7 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = buf[(t + TPT * m) * W + c];
-        transform<NY, false>(v, buf, buf, t, tw, lay);
+        transform_plan<Plan<NY>, NY, false>(v, buf, buf, t, tw, lay, BlockSync{}, rt);
         const float2 pxv = __ldg(px + kx);
         const int kmax = __ldg(kymax + kx);
 #pragma unroll
@@ -566,7 +571,7 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
             const int aky = ky < NY / 2 ? ky : NY - ky;
             v[m] = (aky <= kmax) ? cmul(v[m], cmul(pxv, __ldg(py + ky))) : make_float2(0.f, 0.f);
         }
-        if (!last) transform<NY, true>(v, buf, buf, t, tw, lay);
+        if (!last) transform_plan<Plan<NY>, NY, true>(v, buf, buf, t, tw, lay, BlockSync{}, rt);
         float2* col = psi + (size_t)snap * NY * nx + kx;
 #pragma unroll
         for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
