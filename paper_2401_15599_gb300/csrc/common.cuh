@@ -126,11 +126,23 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // exp(i x) = cos x + i sin x for the transmission phase sigma_e v.  The phase
-// is small in practice, so |x| <= 0.5 uses the Taylor series of sin to x^9
-// and of cos to x^10 (truncation below 2e-11, i.e. far under FP32 rounding),
-// evaluated by Horner's rule; larger phases fall back to sincosf.
+// is small in practice, so it uses truncated Taylor series evaluated by
+// Horner's rule: for |x| <= 0.25 sin to x^7 and cos to x^8, for |x| <= 0.5 sin
+// to x^9 and cos to x^10 (truncation below 2e-11 in both ranges, i.e. far
+// under FP32 rounding); larger phases fall back to sincosf.  The result for x
+// depends on x alone.
+__device__ __forceinline__ void phase_sincos_small(float x, float* s, float* c) {   // |x| <= 0.25
+    const float x2 = x * x;
+    const float ps = fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 5040.f, 1.f / 120.f), -1.f / 6.f), 1.f);
+    *s = x * ps;
+    *c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 40320.f, -1.f / 720.f), 1.f / 24.f), -0.5f), 1.f);
+}
+
 __device__ __forceinline__ void phase_sincos(float x, float* s, float* c) {
-    if (fabsf(x) <= 0.5f) {
+    const float ax = fabsf(x);
+    if (ax <= 0.25f) {
+        phase_sincos_small(x, s, c);
+    } else if (ax <= 0.5f) {
         const float x2 = x * x;
         const float ps = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f),
                                        -1.f / 6.f), 1.f);
@@ -139,6 +151,31 @@ __device__ __forceinline__ void phase_sincos(float x, float* s, float* c) {
                                         1.f / 24.f), -0.5f), 1.f);
     } else {
         sincosf(x, s, c);
+    }
+}
+
+// v[m] *= exp(i x[m]) for a thread's E values: one test of the largest phase
+// selects straight-line code when every phase is small (the same result for
+// each value as phase_sincos, which the other branch calls).
+template <int E>
+__device__ __forceinline__ void transmit(float2 (&v)[E], const float (&x)[E]) {
+    float mx = 0.f;
+#pragma unroll
+    for (int m = 0; m < E; ++m) mx = fmaxf(mx, fabsf(x[m]));
+    if (mx <= 0.25f) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            float sn, cs;
+            phase_sincos_small(x[m], &sn, &cs);
+            v[m] = cmul(v[m], make_float2(cs, sn));
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            float sn, cs;
+            phase_sincos(x[m], &sn, &cs);
+            v[m] = cmul(v[m], make_float2(cs, sn));
+        }
     }
 }
 

@@ -176,12 +176,10 @@ __device__ __forceinline__ void row_body(float2* __restrict__ rowp, const float*
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = inrow[t + TPT * m];
     }
+    float x[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        float sn, cs;
-        phase_sincos(sigma * __ldcs(vrow + t + TPT * m), &sn, &cs);
-        v[m] = cmul(v[m], make_float2(cs, sn));
-    }
+    for (int m = 0; m < E; ++m) x[m] = sigma * __ldcs(vrow + t + TPT * m);
+    transmit<E>(v, x);
     transform<NX, false>(v, b0, b1, t, tw, lay);
 #pragma unroll
     for (int m = 0; m < E; ++m)
@@ -333,12 +331,10 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
             v[m] = kept_column(t + TPT * m, NX, K) ? buf[row * PL + t + TPT * m] : make_float2(0.f, 0.f);
         const auto row_sync = row_sync_of<TPT>(row);   // a row's transforms touch only its own row
         transform_plan<P, NX, true>(v, buf, buf, t, tw, lay, row_sync, rt);
+        float x[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            float sn, cs;
-            phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
-            v[m] = cmul(v[m], make_float2(cs, sn));
-        }
+        for (int m = 0; m < E; ++m) x[m] = sigma * vrow[t + TPT * m];
+        transmit<E>(v, x);
         transform_plan<P, NX, false>(v, buf, buf, t, tw, lay, row_sync, rt);
         const int snap = g / groups_per_snap, y = (g % groups_per_snap) * ROWS + row;
         float2* rowp = psi + ((size_t)snap * ny + y) * NX;
@@ -1154,12 +1150,10 @@ __device__ __forceinline__ void q_row_tile(float2* stage, float2* __restrict__ r
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = __ldg(inrow + t + TPT * m);
     }
+    float x[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        float sn, cs;
-        phase_sincos(sigma * vrow[t + TPT * m], &sn, &cs);
-        v[m] = cmul(v[m], make_float2(cs, sn));
-    }
+    for (int m = 0; m < E; ++m) x[m] = sigma * vrow[t + TPT * m];
+    transmit<E>(v, x);
     transform_plan<Plan<N>, N, false>(v, stage, stage, t, tw, lay, sync);
 #pragma unroll
     for (int m = 0; m < E; ++m)
