@@ -200,20 +200,25 @@ struct IsPadded { static constexpr bool value = false; };
 template <class L>
 struct IsPadded<L, decltype(void(L::kPadded))> { static constexpr bool value = L::kPadded; };
 
-// Twiddles of a plan's last stage held in registers by a thread that owns one
-// butterfly there (E == R): w[r - 1] = W_{NS R}^{jm r}, the table's entries
-// for its jm, loaded once (load_last) by a persistent kernel that runs many
-// transforms with the same thread layout.  NoRegTw: every stage reads the table.
-template <int R>
-struct RegTw { float2 w[R - 1]; };
-struct NoRegTw {};
+// Twiddles of one stage (the one with NS_ = NS) held in registers by a thread
+// whose butterflies there all have the same jm (one butterfly, or TPT a
+// multiple of NS): w[r - 1] = W_{NS R}^{jm r}, the table's entries for its jm,
+// loaded once (load_reg_tw) by a persistent kernel that runs many transforms
+// with the same thread layout.  NoRegTw: every stage reads the table.
+template <int R, int NS_>
+struct RegTw {
+    static constexpr int kNS = NS_;
+    float2 w[R - 1];
+};
+struct NoRegTw { static constexpr int kNS = 0; };
 
 // Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
 template <int N, int E, int R, int NS, int OFF, bool INV, class RT = NoRegTw>
 __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw, const RT& rt = RT{}) {
     constexpr int TPT = N / E;
-    constexpr bool kReg = !std::is_same<RT, NoRegTw>::value;
-    static_assert(!kReg || (E == R && std::is_same<RT, RegTw<R>>::value), "register twiddles: one butterfly");
+    constexpr bool kReg = NS > 1 && RT::kNS == NS;
+    static_assert(!kReg || ((E == R || TPT % NS == 0) && std::is_same<RT, RegTw<R, NS>>::value),
+                  "register twiddles: one jm per thread in this stage");
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         float2* x = v + b * R;
@@ -318,7 +323,7 @@ template <int N, int E, bool INV, int NS, int OFF, class L, class S, class RT, i
 __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
                                            const float2* tw, L lay, S sync, const RT& rt) {
     if constexpr (sizeof...(Rest) > 0) {
-        stage<N, E, R, NS, OFF, INV>(v, t, tw);
+        stage<N, E, R, NS, OFF, INV>(v, t, tw, rt);
         constexpr int RN = First<Rest...>::value;
         constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
         if (b0 == b1) sync();            // one buffer: the previous exchange's reads come first
@@ -340,32 +345,49 @@ __device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[E
     run_stages<N, E, INV, 1, 0, L, S, RT, R0, Rs...>(v, b0, b1, t, tw, lay, sync, rt);
 }
 
-// The last stage of radices Rs: its radix, NS and table offset.
-template <int NS, int OFF, int R, int... Rest>
-struct LastStageOf {
+// The stage of radices Rs whose twiddles a thread of a plan with TPT threads
+// per transform can hold in registers: the last stage when a thread owns one
+// butterfly there (E == its radix), else the latest stage with NS > 1 whose NS
+// divides TPT (all of a thread's butterflies share jm); ns = 0 if none.
+template <int E, int TPT, int NS, int OFF, int R, int... Rest>
+struct RegStageOf {
     static constexpr int kNextOff = OFF + (NS > 1 ? (R - 1) * NS : 0);
-    using Next = LastStageOf<NS * R, kNextOff, Rest...>;
-    static constexpr int radix = Next::radix, ns = Next::ns, off = Next::off;
+    static constexpr bool kLast = sizeof...(Rest) == 0;
+    static constexpr bool kHere = NS > 1 && ((kLast && E == R) || TPT % NS == 0);
+    template <bool LAST, int Dummy = 0>
+    struct Later { static constexpr int radix = 0, ns = 0, off = 0; };
+    template <int Dummy>
+    struct Later<false, Dummy> : RegStageOf<E, TPT, NS * R, kNextOff, Rest...> {};
+    using L = Later<kLast>;
+    static constexpr bool kLater = L::ns > 0;
+    static constexpr int radix = kLater ? L::radix : (kHere ? R : 0);
+    static constexpr int ns = kLater ? L::ns : (kHere ? NS : 0);
+    static constexpr int off = kLater ? L::off : (kHere ? OFF : 0);
 };
-template <int NS, int OFF, int R>
-struct LastStageOf<NS, OFF, R> {
-    static constexpr int radix = R, ns = NS, off = OFF;
-};
-template <class Rs>
-struct LastStage;
-template <int... Rs>
-struct LastStage<Radices<Rs...>> : LastStageOf<1, 0, Rs...> {};
+// RegStage for a transform of N points by plan P (TPT = N / E threads).
+template <class P, int N, class Rs = typename P::R>
+struct RegStageN;
+template <class P, int N, int... Rs>
+struct RegStageN<P, N, Radices<Rs...>> : RegStageOf<P::E, N / P::E, 1, 0, Rs...> {};
 
-// Load the last-stage twiddles of plan P for thread t (one butterfly, j = t)
-// from its table tw (shared memory).
-template <class P>
-__device__ __forceinline__ RegTw<LastStage<typename P::R>::radix> load_last(const float2* tw, int t) {
-    using LS = LastStage<typename P::R>;
-    static_assert(P::E == LS::radix && LS::ns > 1, "one last-stage butterfly per thread");
-    RegTw<LS::radix> rt;
-    const int jm = t % LS::ns;
+// Register twiddles type of plan P at N points (NoRegTw when no stage qualifies).
+template <class P, int N>
+using RegTwOf = typename std::conditional<(RegStageN<P, N>::ns > 0),
+                                          RegTw<(RegStageN<P, N>::radix > 1 ? RegStageN<P, N>::radix : 2),
+                                                RegStageN<P, N>::ns>,
+                                          NoRegTw>::type;
+
+// Load the register twiddles of plan P (N points) for thread t from its table
+// tw (shared memory); an empty NoRegTw when no stage qualifies.
+template <class P, int N>
+__device__ __forceinline__ RegTwOf<P, N> load_reg_tw(const float2* tw, int t) {
+    using RS = RegStageN<P, N>;
+    RegTwOf<P, N> rt{};
+    if constexpr (RS::ns > 0) {
+        const int jm = t % RS::ns;
 #pragma unroll
-    for (int r = 1; r < LS::radix; ++r) rt.w[r - 1] = tw[LS::off + (r - 1) * LS::ns + jm];
+        for (int r = 1; r < RS::radix; ++r) rt.w[r - 1] = tw[RS::off + (r - 1) * RS::ns + jm];
+    }
     return rt;
 }
 
@@ -424,7 +446,7 @@ __device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, f
 
 // The same with an explicit plan P (P::E values per thread, radices P::R; its
 // twiddle table is that of Plan<N> when the radices agree).
-// rt: NoRegTw, or the last stage's twiddles from load_last<P>.
+// rt: NoRegTw, or one stage's twiddles from load_reg_tw<P, N>.
 template <class P, int N, bool INV, class L, class S, class RT = NoRegTw>
 __device__ __forceinline__ void transform_plan(float2 (&v)[P::E], float2* b0, float2* b1, int t,
                                                const float2* tw, L lay, S sync, const RT& rt = RT{}) {

@@ -286,13 +286,12 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     }
     stage_twiddles<NX>(tw, twx);
     __syncthreads();
-    // a thread owns one butterfly of the last stage (8-value plans of 64 and
-    // 512 points): its twiddles stay in registers for every group
-    using LS = LastStage<typename P::R>;
-    constexpr bool kRegLast = P::E == LS::radix && LS::ns > 1;
-    using RT = typename std::conditional<kRegLast, RegTw<LS::radix>, NoRegTw>::type;
+    // the twiddles of one stage in which all of a thread's butterflies share
+    // jm stay in registers for every group (plans of 8 or 16 values; the
+    // 24-value plans have no registers to spare)
+    using RT = typename std::conditional<(P::E <= 16), RegTwOf<P, NX>, NoRegTw>::type;
     RT rt{};
-    if constexpr (kRegLast) rt = load_last<P>(tw, threadIdx.x % TPT);
+    if constexpr (P::E <= 16) rt = load_reg_tw<P, NX>(tw, threadIdx.x % TPT);
     auto issue = [&](int g, int st) {              // thread 0
         const int snap = g / groups_per_snap, y0 = (g % groups_per_snap) * ROWS;
         unsigned char* dst = stage_raw + st * STAGE;
@@ -518,11 +517,7 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
     }
     stage_twiddles<NY>(tw, twy);
     __syncthreads();
-    using LS = LastStage<typename Plan<NY>::R>;
-    constexpr bool kRegLast = Plan<NY>::E == LS::radix && LS::ns > 1;
-    using RT = typename std::conditional<kRegLast, RegTw<LS::radix>, NoRegTw>::type;
-    RT rt{};
-    if constexpr (kRegLast) rt = load_last<Plan<NY>>(tw, t);
+    const RegTwOf<Plan<NY>, NY> rt = load_reg_tw<Plan<NY>, NY>(tw, t);
     auto item_block = [&](long long i, int* snap) {
         *snap = (int)(i / n_kept);
         const int j = (int)(i % n_kept);
