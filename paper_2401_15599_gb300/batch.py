@@ -3,11 +3,13 @@
 Each job has its own grid, slice count, snapshot count and atoms.  Snapshots
 are processed in windows: for every window the slice potentials of each job
 are built, then one multislice call advances all jobs together: with square
-grids ``tacaw_multislice_queue`` (one persistent launch per grid size over a
-device work queue, the default; items of 32 rows or columns, which on uneven
-jobs of 128-768 points beat the queue's default of 16), else
-``tacaw_multislice_batch`` (two launches per slice, shared by the jobs of one
-grid size).
+grids and windows of at least QUEUE_MIN_WINDOW snapshots
+``tacaw_multislice_queue`` (one persistent launch per grid size over a device
+work queue; items of 32 rows or columns, which on uneven jobs of 128-768
+points beat the queue's default of 16), else ``tacaw_multislice_batch`` (two
+launches per slice, shared by the jobs of one grid size).  With windows of a
+few snapshots a slice of the queue has fewer items than the launch has
+blocks, so blocks wait on one another; per-slice launches are faster there.
 
 Two forms of the spectrum (Eq. (9) with the elastic part removed):
 
@@ -54,18 +56,21 @@ class Job:
         return int(self.species.shape[0])
 
 
+QUEUE_MIN_WINDOW = 32      # snapshots per window from which the work queue is the default
+
+
 class BatchTimeToSpectrum:
     def __init__(self, jobs, window=8, precision="bf16x6", device="cuda", chunked=False, queue="auto", wave=0,
                  span=32):
         self.jobs = list(jobs)
-        if queue == "auto":
-            queue = all(j.grid.nx == j.grid.ny for j in self.jobs)
-        self.queue, self.wave, self.span = bool(queue), int(wave), int(span)
         if window == "auto":                    # tuned for the largest grid of the jobs (tuning.py)
             from .tuning import best_multislice_batch
             big = max(self.jobs, key=lambda j: j.grid.nx * j.grid.ny * j.grid.n_slices)
             window = best_multislice_batch(big.grid, device=device)
         self.window = int(window)
+        if queue == "auto":
+            queue = all(j.grid.nx == j.grid.ny for j in self.jobs) and self.window >= QUEUE_MIN_WINDOW
+        self.queue, self.wave, self.span = bool(queue), int(wave), int(span)
         self.precision = precision
         self.chunked = bool(chunked)
         self.device = torch.device(device)

@@ -56,13 +56,17 @@ def _small_jobs():
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
-def test_batch_time_to_spectrum_matches_oracle(api, precision):
+@pytest.mark.parametrize("precision,queue", [("fp32", "auto"), ("bf16x3", "auto"), ("fp32", True)])
+def test_batch_time_to_spectrum_matches_oracle(api, precision, queue):
+    """Both multislice engines of the batched driver (per-slice launches, the
+    default at windows this small, and the work queue) against the oracle."""
     from paper_2401_15599_gb300.batch import BatchTimeToSpectrum, Job
     cases = _small_jobs()
     jobs = [Job(w.grid, torch.from_numpy(p).cuda(), torch.from_numpy(inp.species).cuda(), inp.amp_sigma, w.dt_fs)
             for w, inp, p in cases]
-    run = BatchTimeToSpectrum(jobs, window=5, precision=precision)
+    if queue is True and not all(w.grid.nx == w.grid.ny for w, _, _ in cases):
+        pytest.skip("the work queue runs square grids")
+    run = BatchTimeToSpectrum(jobs, window=5, precision=precision, queue=queue)
     run.prepare()
     res = run.run()
     torch.cuda.synchronize()
@@ -104,7 +108,8 @@ def test_chunked_batch_matches_oracle(api, precision):
     for w, inp, p in cases:
         jobs.append(Job(w.grid, None, torch.from_numpy(inp.species).cuda(), inp.amp_sigma, w.dt_fs,
                         omega_meV=omega, n_t=w.n_t, positions=inp.synth("cuda")))
-    run = BatchTimeToSpectrum(jobs, window=5, precision=precision, chunked=True)
+    run = BatchTimeToSpectrum(jobs, window=5, precision=precision, chunked=True,
+                              queue=all(w.grid.nx == w.grid.ny for w, _, _ in cases))
     run.prepare()
     res = run.run()
     torch.cuda.synchronize()
