@@ -351,6 +351,101 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     }
 }
 
+// Staged row pass with one warp per row (plans of TPT = 32 threads): every
+// warp walks its own rows with its own two-stage ring and mbarriers, so the
+// warps of a block never wait on one another.  Lane 0 issues the bulk copies
+// of the warp's next row (its kept columns and potential row) once every lane
+// has passed the wait for the current one (__syncwarp), when the stage that
+// copy refills is free.  Same arithmetic as row_body, so the results are
+// identical.  A wait that gives up after `polls` polls sets *err; the warp
+// stops and waits (with a fixed long bound) for the copy it was waiting on.
+template <int NX, class P>
+__global__ void __launch_bounds__(kRowThreads, RowStagedMinBlocks<P>::value)
+row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, const float2* __restrict__ twx,
+                     const int* __restrict__ kymax, int ny, int n_slices, int s, float sigma, int n_rows,
+                     int* __restrict__ err, uint32_t polls) {
+    using namespace fft;
+    constexpr int E = P::E;
+    constexpr int TPT = NX / E;
+    static_assert(TPT == 32, "one warp per row");
+    constexpr int WARPS = kRowThreads / 32;
+    constexpr int PL = PaddedLen<NX>::value;
+    constexpr int PSI_BYTES = PL * (int)sizeof(float2);
+    constexpr int STAGE = PSI_BYTES + NX * (int)sizeof(float);   // one row: padded wave slot, then v_s
+    extern __shared__ __align__(128) unsigned char wstage_raw[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    unsigned char* mine = wstage_raw + (size_t)warp * 2 * STAGE;
+    float2* tw = reinterpret_cast<float2*>(wstage_raw + (size_t)WARPS * 2 * STAGE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + TwSize<NX>::value) + 2 * warp;
+    const int K = __ldg(kymax + NX);
+    int a = K + 1;                                 // kept columns [0, a) and [b, NX), 16-byte aligned copies
+    a += a & 1;
+    if (a > NX) a = NX;
+    int b = NX - K;
+    b -= b & 1;
+    if (b < a) b = a;
+    const uint32_t tx_bytes = (uint32_t)((a + NX - b) * (int)sizeof(float2) + NX * (int)sizeof(float));
+    if (lane == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::fence_mbar_init();
+    }
+    stage_twiddles<NX>(tw, twx);
+    __syncthreads();                               // twiddles and barrier initialisation visible
+    using RT = RegTwOf<P, NX>;
+    const RT rt = load_reg_tw<P, NX>(tw, lane);
+    auto issue = [&](int r, int st) {              // lane 0
+        const int snap = r / ny, y = r % ny;
+        unsigned char* dst = mine + st * STAGE;
+        fence_proxy_async_smem();                  // the stage was FFT scratch two rows ago
+        tc::mbar_arrive_expect_tx(&bar[st], tx_bytes);
+        const float2* src = psi + ((size_t)snap * ny + y) * NX;
+        bulk_copy_g2s(dst, src, a * sizeof(float2), &bar[st]);
+        if (b < NX) bulk_copy_g2s(dst + (size_t)b * sizeof(float2), src + b, (NX - b) * sizeof(float2), &bar[st]);
+        bulk_copy_g2s(dst + PSI_BYTES, V + (((size_t)snap * n_slices + s) * ny + y) * NX, NX * sizeof(float),
+                      &bar[st]);
+    };
+    const int step = gridDim.x * WARPS;
+    const int r0 = blockIdx.x * WARPS + warp;
+    if (lane == 0 && r0 < n_rows) issue(r0, 0);
+    int it = 0;
+    bool timed_out = false;
+    for (int r = r0; r < n_rows; r += step, ++it) {
+        const int st = it & 1;
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, polls));
+        if (!ok) {
+            timed_out = true;
+            break;
+        }
+        // every lane has left the previous row, so its stage takes the next copy
+        if (lane == 0 && r + step < n_rows) issue(r + step, st ^ 1);
+        float2* buf = reinterpret_cast<float2*>(mine + st * STAGE);
+        const float* vrow = reinterpret_cast<const float*>(mine + st * STAGE + PSI_BYTES);
+        const PadRowLayout lay{0};
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            v[m] = kept_column(lane + TPT * m, NX, K) ? buf[lane + TPT * m] : make_float2(0.f, 0.f);
+        transform_plan<P, NX, true>(v, buf, buf, lane, tw, lay, WarpSync{}, rt);
+        float x[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = sigma * vrow[lane + TPT * m];
+        transmit<E>(v, x);
+        transform_plan<P, NX, false>(v, buf, buf, lane, tw, lay, WarpSync{}, rt);
+        float2* rowp = psi + ((size_t)(r / ny) * ny + r % ny) * NX;
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            if (kept_column(lane + TPT * m, NX, K)) rowp[lane + TPT * m] = v[m];
+        __syncwarp();                              // the stage is refilled after the next wait
+    }
+    if (timed_out && lane == 0) {
+        atomicExch(err, 1);
+        const int st = it & 1;
+        for (int k = 0; k < 64 && !tc::mbar_wait_quiet(&bar[st], (it >> 1) & 1, 1u << 20); ++k) {
+        }
+    }
+}
+
 // Jobs of one batched launch (all of the same grid size): block row y of the
 // launch belongs to job j with start[j] <= blockIdx.y < start[j + 1].
 constexpr int kMaxBatch = 64;
@@ -711,19 +806,28 @@ cudaError_t launch_row_staged(float2* psi, const float* V, const float2* twx, co
     constexpr int TPT = NX / P::E;
     constexpr int ROWS = kRowThreads / TPT;
     *launched = false;
+    // one warp per row: warps with rings of their own (row_pass_warp_kernel)
+    constexpr bool kWarp = TPT == 32;
+    const void* kern;
+    if constexpr (kWarp) kern = (const void*)row_pass_warp_kernel<NX, P>;
+    else kern = (const void*)row_pass_staged_kernel<NX, P>;
     const size_t smem = 2 * (size_t)ROWS * (fft::PaddedLen<NX>::value * sizeof(float2) + NX * sizeof(float)) +
-                        fft::TwSize<NX>::value * sizeof(float2) + 2 * sizeof(uint64_t);
-    cudaError_t e = ensure_smem((const void*)row_pass_staged_kernel<NX, P>, (int)smem);
+                        fft::TwSize<NX>::value * sizeof(float2) + (kWarp ? 2 * ROWS : 2) * sizeof(uint64_t);
+    cudaError_t e = ensure_smem(kern, (int)smem);
     if (e != cudaSuccess) return e;
     int resident = 0;
-    e = resident_blocks((const void*)row_pass_staged_kernel<NX, P>, kRowThreads, (int)smem, &resident);
+    e = resident_blocks(kern, kRowThreads, (int)smem, &resident);
     if (e != cudaSuccess) return e;
     const long long groups = (long long)(ny / ROWS) * n_t;
-    if (groups > 0x7fffffffLL || ny % ROWS != 0) return cudaSuccess;
+    if (groups * ROWS > 0x7fffffffLL || ny % ROWS != 0) return cudaSuccess;
     const int n_groups = (int)groups;
     const int blocks = resident < n_groups ? resident : n_groups;
-    row_pass_staged_kernel<NX, P><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
-                                                                    n_groups, wc.flag, wc.polls);
+    if constexpr (kWarp)
+        row_pass_warp_kernel<NX, P><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
+                                                                      n_groups * ROWS, wc.flag, wc.polls);
+    else
+        row_pass_staged_kernel<NX, P><<<blocks, kRowThreads, smem, st>>>(psi, V, twx, kymax, ny, n_slices, s, sigma,
+                                                                        n_groups, wc.flag, wc.polls);
     *launched = true;
     return cudaGetLastError();
 }
