@@ -292,8 +292,8 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     using RT = typename std::conditional<(P::E <= 16), RegTwOf<P, NX>, NoRegTw>::type;
     RT rt{};
     if constexpr (P::E <= 16) rt = load_reg_tw<P, NX>(tw, threadIdx.x % TPT);
-    auto issue = [&](int g, int st) {              // thread 0
-        const int snap = g / groups_per_snap, y0 = (g % groups_per_snap) * ROWS;
+    auto issue = [&](int snap, int gi, int st) {   // thread 0: group gi of snapshot snap
+        const int y0 = gi * ROWS;
         unsigned char* dst = stage_raw + st * STAGE;
         fence_proxy_async_smem();                  // the stage was FFT scratch two groups ago
         tc::mbar_arrive_expect_tx(&bar[st], tx_bytes);
@@ -308,7 +308,10 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     };
     const int t = threadIdx.x % TPT;
     const int row = threadIdx.x / TPT;
-    if (threadIdx.x == 0 && (int)blockIdx.x < n_groups) issue(blockIdx.x, 0);
+    // group g = snap * groups_per_snap + gi advances by gridDim.x groups, tracked without divisions
+    const int step_snap = (int)gridDim.x / groups_per_snap, step_gi = (int)gridDim.x % groups_per_snap;
+    int snap = (int)blockIdx.x / groups_per_snap, gi = (int)blockIdx.x % groups_per_snap;
+    if (threadIdx.x == 0 && (int)blockIdx.x < n_groups) issue(snap, gi, 0);
     int it = 0;
     bool timed_out = false;                        // at a timeout: a copy in flight into stage it & 1
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++it) {
@@ -318,9 +321,15 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
             timed_out = true;
             break;
         }
+        float2* rowp = psi + ((size_t)snap * ny + gi * ROWS + row) * NX;
+        snap += step_snap;                         // (snap, gi): the next group
+        gi += step_gi;
+        if (gi >= groups_per_snap) {
+            gi -= groups_per_snap;
+            ++snap;
+        }
         // every thread has left the previous group, so its stage takes the next copy
-        const int gn = g + gridDim.x;
-        if (threadIdx.x == 0 && gn < n_groups) issue(gn, st ^ 1);
+        if (threadIdx.x == 0 && g + (int)gridDim.x < n_groups) issue(snap, gi, st ^ 1);
         float2* buf = reinterpret_cast<float2*>(stage_raw + st * STAGE);
         const float* vrow = reinterpret_cast<const float*>(stage_raw + st * STAGE + PSI_BYTES) + row * NX;
         const PadRowLayout lay{row * PL};
@@ -335,8 +344,6 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
         for (int m = 0; m < E; ++m) x[m] = sigma * vrow[t + TPT * m];
         transmit<E>(v, x);
         transform_plan<P, NX, false>(v, buf, buf, t, tw, lay, row_sync, rt);
-        const int snap = g / groups_per_snap, y = (g % groups_per_snap) * ROWS + row;
-        float2* rowp = psi + ((size_t)snap * ny + y) * NX;
 #pragma unroll
         for (int m = 0; m < E; ++m)
             if (kept_column(t + TPT * m, NX, K)) rowp[t + TPT * m] = v[m];
@@ -394,8 +401,7 @@ row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, cons
     __syncthreads();                               // twiddles and barrier initialisation visible
     using RT = RegTwOf<P, NX>;
     const RT rt = load_reg_tw<P, NX>(tw, lane);
-    auto issue = [&](int r, int st) {              // lane 0
-        const int snap = r / ny, y = r % ny;
+    auto issue = [&](int snap, int y, int st) {    // lane 0
         unsigned char* dst = mine + st * STAGE;
         fence_proxy_async_smem();                  // the stage was FFT scratch two rows ago
         tc::mbar_arrive_expect_tx(&bar[st], tx_bytes);
@@ -405,9 +411,12 @@ row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, cons
         bulk_copy_g2s(dst + PSI_BYTES, V + (((size_t)snap * n_slices + s) * ny + y) * NX, NX * sizeof(float),
                       &bar[st]);
     };
+    // row r = snap * ny + y advances by `step` rows, tracked without divisions
     const int step = gridDim.x * WARPS;
+    const int step_snap = step / ny, step_y = step % ny;
     const int r0 = blockIdx.x * WARPS + warp;
-    if (lane == 0 && r0 < n_rows) issue(r0, 0);
+    int snap = r0 / ny, y = r0 % ny;
+    if (lane == 0 && r0 < n_rows) issue(snap, y, 0);
     int it = 0;
     bool timed_out = false;
     for (int r = r0; r < n_rows; r += step, ++it) {
@@ -417,8 +426,15 @@ row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, cons
             timed_out = true;
             break;
         }
+        float2* rowp = psi + ((size_t)snap * ny + y) * NX;
+        snap += step_snap;                         // (snap, y): the next row
+        y += step_y;
+        if (y >= ny) {
+            y -= ny;
+            ++snap;
+        }
         // every lane has left the previous row, so its stage takes the next copy
-        if (lane == 0 && r + step < n_rows) issue(r + step, st ^ 1);
+        if (lane == 0 && r + step < n_rows) issue(snap, y, st ^ 1);
         float2* buf = reinterpret_cast<float2*>(mine + st * STAGE);
         const float* vrow = reinterpret_cast<const float*>(mine + st * STAGE + PSI_BYTES);
         const PadRowLayout lay{0};
@@ -432,7 +448,6 @@ row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, cons
         for (int m = 0; m < E; ++m) x[m] = sigma * vrow[lane + TPT * m];
         transmit<E>(v, x);
         transform_plan<P, NX, false>(v, buf, buf, lane, tw, lay, WarpSync{}, rt);
-        float2* rowp = psi + ((size_t)(r / ny) * ny + r % ny) * NX;
 #pragma unroll
         for (int m = 0; m < E; ++m)
             if (kept_column(lane + TPT * m, NX, K)) rowp[lane + TPT * m] = v[m];
@@ -613,21 +628,29 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
     stage_twiddles<NY>(tw, twy);
     __syncthreads();
     const RegTwOf<Plan<NY>, NY> rt = load_reg_tw<Plan<NY>, NY>(tw, t);
-    auto item_block = [&](long long i, int* snap) {
-        *snap = (int)(i / n_kept);
-        const int j = (int)(i % n_kept);
-        return j < n_lo ? j : hi0 + (j - n_lo);
+    // item i = snap * n_kept + j is column block j of the kept blocks of snapshot
+    // snap; the position advances by gridDim.x items per step, tracked without
+    // divisions in the loop
+    auto kept_block = [&](int j) { return j < n_lo ? j : hi0 + (j - n_lo); };
+    const int step_snap = (int)(gridDim.x / (unsigned)n_kept), step_j = (int)(gridDim.x % (unsigned)n_kept);
+    auto advance = [&](int& snap, int& j) {
+        snap += step_snap;
+        j += step_j;
+        if (j >= n_kept) {
+            j -= n_kept;
+            ++snap;
+        }
     };
-    auto issue = [&](long long i, int st) {               // thread 0
-        int snap;
-        const int kb = item_block(i, &snap);
+    auto issue = [&](int snap, int j, int st) {           // thread 0
+        const int kb = kept_block(j);
         float2* dst = cstage + st * STAGE;
         fence_proxy_async_smem();                        // the stage was exchange scratch two items ago
         tc::mbar_arrive_expect_tx(&bar[st], STAGE_BYTES);
         tc::tma_load_2d(dst, &map, &bar[st], kb * W, snap * NY);
         tc::tma_load_2d(dst + (NY / 2) * W, &map, &bar[st], kb * W, snap * NY + NY / 2);
     };
-    if (threadIdx.x == 0 && (long long)blockIdx.x < n_items) issue(blockIdx.x, 0);
+    int snap = (int)(blockIdx.x / (unsigned)n_kept), j = (int)(blockIdx.x % (unsigned)n_kept);
+    if (threadIdx.x == 0 && (long long)blockIdx.x < n_items) issue(snap, j, 0);
     int it = 0;
     bool timed_out = false;
     for (long long i = blockIdx.x; i < n_items; i += gridDim.x, ++it) {
@@ -637,11 +660,11 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
             timed_out = true;
             break;
         }
+        const int kb = kept_block(j);
+        const int cur_snap = snap;
+        advance(snap, j);                                // (snap, j): the next item
         // every thread has left the previous item, so its stage takes the next tile
-        const long long inext = i + gridDim.x;
-        if (threadIdx.x == 0 && inext < n_items) issue(inext, st ^ 1);
-        int snap;
-        const int kb = item_block(i, &snap);
+        if (threadIdx.x == 0 && i + gridDim.x < n_items) issue(snap, j, st ^ 1);
         const int kx = kb * W + c;
         float2* buf = cstage + st * STAGE;
         const PadColLayout<W> lay{c};
@@ -658,7 +681,7 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
             v[m] = (aky <= kmax) ? cmul(v[m], cmul(pxv, __ldg(py + ky))) : make_float2(0.f, 0.f);
         }
         if (!last) transform_plan<Plan<NY>, NY, true>(v, buf, buf, t, tw, lay, BlockSync{}, rt);
-        float2* col = psi + (size_t)snap * NY * nx + kx;
+        float2* col = psi + (size_t)cur_snap * NY * nx + kx;
 #pragma unroll
         for (int m = 0; m < E; ++m) col[(size_t)(t + TPT * m) * nx] = v[m];
     }
@@ -819,7 +842,7 @@ cudaError_t launch_row_staged(float2* psi, const float* V, const float2* twx, co
     e = resident_blocks(kern, kRowThreads, (int)smem, &resident);
     if (e != cudaSuccess) return e;
     const long long groups = (long long)(ny / ROWS) * n_t;
-    if (groups * ROWS > 0x7fffffffLL || ny % ROWS != 0) return cudaSuccess;
+    if (groups * ROWS > 0x7fffffffLL - (1LL << 24) || ny % ROWS != 0) return cudaSuccess;   // int counters
     const int n_groups = (int)groups;
     const int blocks = resident < n_groups ? resident : n_groups;
     if constexpr (kWarp)
