@@ -142,7 +142,11 @@ struct Plan<768> { static constexpr int E = 24; using R = Radices<8, 8, 4, 3>; }
 template <int N>
 struct WarpPlan;
 template <>
-struct WarpPlan<512> { static constexpr int E = 16; using R = Radices<8, 8, 8>; };
+struct WarpPlan<512> {
+    static constexpr int E = 16;
+    using R = Radices<8, 8, 8>;
+    static constexpr bool kDeriveTw = true;   // last stage: second butterfly's twiddles derived (see stage)
+};
 
 template <int A, int... Rest>
 struct First { static constexpr int value = A; };
@@ -213,12 +217,32 @@ struct RegTw {
 struct NoRegTw { static constexpr int kNS = 0; };
 
 // Stage compute: registers v[b*R + r] hold input r of butterfly j = t + b*TPT.
-template <int N, int E, int R, int NS, int OFF, bool INV, class RT = NoRegTw>
+// W_16^r = exp(-2 pi i r / 16), r = 0 .. 7.
+__device__ __forceinline__ float2 w16(int r) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+    switch (r) {
+        case 1: return make_float2(c1, -s1);
+        case 2: return make_float2(h, -h);
+        case 3: return make_float2(s1, -c1);
+        case 5: return make_float2(-s1, -c1);
+        case 6: return make_float2(-h, -h);
+        case 7: return make_float2(-c1, -s1);
+        default: return make_float2(1.f, 0.f);
+    }
+}
+
+// DER: in a radix-8 stage where a thread owns two butterflies whose jm differ
+// by TPT = NS / 2, the second butterfly's twiddles are derived from the
+// first's, W_{8 NS}^{(jm + NS/2) r} = W_{8 NS}^{jm r} W_16^r (a product with
+// a constant: one rounding more, no shared-memory load).
+template <int N, int E, int R, int NS, int OFF, bool INV, class RT = NoRegTw, bool DER = false>
 __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw, const RT& rt = RT{}) {
     constexpr int TPT = N / E;
     constexpr bool kReg = NS > 1 && RT::kNS == NS;
     static_assert(!kReg || ((E == R || TPT % NS == 0) && std::is_same<RT, RegTw<R, NS>>::value),
                   "register twiddles: one jm per thread in this stage");
+    constexpr bool kDer = DER && !kReg && NS > 1 && R == 8 && E == 2 * R && NS == 2 * TPT;
+    float2 w0[R - 1];
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         float2* x = v + b * R;
@@ -228,8 +252,15 @@ __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw, c
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 float2 w;
-                if constexpr (kReg) w = rt.w[r - 1];
-                else w = tw[OFF + (r - 1) * NS + jm];
+                if constexpr (kReg) {
+                    w = rt.w[r - 1];
+                } else if (kDer && b == 1) {
+                    const float2 a = w0[r - 1];
+                    w = r == 4 ? make_float2(a.y, -a.x) : cmul(a, w16(r));
+                } else {
+                    w = tw[OFF + (r - 1) * NS + jm];
+                    if (kDer) w0[r - 1] = w;
+                }
                 if (INV) w.y = -w.y;
                 x[r] = cmul(x[r], w);
             }
@@ -319,31 +350,37 @@ struct WarpSync {
     __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
 
-template <int N, int E, bool INV, int NS, int OFF, class L, class S, class RT, int R, int... Rest>
+template <int N, int E, bool INV, int NS, int OFF, class L, class S, class RT, bool DER, int R, int... Rest>
 __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
                                            const float2* tw, L lay, S sync, const RT& rt) {
     if constexpr (sizeof...(Rest) > 0) {
-        stage<N, E, R, NS, OFF, INV>(v, t, tw, rt);
+        stage<N, E, R, NS, OFF, INV, RT, DER>(v, t, tw, rt);
         constexpr int RN = First<Rest...>::value;
         constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
         if (b0 == b1) sync();            // one buffer: the previous exchange's reads come first
         write_out<N, E, R, NS>(v, b0, t, lay);
         sync();
         read_in<N, E, RN>(v, b0, t, lay);
-        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, RT, Rest...>(v, b1, b0, t, tw, lay, sync, rt);
+        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, RT, DER, Rest...>(v, b1, b0, t, tw, lay, sync, rt);
     } else {
-        stage<N, E, R, NS, OFF, INV>(v, t, tw, rt);
+        stage<N, E, R, NS, OFF, INV, RT, DER>(v, t, tw, rt);
         stage_to_canon<E, R>(v);
     }
 }
 
-template <int N, int E, bool INV, class L, class S, class RT, int R0, int... Rs>
+template <int N, int E, bool INV, class L, class S, class RT, bool DER, int R0, int... Rs>
 __device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[E],
                                                float2* b0, float2* b1, int t, const float2* tw,
                                                L lay, S sync, const RT& rt) {
     canon_to_stage<E, R0>(v);
-    run_stages<N, E, INV, 1, 0, L, S, RT, R0, Rs...>(v, b0, b1, t, tw, lay, sync, rt);
+    run_stages<N, E, INV, 1, 0, L, S, RT, DER, R0, Rs...>(v, b0, b1, t, tw, lay, sync, rt);
 }
+
+// Plans whose paired butterflies derive their twiddles (see stage).
+template <class P, class = void>
+struct DerivesTw { static constexpr bool value = false; };
+template <class P>
+struct DerivesTw<P, decltype(void(P::kDeriveTw))> { static constexpr bool value = P::kDeriveTw; };
 
 // The stage of radices Rs whose twiddles a thread of a plan with TPT threads
 // per transform can hold in registers: the last stage when a thread owns one
@@ -441,7 +478,8 @@ template <int N, bool INV, class L, class S = BlockSync>
 __device__ __forceinline__ void transform(float2 (&v)[Plan<N>::E], float2* b0, float2* b1, int t,
                                           const float2* tw, L lay, S sync = S{}) {
     if (b0 != b1) sync();
-    transform_impl<N, Plan<N>::E, INV, L, S>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync, NoRegTw{});
+    transform_impl<N, Plan<N>::E, INV, L, S, NoRegTw, false>(typename Plan<N>::R{}, v, b0, b1, t, tw, lay, sync,
+                                                             NoRegTw{});
 }
 
 // The same with an explicit plan P (P::E values per thread, radices P::R; its
@@ -451,7 +489,7 @@ template <class P, int N, bool INV, class L, class S, class RT = NoRegTw>
 __device__ __forceinline__ void transform_plan(float2 (&v)[P::E], float2* b0, float2* b1, int t,
                                                const float2* tw, L lay, S sync, const RT& rt = RT{}) {
     if (b0 != b1) sync();
-    transform_impl<N, P::E, INV, L, S, RT>(typename P::R{}, v, b0, b1, t, tw, lay, sync, rt);
+    transform_impl<N, P::E, INV, L, S, RT, DerivesTw<P>::value>(typename P::R{}, v, b0, b1, t, tw, lay, sync, rt);
 }
 
 }  // namespace fft
