@@ -171,33 +171,77 @@ struct ColLayout {
     __device__ __forceinline__ int operator()(int p) const { return (p ^ ((p >> 3) & (kGroups - 1))) * W + c; }
 };
 
-// Padded layouts: position p is stored at p + p / 16 (one spare slot after
-// every sixteen), so a transform of N positions takes PaddedLen<N> slots.  In
-// every exchange of these plans a butterfly touches positions base + o whose
-// offsets o keep (base mod 16) + (o mod 16) below 16, so the padded address is
-// the butterfly's padded base plus a compile-time offset: one address
-// computation per butterfly instead of one per element.  For 8-byte elements
-// every exchange of the plans then takes the minimum number of shared-memory
-// wavefronts, for one row per transform (PadRowLayout) as for W interleaved
-// transforms (PadColLayout).
+// Padded layouts: position p is stored at a padded index F(p), so that a
+// butterfly whose positions are base + o (o compile-time offsets) computes
+// F(base) once and reaches its values at F(base) + F(o): F must not carry
+// between base and o, which each policy states as a condition checked below
+// for the exchanges it serves.  Policies:
+//   Pad16:   p + p / 16      (one spare slot after every 16; no carry when
+//            (base mod 16) + (o mod 16) < 16)
+//   Pad8:    p + p / 8       (no carry when (base mod 8) + (o mod 8) < 8)
+//   Pad64x8: p + 8 (p / 64)  (eight spare slots after every 64; no carry when
+//            (base mod 64) + (o mod 64) < 64)
+// A layout takes one policy for the exchange after the first stage and one for
+// the exchanges after it.  Shared memory serves a warp's 8-byte request per
+// half-warp: 16 lanes in one wavefront when they reach 16 distinct bank pairs.
+// Pad16 everywhere gives that for every exchange of the plans except, at 512
+// points, the writes after the second stage of a row (lanes t and t + 8 of a
+// half-warp collide) and the writes after the first stage of interleaved
+// columns (lanes t and t + 1); PadRowL<Pad16, Pad64x8> and
+// PadColL<W, Pad8, Pad16> remove those (every exchange of the 512-point
+// plans at the minimum, checked by enumerating the lanes' addresses on the
+// host).
+struct Pad16 {
+    static constexpr int kRun = 16;
+    __host__ __device__ static constexpr int map(int p) { return p + (p >> 4); }
+    __host__ __device__ static constexpr int size(int n) { return n + n / 16; }
+};
+struct Pad8 {
+    static constexpr int kRun = 8;
+    __host__ __device__ static constexpr int map(int p) { return p + (p >> 3); }
+    __host__ __device__ static constexpr int size(int n) { return n + n / 8; }
+};
+struct Pad64x8 {
+    static constexpr int kRun = 64;
+    __host__ __device__ static constexpr int map(int p) { return p + 8 * (p >> 6); }
+    __host__ __device__ static constexpr int size(int n) { return n + 8 * (n / 64); }
+};
+
 template <int N>
 struct PaddedLen { static constexpr int value = N + N / 16; };
 
 __host__ __device__ constexpr int pad16(int p) { return p + (p >> 4); }
 
-struct PadRowLayout {
+// X: exchange index (0 after the first stage).
+template <class F0, class F1>
+struct PadRowL {
     static constexpr bool kPadded = true;
-    int base;  // row * PaddedLen<N>
-    __device__ __forceinline__ int operator()(int p) const { return base + pad16(p); }
-    __device__ __forceinline__ int at(int pb, int o) const { return base + pb + pad16(o); }   // pb = pad16(b)
+    template <int X>
+    using Pad = typename std::conditional<X == 0, F0, F1>::type;
+    template <int N>
+    __host__ __device__ static constexpr int slot() { return F0::size(N) > F1::size(N) ? F0::size(N) : F1::size(N); }
+    int base;  // row * slot
+    template <class F>
+    __device__ __forceinline__ int at(int pb, int o) const { return base + pb + F::map(o); }   // pb = F(b)
 };
-template <int W>
-struct PadColLayout {
+template <int W, class F0, class F1>
+struct PadColL {
     static constexpr bool kPadded = true;
+    template <int X>
+    using Pad = typename std::conditional<X == 0, F0, F1>::type;
+    template <int N>
+    __host__ __device__ static constexpr int slot() { return F0::size(N) > F1::size(N) ? F0::size(N) : F1::size(N); }
     int c;
-    __device__ __forceinline__ int operator()(int p) const { return pad16(p) * W + c; }
-    __device__ __forceinline__ int at(int pb, int o) const { return (pb + pad16(o)) * W + c; }
+    template <class F>
+    __device__ __forceinline__ int at(int pb, int o) const { return (pb + F::map(o)) * W + c; }
 };
+using PadRowLayout = PadRowL<Pad16, Pad16>;
+template <int W>
+using PadColLayout = PadColL<W, Pad16, Pad16>;
+// The 512-point layouts without half-warp collisions (see above).
+using PadRowLayout512 = PadRowL<Pad16, Pad64x8>;
+template <int W>
+using PadColLayout512 = PadColL<W, Pad8, Pad16>;
 
 template <class L, class = void>
 struct IsPadded { static constexpr bool value = false; };
@@ -269,7 +313,7 @@ __device__ __forceinline__ void stage(float2 (&v)[E], int t, const float2* tw, c
     }
 }
 
-template <int N, int E, int R, int NS, class L>
+template <int N, int E, int R, int NS, int X, class L>
 __device__ __forceinline__ void write_out(const float2 (&v)[E], float2* buf, int t, L lay) {
     constexpr int TPT = N / E;
 #pragma unroll
@@ -277,13 +321,17 @@ __device__ __forceinline__ void write_out(const float2 (&v)[E], float2* buf, int
         const int j = t + b * TPT;
         const int base = (j / NS) * NS * R + (j % NS);
         if constexpr (IsPadded<L>::value) {
-            // base + r NS: NS a multiple of 16; NS = 8 with R even (base mod 16 below 8); or NS = 1
-            // with R dividing 16 (base a multiple of R)
-            static_assert(NS % 16 == 0 || (NS == 8 && R % 2 == 0) || (NS == 1 && 16 % R == 0),
+            using F = typename L::template Pad<X>;
+            // base + r NS, base = (j / NS) NS R + j mod NS: (base mod kRun) + (r NS mod kRun) < kRun
+            // holds when NS is a multiple of kRun; when NS divides kRun and NS R is a multiple of
+            // kRun (the offsets reach at most kRun - NS, j mod NS at most NS - 1); and when NS R
+            // divides kRun (base + r NS stays inside one block of NS R positions)
+            constexpr int K = F::kRun, M = NS * R;
+            static_assert(NS % K == 0 || (K % NS == 0 && M % K == 0) || (M <= K && K % M == 0),
                           "padded exchange needs offsets that do not carry");
-            const int pb = pad16(base);
+            const int pb = F::map(base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[lay.at(pb, r * NS)] = v[b * R + r];
+            for (int r = 0; r < R; ++r) buf[lay.template at<F>(pb, r * NS)] = v[b * R + r];
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) buf[lay(base + r * NS)] = v[b * R + r];
@@ -291,18 +339,21 @@ __device__ __forceinline__ void write_out(const float2 (&v)[E], float2* buf, int
     }
 }
 
-template <int N, int E, int R, class L>
+template <int N, int E, int R, int X, class L>
 __device__ __forceinline__ void read_in(float2 (&v)[E], const float2* buf, int t, L lay) {
     constexpr int TPT = N / E;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const int j = t + b * TPT;
         if constexpr (IsPadded<L>::value) {
-            // j + r N/R: N/R a multiple of 16, or 8 (then j < 8)
-            static_assert((N / R) % 16 == 0 || N / R == 8, "padded exchange needs offsets that do not carry");
-            const int pb = pad16(j);
+            using F = typename L::template Pad<X>;
+            // j + r N/R with j < N/R: no carry when N/R is a multiple of kRun (offsets 0 mod
+            // kRun) or divides kRun (offsets at most kRun - N/R, j at most N/R - 1)
+            static_assert((N / R) % F::kRun == 0 || F::kRun % (N / R) == 0,
+                          "padded exchange needs offsets that do not carry");
+            const int pb = F::map(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay.at(pb, r * (N / R))];
+            for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay.template at<F>(pb, r * (N / R))];
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b * R + r] = buf[lay(j + r * (N / R))];
@@ -350,7 +401,7 @@ struct WarpSync {
     __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
 
-template <int N, int E, bool INV, int NS, int OFF, class L, class S, class RT, bool DER, int R, int... Rest>
+template <int N, int E, bool INV, int NS, int OFF, class L, class S, class RT, bool DER, int X, int R, int... Rest>
 __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b1, int t,
                                            const float2* tw, L lay, S sync, const RT& rt) {
     if constexpr (sizeof...(Rest) > 0) {
@@ -358,10 +409,10 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* b0, float2* b
         constexpr int RN = First<Rest...>::value;
         constexpr int NEXT_OFF = OFF + (NS > 1 ? (R - 1) * NS : 0);
         if (b0 == b1) sync();            // one buffer: the previous exchange's reads come first
-        write_out<N, E, R, NS>(v, b0, t, lay);
+        write_out<N, E, R, NS, X>(v, b0, t, lay);
         sync();
-        read_in<N, E, RN>(v, b0, t, lay);
-        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, RT, DER, Rest...>(v, b1, b0, t, tw, lay, sync, rt);
+        read_in<N, E, RN, X>(v, b0, t, lay);
+        run_stages<N, E, INV, NS * R, NEXT_OFF, L, S, RT, DER, X + 1, Rest...>(v, b1, b0, t, tw, lay, sync, rt);
     } else {
         stage<N, E, R, NS, OFF, INV, RT, DER>(v, t, tw, rt);
         stage_to_canon<E, R>(v);
@@ -373,7 +424,7 @@ __device__ __forceinline__ void transform_impl(Radices<R0, Rs...>, float2 (&v)[E
                                                float2* b0, float2* b1, int t, const float2* tw,
                                                L lay, S sync, const RT& rt) {
     canon_to_stage<E, R0>(v);
-    run_stages<N, E, INV, 1, 0, L, S, RT, DER, R0, Rs...>(v, b0, b1, t, tw, lay, sync, rt);
+    run_stages<N, E, INV, 1, 0, L, S, RT, DER, 0, R0, Rs...>(v, b0, b1, t, tw, lay, sync, rt);
 }
 
 // Plans whose paired butterflies derive their twiddles (see stage).

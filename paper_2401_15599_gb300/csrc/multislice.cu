@@ -358,6 +358,14 @@ row_pass_staged_kernel(float2* __restrict__ psi, const float* __restrict__ V, co
     }
 }
 
+// Exchange layouts of the one-warp-per-row pass and of the staged column pass:
+// at 512 points those without half-warp bank collisions (fft::PadRowLayout512,
+// PadColLayout512, whose slots are longer), else the Pad16 layouts.
+template <int N>
+using WarpRowLay = typename std::conditional<N == 512, fft::PadRowLayout512, fft::PadRowLayout>::type;
+template <int N, int W>
+using StagedColLay = typename std::conditional<N == 512, fft::PadColLayout512<W>, fft::PadColLayout<W>>::type;
+
 // Staged row pass with one warp per row (plans of TPT = 32 threads): every
 // warp walks its own rows with its own two-stage ring and mbarriers, so the
 // warps of a block never wait on one another.  Lane 0 issues the bulk copies
@@ -376,7 +384,8 @@ row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, cons
     constexpr int TPT = NX / E;
     static_assert(TPT == 32, "one warp per row");
     constexpr int WARPS = kRowThreads / 32;
-    constexpr int PL = PaddedLen<NX>::value;
+    using Lay = WarpRowLay<NX>;
+    constexpr int PL = Lay::template slot<NX>();
     constexpr int PSI_BYTES = PL * (int)sizeof(float2);
     constexpr int STAGE = PSI_BYTES + NX * (int)sizeof(float);   // one row: padded wave slot, then v_s
     extern __shared__ __align__(128) unsigned char wstage_raw[];
@@ -437,7 +446,7 @@ row_pass_warp_kernel(float2* __restrict__ psi, const float* __restrict__ V, cons
         if (lane == 0 && r + step < n_rows) issue(snap, y, st ^ 1);
         float2* buf = reinterpret_cast<float2*>(mine + st * STAGE);
         const float* vrow = reinterpret_cast<const float*>(mine + st * STAGE + PSI_BYTES);
-        const PadRowLayout lay{0};
+        const Lay lay{0};
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m)
@@ -605,7 +614,8 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
     constexpr int E = Plan<NY>::E;
     constexpr int TPT = NY / E;
     constexpr int W = ColCfg<NY>::W;
-    constexpr int STAGE = PaddedLen<NY>::value * W;     // float2 per stage: the padded exchange layout
+    using Lay = StagedColLay<NY, W>;
+    constexpr int STAGE = Lay::template slot<NY>() * W;  // float2 per stage: the padded exchange layout
     constexpr uint32_t STAGE_BYTES = NY * W * sizeof(float2);   // what TMA brings (dense)
     extern __shared__ __align__(128) float2 cstage[];
     float2* tw = cstage + 2 * STAGE;
@@ -667,7 +677,7 @@ col_pass_staged_kernel(const __grid_constant__ CUtensorMap map, float2* __restri
         if (threadIdx.x == 0 && i + gridDim.x < n_items) issue(snap, j, st ^ 1);
         const int kx = kb * W + c;
         float2* buf = cstage + st * STAGE;
-        const PadColLayout<W> lay{c};
+        const Lay lay{c};
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = buf[(t + TPT * m) * W + c];
@@ -834,7 +844,8 @@ cudaError_t launch_row_staged(float2* psi, const float* V, const float2* twx, co
     const void* kern;
     if constexpr (kWarp) kern = (const void*)row_pass_warp_kernel<NX, P>;
     else kern = (const void*)row_pass_staged_kernel<NX, P>;
-    const size_t smem = 2 * (size_t)ROWS * (fft::PaddedLen<NX>::value * sizeof(float2) + NX * sizeof(float)) +
+    constexpr int PL = kWarp ? WarpRowLay<NX>::template slot<NX>() : fft::PaddedLen<NX>::value;
+    const size_t smem = 2 * (size_t)ROWS * (PL * sizeof(float2) + NX * sizeof(float)) +
                         fft::TwSize<NX>::value * sizeof(float2) + (kWarp ? 2 * ROWS : 2) * sizeof(uint64_t);
     cudaError_t e = ensure_smem(kern, (int)smem);
     if (e != cudaSuccess) return e;
@@ -931,8 +942,8 @@ cudaError_t launch_col_staged(float2* psi, const float2* twy, const float2* px, 
     if (wc.flag == nullptr || reinterpret_cast<uintptr_t>(psi) % 16 != 0 || nx % W != 0) return cudaSuccess;
     CUtensorMap map;
     if (!encode_wave_map(&map, psi, nx, (long long)n_t * NY, W, NY / 2)) return cudaSuccess;
-    const size_t smem = (2 * (size_t)W * fft::PaddedLen<NY>::value + fft::TwSize<NY>::value) * sizeof(float2) +
-                        2 * sizeof(uint64_t);
+    const size_t smem = (2 * (size_t)W * StagedColLay<NY, W>::template slot<NY>() + fft::TwSize<NY>::value) *
+                            sizeof(float2) + 2 * sizeof(uint64_t);
     cudaError_t e = ensure_smem((const void*)col_pass_staged_kernel<NY>, (int)smem);
     if (e != cudaSuccess) return e;
     int resident = 0;

@@ -1,0 +1,131 @@
+"""Shared-memory layouts of the FFT exchanges (csrc/fft.cuh), checked on the host.
+
+A length-N Stockham transform with E values per thread (TPT = N / E threads)
+writes, after a stage of radix R with NS = R_1 ... R_{l-1}, output r of
+butterfly j = t + b TPT to position (j / NS) NS R + (j mod NS) + r NS, and the
+next stage (radix RN) reads input r of butterfly j at j + r N / RN.  A padded
+layout stores position p at F(p); the kernels compute F(base) once per
+butterfly and add F(offset), which needs F(base + o) = F(base) + F(o) ("no
+carry").  Shared memory serves a warp's 8-byte accesses per half-warp: sixteen
+lanes in one wavefront when they reach sixteen distinct bank pairs (slot index
+mod 16, after multiplying by the W transforms interleaved in a column layout).
+
+These tests restate the three padding policies and check, for the 512-point
+plans of the one-warp-per-row pass (PadRowLayout512) and the staged column pass
+(PadColLayout512), that every exchange is free of carries, injective within the
+slot, and takes the minimum number of wavefronts, and that the plain Pad16
+layouts collide where the 512-point layouts were introduced to avoid it.
+"""
+
+import pytest
+
+
+def pad16(p):
+    return p + p // 16
+
+
+def pad8(p):
+    return p + p // 8
+
+
+def pad64x8(p):
+    return p + 8 * (p // 64)
+
+
+def _stages(radices):
+    ns, out = 1, []
+    for r in radices:
+        out.append((r, ns))
+        ns *= r
+    return out
+
+
+def _wavefronts(addrs):
+    total = 0
+    for half in (addrs[:16], addrs[16:]):
+        banks = {}
+        for a in half:
+            banks.setdefault(a % 16, set()).add(a)
+        total += max(len(v) for v in banks.values())
+    return total
+
+
+def _accesses(n, e, radices, x, layout, lane_map, w, warps):
+    """Per warp instruction, the 32 lanes' slot indices of the write and the read of exchange x."""
+    tpt = n // e
+    st = _stages(radices)
+    r_, ns = st[x]
+    rn = st[x + 1][0]
+    writes, reads = [], []
+    for wp in range(warps):
+        for b in range(e // r_):
+            for r in range(r_):
+                a = []
+                for lane in range(32):
+                    t, c = lane_map(wp, lane)
+                    j = t + b * tpt
+                    a.append(layout(((j // ns) * ns * r_ + j % ns) + r * ns) * w + c)
+                writes.append(a)
+        for b in range(e // rn):
+            for r in range(rn):
+                a = []
+                for lane in range(32):
+                    t, c = lane_map(wp, lane)
+                    a.append(layout(t + b * tpt + r * (n // rn)) * w + c)
+                reads.append(a)
+    return writes, reads
+
+
+def _no_carry(n, e, radices, x, f):
+    tpt = n // e
+    st = _stages(radices)
+    r_, ns = st[x]
+    rn = st[x + 1][0]
+    for t in range(tpt):
+        for b in range(e // r_):
+            j = t + b * tpt
+            base = (j // ns) * ns * r_ + j % ns
+            for r in range(r_):
+                if f(base + r * ns) != f(base) + f(r * ns):
+                    return False
+        for b in range(e // rn):
+            j = t + b * tpt
+            for r in range(rn):
+                if f(j + r * (n // rn)) != f(j) + f(r * (n // rn)):
+                    return False
+    return True
+
+
+ROW = lambda wp, lane: (32 * wp + lane, 0)          # one transform per row, lanes on consecutive positions
+COL4 = lambda wp, lane: (8 * wp + lane // 4, lane % 4)   # four interleaved columns, eight positions per warp
+
+CASES = {
+    # name: (N, E, radices, lane map, W, warps per transform set, layouts per exchange)
+    "warp_row_512": (512, 16, (8, 8, 8), ROW, 1, 1, (pad16, pad64x8)),
+    "staged_col_512": (512, 8, (8, 8, 8), COL4, 4, 8, (pad8, pad16)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_512_layouts_carry_free_injective_minimal(name):
+    n, e, radices, lane_map, w, warps, lays = CASES[name]
+    slot = max(f(n - 1) for f in lays) + 1
+    assert slot <= 576                     # the slot the kernels allocate: 512 + 512 / 8
+    for x, f in enumerate(lays):
+        assert _no_carry(n, e, radices, x, f), (name, x)
+        assert len({f(p) for p in range(n)}) == n and max(f(p) for p in range(n)) < slot
+        writes, reads = _accesses(n, e, radices, x, f, lane_map, w, warps)
+        for a in writes + reads:
+            assert _wavefronts(a) == 2, (name, x)
+
+
+def test_pad16_collides_where_512_layouts_differ():
+    # rows: the write after the second stage; columns: the write after the first stage
+    writes, _ = _accesses(512, 16, (8, 8, 8), 1, pad16, ROW, 1, 1)
+    assert max(_wavefronts(a) for a in writes) == 4
+    writes, _ = _accesses(512, 8, (8, 8, 8), 0, pad16, COL4, 4, 8)
+    assert max(_wavefronts(a) for a in writes) == 4
+    # and Pad16 is minimal for the other exchange of each
+    for x, lm, w, wp, e in ((0, ROW, 1, 1, 16), (1, COL4, 4, 8, 8)):
+        writes, reads = _accesses(512, e, (8, 8, 8), x, pad16, lm, w, wp)
+        assert all(_wavefronts(a) == 2 for a in writes + reads)
