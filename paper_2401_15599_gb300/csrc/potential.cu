@@ -1136,6 +1136,7 @@ potential_lists_kernel(const int* __restrict__ bin_off, const float4* __restrict
                        unsigned char* __restrict__ lists, int* __restrict__ n_list) {
     __shared__ __align__(16) int ckey[kLWarps][kB2Cap + 4];
     __shared__ int skey[kLWarps][kB2Cap];
+    __shared__ __align__(4) unsigned char first_b[kLWarps][kLFirst];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int band = blockIdx.x * kLWarps + warp;
     if (band >= p.n_bands) return;                    // whole warps only: no block barrier below
@@ -1242,24 +1243,27 @@ potential_lists_kernel(const int* __restrict__ bin_off, const float4* __restrict
         }
     }
     __syncwarp();
-    // first[c]: the first entry whose key is >= the lowest key that can reach column group c,
-    // four groups per 32-bit word
+    // first[c]: the first entry whose key is >= want(c) = 8 c - reach_x - 1 + kofs, the lowest
+    // key that can reach column group c; four groups per 32-bit word.  The keys are sorted, so
+    // first[c] = i exactly for the groups with key[i - 1] < want(c) <= key[i] (key[-1] = -inf,
+    // key[total] = +inf): each entry writes the groups of its gap.
     const int ngroups = (p.nx + 7) / 8;
-    uint32_t* fw = reinterpret_cast<uint32_t*>(L);
-    for (int w4 = lane; 4 * w4 < ngroups; w4 += 32) {
-        uint32_t word = 0;
-        for (int b = 0; b < 4; ++b) {
-            const int c = 4 * w4 + b;
-            const int want = 8 * c - p.reach_x - 1 + kofs;
-            int lo = 0, hi = total;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (skey[warp][mid] < want) lo = mid + 1; else hi = mid;
-            }
-            word |= (uint32_t)lo << (8 * b);
-        }
-        fw[w4] = word;
+    const int nwords = (ngroups + 3) / 4;
+    const int c_last = 4 * nwords - 1;
+    const int c0k = kofs - p.reach_x - 1;          // want(c) = 8 c + c0k
+    unsigned char* fb = first_b[warp];
+    for (int i = lane; i <= total; i += 32) {
+        const int lo_key = i == 0 ? -(1 << 29) : skey[warp][i - 1];
+        const int hi_key = i == total ? (1 << 29) : skey[warp][i];
+        const int ca = max(((lo_key - c0k) >> 3) + 1, 0);     // want(c) > lo_key
+        const int cb = min((hi_key - c0k) >> 3, c_last);      // want(c) <= hi_key
+        for (int c = ca; c <= cb; ++c) fb[c] = (unsigned char)i;
     }
+    __syncwarp();
+    uint32_t* fw = reinterpret_cast<uint32_t*>(L);
+    for (int w4 = lane; w4 < nwords; w4 += 32)
+        fw[w4] = (uint32_t)fb[4 * w4] | ((uint32_t)fb[4 * w4 + 1] << 8) | ((uint32_t)fb[4 * w4 + 2] << 16) |
+                 ((uint32_t)fb[4 * w4 + 3] << 24);
     if (lane == 0) *nl = total;
 }
 
@@ -1316,6 +1320,30 @@ __device__ __forceinline__ void slab_accumulate(const BandSmem& sm, int slot, in
                 acc_p[r][m] = fmaf(gy[r], c, acc_p[r][m]);
             }
         }
+    }
+}
+
+// The three slices' accumulators of a thread (k - 1, k, k + 1) in memory, for
+// the out-of-line path below.
+struct SlabAcc { float a[3][kBR][kB2Cols]; };
+
+// An over-full slab list (more entries than a ring slot holds): built here in
+// chunks of sources by the accumulating block itself and added chunk by chunk.
+// Rare, and kept out of line so that the common path's accumulators stay in
+// registers; every thread of the block calls it (it has block barriers).
+template <bool RECUR>
+__device__ __noinline__ void slab_overfull(BandSmem& sm, const PotParams& p, const int* __restrict__ off, int k,
+                                           AxisRange rb, const float4* __restrict__ atoms,
+                                           const int2* __restrict__ atoms_px, const float4* __restrict__ wts,
+                                           int r0, int nrows, int kofs, int ngroups, bool active, int x0,
+                                           SlabAcc* acc) {
+    band_bins(sm, p, off, k, 1, rb);
+    const int nsrc = sm.nsrc[0];
+    for (int c0 = 0; c0 < nsrc; c0 += kB2ChunkSrc) {
+        const int a0 = c0, a1 = min(nsrc, c0 + kB2ChunkSrc), sl = kB2Chunk;
+        band_build(sm, p, atoms, atoms_px, wts, 1, &a0, &a1, &sl, rb.count, r0, nrows, kofs, ngroups);
+        if (active) slab_accumulate<RECUR>(sm, kB2Chunk, x0, p.reach_x, kofs, p.dx, acc->a[0], acc->a[1], acc->a[2]);
+        __syncthreads();                             // the chunk slot is rebuilt next
     }
 }
 
@@ -1394,14 +1422,19 @@ potential_accum_kernel(const int* __restrict__ bin_off, const float4* __restrict
     for (int pass = 0; pass < passes; ++pass) {
         const int x0 = kB2Cols * ((int)threadIdx.x + pass * kB2Threads);
         const bool active = x0 < p.nx;
-        float acc_m[kBR][kB2Cols], acc_0[kBR][kB2Cols], acc_p[kBR][kB2Cols];
+        // slice s accumulates in acc[s % 3]: slab k adds to acc[(k + 2) % 3] (slice k - 1),
+        // acc[k % 3] (slice k) and acc[(k + 1) % 3] (slice k + 1); after slab k slice k - 1 is
+        // stored and its array restarts as slice k + 2.  The slab loop is unrolled by three so
+        // that the arrays' roles rotate without copies.
+        float acc0[kBR][kB2Cols], acc1[kBR][kB2Cols], acc2[kBR][kB2Cols];
 #pragma unroll
         for (int r = 0; r < kBR; ++r)
 #pragma unroll
-            for (int m = 0; m < kB2Cols; ++m) acc_m[r][m] = acc_0[r][m] = acc_p[r][m] = 0.f;
+            for (int m = 0; m < kB2Cols; ++m) acc0[r][m] = acc1[r][m] = acc2[r][m] = 0.f;
         fetch(0);
         fetch(1);
-        for (int k = 0; k < S; ++k) {
+        auto slab = [&](int k, float (&acc_m)[kBR][kB2Cols], float (&acc_0)[kBR][kB2Cols],
+                        float (&acc_p)[kBR][kB2Cols]) {
             fetch(k + 2);
             cp_async_wait_pot<2>();                      // slab k has landed
             __syncthreads();
@@ -1409,27 +1442,43 @@ potential_accum_kernel(const int* __restrict__ bin_off, const float4* __restrict
             if (sm.n[slot] >= 0) {
                 if (active) slab_accumulate<RECUR>(sm, slot, x0, p.reach_x, kofs, p.dx, acc_m, acc_0, acc_p);
             } else {
-                band_bins(sm, p, off, k, 1, rb);
-                const int nsrc = sm.nsrc[0];
-                for (int c0 = 0; c0 < nsrc; c0 += kB2ChunkSrc) {
-                    const int a0 = c0, a1 = min(nsrc, c0 + kB2ChunkSrc), sl = kB2Chunk;
-                    band_build(sm, p, atoms, atoms_px, wts, 1, &a0, &a1, &sl, rb.count, r0, nrows, kofs, ngroups);
-                    if (active)
-                        slab_accumulate<RECUR>(sm, kB2Chunk, x0, p.reach_x, kofs, p.dx, acc_m, acc_0, acc_p);
-                    __syncthreads();                     // the chunk slot is rebuilt next
-                }
+                SlabAcc t;
+#pragma unroll
+                for (int r = 0; r < kBR; ++r)
+#pragma unroll
+                    for (int m = 0; m < kB2Cols; ++m) {
+                        t.a[0][r][m] = acc_m[r][m];
+                        t.a[1][r][m] = acc_0[r][m];
+                        t.a[2][r][m] = acc_p[r][m];
+                    }
+                slab_overfull<RECUR>(sm, p, off, k, rb, atoms, atoms_px, wts, r0, nrows, kofs, ngroups, active, x0,
+                                     &t);
+#pragma unroll
+                for (int r = 0; r < kBR; ++r)
+#pragma unroll
+                    for (int m = 0; m < kB2Cols; ++m) {
+                        acc_m[r][m] = t.a[0][r][m];
+                        acc_0[r][m] = t.a[1][r][m];
+                        acc_p[r][m] = t.a[2][r][m];
+                    }
             }
             if (active && k > 0) store(k - 1, x0, acc_m);     // slice k - 1 has all its slabs
 #pragma unroll
             for (int r = 0; r < kBR; ++r)
 #pragma unroll
-                for (int m = 0; m < kB2Cols; ++m) {
-                    acc_m[r][m] = acc_0[r][m];
-                    acc_0[r][m] = acc_p[r][m];
-                    acc_p[r][m] = 0.f;
-                }
+                for (int m = 0; m < kB2Cols; ++m) acc_m[r][m] = 0.f;
+        };
+        for (int k = 0; k < S; k += 3) {
+            slab(k, acc2, acc0, acc1);
+            if (k + 1 < S) slab(k + 1, acc0, acc1, acc2);
+            if (k + 2 < S) slab(k + 2, acc1, acc2, acc0);
         }
-        if (active) store(S - 1, x0, acc_m);
+        if (active) {                                    // slice S - 1: its slabs S - 2 and S - 1 added
+            const int last = (S - 1) % 3;
+            if (last == 0) store(S - 1, x0, acc0);
+            else if (last == 1) store(S - 1, x0, acc1);
+            else store(S - 1, x0, acc2);
+        }
         cp_async_wait_pot<0>();
         __syncthreads();                                 // the ring is refilled by the next pass
     }
