@@ -730,7 +730,8 @@ def batched_jobs_sample(reps, stream, n_jobs=64, snapshots=64):
             "value_graph": units / (graph_ms * 1e-3), "unit": UNIT}
 
 
-def full_batched_jobs(stream, graph=True, max_jobs=64, max_snapshots=None, v_budget=120e9, max_window=512):
+def full_batched_jobs(stream, graph=True, max_jobs=64, max_snapshots=None, v_budget=120e9, max_window=512,
+                      queue="auto"):
     """The batched configuration as stated: the 64 seeded uneven jobs (seeds
     1000-1063; grids 128-768, 10-150 slices, 512-4096 snapshots, 1-3 species)
     through the time-chunked batched driver, one group per grid size (so one
@@ -763,7 +764,7 @@ def full_batched_jobs(stream, graph=True, max_jobs=64, max_snapshots=None, v_bud
             jobs.append(Job(wj.grid, None, torch.from_numpy(inp.species).cuda(), inp.amp_sigma, wj.dt_fs,
                             omega_meV=omega, n_t=wj.n_t, positions=inp.synth("cuda")))
             units += wj.grid.nx * wj.grid.ny * wj.grid.n_slices * wj.n_t
-        run = BatchTimeToSpectrum(jobs, window=window, precision="bf16x6", chunked=True)
+        run = BatchTimeToSpectrum(jobs, window=window, precision="bf16x6", chunked=True, queue=queue)
         if graph:
             run.capture()                                    # one eager run, then the recording
             ms = _events_ms(run.replay, 1, stream)

@@ -1313,7 +1313,10 @@ __device__ __forceinline__ void q_col_tile(float2* stage, float2* __restrict__ s
         return;
     }
     const int kx = kx0 + c;
-    const PadColLayout<W> lay{c};
+    // the staged column pass's layouts (at 512 points without half-warp bank collisions)
+    using Lay = StagedColLay<N, W>;
+    static_assert(Lay::template slot<N>() * W <= QStage<N>::F2, "column tile fits its stage");
+    const Lay lay{c};
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = stage[(t + TPT * m) * W + c];
