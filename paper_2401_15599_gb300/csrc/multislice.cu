@@ -1111,7 +1111,12 @@ struct QCfg {
     static constexpr int TPT = N / E;                 // threads per transform
     static constexpr int ROWS = kQThreads / TPT;      // rows per row tile = columns per column tile
     static constexpr int SPAN = ROWS > kQSpan ? ROWS : kQSpan;   // default span
-    static constexpr int PL = fft::PaddedLen<N>::value;
+    // row-tile exchange layout: for the 24-value plans (two blocks per SM whatever the stage size)
+    // the second and later exchanges as p + 8 (p / 64), free of half-warp bank collisions; the
+    // 8-value plans keep p + p / 16 everywhere (longer rows would cost them a resident block)
+    using RowLay = typename std::conditional<E == 24, fft::PadRowL<fft::Pad16, fft::Pad64x8>, fft::PadRowLayout>::type;
+    static constexpr int PL = RowLay::template slot<N>();
+    static_assert(PL % 2 == 0, "16-byte aligned rows");
     static constexpr int MIN_BLOCKS = E > 8 ? 2 : 4;    // resident blocks per SM the registers allow
     static_assert(ROWS * TPT == kQThreads && N % SPAN == 0, "queue tiles");
     // a span (rows or columns per item) is a multiple of ROWS that divides N
@@ -1267,7 +1272,7 @@ __device__ __forceinline__ void q_row_tile(float2* stage, float2* __restrict__ r
     using namespace fft;
     using C = QCfg<N>;
     constexpr int E = C::E, TPT = C::TPT;
-    const PadRowLayout lay{row * C::PL};
+    const typename C::RowLay lay{row * C::PL};
     const auto sync = row_sync_of<TPT>(row);
     const float* vrow = reinterpret_cast<const float*>(stage + QStage<N>::PSI) + row * N;
     float2 v[E];
@@ -1313,8 +1318,9 @@ __device__ __forceinline__ void q_col_tile(float2* stage, float2* __restrict__ s
         return;
     }
     const int kx = kx0 + c;
-    // the staged column pass's layouts (at 512 points without half-warp bank collisions)
-    using Lay = StagedColLay<N, W>;
+    // at 512 points (four columns) and for the 24-value plans (eight or sixteen columns) the first
+    // exchange as p + p / 8, free of half-warp bank collisions, the others as p + p / 16
+    using Lay = typename std::conditional<N == 512 || E == 24, fft::PadColLayout512<W>, fft::PadColLayout<W>>::type;
     static_assert(Lay::template slot<N>() * W <= QStage<N>::F2, "column tile fits its stage");
     const Lay lay{c};
     float2 v[E];

@@ -11,10 +11,11 @@ lanes in one wavefront when they reach sixteen distinct bank pairs (slot index
 mod 16, after multiplying by the W transforms interleaved in a column layout).
 
 These tests restate the three padding policies and check, for the 512-point
-plans of the one-warp-per-row pass (PadRowLayout512) and the staged column pass
-(PadColLayout512), that every exchange is free of carries, injective within the
-slot, and takes the minimum number of wavefronts, and that the plain Pad16
-layouts collide where the 512-point layouts were introduced to avoid it.
+plans of the one-warp-per-row pass and the staged column pass and for the
+768- and 384-point row and column tiles of the work queue, that every exchange
+is free of carries, injective within the slot, and takes the minimum number of
+wavefronts, and that the plain Pad16 layouts collide where the other policies
+were introduced to avoid it.
 """
 
 import pytest
@@ -99,19 +100,29 @@ def _no_carry(n, e, radices, x, f):
 ROW = lambda wp, lane: (32 * wp + lane, 0)          # one transform per row, lanes on consecutive positions
 COL4 = lambda wp, lane: (8 * wp + lane // 4, lane % 4)   # four interleaved columns, eight positions per warp
 
+COL8 = lambda wp, lane: (4 * wp + lane // 8, lane % 8)    # eight interleaved columns (768-point queue tiles)
+COL16 = lambda wp, lane: (2 * wp + lane // 16, lane % 16)  # sixteen (384-point queue tiles)
+ROW16 = lambda wp, lane: (lane % 16, 0)                    # a 16-thread row per half-warp (384-point rows)
+
 CASES = {
-    # name: (N, E, radices, lane map, W, warps per transform set, layouts per exchange)
+    # name: (N, E, radices, lane map, W, warps per transform set, layouts per exchange (the last
+    # one serves every later exchange))
     "warp_row_512": (512, 16, (8, 8, 8), ROW, 1, 1, (pad16, pad64x8)),
     "staged_col_512": (512, 8, (8, 8, 8), COL4, 4, 8, (pad8, pad16)),
+    "queue_row_768": (768, 24, (8, 8, 4, 3), ROW, 1, 1, (pad16, pad64x8)),
+    "queue_col_768": (768, 24, (8, 8, 4, 3), COL8, 8, 8, (pad8, pad16)),
+    "queue_row_384": (384, 24, (8, 8, 2, 3), ROW16, 1, 1, (pad16, pad64x8)),
+    "queue_col_384": (384, 24, (8, 8, 2, 3), COL16, 16, 8, (pad8, pad16)),
 }
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_512_layouts_carry_free_injective_minimal(name):
+def test_layouts_carry_free_injective_minimal(name):
     n, e, radices, lane_map, w, warps, lays = CASES[name]
     slot = max(f(n - 1) for f in lays) + 1
-    assert slot <= 576                     # the slot the kernels allocate: 512 + 512 / 8
-    for x, f in enumerate(lays):
+    assert slot <= n + n // 8               # the slot the kernels allocate: the longer policy's size
+    for x in range(len(radices) - 1):
+        f = lays[min(x, len(lays) - 1)]
         assert _no_carry(n, e, radices, x, f), (name, x)
         assert len({f(p) for p in range(n)}) == n and max(f(p) for p in range(n)) < slot
         writes, reads = _accesses(n, e, radices, x, f, lane_map, w, warps)
