@@ -184,13 +184,14 @@ struct ColLayout {
 // A layout takes one policy for the exchange after the first stage and one for
 // the exchanges after it.  Shared memory serves a warp's 8-byte request per
 // half-warp: 16 lanes in one wavefront when they reach 16 distinct bank pairs.
-// Pad16 everywhere gives that for every exchange of the plans except, at 512
-// points, the writes after the second stage of a row (lanes t and t + 8 of a
-// half-warp collide) and the writes after the first stage of interleaved
-// columns (lanes t and t + 1); PadRowL<Pad16, Pad64x8> and
-// PadColL<W, Pad8, Pad16> remove those (every exchange of the 512-point
-// plans at the minimum, checked by enumerating the lanes' addresses on the
-// host).
+// Pad16 everywhere gives that for most exchanges, but not for the writes after
+// the second stage of a row (lanes t and t + 8 of a half-warp collide, in every
+// plan here) nor for the writes after the first stage of four or eight
+// interleaved columns (lanes t and t + 1).  PadRowL<Pad16, Pad64x8> and
+// PadColL<W, Pad8, Pad16> remove those where they are used: the one-warp-per-
+// row pass and the staged column pass at 512 points, and the work queue's
+// tiles of the 24-value plans (every exchange at the minimum, checked by
+// enumerating the lanes' addresses on the host).
 struct Pad16 {
     static constexpr int kRun = 16;
     __host__ __device__ static constexpr int map(int p) { return p + (p >> 4); }
@@ -238,7 +239,7 @@ struct PadColL {
 using PadRowLayout = PadRowL<Pad16, Pad16>;
 template <int W>
 using PadColLayout = PadColL<W, Pad16, Pad16>;
-// The 512-point layouts without half-warp collisions (see above).
+// The layouts without half-warp collisions (see above).
 using PadRowLayout512 = PadRowL<Pad16, Pad64x8>;
 template <int W>
 using PadColLayout512 = PadColL<W, Pad8, Pad16>;
