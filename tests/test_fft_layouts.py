@@ -140,3 +140,49 @@ def test_pad16_collides_where_512_layouts_differ():
     for x, lm, w, wp, e in ((0, ROW, 1, 1, 16), (1, COL4, 4, 8, 8)):
         writes, reads = _accesses(512, e, (8, 8, 8), x, pad16, lm, w, wp)
         assert all(_wavefronts(a) == 2 for a in writes + reads)
+
+
+PLANS = {
+    # N: (E, radices) of fft::Plan<N> and fft::WarpPlan<512>
+    64: (8, (8, 8)), 128: (8, (8, 4, 4)), 256: (8, (8, 8, 4)), 512: (8, (8, 8, 8)),
+    1024: (8, (8, 8, 4, 4)), 2048: (16, (8, 8, 8, 4)), 4096: (16, (8, 8, 8, 8)),
+    384: (24, (8, 8, 2, 3)), 768: (24, (8, 8, 4, 3)), "warp512": (16, (8, 8, 8)),
+}
+POLICIES = {"Pad16": (pad16, 16), "Pad8": (pad8, 8), "Pad64x8": (pad64x8, 64)}
+
+
+def _write_ok(ns, r, k):
+    # the compile-time condition of write_out (fft.cuh)
+    m = ns * r
+    return ns % k == 0 or (k % ns == 0 and m % k == 0) or (m <= k and k % m == 0)
+
+
+def _read_ok(n, rn, k):
+    # the compile-time condition of read_in (fft.cuh)
+    return (n // rn) % k == 0 or k % (n // rn) == 0
+
+
+@pytest.mark.parametrize("plan", sorted(PLANS, key=str))
+@pytest.mark.parametrize("policy", sorted(POLICIES))
+def test_static_carry_conditions_are_sound(plan, policy):
+    """Wherever the kernels' static_asserts accept a policy for an exchange,
+    the padded addresses really are base plus offset for every butterfly."""
+    n = 512 if plan == "warp512" else plan
+    e, radices = PLANS[plan]
+    f, k = POLICIES[policy]
+    st = _stages(radices)
+    for x in range(len(radices) - 1):
+        r_, ns = st[x]
+        rn = st[x + 1][0]
+        if _write_ok(ns, r_, k) and _read_ok(n, rn, k):
+            assert _no_carry(n, e, radices, x, f), (plan, policy, x)
+
+
+def test_pad16_accepted_for_every_plan():
+    # the layouts every other kernel uses must compile for every plan
+    for plan, (e, radices) in PLANS.items():
+        n = 512 if plan == "warp512" else plan
+        st = _stages(radices)
+        for x in range(len(radices) - 1):
+            r_, ns = st[x]
+            assert _write_ok(ns, r_, 16) and _read_ok(n, st[x + 1][0], 16), (plan, x)
