@@ -59,6 +59,13 @@ class Job:
 QUEUE_MIN_WINDOW = 32      # snapshots per window from which the work queue is the default
 
 
+def queue_by_default(grids, window) -> bool:
+    """The multislice engine ``queue="auto"`` picks: the work queue when every
+    grid is square (the queue's tiles) and a window holds at least
+    QUEUE_MIN_WINDOW snapshots, else per-slice batch launches."""
+    return all(int(g.nx) == int(g.ny) for g in grids) and int(window) >= QUEUE_MIN_WINDOW
+
+
 class BatchTimeToSpectrum:
     def __init__(self, jobs, window=8, precision="bf16x6", device="cuda", chunked=False, queue="auto", wave=0,
                  span=32):
@@ -69,7 +76,7 @@ class BatchTimeToSpectrum:
             window = best_multislice_batch(big.grid, device=device)
         self.window = int(window)
         if queue == "auto":
-            queue = all(j.grid.nx == j.grid.ny for j in self.jobs) and self.window >= QUEUE_MIN_WINDOW
+            queue = queue_by_default([j.grid for j in self.jobs], self.window)
         self.queue, self.wave, self.span = bool(queue), int(wave), int(span)
         self.precision = precision
         self.chunked = bool(chunked)
